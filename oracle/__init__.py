@@ -1,0 +1,330 @@
+"""FP64 CPU oracle for the differentiable MAC-grid fluid step (arXiv 2503.00868).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` may import this package. The CUDA product path
+never does, and the two share no code (this package is plain C in ``oracle.c``
+behind ctypes, compiled with gcc).
+
+Fields are tuples ``(u, v, w)`` of dense float64 arrays with shapes
+``(nz, ny, nx+1)``, ``(nz, ny+1, nx)``, ``(nz+1, ny, nx)``; cell arrays have shape
+``(nz, ny, nx)``; cell types are uint8 (0 air, 1 liquid, 2 solid).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+PC_NONE, PC_JACOBI, PC_MIC0 = 0, 1, 2
+NET_CH = (2, 16, 16, 16, 16, 1)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into a shared library (gcc, portable flags)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("type", C.POINTER(C.c_uint8)),
+                ("bc", C.POINTER(C.c_double) * 3),
+                ("dx", C.c_double), ("dt", C.c_double), ("nu", C.c_double),
+                ("g", C.c_double * 3),
+                ("tol_p", C.c_double), ("tol_v", C.c_double),
+                ("maxit_p", C.c_int), ("maxit_v", C.c_int),
+                ("precond", C.c_int),
+                ("mic_tau", C.c_double), ("mic_sigma", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("status", C.c_int),
+                ("relres", C.c_double), ("true_relres", C.c_double)]
+
+    def as_dict(self):
+        return {"iters": self.iters, "status": self.status, "relres": self.relres,
+                "true_relres": self.true_relres}
+
+
+_D = C.POINTER(C.c_double)
+_P3 = _D * 3
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = C.CDLL(path)
+            G = C.POINTER(_Grid)
+            sig = {
+                "or_face_class": [G, C.c_int, C.POINTER(C.c_uint8)],
+                "or_advect": [G, _P3, _P3],
+                "or_advect_adjoint": [G, _P3, _P3, _P3],
+                "or_visc_apply": [G, _P3, _P3],
+                "or_visc_solve": [G, _P3, _P3, C.POINTER(Stats)],
+                "or_divergence": [G, _P3, _D],
+                "or_poisson_apply": [G, _D, _D],
+                "or_grad_subtract": [G, _D, _P3],
+                "or_is_singular": [G],
+                "or_mic0_factor": [G, C.c_double, C.c_double, _D],
+                "or_mic0_apply": [G, _D, _D, _D],
+                "or_pcg": [G, _D, _D, C.c_int, C.POINTER(Stats)],
+                "or_project": [G, _P3, _D, C.POINTER(Stats)],
+                "or_step": [G, _P3, _P3, C.c_void_p, C.POINTER(Stats)],
+                "or_adjoint_step": [G, _P3, _P3, _P3, _D, C.POINTER(Stats)],
+                "or_band_cells": [G, C.c_int, C.POINTER(C.c_uint8)],
+                "or_loss_grad": [G, _P3, _P3, C.c_int, C.c_double, C.c_double, _D, _P3],
+                "or_bf16_round": [C.c_double],
+                "or_net_forward": [G, _D * 5, _D * 5, _D, _D, _D],
+                "or_net_loss_grad": [G, _D * 5, _D * 5, _D, _D, _D * 5, _D * 5],
+            }
+            for name, args in sig.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = None
+            L.or_is_singular.restype = C.c_int
+            L.or_bf16_round.restype = C.c_double
+            L.or_net_forward.restype = C.c_double
+            L.or_net_loss_grad.restype = C.c_double
+            _lib = L
+    return _lib
+
+
+def face_shapes(nx, ny, nz):
+    return (nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_D)
+
+
+def _p3(arrs):
+    return _P3(*[_ptr(a) for a in arrs])
+
+
+class Grid:
+    """A grid, its cell types, prescribed face values and step parameters."""
+
+    def __init__(self, types, dx, dt, nu, g=(0.0, 0.0, 0.0), bc=None, tol_p=1e-13,
+                 tol_v=1e-13, maxit_p=100000, maxit_v=100000, precond=PC_JACOBI,
+                 mic_tau=0.97, mic_sigma=0.25):
+        self.types = np.ascontiguousarray(types, dtype=np.uint8)
+        self.nz, self.ny, self.nx = self.types.shape
+        self.bc = None if bc is None else tuple(_f64(a) for a in bc)
+        if self.bc is not None:
+            for a, s in zip(self.bc, face_shapes(self.nx, self.ny, self.nz)):
+                assert a.shape == s, (a.shape, s)
+        self.dx, self.dt, self.nu = float(dx), float(dt), float(nu)
+        self.g = tuple(float(x) for x in g)
+        self.tol_p, self.tol_v = float(tol_p), float(tol_v)
+        self.maxit_p, self.maxit_v = int(maxit_p), int(maxit_v)
+        self.precond = int(precond)
+        self.mic_tau, self.mic_sigma = float(mic_tau), float(mic_sigma)
+
+    def shapes(self):
+        return face_shapes(self.nx, self.ny, self.nz)
+
+    def zeros(self):
+        return tuple(np.zeros(s) for s in self.shapes())
+
+    def cstruct(self):
+        s = _Grid()
+        s.nx, s.ny, s.nz = self.nx, self.ny, self.nz
+        s.type = self.types.ctypes.data_as(C.POINTER(C.c_uint8))
+        for c in range(3):
+            s.bc[c] = _ptr(self.bc[c]) if self.bc is not None else _D()
+        s.dx, s.dt, s.nu = self.dx, self.dt, self.nu
+        for c in range(3):
+            s.g[c] = self.g[c]
+        s.tol_p, s.tol_v = self.tol_p, self.tol_v
+        s.maxit_p, s.maxit_v = self.maxit_p, self.maxit_v
+        s.precond = self.precond
+        s.mic_tau, s.mic_sigma = self.mic_tau, self.mic_sigma
+        self._keep = s
+        return C.byref(s)
+
+
+def _field(g: Grid, u):
+    out = tuple(_f64(a) for a in u)
+    for a, s in zip(out, g.shapes()):
+        assert a.shape == s, (a.shape, s)
+    return out
+
+
+def face_class(g: Grid, c: int):
+    out = np.zeros(g.shapes()[c], dtype=np.uint8)
+    lib().or_face_class(g.cstruct(), c, out.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return out
+
+
+def advect(g: Grid, u):
+    u = _field(g, u)
+    out = g.zeros()
+    lib().or_advect(g.cstruct(), _p3(u), _p3(out))
+    return out
+
+
+def advect_adjoint(g: Grid, u, ga):
+    u, ga = _field(g, u), _field(g, ga)
+    out = g.zeros()
+    lib().or_advect_adjoint(g.cstruct(), _p3(u), _p3(ga), _p3(out))
+    return out
+
+
+def visc_apply(g: Grid, x):
+    x = _field(g, x)
+    out = g.zeros()
+    lib().or_visc_apply(g.cstruct(), _p3(x), _p3(out))
+    return out
+
+
+def visc_solve(g: Grid, ub):
+    ub = _field(g, ub)
+    out = g.zeros()
+    st = Stats()
+    lib().or_visc_solve(g.cstruct(), _p3(ub), _p3(out), C.byref(st))
+    return out, st.as_dict()
+
+
+def divergence(g: Grid, u):
+    u = _field(g, u)
+    b = np.zeros((g.nz, g.ny, g.nx))
+    lib().or_divergence(g.cstruct(), _p3(u), _ptr(b))
+    return b
+
+
+def poisson_apply(g: Grid, x):
+    x = _f64(x)
+    y = np.zeros_like(x)
+    lib().or_poisson_apply(g.cstruct(), _ptr(x), _ptr(y))
+    return y
+
+
+def grad_subtract(g: Grid, q, u):
+    q = _f64(q)
+    u = tuple(a.copy() for a in _field(g, u))
+    lib().or_grad_subtract(g.cstruct(), _ptr(q), _p3(u))
+    return u
+
+
+def is_singular(g: Grid) -> bool:
+    return bool(lib().or_is_singular(g.cstruct()))
+
+
+def mic0_factor(g: Grid, tau=None, sigma=None):
+    prec = np.zeros((g.nz, g.ny, g.nx))
+    lib().or_mic0_factor(g.cstruct(), g.mic_tau if tau is None else tau,
+                         g.mic_sigma if sigma is None else sigma, _ptr(prec))
+    return prec
+
+
+def mic0_apply(g: Grid, prec, r):
+    prec, r = _f64(prec), _f64(r)
+    z = np.zeros_like(r)
+    lib().or_mic0_apply(g.cstruct(), _ptr(prec), _ptr(r), _ptr(z))
+    return z
+
+
+def pcg(g: Grid, b, precond=None):
+    b = _f64(b)
+    x = np.zeros_like(b)
+    st = Stats()
+    lib().or_pcg(g.cstruct(), _ptr(b), _ptr(x), g.precond if precond is None else precond,
+                 C.byref(st))
+    return x, st.as_dict()
+
+
+def project(g: Grid, u):
+    u = tuple(a.copy() for a in _field(g, u))
+    q = np.zeros((g.nz, g.ny, g.nx))
+    st = Stats()
+    lib().or_project(g.cstruct(), _p3(u), _ptr(q), C.byref(st))
+    return u, q, st.as_dict()
+
+
+def step(g: Grid, u, save_visc=False):
+    u = _field(g, u)
+    out = g.zeros()
+    st = (Stats * 2)()
+    uv = g.zeros() if save_visc else None
+    uv_ptrs = _p3(uv) if save_visc else None
+    lib().or_step(g.cstruct(), _p3(u), _p3(out),
+                  C.cast(uv_ptrs, C.c_void_p) if save_visc else None, st)
+    stats = {"visc": st[0].as_dict(), "pressure": st[1].as_dict()}
+    return (out, uv, stats) if save_visc else (out, stats)
+
+
+def adjoint_step(g: Grid, u, g_out):
+    u, g_out = _field(g, u), _field(g, g_out)
+    g_in = g.zeros()
+    gnu = C.c_double(0.0)
+    st = (Stats * 3)()
+    lib().or_adjoint_step(g.cstruct(), _p3(u), _p3(g_out), _p3(g_in), C.byref(gnu), st)
+    return g_in, gnu.value
+
+
+def band_cells(g: Grid, kind=0):
+    out = np.zeros((g.nz, g.ny, g.nx), dtype=np.uint8)
+    lib().or_band_cells(g.cstruct(), kind, out.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return out
+
+
+def loss_grad(g: Grid, u, target, kind=0, alpha=0.0, beta=1.0):
+    u, target = _field(g, u), _field(g, target)
+    grad = g.zeros()
+    loss = C.c_double(0.0)
+    lib().or_loss_grad(g.cstruct(), _p3(u), _p3(target), kind, alpha, beta, C.byref(loss),
+                       _p3(grad))
+    return loss.value, grad
+
+
+def bf16_round(x):
+    f = np.vectorize(lib().or_bf16_round, otypes=[np.float64])
+    return f(np.asarray(x, dtype=np.float64))
+
+
+def _net_ptrs(arrs):
+    return (_D * 5)(*[_ptr(a) for a in arrs])
+
+
+def net_forward(g: Grid, W, B, r, return_acts=False):
+    """W: 5 arrays [co, ci, 3, 3, 3]; B: 5 arrays [co]. Returns z (and s, acts)."""
+    W = [_f64(w) for w in W]
+    B = [_f64(b) for b in B]
+    r = _f64(r)
+    z = np.zeros_like(r)
+    n = r.size
+    acts = np.zeros(sum(NET_CH) * n)
+    s = lib().or_net_forward(g.cstruct(), _net_ptrs(W), _net_ptrs(B), _ptr(r), _ptr(z), _ptr(acts))
+    if return_acts:
+        return z, s, acts
+    return z
+
+
+def net_loss_grad(g: Grid, W, B, b, q):
+    W = [_f64(w) for w in W]
+    B = [_f64(x) for x in B]
+    gW = [np.zeros_like(w) for w in W]
+    gB = [np.zeros_like(x) for x in B]
+    loss = lib().or_net_loss_grad(g.cstruct(), _net_ptrs(W), _net_ptrs(B), _ptr(_f64(b)),
+                                  _ptr(_f64(q)), _net_ptrs(gW), _net_ptrs(gB))
+    return loss, gW, gB

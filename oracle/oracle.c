@@ -1,0 +1,1082 @@
+/*
+ * oracle.c -- plain, slow FP64 CPU restatement of the differentiable MAC-grid
+ * fluid step of arXiv 2503.00868 ("3D Dynamic Fluid Assets from Single-View
+ * Videos with Generative Gaussian Splatting").
+ *
+ * TEST INFRASTRUCTURE ONLY. The tests, the smoke check and the CPU-baseline leg
+ * of the benchmark may load this library; the product path never does. It shares
+ * no code, header, table or helper with the CUDA implementation.
+ *
+ * What it computes (paper passages):
+ *   - Eq. (eq::v), Sec. 3.2.2: dv/dt = -grad p / rho + div(2 nu S) + g, solved by
+ *     operator splitting (Chorin) with a pressure Poisson equation.
+ *   - Sec. 3.4.1: grid convection by semi-Lagrangian back-tracing (Stam).
+ *   - Sec. 3.4.1: the Poisson pressure equation (solved here by (P)CG; the paper
+ *     replaces the implicit solve by PeRCNN, which is fitted to solver output).
+ *   - Sec. 3.4.2, Eq. (eq::optLoss): masked cosine + L2 loss on grid velocities.
+ *   - Sec. 3.4.1, Fig. percnn_str_fit: a small 3D convolution network that maps a
+ *     pressure right-hand side to a pressure (used as a PCG preconditioner).
+ *
+ * Readings where the paper is silent (each is restated where it is used):
+ *   R1 split order: advect -> body force -> implicit viscosity -> projection, so
+ *      every step ends divergence-free.
+ *   R2 viscosity: constant nu, backward Euler (I + nu dt L_f) u_v = u_b per
+ *      component on fluid faces.
+ *   R3 advection: one forward-Euler back-trace in index space, trilinear sample
+ *      of the own component, continuous index clamped to [0, n-1].
+ *   R4 pressure: p = 0 in air cells, solid walls are Neumann, the all-liquid
+ *      closed box removes the mean of the right-hand side.
+ *   R5 MIC(0) (Bridson, Fluid Simulation for Computer Graphics, 2nd ed.):
+ *      tau = 0.97, safety sigma = 0.25, lexicographic order with x fastest.
+ *   R6 loss: halved squared L2 averaged over band faces plus (1 - cos) averaged
+ *      over band cells on cell-centred velocities, eps = 1e-8.
+ *
+ * Dense array layout (C order, x fastest), all FP64:
+ *   cells        (nz, ny, nx)        index (k*ny + j)*nx + i
+ *   u  faces     (nz, ny, nx+1)      u(i,j,k) sits between cells (i-1,j,k), (i,j,k)
+ *   v  faces     (nz, ny+1, nx)      v(i,j,k) sits between cells (i,j-1,k), (i,j,k)
+ *   w  faces     (nz+1, ny, nx)      w(i,j,k) sits between cells (i,j,k-1), (i,j,k)
+ * Cell types: 0 air, 1 liquid, 2 solid; cells outside the array are solid.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { AIR = 0, LIQUID = 1, SOLID = 2 };
+enum { FC_AIR = 0, FC_FLUID = 1, FC_FIXED = 2 };
+enum { PC_NONE = 0, PC_JACOBI = 1, PC_MIC0 = 2 };
+enum { ST_OK = 0, ST_NOCONV = 1, ST_BREAKDOWN = 2 };
+
+typedef struct {
+    int nx, ny, nz;
+    const uint8_t *type;        /* cell types, (nz, ny, nx) */
+    const double *bc[3];        /* prescribed values on fixed faces; NULL = 0 */
+    double dx, dt, nu;
+    double g[3];                /* body force (acceleration) per component */
+    double tol_p, tol_v;        /* relative residual targets of the two solves */
+    int maxit_p, maxit_v;
+    int precond;                /* pressure preconditioner: PC_NONE/JACOBI/MIC0 */
+    double mic_tau, mic_sigma;
+} or_grid;
+
+typedef struct {
+    int iters;
+    int status;
+    double relres;       /* recursive residual at exit, relative */
+    double true_relres;  /* |b - A x| / |b| recomputed at exit */
+} or_stats;
+
+/* ------------------------------------------------------------------------ */
+/* indexing                                                                  */
+/* ------------------------------------------------------------------------ */
+
+static void face_dims(const or_grid *g, int c, int d[3])
+{
+    d[0] = g->nx; d[1] = g->ny; d[2] = g->nz;
+    d[c] += 1;
+}
+
+static long fidx(const int d[3], int i, int j, int k)
+{
+    return ((long)k * d[1] + j) * d[0] + i;
+}
+
+static long ncells(const or_grid *g) { return (long)g->nx * g->ny * g->nz; }
+
+static long nfaces(const or_grid *g, int c)
+{
+    int d[3];
+    face_dims(g, c, d);
+    return (long)d[0] * d[1] * d[2];
+}
+
+static long cidx(const or_grid *g, int i, int j, int k)
+{
+    return ((long)k * g->ny + j) * g->nx + i;
+}
+
+static int cell_type(const or_grid *g, int i, int j, int k)
+{
+    if (i < 0 || j < 0 || k < 0 || i >= g->nx || j >= g->ny || k >= g->nz)
+        return SOLID;
+    return g->type[cidx(g, i, j, k)];
+}
+
+/* A face touching a solid cell has a prescribed (fixed) value. A face between two
+ * non-solid cells with at least one liquid side is a fluid face (an unknown of the
+ * viscosity solve, moved by the pressure gradient). A face between two air cells
+ * holds zero. */
+static int face_class(const or_grid *g, int c, int i, int j, int k)
+{
+    int o[3] = {0, 0, 0};
+    o[c] = 1;
+    int tl = cell_type(g, i - o[0], j - o[1], k - o[2]);
+    int tr = cell_type(g, i, j, k);
+    if (tl == SOLID || tr == SOLID) return FC_FIXED;
+    if (tl == LIQUID || tr == LIQUID) return FC_FLUID;
+    return FC_AIR;
+}
+
+static double bc_value(const or_grid *g, int c, long f)
+{
+    return g->bc[c] ? g->bc[c][f] : 0.0;
+}
+
+void or_face_class(const or_grid *g, int c, uint8_t *out)
+{
+    int d[3];
+    face_dims(g, c, d);
+    for (int k = 0; k < d[2]; k++)
+        for (int j = 0; j < d[1]; j++)
+            for (int i = 0; i < d[0]; i++)
+                out[fidx(d, i, j, k)] = (uint8_t)face_class(g, c, i, j, k);
+}
+
+/* ------------------------------------------------------------------------ */
+/* vector helpers over concatenated face fields                              */
+/* ------------------------------------------------------------------------ */
+
+static double dot(const double *a, const double *b, long n)
+{
+    double s = 0.0;
+    for (long t = 0; t < n; t++) s += a[t] * b[t];
+    return s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* a1 + a2: semi-Lagrangian advection with body force (Sec. 3.4.1; Eq. eq::v)  */
+/* ------------------------------------------------------------------------ */
+
+/* Per-dimension trilinear set-up for a continuous index s on an axis of n
+ * samples: clamp to [0, n-1]; base = min(floor(s), n-2); frac = s - base.
+ * `active` is 0 when the clamp bound (the derivative w.r.t. s is then zero). */
+static void axis_setup(double s, int n, int *base, double *frac, int *active)
+{
+    *active = 1;
+    if (s < 0.0) { s = 0.0; *active = 0; }
+    if (s > (double)(n - 1)) { s = (double)(n - 1); *active = 0; }
+    int b = (int)floor(s);
+    if (b > n - 2) b = n - 2;
+    *base = b;
+    *frac = s - (double)b;
+}
+
+/* The velocity seen by face (i,j,k) of component c: its own value, and for each
+ * other component e the mean of the four e-faces of the two cells that share the
+ * face. */
+static void face_velocity(const or_grid *g, int c, int i, int j, int k,
+                          const double *const u[3], double vel[3])
+{
+    int dc[3];
+    face_dims(g, c, dc);
+    vel[c] = u[c][fidx(dc, i, j, k)];
+    int L[3] = {i, j, k}, R[3] = {i, j, k};
+    L[c] -= 1;
+    for (int e = 0; e < 3; e++) {
+        if (e == c) continue;
+        int de[3];
+        face_dims(g, e, de);
+        int Lp[3] = {L[0], L[1], L[2]}, Rp[3] = {R[0], R[1], R[2]};
+        Lp[e] += 1;
+        Rp[e] += 1;
+        vel[e] = 0.25 * (u[e][fidx(de, L[0], L[1], L[2])] + u[e][fidx(de, Lp[0], Lp[1], Lp[2])] +
+                         u[e][fidx(de, R[0], R[1], R[2])] + u[e][fidx(de, Rp[0], Rp[1], Rp[2])]);
+    }
+}
+
+typedef struct {
+    int base[3];
+    double frac[3];
+    int active[3];
+} trace_t;
+
+static void back_trace(const or_grid *g, int c, int i, int j, int k,
+                       const double vel[3], trace_t *t)
+{
+    int dc[3];
+    face_dims(g, c, dc);
+    int idx[3] = {i, j, k};
+    double h = g->dt / g->dx;
+    for (int e = 0; e < 3; e++) {
+        double s = (double)idx[e] - h * vel[e];
+        axis_setup(s, dc[e], &t->base[e], &t->frac[e], &t->active[e]);
+    }
+}
+
+static double trilinear(const double *f, const int d[3], const trace_t *t)
+{
+    double acc = 0.0;
+    for (int cz = 0; cz < 2; cz++)
+        for (int cy = 0; cy < 2; cy++)
+            for (int cx = 0; cx < 2; cx++) {
+                double w = (cx ? t->frac[0] : 1.0 - t->frac[0]) *
+                           (cy ? t->frac[1] : 1.0 - t->frac[1]) *
+                           (cz ? t->frac[2] : 1.0 - t->frac[2]);
+                acc += w * f[fidx(d, t->base[0] + cx, t->base[1] + cy, t->base[2] + cz)];
+            }
+    return acc;
+}
+
+void or_advect(const or_grid *g, const double *const u[3], double *const ua[3])
+{
+    for (int c = 0; c < 3; c++) {
+        int d[3];
+        face_dims(g, c, d);
+        for (int k = 0; k < d[2]; k++)
+            for (int j = 0; j < d[1]; j++)
+                for (int i = 0; i < d[0]; i++) {
+                    long f = fidx(d, i, j, k);
+                    int cls = face_class(g, c, i, j, k);
+                    if (cls == FC_FIXED) { ua[c][f] = bc_value(g, c, f); continue; }
+                    if (cls == FC_AIR) { ua[c][f] = 0.0; continue; }
+                    double vel[3];
+                    trace_t t;
+                    face_velocity(g, c, i, j, k, u, vel);
+                    back_trace(g, c, i, j, k, vel, &t);
+                    ua[c][f] = trilinear(u[c], d, &t) + g->dt * g->g[c];
+                }
+    }
+}
+
+/* Exact discrete adjoint of or_advect w.r.t. the input field: given the
+ * cotangent ga of the advected field, ACCUMULATE d<ga, advect(u)>/du into gu.
+ * Fixed and air faces of the output are constants and contribute nothing. */
+void or_advect_adjoint(const or_grid *g, const double *const u[3],
+                       const double *const ga[3], double *const gu[3])
+{
+    double h = g->dt / g->dx;
+    for (int c = 0; c < 3; c++) {
+        int d[3];
+        face_dims(g, c, d);
+        for (int k = 0; k < d[2]; k++)
+            for (int j = 0; j < d[1]; j++)
+                for (int i = 0; i < d[0]; i++) {
+                    long f = fidx(d, i, j, k);
+                    if (face_class(g, c, i, j, k) != FC_FLUID) continue;
+                    double w = ga[c][f];
+                    if (w == 0.0) continue;
+                    double vel[3];
+                    trace_t t;
+                    face_velocity(g, c, i, j, k, u, vel);
+                    back_trace(g, c, i, j, k, vel, &t);
+                    /* value term: the trilinear weights */
+                    double dsd[3] = {0.0, 0.0, 0.0}; /* d sample / d s_e */
+                    for (int cz = 0; cz < 2; cz++)
+                        for (int cy = 0; cy < 2; cy++)
+                            for (int cx = 0; cx < 2; cx++) {
+                                double wx = cx ? t.frac[0] : 1.0 - t.frac[0];
+                                double wy = cy ? t.frac[1] : 1.0 - t.frac[1];
+                                double wz = cz ? t.frac[2] : 1.0 - t.frac[2];
+                                long fc = fidx(d, t.base[0] + cx, t.base[1] + cy, t.base[2] + cz);
+                                gu[c][fc] += w * wx * wy * wz;
+                                double val = u[c][fc];
+                                dsd[0] += (cx ? 1.0 : -1.0) * wy * wz * val;
+                                dsd[1] += wx * (cy ? 1.0 : -1.0) * wz * val;
+                                dsd[2] += wx * wy * (cz ? 1.0 : -1.0) * val;
+                            }
+                    /* position term: s_e = idx_e - h * vel_e, unless clamped */
+                    for (int e = 0; e < 3; e++) {
+                        if (!t.active[e]) continue;
+                        double gv = -h * dsd[e] * w; /* d/d vel_e */
+                        if (e == c) {
+                            gu[c][f] += gv;
+                        } else {
+                            int de[3];
+                            face_dims(g, e, de);
+                            int L[3] = {i, j, k}, R[3] = {i, j, k};
+                            L[c] -= 1;
+                            int Lp[3] = {L[0], L[1], L[2]}, Rp[3] = {R[0], R[1], R[2]};
+                            Lp[e] += 1;
+                            Rp[e] += 1;
+                            gu[e][fidx(de, L[0], L[1], L[2])] += 0.25 * gv;
+                            gu[e][fidx(de, Lp[0], Lp[1], Lp[2])] += 0.25 * gv;
+                            gu[e][fidx(de, R[0], R[1], R[2])] += 0.25 * gv;
+                            gu[e][fidx(de, Rp[0], Rp[1], Rp[2])] += 0.25 * gv;
+                        }
+                    }
+                }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* a3: implicit viscosity (Eq. eq::v viscous stress, backward Euler)          */
+/* ------------------------------------------------------------------------ */
+
+/* Neighbour rule for the face Laplacian of a fluid face: a fluid neighbour is
+ * coupled, a fixed neighbour is a Dirichlet value, an air neighbour or one
+ * beyond the array (tangential at a box wall) is a mirror (zero flux). */
+
+/* y = (I + nu dt L_f) x on fluid faces, zero elsewhere; Dirichlet values are
+ * left out (they belong to the right-hand side). */
+void or_visc_apply(const or_grid *g, const double *const x[3], double *const y[3])
+{
+    double cc = g->nu * g->dt / (g->dx * g->dx);
+    for (int c = 0; c < 3; c++) {
+        int d[3];
+        face_dims(g, c, d);
+        for (int k = 0; k < d[2]; k++)
+            for (int j = 0; j < d[1]; j++)
+                for (int i = 0; i < d[0]; i++) {
+                    long f = fidx(d, i, j, k);
+                    if (face_class(g, c, i, j, k) != FC_FLUID) { y[c][f] = 0.0; continue; }
+                    double xf = x[c][f], acc = xf;
+                    int idx[3] = {i, j, k};
+                    for (int e = 0; e < 3; e++)
+                        for (int sgn = -1; sgn <= 1; sgn += 2) {
+                            int n[3] = {idx[0], idx[1], idx[2]};
+                            n[e] += sgn;
+                            if (n[e] < 0 || n[e] >= d[e]) continue;
+                            int cl = face_class(g, c, n[0], n[1], n[2]);
+                            if (cl == FC_FLUID) acc += cc * (xf - x[c][fidx(d, n[0], n[1], n[2])]);
+                            else if (cl == FC_FIXED) acc += cc * xf;
+                        }
+                    y[c][f] = acc;
+                }
+    }
+}
+
+/* Dirichlet part of the right-hand side: cc * sum of fixed neighbour values. */
+static void visc_dirichlet(const or_grid *g, double *const out[3])
+{
+    double cc = g->nu * g->dt / (g->dx * g->dx);
+    for (int c = 0; c < 3; c++) {
+        int d[3];
+        face_dims(g, c, d);
+        for (int k = 0; k < d[2]; k++)
+            for (int j = 0; j < d[1]; j++)
+                for (int i = 0; i < d[0]; i++) {
+                    long f = fidx(d, i, j, k);
+                    out[c][f] = 0.0;
+                    if (face_class(g, c, i, j, k) != FC_FLUID) continue;
+                    int idx[3] = {i, j, k};
+                    for (int e = 0; e < 3; e++)
+                        for (int sgn = -1; sgn <= 1; sgn += 2) {
+                            int n[3] = {idx[0], idx[1], idx[2]};
+                            n[e] += sgn;
+                            if (n[e] < 0 || n[e] >= d[e]) continue;
+                            if (face_class(g, c, n[0], n[1], n[2]) == FC_FIXED)
+                                out[c][f] += cc * bc_value(g, c, fidx(d, n[0], n[1], n[2]));
+                        }
+                }
+    }
+}
+
+/* The face Laplacian with Dirichlet values taken from the field itself
+ * ((L~ u)_f = sum over coupled and fixed neighbours of (u_f - u_n) / dx^2);
+ * used by the viscosity gradient. Zero off fluid faces. */
+static void visc_laplacian_full(const or_grid *g, const double *const u[3], double *const y[3])
+{
+    double inv = 1.0 / (g->dx * g->dx);
+    for (int c = 0; c < 3; c++) {
+        int d[3];
+        face_dims(g, c, d);
+        for (int k = 0; k < d[2]; k++)
+            for (int j = 0; j < d[1]; j++)
+                for (int i = 0; i < d[0]; i++) {
+                    long f = fidx(d, i, j, k);
+                    y[c][f] = 0.0;
+                    if (face_class(g, c, i, j, k) != FC_FLUID) continue;
+                    int idx[3] = {i, j, k};
+                    double acc = 0.0;
+                    for (int e = 0; e < 3; e++)
+                        for (int sgn = -1; sgn <= 1; sgn += 2) {
+                            int n[3] = {idx[0], idx[1], idx[2]};
+                            n[e] += sgn;
+                            if (n[e] < 0 || n[e] >= d[e]) continue;
+                            int cl = face_class(g, c, n[0], n[1], n[2]);
+                            if (cl == FC_AIR) continue;
+                            acc += u[c][f] - u[c][fidx(d, n[0], n[1], n[2])];
+                        }
+                    y[c][f] = acc * inv;
+                }
+    }
+}
+
+/* Conjugate gradients on the fluid faces for (I + nu dt L_f) x = rhs, starting
+ * from x = 0, stopping at |r|/|rhs| <= tol_v. Vectors are zero off fluid faces. */
+static void visc_cg(const or_grid *g, double *const rhs[3], double *const x[3], or_stats *st)
+{
+    long n[3] = {nfaces(g, 0), nfaces(g, 1), nfaces(g, 2)};
+    long ntot = n[0] + n[1] + n[2];
+    double *buf = (double *)calloc((size_t)ntot * 3, sizeof(double));
+    double *r = buf, *p = buf + ntot, *q = buf + 2 * ntot;
+    double *rr3[3] = {r, r + n[0], r + n[0] + n[1]};
+    double *pp3[3] = {p, p + n[0], p + n[0] + n[1]};
+    double *qq3[3] = {q, q + n[0], q + n[0] + n[1]};
+    for (int c = 0; c < 3; c++) {
+        memcpy(rr3[c], rhs[c], (size_t)n[c] * sizeof(double));
+        memset(x[c], 0, (size_t)n[c] * sizeof(double));
+    }
+    memcpy(p, r, (size_t)ntot * sizeof(double));
+    double bb = dot(r, r, ntot), rr = bb;
+    st->iters = 0;
+    st->status = ST_OK;
+    st->relres = 0.0;
+    if (bb > 0.0) {
+        int it;
+        for (it = 1; it <= g->maxit_v; it++) {
+            or_visc_apply(g, (const double *const *)pp3, qq3);
+            double pq = dot(p, q, ntot);
+            if (!(pq > 0.0)) { st->status = ST_BREAKDOWN; break; }
+            double alpha = rr / pq;
+            for (int c = 0; c < 3; c++)
+                for (long t = 0; t < n[c]; t++) x[c][t] += alpha * pp3[c][t];
+            for (long t = 0; t < ntot; t++) r[t] -= alpha * q[t];
+            double rr_new = dot(r, r, ntot);
+            st->iters = it;
+            if (sqrt(rr_new / bb) <= g->tol_v) { rr = rr_new; break; }
+            double beta = rr_new / rr;
+            rr = rr_new;
+            for (long t = 0; t < ntot; t++) p[t] = r[t] + beta * p[t];
+        }
+        if (it > g->maxit_v) st->status = ST_NOCONV;
+        st->relres = sqrt(rr / bb);
+    }
+    /* true residual */
+    or_visc_apply(g, (const double *const *)x, qq3);
+    double tr = 0.0;
+    for (int c = 0; c < 3; c++)
+        for (long t = 0; t < n[c]; t++) {
+            double e = rhs[c][t] - qq3[c][t];
+            tr += e * e;
+        }
+    st->true_relres = bb > 0.0 ? sqrt(tr / bb) : 0.0;
+    free(buf);
+}
+
+/* Solve the viscosity step: fluid faces from the implicit solve, fixed faces take
+ * their prescribed values, air faces are zero. `dirichlet` selects whether the
+ * fixed neighbours' values enter the right-hand side (forward) or not (adjoint). */
+static void visc_solve_impl(const or_grid *g, const double *const ub[3], double *const uv[3],
+                            int dirichlet, or_stats *st)
+{
+    long n[3] = {nfaces(g, 0), nfaces(g, 1), nfaces(g, 2)};
+    double *rhs[3], *x[3];
+    for (int c = 0; c < 3; c++) {
+        rhs[c] = (double *)calloc((size_t)n[c], sizeof(double));
+        x[c] = (double *)calloc((size_t)n[c], sizeof(double));
+    }
+    if (dirichlet) visc_dirichlet(g, rhs);
+    for (int c = 0; c < 3; c++) {
+        uint8_t *cls = (uint8_t *)malloc((size_t)n[c]);
+        or_face_class(g, c, cls);
+        for (long t = 0; t < n[c]; t++)
+            rhs[c][t] = (cls[t] == FC_FLUID) ? rhs[c][t] + ub[c][t] : 0.0;
+        free(cls);
+    }
+    visc_cg(g, rhs, x, st);
+    for (int c = 0; c < 3; c++) {
+        uint8_t *cls = (uint8_t *)malloc((size_t)n[c]);
+        or_face_class(g, c, cls);
+        for (long t = 0; t < n[c]; t++) {
+            if (cls[t] == FC_FLUID) uv[c][t] = x[c][t];
+            else if (cls[t] == FC_FIXED) uv[c][t] = dirichlet ? bc_value(g, c, t) : 0.0;
+            else uv[c][t] = 0.0;
+        }
+        free(cls);
+        free(rhs[c]);
+        free(x[c]);
+    }
+}
+
+void or_visc_solve(const or_grid *g, const double *const ub[3], double *const uv[3], or_stats *st)
+{
+    visc_solve_impl(g, ub, uv, 1, st);
+}
+
+/* ------------------------------------------------------------------------ */
+/* a4-a6: projection (Sec. 3.2.2 splitting; Poisson pressure equation)        */
+/* ------------------------------------------------------------------------ */
+
+/* b_i = -dx * (net outflow of cell i) for liquid cells, zero elsewhere. */
+void or_divergence(const or_grid *g, const double *const u[3], double *b)
+{
+    for (int k = 0; k < g->nz; k++)
+        for (int j = 0; j < g->ny; j++)
+            for (int i = 0; i < g->nx; i++) {
+                long ci = cidx(g, i, j, k);
+                if (g->type[ci] != LIQUID) { b[ci] = 0.0; continue; }
+                double div = 0.0;
+                for (int c = 0; c < 3; c++) {
+                    int d[3];
+                    face_dims(g, c, d);
+                    int hi[3] = {i, j, k};
+                    hi[c] += 1;
+                    div += u[c][fidx(d, hi[0], hi[1], hi[2])] - u[c][fidx(d, i, j, k)];
+                }
+                b[ci] = -g->dx * div;
+            }
+}
+
+/* Seven-point pressure operator on liquid cells: each non-solid neighbour adds
+ * one to the diagonal, each liquid neighbour -1 off the diagonal; air cells hold
+ * p = 0 and solid neighbours add nothing. Zero on non-liquid cells. */
+void or_poisson_apply(const or_grid *g, const double *x, double *y)
+{
+    static const int off[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+    for (int k = 0; k < g->nz; k++)
+        for (int j = 0; j < g->ny; j++)
+            for (int i = 0; i < g->nx; i++) {
+                long ci = cidx(g, i, j, k);
+                if (g->type[ci] != LIQUID) { y[ci] = 0.0; continue; }
+                double acc = 0.0;
+                for (int m = 0; m < 6; m++) {
+                    int a = i + off[m][0], b = j + off[m][1], cc = k + off[m][2];
+                    int t = cell_type(g, a, b, cc);
+                    if (t == SOLID) continue;
+                    acc += x[ci];
+                    if (t == LIQUID) acc -= x[cidx(g, a, b, cc)];
+                }
+                y[ci] = acc;
+            }
+}
+
+static int poisson_diag(const or_grid *g, int i, int j, int k)
+{
+    static const int off[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+    int dcount = 0;
+    for (int m = 0; m < 6; m++)
+        if (cell_type(g, i + off[m][0], j + off[m][1], k + off[m][2]) != SOLID) dcount++;
+    return dcount;
+}
+
+/* Coupling to the next cell along +x, +y, +z: -1 when both are liquid. */
+static double poisson_off(const or_grid *g, int i, int j, int k, int e)
+{
+    int o[3] = {0, 0, 0};
+    o[e] = 1;
+    if (cell_type(g, i, j, k) != LIQUID) return 0.0;
+    if (cell_type(g, i + o[0], j + o[1], k + o[2]) != LIQUID) return 0.0;
+    return -1.0;
+}
+
+/* u_f -= (q_R - q_L) / dx on fluid faces; q is zero in non-liquid cells. */
+void or_grad_subtract(const or_grid *g, const double *q, double *const u[3])
+{
+    for (int c = 0; c < 3; c++) {
+        int d[3];
+        face_dims(g, c, d);
+        for (int k = 0; k < d[2]; k++)
+            for (int j = 0; j < d[1]; j++)
+                for (int i = 0; i < d[0]; i++) {
+                    if (face_class(g, c, i, j, k) != FC_FLUID) continue;
+                    int L[3] = {i, j, k};
+                    L[c] -= 1;
+                    double qr = cell_type(g, i, j, k) == LIQUID ? q[cidx(g, i, j, k)] : 0.0;
+                    double ql = cell_type(g, L[0], L[1], L[2]) == LIQUID ? q[cidx(g, L[0], L[1], L[2])] : 0.0;
+                    u[c][fidx(d, i, j, k)] -= (qr - ql) / g->dx;
+                }
+    }
+}
+
+/* The pressure operator is singular when the liquid touches no air cell (a
+ * closed box full of liquid): its null space is then the constant on the liquid. */
+int or_is_singular(const or_grid *g)
+{
+    static const int off[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+    int any = 0;
+    for (int k = 0; k < g->nz; k++)
+        for (int j = 0; j < g->ny; j++)
+            for (int i = 0; i < g->nx; i++) {
+                if (cell_type(g, i, j, k) != LIQUID) continue;
+                any = 1;
+                for (int m = 0; m < 6; m++)
+                    if (cell_type(g, i + off[m][0], j + off[m][1], k + off[m][2]) == AIR) return 0;
+            }
+    return any;
+}
+
+static void remove_liquid_mean(const or_grid *g, double *x)
+{
+    long n = ncells(g), cnt = 0;
+    double s = 0.0;
+    for (long t = 0; t < n; t++)
+        if (g->type[t] == LIQUID) { s += x[t]; cnt++; }
+    if (!cnt) return;
+    s /= (double)cnt;
+    for (long t = 0; t < n; t++)
+        if (g->type[t] == LIQUID) x[t] -= s;
+}
+
+/* MIC(0) factor (Bridson): for each liquid cell in lexicographic order,
+ *   e = A_ii - sum_{lower nbr m} (A_mi * prec_m)^2
+ *         - tau * sum_{lower nbr m} A_mi * (sum of m's other forward couplings) * prec_m^2,
+ *   e < sigma * A_ii  =>  e = A_ii;   prec_i = 1 / sqrt(e).
+ * The factor is L with L_ii = 1/prec_i and L_im = A_im * prec_m (m lower). */
+void or_mic0_factor(const or_grid *g, double tau, double sigma, double *prec)
+{
+    for (int k = 0; k < g->nz; k++)
+        for (int j = 0; j < g->ny; j++)
+            for (int i = 0; i < g->nx; i++) {
+                long ci = cidx(g, i, j, k);
+                prec[ci] = 0.0;
+                if (g->type[ci] != LIQUID) continue;
+                double diag = (double)poisson_diag(g, i, j, k);
+                double e = diag;
+                /* lower neighbours along x, y, z */
+                int lo[3][3] = {{i - 1, j, k}, {i, j - 1, k}, {i, j, k - 1}};
+                for (int a = 0; a < 3; a++) {
+                    int *m = lo[a];
+                    if (cell_type(g, m[0], m[1], m[2]) != LIQUID) continue;
+                    double pm = prec[cidx(g, m[0], m[1], m[2])];
+                    double amc = poisson_off(g, m[0], m[1], m[2], a); /* coupling m -> this cell */
+                    double other = 0.0;
+                    for (int b = 0; b < 3; b++)
+                        if (b != a) other += poisson_off(g, m[0], m[1], m[2], b);
+                    e -= (amc * pm) * (amc * pm);
+                    e -= tau * amc * other * pm * pm;
+                }
+                if (e < sigma * diag) e = diag;
+                prec[ci] = diag > 0.0 ? 1.0 / sqrt(e) : 0.0; /* a liquid cell walled in on all sides */
+            }
+}
+
+/* z = (L L^T)^{-1} r with the MIC(0) factor: forward then backward substitution. */
+void or_mic0_apply(const or_grid *g, const double *prec, const double *r, double *z)
+{
+    long n = ncells(g);
+    double *y = (double *)calloc((size_t)n, sizeof(double));
+    for (int k = 0; k < g->nz; k++)
+        for (int j = 0; j < g->ny; j++)
+            for (int i = 0; i < g->nx; i++) {
+                long ci = cidx(g, i, j, k);
+                if (g->type[ci] != LIQUID) continue;
+                double t = r[ci];
+                int lo[3][3] = {{i - 1, j, k}, {i, j - 1, k}, {i, j, k - 1}};
+                for (int a = 0; a < 3; a++) {
+                    int *m = lo[a];
+                    if (cell_type(g, m[0], m[1], m[2]) != LIQUID) continue;
+                    long mi = cidx(g, m[0], m[1], m[2]);
+                    t -= poisson_off(g, m[0], m[1], m[2], a) * prec[mi] * y[mi];
+                }
+                y[ci] = t * prec[ci];
+            }
+    for (long t = 0; t < n; t++) z[t] = 0.0;
+    for (int k = g->nz - 1; k >= 0; k--)
+        for (int j = g->ny - 1; j >= 0; j--)
+            for (int i = g->nx - 1; i >= 0; i--) {
+                long ci = cidx(g, i, j, k);
+                if (g->type[ci] != LIQUID) continue;
+                double t = y[ci];
+                int hi[3][3] = {{i + 1, j, k}, {i, j + 1, k}, {i, j, k + 1}};
+                for (int a = 0; a < 3; a++) {
+                    int *m = hi[a];
+                    if (cell_type(g, m[0], m[1], m[2]) != LIQUID) continue;
+                    t -= poisson_off(g, i, j, k, a) * prec[ci] * z[cidx(g, m[0], m[1], m[2])];
+                }
+                z[ci] = t * prec[ci];
+            }
+    free(y);
+}
+
+/* Preconditioned CG for the pressure operator from x = 0 (the null-space mean
+ * of b is removed first when the operator is singular). Stops at
+ * |r|/|b| <= tol_p or after maxit_p iterations. */
+void or_pcg(const or_grid *g, const double *b_in, double *x, int precond, or_stats *st)
+{
+    long n = ncells(g);
+    double *b = (double *)malloc((size_t)n * sizeof(double));
+    double *r = (double *)malloc((size_t)n * sizeof(double));
+    double *z = (double *)calloc((size_t)n, sizeof(double));
+    double *p = (double *)calloc((size_t)n, sizeof(double));
+    double *q = (double *)calloc((size_t)n, sizeof(double));
+    double *prec = NULL;
+    memcpy(b, b_in, (size_t)n * sizeof(double));
+    for (long t = 0; t < n; t++) if (g->type[t] != LIQUID) b[t] = 0.0;
+    int singular = or_is_singular(g);
+    if (singular) remove_liquid_mean(g, b);
+    if (precond == PC_MIC0) {
+        prec = (double *)calloc((size_t)n, sizeof(double));
+        or_mic0_factor(g, g->mic_tau, g->mic_sigma, prec);
+    }
+    for (long t = 0; t < n; t++) x[t] = 0.0;
+    memcpy(r, b, (size_t)n * sizeof(double));
+    double bb = dot(b, b, n), rr = bb;
+    st->iters = 0;
+    st->status = ST_OK;
+    st->relres = 0.0;
+    st->true_relres = 0.0;
+    if (bb > 0.0) {
+#define APPLY_PREC()                                                                    \
+    do {                                                                                \
+        if (precond == PC_MIC0) or_mic0_apply(g, prec, r, z);                           \
+        else if (precond == PC_JACOBI) {                                                \
+            for (int kk = 0; kk < g->nz; kk++)                                          \
+                for (int jj = 0; jj < g->ny; jj++)                                      \
+                    for (int ii = 0; ii < g->nx; ii++) {                                \
+                        long cc = cidx(g, ii, jj, kk);                                  \
+                        int dg = poisson_diag(g, ii, jj, kk);                   \
+                        z[cc] = (g->type[cc] == LIQUID && dg > 0) ? r[cc] / dg : 0.0; \
+                    }                                                                   \
+        } else memcpy(z, r, (size_t)n * sizeof(double));                                \
+    } while (0)
+        APPLY_PREC();
+        memcpy(p, z, (size_t)n * sizeof(double));
+        double rz = dot(r, z, n);
+        int it;
+        for (it = 1; it <= g->maxit_p; it++) {
+            or_poisson_apply(g, p, q);
+            double pq = dot(p, q, n);
+            if (!(pq > 0.0)) { st->status = ST_BREAKDOWN; break; }
+            double alpha = rz / pq;
+            for (long t = 0; t < n; t++) { x[t] += alpha * p[t]; r[t] -= alpha * q[t]; }
+            rr = dot(r, r, n);
+            st->iters = it;
+            if (sqrt(rr / bb) <= g->tol_p) break;
+            APPLY_PREC();
+            double rz_new = dot(r, z, n);
+            double beta = rz_new / rz;
+            rz = rz_new;
+            for (long t = 0; t < n; t++) p[t] = z[t] + beta * p[t];
+        }
+#undef APPLY_PREC
+        if (it > g->maxit_p) st->status = ST_NOCONV;
+        st->relres = sqrt(rr / bb);
+        if (singular) remove_liquid_mean(g, x);
+        or_poisson_apply(g, x, q);
+        double tr = 0.0;
+        for (long t = 0; t < n; t++) { double e = b[t] - q[t]; tr += e * e; }
+        st->true_relres = sqrt(tr / bb);
+    }
+    free(b); free(r); free(z); free(p); free(q); free(prec);
+}
+
+/* Project u in place onto the discretely divergence-free fields: b = div RHS,
+ * solve for q, subtract the pressure gradient. q_out (nullable) receives q. */
+void or_project(const or_grid *g, double *const u[3], double *q_out, or_stats *st)
+{
+    long n = ncells(g);
+    double *b = (double *)malloc((size_t)n * sizeof(double));
+    double *q = (double *)calloc((size_t)n, sizeof(double));
+    or_divergence(g, (const double *const *)u, b);
+    or_pcg(g, b, q, g->precond, st);
+    or_grad_subtract(g, q, u);
+    if (q_out) memcpy(q_out, q, (size_t)n * sizeof(double));
+    free(b);
+    free(q);
+}
+
+/* ------------------------------------------------------------------------ */
+/* the step and its adjoint                                                  */
+/* ------------------------------------------------------------------------ */
+
+static void alloc3(const or_grid *g, double *a[3])
+{
+    for (int c = 0; c < 3; c++) a[c] = (double *)calloc((size_t)nfaces(g, c), sizeof(double));
+}
+
+static void free3(double *a[3])
+{
+    for (int c = 0; c < 3; c++) free(a[c]);
+}
+
+/* One step: advect (+ body force, fixed faces), implicit viscosity, projection.
+ * u_visc (nullable) receives the field after viscosity. st[0] viscosity, st[1]
+ * pressure. */
+void or_step(const or_grid *g, const double *const u_in[3], double *const u_out[3],
+             double *const *u_visc, or_stats *st)
+{
+    double *ua[3];
+    alloc3(g, ua);
+    or_advect(g, u_in, ua);
+    or_visc_solve(g, (const double *const *)ua, u_out, &st[0]);
+    free3(ua);
+    if (u_visc)
+        for (int c = 0; c < 3; c++) memcpy(u_visc[c], u_out[c], (size_t)nfaces(g, c) * sizeof(double));
+    or_project(g, u_out, NULL, &st[1]);
+}
+
+/* Reverse of one step. Given the input field u_in and the cotangent g_out of the
+ * step's output, write the cotangent g_in of the input and add dL/dnu to *g_nu.
+ *   projection:  P is an orthogonal projector on the fluid faces, so the
+ *                cotangent is projected by the same operator (fixed and air
+ *                faces of the output are constants: their cotangent is dropped);
+ *   viscosity:   (I + nu dt L_f) is symmetric: one more solve; with
+ *                A(nu) u_v = u_b + Dirichlet(nu), dL/dnu = -dt <gb, L~ u_v>;
+ *   advection:   the exact discrete adjoint of the trilinear back-trace. */
+void or_adjoint_step(const or_grid *g, const double *const u_in[3], const double *const g_out[3],
+                     double *const g_in[3], double *g_nu, or_stats *st)
+{
+    double *ua[3], *uv[3], *gv[3], *gb[3], *lu[3];
+    alloc3(g, ua); alloc3(g, uv); alloc3(g, gv); alloc3(g, gb); alloc3(g, lu);
+    or_advect(g, u_in, ua);
+    or_visc_solve(g, (const double *const *)ua, uv, &st[0]);
+    /* projection adjoint */
+    for (int c = 0; c < 3; c++) {
+        int d[3];
+        face_dims(g, c, d);
+        for (int k = 0; k < d[2]; k++)
+            for (int j = 0; j < d[1]; j++)
+                for (int i = 0; i < d[0]; i++) {
+                    long f = fidx(d, i, j, k);
+                    gv[c][f] = face_class(g, c, i, j, k) == FC_FLUID ? g_out[c][f] : 0.0;
+                }
+    }
+    or_project(g, gv, NULL, &st[1]);
+    /* viscosity adjoint (no Dirichlet values: the cotangent of a fixed face is 0) */
+    visc_solve_impl(g, (const double *const *)gv, gb, 0, &st[2]);
+    visc_laplacian_full(g, (const double *const *)uv, lu);
+    double s = 0.0;
+    for (int c = 0; c < 3; c++) s += dot(gb[c], lu[c], nfaces(g, c));
+    *g_nu += -g->dt * s;
+    /* advection adjoint (body force is an additive constant) */
+    for (int c = 0; c < 3; c++) memset(g_in[c], 0, (size_t)nfaces(g, c) * sizeof(double));
+    or_advect_adjoint(g, u_in, (const double *const *)gb, g_in);
+    free3(ua); free3(uv); free3(gv); free3(gb); free3(lu);
+}
+
+/* ------------------------------------------------------------------------ */
+/* a7: loss of Eq. (eq::optLoss) and its gradient                             */
+/* ------------------------------------------------------------------------ */
+
+/* Band cells: kind 0 (surface) = liquid cells with at least one air neighbour;
+ * kind 1 (occupied) = all liquid cells. */
+void or_band_cells(const or_grid *g, int kind, uint8_t *band)
+{
+    static const int off[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+    for (int k = 0; k < g->nz; k++)
+        for (int j = 0; j < g->ny; j++)
+            for (int i = 0; i < g->nx; i++) {
+                long ci = cidx(g, i, j, k);
+                band[ci] = 0;
+                if (g->type[ci] != LIQUID) continue;
+                if (kind == 1) { band[ci] = 1; continue; }
+                for (int m = 0; m < 6; m++)
+                    if (cell_type(g, i + off[m][0], j + off[m][1], k + off[m][2]) == AIR) { band[ci] = 1; break; }
+            }
+}
+
+/* L = beta/(2|B|) sum_{f in B} (u_f - t_f)^2 + alpha/|Bc| sum_{c in Bc} (1 - cos(ubar_c, tbar_c))
+ * B = fluid faces with a band cell on either side; Bc = band cells; ubar = mean of a
+ * cell's two faces per component; cos(a,b) = a.b / (sqrt(|a|^2+eps^2) sqrt(|b|^2+eps^2)).
+ * Adds L to *loss and dL/du to grad. */
+void or_loss_grad(const or_grid *g, const double *const u[3], const double *const tgt[3],
+                  int kind, double alpha, double beta, double *loss, double *const grad[3])
+{
+    const double eps = 1e-8;
+    long nc = ncells(g);
+    uint8_t *band = (uint8_t *)malloc((size_t)nc);
+    or_band_cells(g, kind, band);
+    long nb_cells = 0, nb_faces = 0;
+    for (long t = 0; t < nc; t++) nb_cells += band[t];
+    /* count band faces */
+    for (int c = 0; c < 3; c++) {
+        int d[3];
+        face_dims(g, c, d);
+        for (int k = 0; k < d[2]; k++)
+            for (int j = 0; j < d[1]; j++)
+                for (int i = 0; i < d[0]; i++) {
+                    if (face_class(g, c, i, j, k) != FC_FLUID) continue;
+                    int L[3] = {i, j, k};
+                    L[c] -= 1;
+                    int inb = (cell_type(g, i, j, k) == LIQUID && band[cidx(g, i, j, k)]) ||
+                              (cell_type(g, L[0], L[1], L[2]) == LIQUID && band[cidx(g, L[0], L[1], L[2])]);
+                    nb_faces += inb;
+                }
+    }
+    double l2 = 0.0, lcos = 0.0;
+    if (nb_faces > 0 && beta != 0.0) {
+        for (int c = 0; c < 3; c++) {
+            int d[3];
+            face_dims(g, c, d);
+            for (int k = 0; k < d[2]; k++)
+                for (int j = 0; j < d[1]; j++)
+                    for (int i = 0; i < d[0]; i++) {
+                        if (face_class(g, c, i, j, k) != FC_FLUID) continue;
+                        int L[3] = {i, j, k};
+                        L[c] -= 1;
+                        int inb = (cell_type(g, i, j, k) == LIQUID && band[cidx(g, i, j, k)]) ||
+                                  (cell_type(g, L[0], L[1], L[2]) == LIQUID && band[cidx(g, L[0], L[1], L[2])]);
+                        if (!inb) continue;
+                        long f = fidx(d, i, j, k);
+                        double e = u[c][f] - tgt[c][f];
+                        l2 += 0.5 * e * e;
+                        grad[c][f] += beta * e / (double)nb_faces;
+                    }
+        }
+        l2 *= beta / (double)nb_faces;
+    }
+    if (nb_cells > 0 && alpha != 0.0) {
+        for (int k = 0; k < g->nz; k++)
+            for (int j = 0; j < g->ny; j++)
+                for (int i = 0; i < g->nx; i++) {
+                    long ci = cidx(g, i, j, k);
+                    if (!band[ci]) continue;
+                    double a[3], b[3];
+                    long lo[3], hi[3];
+                    for (int c = 0; c < 3; c++) {
+                        int d[3];
+                        face_dims(g, c, d);
+                        int h[3] = {i, j, k};
+                        h[c] += 1;
+                        lo[c] = fidx(d, i, j, k);
+                        hi[c] = fidx(d, h[0], h[1], h[2]);
+                        a[c] = 0.5 * (u[c][lo[c]] + u[c][hi[c]]);
+                        b[c] = 0.5 * (tgt[c][lo[c]] + tgt[c][hi[c]]);
+                    }
+                    double ab = a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+                    double na = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + eps * eps);
+                    double nbv = sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2] + eps * eps);
+                    double cs = ab / (na * nbv);
+                    lcos += 1.0 - cs;
+                    for (int c = 0; c < 3; c++) {
+                        double dcos = b[c] / (na * nbv) - ab * a[c] / (na * na * na * nbv);
+                        double gcell = -alpha * dcos / (double)nb_cells;
+                        grad[c][lo[c]] += 0.5 * gcell;
+                        grad[c][hi[c]] += 0.5 * gcell;
+                    }
+                }
+        lcos *= alpha / (double)nb_cells;
+    }
+    *loss += l2 + lcos;
+    free(band);
+}
+
+/* ------------------------------------------------------------------------ */
+/* a12/a13: the convolutional preconditioner network (Sec. 3.4.1)            */
+/* ------------------------------------------------------------------------ */
+
+/* Five 3x3x3 convolutions, channels 2 -> 16 -> 16 -> 16 -> 16 -> 1, zero
+ * padding, ReLU after the first four. Weights W_l are [co][ci][3][3][3]
+ * (values already rounded to bf16 by the caller), biases FP64. Inputs: channel 0
+ * = r / s on liquid cells (s = max |r| over liquid cells), channel 1 = cell type
+ * code (liquid 1, air 0, solid -1). Activations are rounded to bf16 after each
+ * hidden layer, as the GPU stores them. Output z = s * y on liquid cells. */
+#define NET_LAYERS 5
+static const int net_ch[NET_LAYERS + 1] = {2, 16, 16, 16, 16, 1};
+
+double or_bf16_round(double v)
+{
+    float f = (float)v;
+    uint32_t bits;
+    memcpy(&bits, &f, 4);
+    if ((bits & 0x7f800000u) == 0x7f800000u) return (double)f; /* inf / nan */
+    uint32_t lsb = (bits >> 16) & 1u;
+    bits += 0x7fffu + lsb;
+    bits &= 0xffff0000u;
+    memcpy(&f, &bits, 4);
+    return (double)f;
+}
+
+static void conv3d(const or_grid *g, const double *in, int ci_n, const double *W, const double *B,
+                   int co_n, double *out)
+{
+    int nx = g->nx, ny = g->ny, nz = g->nz;
+    long n = ncells(g);
+    for (int co = 0; co < co_n; co++)
+        for (int k = 0; k < nz; k++)
+            for (int j = 0; j < ny; j++)
+                for (int i = 0; i < nx; i++) {
+                    double acc = B[co];
+                    for (int ci = 0; ci < ci_n; ci++)
+                        for (int dz = -1; dz <= 1; dz++)
+                            for (int dy = -1; dy <= 1; dy++)
+                                for (int dxo = -1; dxo <= 1; dxo++) {
+                                    int a = i + dxo, b = j + dy, c = k + dz;
+                                    if (a < 0 || b < 0 || c < 0 || a >= nx || b >= ny || c >= nz) continue;
+                                    double wv = W[(((long)co * ci_n + ci) * 3 + (dz + 1)) * 9 + (dy + 1) * 3 + (dxo + 1)];
+                                    acc += wv * in[(long)ci * n + cidx(g, a, b, c)];
+                                }
+                    out[(long)co * n + cidx(g, i, j, k)] = acc;
+                }
+}
+
+/* acts (nullable) receives the stored (post-ReLU, bf16-rounded) input of each
+ * layer: layer l's input at acts + offset_l, offsets sum(ch[m] * n, m < l). The
+ * last slot holds the raw network output y (before scaling by s). Returns s. */
+double or_net_forward(const or_grid *g, const double *const W[NET_LAYERS],
+                      const double *const B[NET_LAYERS], const double *r, double *z, double *acts)
+{
+    long n = ncells(g);
+    double s = 0.0;
+    for (long t = 0; t < n; t++)
+        if (g->type[t] == LIQUID && fabs(r[t]) > s) s = fabs(r[t]);
+    double *cur = (double *)calloc((size_t)n * 16, sizeof(double));
+    double *nxt = (double *)calloc((size_t)n * 16, sizeof(double));
+    for (long t = 0; t < n; t++) {
+        double x0 = (g->type[t] == LIQUID && s > 0.0) ? r[t] / s : 0.0;
+        cur[t] = or_bf16_round(x0);
+        cur[n + t] = g->type[t] == LIQUID ? 1.0 : (g->type[t] == SOLID ? -1.0 : 0.0);
+    }
+    long off = 0;
+    for (int l = 0; l < NET_LAYERS; l++) {
+        if (acts) memcpy(acts + off, cur, (size_t)net_ch[l] * n * sizeof(double));
+        off += (long)net_ch[l] * n;
+        conv3d(g, cur, net_ch[l], W[l], B[l], net_ch[l + 1], nxt);
+        if (l < NET_LAYERS - 1)
+            for (long t = 0; t < (long)net_ch[l + 1] * n; t++)
+                nxt[t] = or_bf16_round(nxt[t] > 0.0 ? nxt[t] : 0.0);
+        double *tmp = cur; cur = nxt; nxt = tmp;
+    }
+    if (acts) memcpy(acts + off, cur, (size_t)n * sizeof(double));
+    for (long t = 0; t < n; t++) z[t] = (g->type[t] == LIQUID) ? s * cur[t] : 0.0;
+    free(cur);
+    free(nxt);
+    return s;
+}
+
+/* Training loss for one (b, q) pair with A q = b:
+ *   s = max |b| over liquid;  y = Net(b / s);
+ *   loss = sum_liquid (y - q/s)^2 / sum_liquid (q/s)^2.
+ * Returns the loss and ADDS its gradient to gW, gB (same layouts as W, B). */
+double or_net_loss_grad(const or_grid *g, const double *const W[NET_LAYERS],
+                        const double *const B[NET_LAYERS], const double *b, const double *q,
+                        double *const gW[NET_LAYERS], double *const gB[NET_LAYERS])
+{
+    long n = ncells(g);
+    long tot = 0;
+    for (int l = 0; l <= NET_LAYERS; l++) tot += (long)net_ch[l] * n;
+    double *acts = (double *)calloc((size_t)tot, sizeof(double));
+    double *z = (double *)calloc((size_t)n, sizeof(double));
+    double s = or_net_forward(g, W, B, b, z, acts);
+    if (s == 0.0) { free(acts); free(z); return 0.0; }
+    long offs[NET_LAYERS + 1];
+    offs[0] = 0;
+    for (int l = 1; l <= NET_LAYERS; l++) offs[l] = offs[l - 1] + (long)net_ch[l - 1] * n;
+    const double *y = acts + offs[NET_LAYERS];
+    double den = 0.0, num = 0.0;
+    for (long t = 0; t < n; t++)
+        if (g->type[t] == LIQUID) { double tq = q[t] / s; den += tq * tq; }
+    double *gy = (double *)calloc((size_t)n * 16, sizeof(double));
+    double *gx = (double *)calloc((size_t)n * 16, sizeof(double));
+    for (long t = 0; t < n; t++)
+        if (g->type[t] == LIQUID) {
+            double e = y[t] - q[t] / s;
+            num += e * e;
+            gy[t] = 2.0 * e / den;
+        }
+    int nx = g->nx, ny = g->ny, nz = g->nz;
+    for (int l = NET_LAYERS - 1; l >= 0; l--) {
+        int ci_n = net_ch[l], co_n = net_ch[l + 1];
+        const double *in = acts + offs[l];
+        /* ReLU mask on this layer's output (all but the last layer) */
+        if (l < NET_LAYERS - 1) {
+            const double *outv = acts + offs[l + 1];
+            for (long t = 0; t < (long)co_n * n; t++) if (!(outv[t] > 0.0)) gy[t] = 0.0;
+        }
+        memset(gx, 0, (size_t)ci_n * n * sizeof(double));
+        for (int co = 0; co < co_n; co++)
+            for (int k = 0; k < nz; k++)
+                for (int j = 0; j < ny; j++)
+                    for (int i = 0; i < nx; i++) {
+                        double go = gy[(long)co * n + cidx(g, i, j, k)];
+                        if (go == 0.0) continue;
+                        gB[l][co] += go;
+                        for (int ci = 0; ci < ci_n; ci++)
+                            for (int dz = -1; dz <= 1; dz++)
+                                for (int dy = -1; dy <= 1; dy++)
+                                    for (int dxo = -1; dxo <= 1; dxo++) {
+                                        int a = i + dxo, bb = j + dy, c = k + dz;
+                                        if (a < 0 || bb < 0 || c < 0 || a >= nx || bb >= ny || c >= nz) continue;
+                                        long wi = (((long)co * ci_n + ci) * 3 + (dz + 1)) * 9 + (dy + 1) * 3 + (dxo + 1);
+                                        long xi = (long)ci * n + cidx(g, a, bb, c);
+                                        gW[l][wi] += go * in[xi];
+                                        gx[xi] += go * W[l][wi];
+                                    }
+                    }
+        double *tmp = gy; gy = gx; gx = tmp;
+    }
+    free(acts); free(z); free(gy); free(gx);
+    return num / den;
+}
