@@ -1,0 +1,207 @@
+/*
+ * fluidstep.h -- C ABI of the differentiable MAC-grid fluid step on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The method (arXiv 2503.00868, Sec. 3.4) fits simulation parameters by
+ * evolving a grid velocity field through the split incompressible Navier-Stokes
+ * equations (Eq. eq::v, Sec. 3.2.2), with grid convection by back-tracing
+ * (Sec. 3.4.1), under the masked loss of Eq. eq::optLoss (Sec. 3.4.2). The problem
+ * statement there is v_sim^{i+n} = DiffSim^n(v^i; nu, v_in, g, dt, ...): these
+ * calls provide one step of DiffSim, its reverse-mode adjoint and the loss.
+ *
+ * One step (fs_step) is:
+ *   1. semi-Lagrangian advection: each fluid face samples its own component
+ *      trilinearly at x_f - dt * u(x_f) (other components at the face are the mean
+ *      of the 4 surrounding faces); the continuous index is clamped to the array;
+ *   2. body force: + dt * g on fluid faces; fixed faces take their prescribed
+ *      values, faces between two air cells are zero;
+ *   3. implicit viscosity: (I + nu dt L_f) u_v = u_b on the fluid faces, per
+ *      component, L_f the 7-point face Laplacian (fluid neighbours coupled, fixed
+ *      neighbours Dirichlet, air neighbours and box-wall tangential neighbours
+ *      zero-flux), solved by Jacobi-preconditioned CG;
+ *   4. projection: b = -dx * div(u_v) on liquid cells, L_p q = b (7-point, p = 0
+ *      in air, solid walls zero-flux) by PCG, then u -= grad q / dx on fluid faces.
+ *      The pressure is p = rho * q / dt.
+ *
+ * Cell types: FS_AIR, FS_LIQUID, FS_SOLID; every cell outside the grid is solid.
+ * A face is FIXED if a solid cell touches it, FLUID if it touches a liquid cell
+ * and no solid cell, AIR otherwise.
+ *
+ * Memory layout. Every field the caller passes is a DEVICE array of floats (or
+ * bytes) in the library layout returned by fs_layout(): element (i, j, k) of any
+ * cell array or of any face component lives at
+ *     (k * rows + j) * pitch + i,     rows = ny + 1, planes = nz + 1,
+ * with pitch >= nx + 1 a multiple of 4, and every array holds `nelems` =
+ * pitch * rows * planes elements. u-faces use i <= nx, v-faces j <= ny, w-faces
+ * k <= nz; u(i,j,k) lies between cells (i-1,j,k) and (i,j,k) (likewise v, w).
+ * Entries outside an array's valid range are padding: the library never reads
+ * them and writes zeros there in its outputs.
+ *
+ * Ownership. The caller owns every array it passes and must keep it alive until
+ * the call returns. The context owns its scratch (solver vectors, flags, the
+ * reduction buffers, pinned read-back memory) and frees it in fs_destroy. The
+ * library never frees caller memory and never returns memory to the caller.
+ *
+ * Streams and synchronisation. All work is enqueued on the context's stream.
+ * Calls that run an iterative solve or return a scalar (fs_step, fs_project,
+ * fs_adjoint_step, fs_loss_grad, fs_set_mask) read the result back from pinned
+ * memory and return after the stream has reached the end of their work. A
+ * context must not be used from two host threads at once.
+ *
+ * Errors. Every call returns an FS_* status. Argument errors (FS_EINVAL) are
+ * reported before anything is enqueued. FS_ENOCONV means an iteration cap was
+ * reached: the best iterate is still written and the stats are filled.
+ * fs_last_error() returns a per-thread message for the last failing call.
+ */
+#ifndef FLUIDSTEP_H
+#define FLUIDSTEP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    FS_OK = 0,
+    FS_EINVAL = 1,      /* bad argument (sizes, null pointer, parameter range) */
+    FS_ENOMEM = 2,      /* device or pinned allocation failed at init */
+    FS_ECUDA = 3,       /* a CUDA call failed; see fs_last_error() */
+    FS_ENOCONV = 4,     /* a solve hit its iteration cap (result still written) */
+    FS_ENONFINITE = 5,  /* a non-finite value appeared in a solve */
+    FS_ESTATE = 6,      /* call out of order (e.g. no mask set yet) */
+    FS_ETIMEOUT = 7,    /* a bounded device-side wait ran out */
+    FS_EBREAKDOWN = 8   /* a solve lost positive definiteness (p.Ap <= 0) */
+};
+
+enum { FS_AIR = 0, FS_LIQUID = 1, FS_SOLID = 2 };
+
+enum {
+    FS_PRECOND_JACOBI = 0,  /* diagonal scaling */
+    FS_PRECOND_MIC0 = 1,    /* modified incomplete Cholesky, level 0 */
+    FS_PRECOND_LEARNED = 2  /* the convolutional network, in flexible CG */
+};
+
+enum {
+    FS_MASK_SURFACE = 0,   /* liquid cells with an air neighbour (the surface band) */
+    FS_MASK_OCCUPIED = 1   /* every liquid cell */
+};
+
+typedef struct fs_ctx fs_ctx;
+
+/* A MAC velocity field: three caller-owned DEVICE arrays in the library layout. */
+typedef struct {
+    float *u, *v, *w;
+} fs_mac;
+
+typedef struct {
+    double dx;         /* cell size, > 0 */
+    double dt;         /* time step, >= 0 */
+    double nu;         /* kinematic viscosity, >= 0 */
+    double rho;        /* density, > 0; only scales the reported pressure */
+    double g[3];       /* body acceleration per component */
+    int precond;       /* FS_PRECOND_* for the pressure solve */
+    int maxit_p;       /* pressure iteration cap, >= 1 */
+    int maxit_v;       /* viscosity iteration cap, >= 1 */
+    double tol_p;      /* pressure relative residual target |r|/|b|, > 0 */
+    double tol_v;      /* viscosity relative residual target, > 0 */
+    int check_every;   /* iterations between host convergence checks, >= 1 */
+    int spin_limit;    /* cap on every device-side spin-wait (iterations), >= 1 */
+    double mic_tau;    /* MIC(0) modification, in [0, 1] */
+    double mic_sigma;  /* MIC(0) safety threshold, in [0, 1) */
+} fs_params;
+
+typedef struct {
+    int status;            /* FS_OK, FS_ENOCONV, FS_ENONFINITE or FS_EBREAKDOWN */
+    int iters_p;           /* pressure iterations, summed over the call's solves */
+    int iters_v;           /* viscosity iterations, summed over the call's solves */
+    double relres_p;       /* last pressure solve: recursive |r|/|b| at exit */
+    double relres_v;       /* last viscosity solve: recursive |r|/|b| at exit */
+    double true_relres_p;  /* last pressure solve: |b - A q|/|b| recomputed at exit */
+} fs_stats;
+
+typedef struct {
+    int nx, ny, nz;        /* cells */
+    int pitch;             /* elements per row, >= nx + 1, multiple of 4 */
+    int rows;              /* ny + 1 */
+    int planes;            /* nz + 1 */
+    long long nelems;      /* pitch * rows * planes: the size of every array */
+} fs_layout_t;
+
+/* Default parameters: dx = 1/ny is left to the caller (set to 1), dt = 1/30,
+ * nu = 0.01, rho = 1000, g = 0, Jacobi, tolerances 1e-6, caps 20000/2000,
+ * check_every 8, spin_limit 1<<22, MIC(0) tau = 0.97, sigma = 0.25. */
+void fs_default_params(fs_params *p);
+
+/* Create a context for an nx * ny * nz grid (each >= 2) bound to `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream) on the current device.
+ * Allocates all scratch. Errors: FS_EINVAL for sizes or parameters,
+ * FS_ENOMEM, FS_ECUDA. *out is NULL on failure. */
+int fs_init_grid(fs_ctx **out, int nx, int ny, int nz, const fs_params *p, void *cuda_stream);
+
+/* Free the context and its scratch (waits for its stream). NULL is a no-op. */
+int fs_destroy(fs_ctx *c);
+
+/* The array layout shared by every field of this context. */
+int fs_layout(const fs_ctx *c, fs_layout_t *out);
+
+/* Rebind the context to another stream. */
+int fs_set_stream(fs_ctx *c, void *cuda_stream);
+
+/* Replace the step parameters (e.g. a new nu during a fit). Same checks as init. */
+int fs_set_params(fs_ctx *c, const fs_params *p);
+
+/* Set the grid-type mask (Sec. 3.4.2, "grid types of surface, occupation, or
+ * empty"; the liquid cells come from the particle-to-grid transfer of Sec. 3.4.1).
+ * cell_type_dense: DEVICE uint8 array of nx*ny*nz values FS_AIR/FS_LIQUID/FS_SOLID
+ * in dense C order (index (k*ny + j)*nx + i), read during the call.
+ * bc: nullable DEVICE field (library layout) holding the prescribed velocity of
+ * each fixed face (e.g. an inflow v_in on wall faces); NULL means all fixed faces
+ * are zero. It is copied. Derives face classes, the surface band and whether the
+ * pressure operator is singular (liquid touching no air cell: the mean of the
+ * right-hand side is then removed). Errors: FS_EINVAL for a type value > 2. */
+int fs_set_mask(fs_ctx *c, const uint8_t *cell_type_dense, const fs_mac *bc);
+
+/* One step of the grid velocity evolution (Eq. eq::v split as in Sec. 3.2.2, with
+ * back-traced convection of Sec. 3.4.1): u_out = Project(Visc(Advect(u_in) + dt g)).
+ * u_in, u_out: DEVICE fields, must not alias. u_visc: nullable DEVICE field that
+ * receives the field after viscosity (the input of the projection), which
+ * fs_adjoint_step can reuse instead of recomputing it. st: nullable host stats.
+ * Returns FS_ENOCONV/FS_ENONFINITE/FS_EBREAKDOWN from the solves. */
+int fs_step(fs_ctx *c, const fs_mac *u_in, fs_mac *u_out, fs_mac *u_visc, fs_stats *st);
+
+/* Pressure projection alone (Sec. 3.2.2, Poisson pressure equation), in place on u.
+ * q_out: nullable DEVICE cell array (library layout) receiving q, where the
+ * pressure is p = rho * q / dt (q is mean-free when the operator is singular). */
+int fs_project(fs_ctx *c, fs_mac *u, float *q_out, fs_stats *st);
+
+/* Reverse mode of fs_step (derived from the step; Sec. 3.4.2 optimises through
+ * it). Given the step input u_in and the cotangent g_out = dL/du_out, writes
+ * g_in = dL/du_in (overwritten, every face) and ADDS dL/dnu to *g_nu (host).
+ * The adjoint of the projection is the projection itself (an orthogonal
+ * projector on the fluid faces), the viscosity solve is self-adjoint, and the
+ * advection adjoint is the exact discrete adjoint of the trilinear back-trace
+ * (accumulated with atomics, so its summation order is not fixed).
+ * u_visc: nullable; the u_visc that fs_step wrote for this u_in (saves one
+ * advection and one viscosity solve). g_in must not alias u_in or g_out. */
+int fs_adjoint_step(fs_ctx *c, const fs_mac *u_in, const fs_mac *u_visc,
+                    const fs_mac *g_out, fs_mac *g_in, double *g_nu, fs_stats *st);
+
+/* The masked loss of Eq. eq::optLoss (Sec. 3.4.2) at one frame:
+ *   L = beta/(2|B|) sum_{f in B} (u_f - t_f)^2
+ *     + alpha/|Bc| sum_{c in Bc} (1 - cos(ubar_c, tbar_c)),
+ * Bc = band cells of `mask_kind` (FS_MASK_SURFACE or FS_MASK_OCCUPIED),
+ * B = fluid faces touching a band cell, ubar = cell-centred velocity (mean of the
+ * two faces per component), cos(a, b) = a.b / (sqrt(|a|^2+e^2) sqrt(|b|^2+e^2)),
+ * e = 1e-8. ADDS L to *loss (host) and, if g is non-NULL, dL/du to g (device). */
+int fs_loss_grad(fs_ctx *c, const fs_mac *u, const fs_mac *target, int mask_kind,
+                 double alpha, double beta, double *loss, fs_mac *g);
+
+/* The per-thread message of the last failing call ("" if none). */
+const char *fs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLUIDSTEP_H */

@@ -1,0 +1,362 @@
+// fs_api.cu -- the C ABI declared in include/fluidstep.h: argument checks,
+// context memory and the order of kernels for one step, its adjoint and the loss
+// (arXiv 2503.00868: Eq. eq::v split as in Sec. 3.2.2, back-traced convection of
+// Sec. 3.4.1, loss of Eq. eq::optLoss in Sec. 3.4.2).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "fs_internal.cuh"
+
+namespace fs {
+
+static thread_local char g_err[512] = "";
+
+int set_error(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int check_cuda(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return 0;
+    return set_error(FS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static int check_params(const fs_params *p)
+{
+    if (!p) return set_error(FS_EINVAL, "params is NULL");
+    if (!(p->dx > 0.0) || !std::isfinite(p->dx)) return set_error(FS_EINVAL, "dx must be > 0");
+    if (!(p->dt >= 0.0) || !std::isfinite(p->dt)) return set_error(FS_EINVAL, "dt must be >= 0");
+    if (!(p->nu >= 0.0) || !std::isfinite(p->nu)) return set_error(FS_EINVAL, "nu must be >= 0");
+    if (!(p->rho > 0.0) || !std::isfinite(p->rho)) return set_error(FS_EINVAL, "rho must be > 0");
+    for (int c = 0; c < 3; c++)
+        if (!std::isfinite(p->g[c])) return set_error(FS_EINVAL, "g must be finite");
+    if (p->precond < FS_PRECOND_JACOBI || p->precond > FS_PRECOND_LEARNED)
+        return set_error(FS_EINVAL, "unknown preconditioner %d", p->precond);
+    if (p->maxit_p < 1 || p->maxit_v < 1) return set_error(FS_EINVAL, "iteration caps must be >= 1");
+    if (!(p->tol_p > 0.0) || !(p->tol_v > 0.0)) return set_error(FS_EINVAL, "tolerances must be > 0");
+    if (p->check_every < 1 || p->check_every > 4096) return set_error(FS_EINVAL, "check_every must be in [1, 4096]");
+    if (p->spin_limit < 1) return set_error(FS_EINVAL, "spin_limit must be >= 1");
+    if (!(p->mic_tau >= 0.0 && p->mic_tau <= 1.0)) return set_error(FS_EINVAL, "mic_tau must be in [0, 1]");
+    if (!(p->mic_sigma >= 0.0 && p->mic_sigma < 1.0)) return set_error(FS_EINVAL, "mic_sigma must be in [0, 1)");
+    return FS_OK;
+}
+
+static int check_field(const fs_mac *m, const char *name, bool nullable)
+{
+    if (!m) return nullable ? FS_OK : set_error(FS_EINVAL, "%s is NULL", name);
+    const float *p[3] = {m->u, m->v, m->w};
+    for (int c = 0; c < 3; c++) {
+        if (!p[c]) return set_error(FS_EINVAL, "%s component %d is NULL", name, c);
+        if (reinterpret_cast<uintptr_t>(p[c]) % 16) return set_error(FS_EINVAL, "%s component %d is not 16-byte aligned", name, c);
+    }
+    return FS_OK;
+}
+
+static bool same_field(const fs_mac *a, const fs_mac *b)
+{
+    if (!a || !b) return false;
+    return a->u == b->u || a->v == b->v || a->w == b->w;
+}
+
+static CF3 cf3(const fs_mac *m) { return CF3{{m->u, m->v, m->w}}; }
+static F3 f3(fs_mac *m) { return F3{{m->u, m->v, m->w}}; }
+
+static int alloc_zero(void **p, size_t bytes)
+{
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return set_error(FS_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    return check_cuda(cudaMemset(*p, 0, bytes), "cudaMemset");
+}
+
+static void free_ctx(fs_ctx *c)
+{
+    if (!c) return;
+    void *ptrs[] = {c->cflag, c->fflag, c->bc, c->dsum, c->pb, c->pr, c->pp[0], c->pp[1], c->pq, c->px, c->pz,
+                    c->vx, c->vr, c->vp[0], c->vp[1], c->vq, c->fu[0], c->fu[1], c->fu[2], c->fg[0], c->fg[1],
+                    c->fg[2], c->gc[0], c->gc[1], c->gc[2], c->mic_prec, c->scal, c->partials, c->err_word};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c->scal_host) cudaFreeHost(c->scal_host);
+    delete c;
+}
+
+}  // namespace fs
+
+using namespace fs;
+
+extern "C" {
+
+void fs_default_params(fs_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->dx = 1.0;
+    p->dt = 1.0 / 30.0;
+    p->nu = 0.01;
+    p->rho = 1000.0;
+    p->precond = FS_PRECOND_JACOBI;
+    p->maxit_p = 20000;
+    p->maxit_v = 2000;
+    p->tol_p = 1e-6;
+    p->tol_v = 1e-6;
+    p->check_every = 8;
+    p->spin_limit = 1 << 22;
+    p->mic_tau = 0.97;
+    p->mic_sigma = 0.25;
+}
+
+const char *fs_last_error(void) { return g_err; }
+
+int fs_init_grid(fs_ctx **out, int nx, int ny, int nz, const fs_params *p, void *cuda_stream)
+{
+    g_err[0] = 0;
+    if (!out) return set_error(FS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nx < 2 || ny < 2 || nz < 2) return set_error(FS_EINVAL, "grid sizes must be >= 2 (got %d %d %d)", nx, ny, nz);
+    int rc = check_params(p);
+    if (rc) return rc;
+    Layout L;
+    L.nx = nx;
+    L.ny = ny;
+    L.nz = nz;
+    L.P = (nx + 1 + 3) / 4 * 4;
+    L.R = ny + 1;
+    L.Z = nz + 1;
+    const long long PL = (long long)L.P * L.R, S = PL * L.Z;
+    const long long nF = 3 * (S + PL) + PL;
+    if (nF + 8 >= (1LL << 31)) return set_error(FS_EINVAL, "grid too large for 32-bit indexing");
+    L.PL = (int)PL;
+    L.S = (int)S;
+    L.nC = (int)(S + 2 * PL);
+    L.nF = (int)nF;
+
+    fs_ctx *c = new (std::nothrow) fs_ctx();
+    if (!c) return set_error(FS_ENOMEM, "host allocation failed");
+    c->L = L;
+    c->prm = *p;
+    c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    if ((rc = check_cuda(cudaGetDevice(&c->device), "cudaGetDevice"))) { free_ctx(c); return rc; }
+    if ((rc = check_cuda(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device),
+                         "cudaDeviceGetAttribute"))) { free_ctx(c); return rc; }
+    c->max_blocks = c->num_sms * 8;
+    const size_t cb = (size_t)L.nC * sizeof(float), fb = (size_t)L.nF * sizeof(float), sb = (size_t)L.S * sizeof(float);
+#define ALLOC(ptr, bytes)                                                   \
+    do {                                                                    \
+        if ((rc = alloc_zero((void **)&(ptr), (bytes)))) { free_ctx(c); return rc; } \
+    } while (0)
+    ALLOC(c->cflag, (size_t)L.nC);
+    ALLOC(c->fflag, (size_t)L.nF);
+    ALLOC(c->bc, fb);
+    ALLOC(c->dsum, fb);
+    ALLOC(c->pb, cb);
+    ALLOC(c->pr, cb);
+    ALLOC(c->pp[0], cb);
+    ALLOC(c->pp[1], cb);
+    ALLOC(c->pq, cb);
+    ALLOC(c->px, cb);
+    ALLOC(c->pz, cb);
+    ALLOC(c->vx, fb);
+    ALLOC(c->vr, fb);
+    ALLOC(c->vp[0], fb);
+    ALLOC(c->vp[1], fb);
+    ALLOC(c->vq, fb);
+    for (int k = 0; k < 3; k++) {
+        ALLOC(c->fu[k], sb);
+        ALLOC(c->fg[k], sb);
+        ALLOC(c->gc[k], cb);
+    }
+    ALLOC(c->mic_prec, cb);
+    ALLOC(c->scal, 4 * sizeof(SolveScal));
+    ALLOC(c->partials, (size_t)c->max_blocks * 8 * sizeof(double));
+    ALLOC(c->err_word, 16);
+#undef ALLOC
+    if (cudaHostAlloc((void **)&c->scal_host, 4 * sizeof(SolveScal), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        c->scal_host = nullptr;
+        free_ctx(c);
+        return set_error(FS_ENOMEM, "pinned allocation failed");
+    }
+    *out = c;
+    return FS_OK;
+}
+
+int fs_destroy(fs_ctx *c)
+{
+    if (!c) return FS_OK;
+    cudaStreamSynchronize(c->stream);
+    free_ctx(c);
+    return FS_OK;
+}
+
+int fs_layout(const fs_ctx *c, fs_layout_t *out)
+{
+    if (!c || !out) return set_error(FS_EINVAL, "NULL argument");
+    out->nx = c->L.nx;
+    out->ny = c->L.ny;
+    out->nz = c->L.nz;
+    out->pitch = c->L.P;
+    out->rows = c->L.R;
+    out->planes = c->L.Z;
+    out->nelems = c->L.S;
+    return FS_OK;
+}
+
+int fs_set_stream(fs_ctx *c, void *cuda_stream)
+{
+    if (!c) return set_error(FS_EINVAL, "NULL context");
+    c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    return FS_OK;
+}
+
+int fs_set_params(fs_ctx *c, const fs_params *p)
+{
+    if (!c) return set_error(FS_EINVAL, "NULL context");
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (p->mic_tau != c->prm.mic_tau || p->mic_sigma != c->prm.mic_sigma) c->mic_ready = 0;
+    c->prm = *p;
+    return FS_OK;
+}
+
+int fs_set_mask(fs_ctx *c, const uint8_t *cell_type_dense, const fs_mac *bc)
+{
+    if (!c) return set_error(FS_EINVAL, "NULL context");
+    g_err[0] = 0;
+    if (!cell_type_dense) return set_error(FS_EINVAL, "cell_type_dense is NULL");
+    int rc = check_field(bc, "bc", true);
+    if (rc) return rc;
+    c->mask_set = 0;
+    return build_mask(c, cell_type_dense, bc);
+}
+
+static int need_mask(const fs_ctx *c)
+{
+    if (!c) return set_error(FS_EINVAL, "NULL context");
+    if (!c->mask_set) return set_error(FS_ESTATE, "fs_set_mask has not been called");
+    return FS_OK;
+}
+
+int fs_step(fs_ctx *c, const fs_mac *u_in, fs_mac *u_out, fs_mac *u_visc, fs_stats *st)
+{
+    int rc = need_mask(c);
+    if (rc) return rc;
+    g_err[0] = 0;
+    if ((rc = check_field(u_in, "u_in", false)) || (rc = check_field(u_out, "u_out", false)) ||
+        (rc = check_field(u_visc, "u_visc", true)))
+        return rc;
+    if (same_field(u_visc, u_out)) return set_error(FS_EINVAL, "u_visc must not alias u_out");
+    fs_stats local{};
+    fs_stats *s = st ? st : &local;
+    std::memset(s, 0, sizeof(*s));
+    // advection + body force -> face space; implicit viscosity in place
+    if ((rc = launch_advect(c, cf3(u_in)))) return rc;
+    int rv = solve_viscosity(c, true, s);
+    if (rv == FS_ECUDA) return rv;
+    // full field after viscosity, then the projection
+    fs_mac *uv = u_visc ? u_visc : u_out;
+    if ((rc = launch_compose(c, f3(uv)))) return rc;
+    if ((rc = launch_divergence(c, cf3(uv)))) return rc;
+    int rp = solve_pressure(c, s);
+    if (rp == FS_ECUDA || rp == FS_EINVAL) return rp;
+    if ((rc = launch_grad_subtract(c, cf3(uv), f3(u_out), nullptr))) return rc;
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    return s->status;
+}
+
+int fs_project(fs_ctx *c, fs_mac *u, float *q_out, fs_stats *st)
+{
+    int rc = need_mask(c);
+    if (rc) return rc;
+    g_err[0] = 0;
+    if ((rc = check_field(u, "u", false))) return rc;
+    fs_stats local{};
+    fs_stats *s = st ? st : &local;
+    std::memset(s, 0, sizeof(*s));
+    if ((rc = launch_divergence(c, cf3(u)))) return rc;
+    int rp = solve_pressure(c, s);
+    if (rp == FS_ECUDA || rp == FS_EINVAL) return rp;
+    if ((rc = launch_grad_subtract(c, cf3(u), f3(u), q_out))) return rc;
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    return s->status;
+}
+
+int fs_adjoint_step(fs_ctx *c, const fs_mac *u_in, const fs_mac *u_visc, const fs_mac *g_out, fs_mac *g_in,
+                    double *g_nu, fs_stats *st)
+{
+    int rc = need_mask(c);
+    if (rc) return rc;
+    g_err[0] = 0;
+    if ((rc = check_field(u_in, "u_in", false)) || (rc = check_field(u_visc, "u_visc", true)) ||
+        (rc = check_field(g_out, "g_out", false)) || (rc = check_field(g_in, "g_in", false)))
+        return rc;
+    if (same_field(g_in, u_in) || same_field(g_in, u_visc))
+        return set_error(FS_EINVAL, "g_in must not alias u_in or u_visc");
+    fs_stats local{};
+    fs_stats *s = st ? st : &local;
+    std::memset(s, 0, sizeof(*s));
+    // the field after viscosity: given, or recomputed from u_in
+    CF3 uv;
+    if (u_visc) {
+        uv = cf3(u_visc);
+    } else {
+        if ((rc = launch_advect(c, cf3(u_in)))) return rc;
+        int rv = solve_viscosity(c, true, s);
+        if (rv == FS_ECUDA) return rv;
+        F3 fu{{c->fu[0], c->fu[1], c->fu[2]}};
+        if ((rc = launch_compose(c, fu))) return rc;
+        uv = CF3{{c->fu[0], c->fu[1], c->fu[2]}};
+    }
+    // projection adjoint: the cotangent of fixed and air faces is dropped, then P
+    F3 fg{{c->fg[0], c->fg[1], c->fg[2]}};
+    CF3 fgc{{c->fg[0], c->fg[1], c->fg[2]}};
+    if ((rc = launch_mask_fluid(c, cf3(g_out), fg))) return rc;
+    if ((rc = launch_divergence(c, fgc))) return rc;
+    int rp = solve_pressure(c, s);
+    if (rp == FS_ECUDA || rp == FS_EINVAL) return rp;
+    if ((rc = launch_grad_subtract(c, fgc, fg, nullptr))) return rc;
+    // viscosity adjoint: one more solve with the same operator, no Dirichlet part
+    if ((rc = launch_to_face_space(c, fgc))) return rc;
+    int rv = solve_viscosity(c, false, s);
+    if (rv == FS_ECUDA) return rv;
+    if (g_nu) {
+        double dot = 0.0;
+        if ((rc = launch_nu_grad(c, uv, &dot))) return rc;
+        *g_nu += -c->prm.dt * dot;
+    }
+    // advection adjoint (the body force adds a constant)
+    if ((rc = launch_advect_adjoint(c, cf3(u_in), f3(g_in)))) return rc;
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    return s->status;
+}
+
+int fs_loss_grad(fs_ctx *c, const fs_mac *u, const fs_mac *target, int mask_kind, double alpha, double beta,
+                 double *loss, fs_mac *g)
+{
+    int rc = need_mask(c);
+    if (rc) return rc;
+    g_err[0] = 0;
+    if ((rc = check_field(u, "u", false)) || (rc = check_field(target, "target", false)) ||
+        (rc = check_field(g, "g", true)))
+        return rc;
+    if (!loss) return set_error(FS_EINVAL, "loss is NULL");
+    if (mask_kind != FS_MASK_SURFACE && mask_kind != FS_MASK_OCCUPIED)
+        return set_error(FS_EINVAL, "unknown mask kind %d", mask_kind);
+    if (!std::isfinite(alpha) || !std::isfinite(beta)) return set_error(FS_EINVAL, "alpha, beta must be finite");
+    F3 gg = g ? f3(g) : F3{{nullptr, nullptr, nullptr}};
+    return launch_loss(c, cf3(u), cf3(target), mask_kind, alpha, beta, gg, loss);
+}
+
+}  // extern "C"

@@ -1,0 +1,229 @@
+// fs_internal.cuh -- shared declarations of the CUDA implementation of the
+// differentiable MAC-grid fluid step (arXiv 2503.00868, Sec. 3.4.1-3.4.2).
+//
+// Internal vectors. Solver vectors live in flat, guarded buffers so that every
+// 7-point stencil reads its neighbours at fixed offsets (+-1, +-pitch, +-plane)
+// without bounds checks:
+//   cell space  [guard: plane][cells: S][guard: plane]
+//   face space  [guard][u: S][guard][v: S][guard][w: S][guard]
+// where S = pitch * rows * planes is the size of one array of the public layout
+// and plane = pitch * rows. Guards and padding hold zero and flag byte 0, so a
+// neighbour outside the grid contributes nothing.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fluidstep.h"
+
+namespace fs {
+
+// ---- flag bytes ------------------------------------------------------------
+// cell flags: bits 0-2 = number of non-solid neighbours (pressure diagonal)
+constexpr uint8_t CF_D = 0x07;
+constexpr uint8_t CF_LIQ = 0x08;
+constexpr uint8_t CF_AIR = 0x10;
+constexpr uint8_t CF_SOLID = 0x20;
+constexpr uint8_t CF_BAND = 0x40;  // liquid with an air neighbour
+// face flags: bits 0-2 = number of fluid or fixed neighbours (viscosity diagonal)
+constexpr uint8_t FF_N = 0x07;
+constexpr uint8_t FF_FLUID = 0x08;
+constexpr uint8_t FF_FIXED = 0x10;
+constexpr uint8_t FF_AIR = 0x20;
+
+// ---- solver scalars (device memory; mirrored to pinned host memory) --------
+struct SolveScal {
+    double rz;      // r.z of the current iterate
+    double pq;      // p.Ap
+    double rr;      // r.r
+    double bb;      // b.b (right-hand side)
+    double tol2;    // tol^2
+    double alpha;
+    double beta;
+    double aux[4];  // misc reductions (sums, counts, losses)
+    int iter;
+    int maxit;
+    int done;
+    int status;     // FS_OK / FS_ENOCONV / FS_ENONFINITE / FS_EBREAKDOWN
+    unsigned ticket;
+    int pad;
+};
+
+struct Layout {
+    int nx, ny, nz;
+    int P;      // pitch
+    int R;      // rows = ny + 1
+    int Z;      // planes = nz + 1
+    int PL;     // plane = P * R
+    int S;      // P * R * Z
+    int nC;     // cell space length  = S + 2 * PL
+    int nF;     // face space length  = 3 * (S + PL) + PL
+    __host__ __device__ int face_origin(int c) const { return PL + c * (S + PL); }
+};
+
+struct F3 {
+    float *c[3];
+};
+struct CF3 {
+    const float *c[3];
+};
+
+}  // namespace fs
+
+struct fs_ctx {
+    fs::Layout L;
+    fs_params prm;
+    cudaStream_t stream;
+    int device;
+    int num_sms;
+    int mask_set;
+    int singular;
+    int has_bc;
+    long long n_liquid, n_band_cells[2], n_band_faces[2];
+
+    uint8_t *cflag;       // cell space
+    uint8_t *fflag;       // face space
+    float *bc;            // face space: prescribed values on fixed faces
+    float *dsum;          // face space: sum of fixed neighbours' values (fluid faces)
+
+    // pressure solve (cell space)
+    float *pb, *pr, *pp[2], *pq, *px, *pz;
+    // viscosity solve (face space)
+    float *vx, *vr, *vp[2], *vq;
+    // full-layout scratch fields (3 * S each, public layout)
+    float *fu[3];         // u_visc when the caller does not keep it
+    float *fg[3];         // adjoint cotangent being projected
+    float *gc[3];         // cell space x3: per-cell cosine-loss gradient
+
+    // MIC(0)
+    float *mic_prec;      // cell space
+    int mic_ready;
+
+    // reductions
+    fs::SolveScal *scal;        // device [4]: 0 pressure, 1 viscosity, 2 misc, 3 misc
+    fs::SolveScal *scal_host;   // pinned mirror
+    double *partials;           // device [max_blocks * 8]
+    int max_blocks;
+    unsigned *err_word;         // device error word of bounded waits
+};
+
+namespace fs {
+
+int set_error(int code, const char *fmt, ...);
+int check_cuda(cudaError_t e, const char *what);
+#define FS_CUDA(call)                                              \
+    do {                                                           \
+        int _rc = ::fs::check_cuda((call), #call);                 \
+        if (_rc) return _rc;                                       \
+    } while (0)
+
+inline int grid_blocks(const fs_ctx *c, long long n, int threads, int per_thread = 1)
+{
+    long long need = (n + (long long)threads * per_thread - 1) / ((long long)threads * per_thread);
+    if (need < 1) need = 1;
+    return (int)(need < c->max_blocks ? need : c->max_blocks);
+}
+
+// ---- deterministic grid reduction ------------------------------------------
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Compensated FP32 accumulation (Kahan): keeps per-thread partial sums of FP32
+// products accurate to about one FP32 rounding before the FP64 tree.
+struct KSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        float y = x - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// Sums K doubles over the grid. Each block writes its partials; the last block
+// to arrive adds the partials in block order (so the result does not depend on
+// scheduling) and returns true in all its threads with the totals in `tot`
+// (valid in thread 0). Requires blockDim.x a multiple of 32, <= 1024.
+template <int K>
+__device__ __forceinline__ bool grid_reduce(double (&v)[K], double *partials, unsigned *ticket,
+                                            double (&tot)[K])
+{
+    __shared__ double sh[32][K];
+    __shared__ int last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = warp_sum(v[k]);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; k++) sh[wid][k] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            double t = lane < nw ? sh[lane][k] : 0.0;
+            t = warp_sum(t);
+            if (lane == 0) partials[(size_t)blockIdx.x * K + k] = t;
+        }
+        if (lane == 0) {
+            __threadfence();
+            unsigned t = atomicAdd(ticket, 1u);
+            last = (t == gridDim.x - 1);
+        }
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        double t = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+            t += __ldcg(&partials[(size_t)b * K + k]);
+        tot[k] = warp_sum(t);
+    }
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; k++) sh[wid][k] = tot[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            double t = 0.0;
+            for (int w = 0; w < nw; w++) t += sh[w][k];
+            tot[k] = t;
+        }
+        *ticket = 0u;
+    }
+    return true;
+}
+
+// ---- launchers implemented in the .cu files --------------------------------
+// fs_mask.cu
+int build_mask(fs_ctx *c, const uint8_t *types_dense, const fs_mac *bc);
+// fs_pcg.cu
+int solve_pressure(fs_ctx *c, fs_stats *st);             // pb -> px
+int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st);  // vx (guess, rhs) -> vx
+int launch_divergence(fs_ctx *c, CF3 u);                 // u -> pb, with bb/mean handling
+int launch_grad_subtract(fs_ctx *c, CF3 in, F3 out, float *q_out);
+int launch_compose(fs_ctx *c, F3 out);                   // vx + bc -> full field
+int launch_mask_fluid(fs_ctx *c, CF3 in, F3 out);        // zero off fluid faces
+int launch_to_face_space(fs_ctx *c, CF3 in);             // full field (fluid) -> vx
+int launch_nu_grad(fs_ctx *c, CF3 uv, double *dot);      // <vx, L~ uv>
+int launch_loss(fs_ctx *c, CF3 u, CF3 t, int kind, double alpha, double beta, F3 g,
+                double *loss);
+// fs_advect.cu
+int launch_advect(fs_ctx *c, CF3 u);                     // u -> vx (fluid faces)
+int launch_advect_adjoint(fs_ctx *c, CF3 u, F3 g);       // vx cotangent -> g (+=)
+// fs_mic0.cu
+int mic0_factor(fs_ctx *c);
+int mic0_apply(fs_ctx *c, const float *r, float *z);
+
+int read_scal(fs_ctx *c, int which, SolveScal *out);
+
+}  // namespace fs

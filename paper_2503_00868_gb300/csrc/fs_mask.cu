@@ -1,0 +1,191 @@
+// fs_mask.cu -- grid-type mask set-up: cell and face flag bytes, prescribed
+// face values, Dirichlet sums of the viscosity operator, band and singularity
+// counts. Runs once per mask (Sec. 3.4.2: "grid types of surface, occupation,
+// or empty").
+#include "fs_internal.cuh"
+
+namespace fs {
+namespace {
+
+// Decode a public-layout index into (i, j, k).
+__device__ __forceinline__ void decode(const Layout &L, int idx, int &i, int &j, int &k)
+{
+    i = idx % L.P;
+    int row = idx / L.P;
+    j = row % L.R;
+    k = row / L.R;
+}
+
+__global__ void k_cell_types(Layout L, const uint8_t *__restrict__ types, uint8_t *cflag,
+                             unsigned *err)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < L.nC; t += gridDim.x * blockDim.x) {
+        int idx = t - L.PL;
+        uint8_t f = 0;
+        if (idx >= 0 && idx < L.S) {
+            int i, j, k;
+            decode(L, idx, i, j, k);
+            if (i < L.nx && j < L.ny && k < L.nz) {
+                uint8_t ty = types[((size_t)k * L.ny + j) * L.nx + i];
+                if (ty == FS_LIQUID) f = CF_LIQ;
+                else if (ty == FS_AIR) f = CF_AIR;
+                else if (ty == FS_SOLID) f = CF_SOLID;
+                else { atomicOr(err, 1u); f = CF_SOLID; }
+            }
+        }
+        cflag[t] = f;
+    }
+}
+
+// Number of non-solid neighbours and the surface band bit. Out-of-grid
+// neighbours read flag 0 (guard or padding), i.e. solid.
+__global__ void k_cell_flags(Layout L, uint8_t *cflag)
+{
+    for (int t = L.PL + blockIdx.x * blockDim.x + threadIdx.x; t < L.PL + L.S;
+         t += gridDim.x * blockDim.x) {
+        uint8_t f = cflag[t];
+        if (!(f & (CF_LIQ | CF_AIR | CF_SOLID))) continue;
+        const int off[6] = {-1, 1, -L.P, L.P, -L.PL, L.PL};
+        int d = 0, air = 0;
+        for (int m = 0; m < 6; m++) {
+            uint8_t g = cflag[t + off[m]];
+            d += (g & (CF_LIQ | CF_AIR)) ? 1 : 0;
+            air |= (g & CF_AIR) ? 1 : 0;
+        }
+        uint8_t base = f & (CF_LIQ | CF_AIR | CF_SOLID);
+        uint8_t band = ((f & CF_LIQ) && air) ? CF_BAND : 0;
+        cflag[t] = base | (uint8_t)d | band;
+    }
+}
+
+__device__ __forceinline__ bool solid_like(uint8_t f) { return (f & CF_SOLID) || !(f & (CF_LIQ | CF_AIR)); }
+
+__global__ void k_face_class(Layout L, const uint8_t *__restrict__ cflag, uint8_t *fflag)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < L.nF; t += gridDim.x * blockDim.x) {
+        uint8_t out = 0;
+        int seg = t - L.PL;
+        int c = seg >= 0 ? seg / (L.S + L.PL) : -1;
+        int idx = seg - c * (L.S + L.PL);
+        if (c >= 0 && c < 3 && idx >= 0 && idx < L.S) {
+            int i, j, k;
+            decode(L, idx, i, j, k);
+            int dims[3] = {L.nx, L.ny, L.nz};
+            dims[c] += 1;
+            if (i < dims[0] && j < dims[1] && k < dims[2]) {
+                int off = c == 0 ? 1 : (c == 1 ? L.P : L.PL);
+                uint8_t fr = cflag[L.PL + idx], fl = cflag[L.PL + idx - off];
+                if (solid_like(fl) || solid_like(fr)) out = FF_FIXED;
+                else if ((fl & CF_LIQ) || (fr & CF_LIQ)) out = FF_FLUID;
+                else out = FF_AIR;
+            }
+        }
+        fflag[t] = out;
+    }
+}
+
+// Viscosity neighbour count of fluid faces and the Dirichlet sums; copies the
+// prescribed values of fixed faces into face space.
+__global__ void k_face_count(Layout L, uint8_t *fflag, CF3 bc_user, float *bc, float *dsum)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < L.nF; t += gridDim.x * blockDim.x) {
+        uint8_t f = fflag[t];
+        int seg = t - L.PL;
+        int c = seg >= 0 ? seg / (L.S + L.PL) : -1;
+        int idx = seg - c * (L.S + L.PL);
+        float bv = 0.f;
+        if ((f & FF_FIXED) && bc_user.c[0]) bv = bc_user.c[c][idx];
+        bc[t] = bv;
+        if (!(f & FF_FLUID)) continue;
+        const int off[6] = {-1, 1, -L.P, L.P, -L.PL, L.PL};
+        int n = 0;
+        float ds = 0.f;
+        for (int m = 0; m < 6; m++) {
+            uint8_t g = fflag[t + off[m]];
+            if (g & (FF_FLUID | FF_FIXED)) n++;
+            if ((g & FF_FIXED) && bc_user.c[0]) ds += bc_user.c[c][idx + off[m]];
+        }
+        fflag[t] = (uint8_t)(f | n);
+        if (dsum) dsum[t] = ds;
+    }
+}
+
+// counts: 0 liquid cells, 1 surface band cells, 2 surface band faces, 3 occupied band faces
+__global__ void k_counts(Layout L, const uint8_t *__restrict__ cflag, const uint8_t *__restrict__ fflag,
+                         unsigned long long *cnt)
+{
+    unsigned long long a = 0, b = 0, cs = 0, co = 0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < L.nF; t += gridDim.x * blockDim.x) {
+        if (t < L.nC) {
+            uint8_t f = cflag[t];
+            a += (f & CF_LIQ) ? 1 : 0;
+            b += (f & CF_BAND) ? 1 : 0;
+        }
+        uint8_t g = fflag[t];
+        if (g & FF_FLUID) {
+            int seg = t - L.PL;
+            int c = seg / (L.S + L.PL);
+            int idx = seg - c * (L.S + L.PL);
+            int off = c == 0 ? 1 : (c == 1 ? L.P : L.PL);
+            uint8_t fr = cflag[L.PL + idx], fl = cflag[L.PL + idx - off];
+            cs += ((fr | fl) & CF_BAND) ? 1 : 0;
+            co += ((fr | fl) & CF_LIQ) ? 1 : 0;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+        cs += __shfl_down_sync(0xffffffffu, cs, o);
+        co += __shfl_down_sync(0xffffffffu, co, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&cnt[0], a);
+        atomicAdd(&cnt[1], b);
+        atomicAdd(&cnt[2], cs);
+        atomicAdd(&cnt[3], co);
+    }
+}
+
+}  // namespace
+
+int build_mask(fs_ctx *c, const uint8_t *types_dense, const fs_mac *bc)
+{
+    const Layout &L = c->L;
+    const int th = 256;
+    CF3 bcu{{nullptr, nullptr, nullptr}};
+    if (bc) {
+        bcu.c[0] = bc->u;
+        bcu.c[1] = bc->v;
+        bcu.c[2] = bc->w;
+    }
+    c->has_bc = bc ? 1 : 0;
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(c->partials);
+    FS_CUDA(cudaMemsetAsync(c->err_word, 0, sizeof(unsigned), c->stream));
+    FS_CUDA(cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), c->stream));
+    k_cell_types<<<grid_blocks(c, L.nC, th), th, 0, c->stream>>>(L, types_dense, c->cflag, c->err_word);
+    k_cell_flags<<<grid_blocks(c, L.S, th), th, 0, c->stream>>>(L, c->cflag);
+    k_face_class<<<grid_blocks(c, L.nF, th), th, 0, c->stream>>>(L, c->cflag, c->fflag);
+    k_face_count<<<grid_blocks(c, L.nF, th), th, 0, c->stream>>>(L, c->fflag, bcu, c->bc,
+                                                                  bc ? c->dsum : nullptr);
+    k_counts<<<grid_blocks(c, L.nF, th), th, 0, c->stream>>>(L, c->cflag, c->fflag, cnt);
+    FS_CUDA(cudaGetLastError());
+    unsigned long long h[4];
+    unsigned herr = 0;
+    FS_CUDA(cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    FS_CUDA(cudaMemcpyAsync(&herr, c->err_word, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    if (herr) return set_error(FS_EINVAL, "fs_set_mask: a cell type is not 0 (air), 1 (liquid) or 2 (solid)");
+    c->n_liquid = (long long)h[0];
+    c->n_band_cells[FS_MASK_SURFACE] = (long long)h[1];
+    c->n_band_cells[FS_MASK_OCCUPIED] = (long long)h[0];
+    c->n_band_faces[FS_MASK_SURFACE] = (long long)h[2];
+    c->n_band_faces[FS_MASK_OCCUPIED] = (long long)h[3];
+    // The pressure operator has the constant on the liquid as null vector when no
+    // liquid cell touches air (a closed box full of liquid).
+    c->singular = (h[0] > 0 && h[1] == 0) ? 1 : 0;
+    c->mask_set = 1;
+    c->mic_ready = 0;
+    return FS_OK;
+}
+
+}  // namespace fs

@@ -1,0 +1,644 @@
+// fs_pcg.cu -- the two linear solves of the step and the field kernels around
+// them (arXiv 2503.00868, Eq. eq::v split as in Sec. 3.2.2):
+//   * pressure: L_p q = b on liquid cells (7-point, p = 0 in air), PCG;
+//   * viscosity: (I + nu dt L_f) u = rhs on fluid faces, Jacobi-PCG;
+//   * divergence, pressure-gradient subtraction, the nu-gradient of the
+//     viscosity solve and the loss of Eq. eq::optLoss (Sec. 3.4.2).
+//
+// The CG scalars (alpha, beta, r.z, r.r) stay on the device: the last block of
+// each reducing kernel updates them, so a batch of iterations runs without a
+// host round trip; the host reads the convergence flag every `check_every`
+// iterations. Once `done` is set every later kernel of the batch returns at once.
+#include <cmath>
+
+#include "fs_internal.cuh"
+
+namespace fs {
+namespace {
+
+constexpr int TH = 256;
+
+struct PoisOp {
+    static constexpr uint8_t ACTIVE = CF_LIQ;
+    __device__ static __forceinline__ float diag(uint8_t f, float) { return (float)(f & CF_D); }
+    __device__ static __forceinline__ float offc(float) { return 1.f; }
+};
+
+struct HelmOp {
+    static constexpr uint8_t ACTIVE = FF_FLUID;
+    __device__ static __forceinline__ float diag(uint8_t f, float cc) { return 1.f + cc * (float)(f & FF_N); }
+    __device__ static __forceinline__ float offc(float cc) { return cc; }
+};
+
+template <class Op>
+__device__ __forceinline__ float inv_diag(uint8_t f, float cc)
+{
+    if (!(f & Op::ACTIVE)) return 0.f;
+    float d = Op::diag(f, cc);
+    return d > 0.f ? __frcp_rn(d) : 0.f;
+}
+
+// p_new = z + beta p_old (z = r / diag for Jacobi, else the stored z), then
+// q = A p_new and the partial sums of p_new . q. alpha = r.z / p.q at the end.
+template <class Op, bool JAC>
+__global__ void __launch_bounds__(TH) k_spmv(const float *__restrict__ src, const float *__restrict__ pold,
+                                             float *__restrict__ pnew, float *__restrict__ q,
+                                             const uint8_t *__restrict__ fl, int n, int P, int PL, float cc,
+                                             SolveScal *s, double *partials)
+{
+    if (s->done) return;
+    const float beta = (float)s->beta;
+    KSum acc;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const uint8_t f = fl[t];
+        float pc = 0.f, qv = 0.f;
+        if (f & Op::ACTIVE) {
+            auto pn = [&](int u) -> float {
+                float z = JAC ? __ldg(src + u) * inv_diag<Op>(__ldg(fl + u), cc) : __ldg(src + u);
+                return z + beta * __ldg(pold + u);
+            };
+            pc = pn(t);
+            float nb = (pn(t - 1) + pn(t + 1)) + (pn(t - P) + pn(t + P)) + (pn(t - PL) + pn(t + PL));
+            qv = Op::diag(f, cc) * pc - Op::offc(cc) * nb;
+            acc.add(pc * qv);
+        }
+        pnew[t] = pc;
+        q[t] = qv;
+    }
+    double v[1] = {acc.value()}, tot[1];
+    if (grid_reduce<1>(v, partials, &s->ticket, tot) && threadIdx.x == 0) {
+        double pq = tot[0];
+        s->pq = pq;
+        if (!isfinite(pq)) { s->done = 1; s->status = FS_ENONFINITE; }
+        else if (!(pq > 0.0)) { s->done = 1; s->status = FS_EBREAKDOWN; }
+        else s->alpha = s->rz / pq;
+    }
+}
+
+// x += alpha p, r -= alpha q; partial sums of r.r (and r.z for Jacobi); the
+// last block counts the iteration and decides convergence.
+template <class Op, bool JAC>
+__global__ void __launch_bounds__(TH) k_update(float *__restrict__ x, float *__restrict__ r,
+                                               const float *__restrict__ p, const float *__restrict__ q,
+                                               const uint8_t *__restrict__ fl, int n4, float cc,
+                                               SolveScal *s, double *partials)
+{
+    if (s->done) return;
+    const float alpha = (float)s->alpha;
+    KSum rz, rr;
+    float4 *x4 = reinterpret_cast<float4 *>(x);
+    float4 *r4 = reinterpret_cast<float4 *>(r);
+    const float4 *p4 = reinterpret_cast<const float4 *>(p);
+    const float4 *q4 = reinterpret_cast<const float4 *>(q);
+    const uchar4 *f4 = reinterpret_cast<const uchar4 *>(fl);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += gridDim.x * blockDim.x) {
+        float4 xv = x4[t], rv = r4[t];
+        const float4 pv = __ldg(p4 + t), qv = __ldg(q4 + t);
+        xv.x += alpha * pv.x; xv.y += alpha * pv.y; xv.z += alpha * pv.z; xv.w += alpha * pv.w;
+        rv.x -= alpha * qv.x; rv.y -= alpha * qv.y; rv.z -= alpha * qv.z; rv.w -= alpha * qv.w;
+        x4[t] = xv;
+        r4[t] = rv;
+        rr.add(rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w);
+        if (JAC) {
+            const uchar4 fv = f4[t];
+            rz.add(rv.x * rv.x * inv_diag<Op>(fv.x, cc) + rv.y * rv.y * inv_diag<Op>(fv.y, cc) +
+                   rv.z * rv.z * inv_diag<Op>(fv.z, cc) + rv.w * rv.w * inv_diag<Op>(fv.w, cc));
+        }
+    }
+    double v[2] = {rr.value(), rz.value()}, tot[2];
+    if (grid_reduce<2>(v, partials, &s->ticket, tot) && threadIdx.x == 0) {
+        s->iter += 1;
+        s->rr = tot[0];
+        if (!isfinite(tot[0]) || !isfinite(tot[1])) { s->done = 1; s->status = FS_ENONFINITE; }
+        else if (tot[0] <= s->tol2 * s->bb) { s->done = 1; s->status = FS_OK; }
+        else if (s->iter >= s->maxit) { s->done = 1; s->status = FS_ENOCONV; }
+        else if (JAC) {
+            s->beta = tot[1] / s->rz;
+            s->rz = tot[1];
+        }
+    }
+}
+
+// r.z for a stored z (MIC(0) / learned): beta = rz_new / rz (first: beta = 0).
+__global__ void __launch_bounds__(TH) k_rz(const float *__restrict__ r, const float *__restrict__ z, int n4,
+                                           int first, SolveScal *s, double *partials)
+{
+    if (s->done) return;
+    KSum acc;
+    const float4 *r4 = reinterpret_cast<const float4 *>(r);
+    const float4 *z4 = reinterpret_cast<const float4 *>(z);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += gridDim.x * blockDim.x) {
+        const float4 a = __ldg(r4 + t), b = __ldg(z4 + t);
+        acc.add(a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w);
+    }
+    double v[1] = {acc.value()}, tot[1];
+    if (grid_reduce<1>(v, partials, &s->ticket, tot) && threadIdx.x == 0) {
+        if (!isfinite(tot[0])) { s->done = 1; s->status = FS_ENONFINITE; return; }
+        s->beta = first ? 0.0 : tot[0] / s->rz;
+        s->rz = tot[0];
+    }
+}
+
+__device__ __forceinline__ void init_scalars(SolveScal *s, double bb, double rr, double rz, double tol2,
+                                             int maxit)
+{
+    s->bb = bb;
+    s->rr = rr;
+    s->rz = rz;
+    s->tol2 = tol2;
+    s->alpha = 0.0;
+    s->beta = 0.0;
+    s->pq = 0.0;
+    s->iter = 0;
+    s->maxit = maxit;
+    s->status = FS_OK;
+    s->done = 0;
+    if (!isfinite(bb) || !isfinite(rr)) { s->done = 1; s->status = FS_ENONFINITE; }
+    else if (bb == 0.0 || rr <= tol2 * bb) s->done = 1;
+}
+
+// Pressure start: x = 0, r = b, both p buffers 0.
+template <bool JAC>
+__global__ void __launch_bounds__(TH) k_pois_init(const float *__restrict__ b, float *__restrict__ x,
+                                                  float *__restrict__ r, float *__restrict__ p0,
+                                                  float *__restrict__ p1, const uint8_t *__restrict__ fl,
+                                                  int n4, double tol2, int maxit, SolveScal *s,
+                                                  double *partials)
+{
+    KSum bb, rz;
+    const float4 *b4 = reinterpret_cast<const float4 *>(b);
+    const uchar4 *f4 = reinterpret_cast<const uchar4 *>(fl);
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += gridDim.x * blockDim.x) {
+        const float4 v = __ldg(b4 + t);
+        reinterpret_cast<float4 *>(r)[t] = v;
+        reinterpret_cast<float4 *>(x)[t] = zero;
+        reinterpret_cast<float4 *>(p0)[t] = zero;
+        reinterpret_cast<float4 *>(p1)[t] = zero;
+        bb.add(v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w);
+        if (JAC) {
+            const uchar4 fv = f4[t];
+            rz.add(v.x * v.x * inv_diag<PoisOp>(fv.x, 0.f) + v.y * v.y * inv_diag<PoisOp>(fv.y, 0.f) +
+                   v.z * v.z * inv_diag<PoisOp>(fv.z, 0.f) + v.w * v.w * inv_diag<PoisOp>(fv.w, 0.f));
+        }
+    }
+    double v[2] = {bb.value(), rz.value()}, tot[2];
+    if (grid_reduce<2>(v, partials, &s->ticket, tot) && threadIdx.x == 0)
+        init_scalars(s, tot[0], tot[0], tot[1], tol2, maxit);
+}
+
+// Viscosity start from the guess x (fluid faces): rhs = x + cc * dsum (forward,
+// Dirichlet values) or rhs = x (adjoint); r = rhs - A x.
+__global__ void __launch_bounds__(TH) k_helm_init(const float *__restrict__ x, const float *__restrict__ dsum,
+                                                  float *__restrict__ r, float *__restrict__ p0,
+                                                  float *__restrict__ p1, const uint8_t *__restrict__ fl,
+                                                  int n, int P, int PL, float cc, double tol2, int maxit,
+                                                  SolveScal *s, double *partials)
+{
+    KSum bb, rr, rz;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const uint8_t f = fl[t];
+        float rv = 0.f;
+        if (f & FF_FLUID) {
+            const float xc = x[t];
+            const float rhs = dsum ? xc + cc * dsum[t] : xc;
+            const float nb = (x[t - 1] + x[t + 1]) + (x[t - P] + x[t + P]) + (x[t - PL] + x[t + PL]);
+            const float ax = HelmOp::diag(f, cc) * xc - cc * nb;
+            rv = rhs - ax;
+            bb.add(rhs * rhs);
+            rr.add(rv * rv);
+            rz.add(rv * rv * inv_diag<HelmOp>(f, cc));
+        }
+        r[t] = rv;
+        p0[t] = 0.f;
+        p1[t] = 0.f;
+    }
+    double v[3] = {bb.value(), rr.value(), rz.value()}, tot[3];
+    if (grid_reduce<3>(v, partials, &s->ticket, tot) && threadIdx.x == 0)
+        init_scalars(s, tot[0], tot[1], tot[2], tol2, maxit);
+}
+
+// |b - A x|^2 of the pressure system -> s->aux[0].
+__global__ void __launch_bounds__(TH) k_pois_true_res(const float *__restrict__ b, const float *__restrict__ x,
+                                                      const uint8_t *__restrict__ fl, int n, int P, int PL,
+                                                      SolveScal *s, double *partials)
+{
+    double acc = 0.0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const uint8_t f = fl[t];
+        if (!(f & CF_LIQ)) continue;
+        const float nb = (x[t - 1] + x[t + 1]) + (x[t - P] + x[t + P]) + (x[t - PL] + x[t + PL]);
+        const float ax = PoisOp::diag(f, 0.f) * x[t] - nb;
+        const double e = (double)b[t] - (double)ax;
+        acc += e * e;
+    }
+    double v[1] = {acc}, tot[1];
+    if (grid_reduce<1>(v, partials, &s->ticket, tot) && threadIdx.x == 0) s->aux[0] = tot[0];
+}
+
+// Sum and count of a cell vector over the liquid -> s->aux[0], s->aux[1].
+__global__ void __launch_bounds__(TH) k_liquid_sum(const float *__restrict__ x, const uint8_t *__restrict__ fl,
+                                                   int n, SolveScal *s, double *partials)
+{
+    double a = 0.0, c = 0.0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+        if (fl[t] & CF_LIQ) { a += x[t]; c += 1.0; }
+    double v[2] = {a, c}, tot[2];
+    if (grid_reduce<2>(v, partials, &s->ticket, tot) && threadIdx.x == 0) {
+        s->aux[0] = tot[0];
+        s->aux[1] = tot[1];
+    }
+}
+
+__global__ void k_sub_liquid_mean(float *x, const uint8_t *__restrict__ fl, int n, const SolveScal *s)
+{
+    const float mean = s->aux[1] > 0.0 ? (float)(s->aux[0] / s->aux[1]) : 0.f;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+        if (fl[t] & CF_LIQ) x[t] -= mean;
+}
+
+// b = -dx * div(u) on liquid cells (cell space), u a public-layout field.
+__global__ void __launch_bounds__(TH) k_divergence(CF3 u, float *__restrict__ b, const uint8_t *__restrict__ cf,
+                                                   Layout L, float dx)
+{
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < L.S; idx += gridDim.x * blockDim.x) {
+        const int t = L.PL + idx;
+        float v = 0.f;
+        if (cf[t] & CF_LIQ) {
+            const float div = (__ldg(u.c[0] + idx + 1) - __ldg(u.c[0] + idx)) +
+                              (__ldg(u.c[1] + idx + L.P) - __ldg(u.c[1] + idx)) +
+                              (__ldg(u.c[2] + idx + L.PL) - __ldg(u.c[2] + idx));
+            v = -dx * div;
+        }
+        b[t] = v;
+    }
+}
+
+// out = in - grad q / dx on fluid faces, in elsewhere, 0 in padding; the
+// y = 3 slice copies q to q_out (public layout).
+__global__ void __launch_bounds__(TH) k_grad_subtract(CF3 in, F3 out, const float *__restrict__ q,
+                                                      float *q_out, const uint8_t *__restrict__ ff, Layout L,
+                                                      float inv_dx)
+{
+    const int c = blockIdx.y;
+    if (c == 3) {
+        if (!q_out) return;
+        for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < L.S; idx += gridDim.x * blockDim.x)
+            q_out[idx] = q[L.PL + idx];
+        return;
+    }
+    const int off = c == 0 ? 1 : (c == 1 ? L.P : L.PL);
+    const uint8_t *fc = ff + L.face_origin(c);
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < L.S; idx += gridDim.x * blockDim.x) {
+        const uint8_t f = fc[idx];
+        float v = 0.f;
+        if (f) {
+            v = in.c[c][idx];
+            if (f & FF_FLUID) v -= (q[L.PL + idx] - q[L.PL + idx - off]) * inv_dx;
+        }
+        out.c[c][idx] = v;
+    }
+}
+
+// Full field from the viscosity solution: fluid faces from face space, fixed
+// faces their prescribed values, zero elsewhere.
+__global__ void __launch_bounds__(TH) k_compose(const float *__restrict__ vx, const float *__restrict__ bc,
+                                                const uint8_t *__restrict__ ff, F3 out, Layout L)
+{
+    const int c = blockIdx.y;
+    const int o = L.face_origin(c);
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < L.S; idx += gridDim.x * blockDim.x) {
+        const uint8_t f = ff[o + idx];
+        out.c[c][idx] = (f & FF_FLUID) ? vx[o + idx] : ((f & FF_FIXED) ? bc[o + idx] : 0.f);
+    }
+}
+
+__global__ void __launch_bounds__(TH) k_mask_fluid(CF3 in, F3 out, const uint8_t *__restrict__ ff, Layout L)
+{
+    const int c = blockIdx.y;
+    const int o = L.face_origin(c);
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < L.S; idx += gridDim.x * blockDim.x)
+        out.c[c][idx] = (ff[o + idx] & FF_FLUID) ? in.c[c][idx] : 0.f;
+}
+
+__global__ void __launch_bounds__(TH) k_to_face_space(CF3 in, float *__restrict__ vx,
+                                                      const uint8_t *__restrict__ ff, Layout L)
+{
+    const int c = blockIdx.y;
+    const int o = L.face_origin(c);
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < L.S; idx += gridDim.x * blockDim.x)
+        vx[o + idx] = (ff[o + idx] & FF_FLUID) ? in.c[c][idx] : 0.f;
+}
+
+// <x, L~ uv> over fluid faces, L~ u = n_f u_f - sum of fluid/fixed neighbours
+// (the 1/dx^2 is applied by the host) -> s->aux[0].
+__global__ void __launch_bounds__(TH) k_nu_grad(const float *__restrict__ vx, CF3 uv,
+                                                const uint8_t *__restrict__ ff, Layout L, SolveScal *s,
+                                                double *partials)
+{
+    KSum acc;
+    const int off[6] = {-1, 1, -L.P, L.P, -L.PL, L.PL};
+    for (int c = 0; c < 3; c++) {
+        const int o = L.face_origin(c);
+        const float *u = uv.c[c];
+        for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < L.S; idx += gridDim.x * blockDim.x) {
+            const uint8_t f = ff[o + idx];
+            if (!(f & FF_FLUID)) continue;
+            float nb = 0.f;
+#pragma unroll
+            for (int m = 0; m < 6; m++)
+                if (ff[o + idx + off[m]] & (FF_FLUID | FF_FIXED)) nb += u[idx + off[m]];
+            const float lu = (float)(f & FF_N) * u[idx] - nb;
+            acc.add(vx[o + idx] * lu);
+        }
+    }
+    double v[1] = {acc.value()}, tot[1];
+    if (grid_reduce<1>(v, partials, &s->ticket, tot) && threadIdx.x == 0) s->aux[0] = tot[0];
+}
+
+// Cosine term of the loss on band cells: writes the per-cell gradient w.r.t.
+// the cell-centred velocity (scaled by -alpha/|Bc|) and sums 1 - cos.
+__global__ void __launch_bounds__(TH) k_loss_cell(CF3 u, CF3 tg, const uint8_t *__restrict__ cf, uint8_t bandbit,
+                                                  F3 gc, Layout L, float scale, SolveScal *s,
+                                                  double *partials)
+{
+    double acc = 0.0;
+    const float eps2 = 1e-16f;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < L.S; idx += gridDim.x * blockDim.x) {
+        const int t = L.PL + idx;
+        float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+        if (cf[t] & bandbit) {
+            const float a0 = 0.5f * (u.c[0][idx] + u.c[0][idx + 1]);
+            const float a1 = 0.5f * (u.c[1][idx] + u.c[1][idx + L.P]);
+            const float a2 = 0.5f * (u.c[2][idx] + u.c[2][idx + L.PL]);
+            const float b0 = 0.5f * (tg.c[0][idx] + tg.c[0][idx + 1]);
+            const float b1 = 0.5f * (tg.c[1][idx] + tg.c[1][idx + L.P]);
+            const float b2 = 0.5f * (tg.c[2][idx] + tg.c[2][idx + L.PL]);
+            const float ab = a0 * b0 + a1 * b1 + a2 * b2;
+            const float na = sqrtf(a0 * a0 + a1 * a1 + a2 * a2 + eps2);
+            const float nbv = sqrtf(b0 * b0 + b1 * b1 + b2 * b2 + eps2);
+            const float inv = 1.f / (na * nbv);
+            const float cs = ab * inv;
+            acc += 1.0 - (double)cs;
+            const float k2 = cs / (na * na);
+            g0 = -scale * (b0 * inv - k2 * a0);
+            g1 = -scale * (b1 * inv - k2 * a1);
+            g2 = -scale * (b2 * inv - k2 * a2);
+        }
+        gc.c[0][t] = g0;
+        gc.c[1][t] = g1;
+        gc.c[2][t] = g2;
+    }
+    double v[1] = {acc}, tot[1];
+    if (grid_reduce<1>(v, partials, &s->ticket, tot) && threadIdx.x == 0) s->aux[1] = tot[0];
+}
+
+// L2 term on band faces plus the gather of the cosine gradient onto faces:
+// g += beta (u - t)/|B| on band faces + (gc(L) + gc(R))/2 on every face.
+__global__ void __launch_bounds__(TH) k_loss_face(CF3 u, CF3 tg, const uint8_t *__restrict__ cf,
+                                                  const uint8_t *__restrict__ ff, uint8_t bandbit, CF3 gc,
+                                                  int use_gc, F3 g, Layout L, float beta_over_B,
+                                                  SolveScal *s, double *partials)
+{
+    double acc = 0.0;
+    for (int c = 0; c < 3; c++) {
+        const int o = L.face_origin(c);
+        const int off = c == 0 ? 1 : (c == 1 ? L.P : L.PL);
+        for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < L.S; idx += gridDim.x * blockDim.x) {
+            const uint8_t f = ff[o + idx];
+            if (!f) continue;
+            float gv = 0.f;
+            const uint8_t fr = cf[L.PL + idx], fl = cf[L.PL + idx - off];
+            if ((f & FF_FLUID) && ((fr | fl) & bandbit)) {
+                const float e = u.c[c][idx] - tg.c[c][idx];
+                acc += 0.5 * (double)e * (double)e;
+                gv += beta_over_B * e;
+            }
+            if (use_gc) gv += 0.5f * (gc.c[c][L.PL + idx] + gc.c[c][L.PL + idx - off]);
+            if (g.c[0] && gv != 0.f) g.c[c][idx] += gv;
+        }
+    }
+    double v[1] = {acc}, tot[1];
+    if (grid_reduce<1>(v, partials, &s->ticket, tot) && threadIdx.x == 0) s->aux[0] = tot[0];
+}
+
+}  // namespace
+
+int read_scal(fs_ctx *c, int which, SolveScal *out)
+{
+    FS_CUDA(cudaMemcpyAsync(c->scal_host + which, c->scal + which, sizeof(SolveScal), cudaMemcpyDeviceToHost,
+                            c->stream));
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    *out = c->scal_host[which];
+    return FS_OK;
+}
+
+static int finish_status(int st)
+{
+    return st == FS_OK ? FS_OK : st;
+}
+
+int launch_divergence(fs_ctx *c, CF3 u)
+{
+    const Layout &L = c->L;
+    k_divergence<<<grid_blocks(c, L.S, TH), TH, 0, c->stream>>>(u, c->pb, c->cflag, L, (float)c->prm.dx);
+    if (c->singular) {
+        // the right-hand side must lie in the range of the singular operator
+        k_liquid_sum<<<grid_blocks(c, L.nC, TH), TH, 0, c->stream>>>(c->pb, c->cflag, L.nC, c->scal + 2,
+                                                                     c->partials);
+        k_sub_liquid_mean<<<grid_blocks(c, L.nC, TH), TH, 0, c->stream>>>(c->pb, c->cflag, L.nC, c->scal + 2);
+    }
+    FS_CUDA(cudaGetLastError());
+    return FS_OK;
+}
+
+int solve_pressure(fs_ctx *c, fs_stats *st)
+{
+    const Layout &L = c->L;
+    SolveScal *s = c->scal + 0;
+    const bool jac = c->prm.precond == FS_PRECOND_JACOBI;
+    const int n4 = L.nC / 4;
+    const double tol2 = c->prm.tol_p * c->prm.tol_p;
+    if (!jac && c->prm.precond == FS_PRECOND_MIC0 && !c->mic_ready) {
+        int rc = mic0_factor(c);
+        if (rc) return rc;
+    }
+    if (jac)
+        k_pois_init<true><<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(
+            c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, n4, tol2, c->prm.maxit_p, s, c->partials);
+    else {
+        k_pois_init<false><<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(
+            c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, n4, tol2, c->prm.maxit_p, s, c->partials);
+        int rc = mic0_apply(c, c->pr, c->pz);
+        if (rc) return rc;
+        k_rz<<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(c->pr, c->pz, n4, 1, s, c->partials);
+    }
+    FS_CUDA(cudaGetLastError());
+    const int bs = grid_blocks(c, L.nC, TH);
+    const int b4 = grid_blocks(c, n4, TH);
+    int cur = 0;
+    long long launched = 0;
+    SolveScal h;
+    for (;;) {
+        for (int b = 0; b < c->prm.check_every; b++) {
+            if (jac) {
+                k_spmv<PoisOp, true><<<bs, TH, 0, c->stream>>>(c->pr, c->pp[cur], c->pp[cur ^ 1], c->pq, c->cflag,
+                                                               L.nC, L.P, L.PL, 0.f, s, c->partials);
+                k_update<PoisOp, true><<<b4, TH, 0, c->stream>>>(c->px, c->pr, c->pp[cur ^ 1], c->pq, c->cflag,
+                                                                 n4, 0.f, s, c->partials);
+            } else {
+                k_spmv<PoisOp, false><<<bs, TH, 0, c->stream>>>(c->pz, c->pp[cur], c->pp[cur ^ 1], c->pq,
+                                                                c->cflag, L.nC, L.P, L.PL, 0.f, s, c->partials);
+                k_update<PoisOp, false><<<b4, TH, 0, c->stream>>>(c->px, c->pr, c->pp[cur ^ 1], c->pq, c->cflag,
+                                                                  n4, 0.f, s, c->partials);
+                int rc = mic0_apply(c, c->pr, c->pz);
+                if (rc) return rc;
+                k_rz<<<b4, TH, 0, c->stream>>>(c->pr, c->pz, n4, 0, s, c->partials);
+            }
+            cur ^= 1;
+        }
+        launched += c->prm.check_every;
+        FS_CUDA(cudaGetLastError());
+        int rc = read_scal(c, 0, &h);
+        if (rc) return rc;
+        if (h.done) break;
+        if (launched > (long long)c->prm.maxit_p + c->prm.check_every)
+            return set_error(FS_ECUDA, "pressure solve: iteration flag never set");
+    }
+    // true residual, then the mean-free representative of a singular solve
+    k_pois_true_res<<<bs, TH, 0, c->stream>>>(c->pb, c->px, c->cflag, L.nC, L.P, L.PL, c->scal + 2, c->partials);
+    if (c->singular) {
+        k_liquid_sum<<<bs, TH, 0, c->stream>>>(c->px, c->cflag, L.nC, c->scal + 3, c->partials);
+        k_sub_liquid_mean<<<bs, TH, 0, c->stream>>>(c->px, c->cflag, L.nC, c->scal + 3);
+    }
+    FS_CUDA(cudaGetLastError());
+    SolveScal m;
+    int rc = read_scal(c, 2, &m);
+    if (rc) return rc;
+    if (st) {
+        st->iters_p += h.iter;
+        st->relres_p = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
+        st->true_relres_p = h.bb > 0 ? std::sqrt(m.aux[0] / h.bb) : 0.0;
+        if (h.status != FS_OK && st->status == FS_OK) st->status = h.status;
+    }
+    return finish_status(h.status);
+}
+
+int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st)
+{
+    const Layout &L = c->L;
+    SolveScal *s = c->scal + 1;
+    const float cc = (float)(c->prm.nu * c->prm.dt / (c->prm.dx * c->prm.dx));
+    const int n4 = L.nF / 4;
+    const double tol2 = c->prm.tol_v * c->prm.tol_v;
+    const int bs = grid_blocks(c, L.nF, TH);
+    const int b4 = grid_blocks(c, n4, TH);
+    k_helm_init<<<bs, TH, 0, c->stream>>>(c->vx, (dirichlet && c->has_bc) ? c->dsum : nullptr, c->vr, c->vp[0],
+                                         c->vp[1], c->fflag, L.nF, L.P, L.PL, cc, tol2, c->prm.maxit_v, s,
+                                         c->partials);
+    FS_CUDA(cudaGetLastError());
+    int cur = 0;
+    long long launched = 0;
+    SolveScal h;
+    for (;;) {
+        for (int b = 0; b < c->prm.check_every; b++) {
+            k_spmv<HelmOp, true><<<bs, TH, 0, c->stream>>>(c->vr, c->vp[cur], c->vp[cur ^ 1], c->vq, c->fflag,
+                                                           L.nF, L.P, L.PL, cc, s, c->partials);
+            k_update<HelmOp, true><<<b4, TH, 0, c->stream>>>(c->vx, c->vr, c->vp[cur ^ 1], c->vq, c->fflag, n4,
+                                                             cc, s, c->partials);
+            cur ^= 1;
+        }
+        launched += c->prm.check_every;
+        FS_CUDA(cudaGetLastError());
+        int rc = read_scal(c, 1, &h);
+        if (rc) return rc;
+        if (h.done) break;
+        if (launched > (long long)c->prm.maxit_v + c->prm.check_every)
+            return set_error(FS_ECUDA, "viscosity solve: iteration flag never set");
+    }
+    if (st) {
+        st->iters_v += h.iter;
+        st->relres_v = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
+        if (h.status != FS_OK && st->status == FS_OK) st->status = h.status;
+    }
+    return finish_status(h.status);
+}
+
+int launch_grad_subtract(fs_ctx *c, CF3 in, F3 out, float *q_out)
+{
+    const Layout &L = c->L;
+    dim3 grid(grid_blocks(c, L.S, TH), 4);
+    k_grad_subtract<<<grid, TH, 0, c->stream>>>(in, out, c->px, q_out, c->fflag, L, (float)(1.0 / c->prm.dx));
+    FS_CUDA(cudaGetLastError());
+    return FS_OK;
+}
+
+int launch_compose(fs_ctx *c, F3 out)
+{
+    const Layout &L = c->L;
+    dim3 grid(grid_blocks(c, L.S, TH), 3);
+    k_compose<<<grid, TH, 0, c->stream>>>(c->vx, c->bc, c->fflag, out, L);
+    FS_CUDA(cudaGetLastError());
+    return FS_OK;
+}
+
+int launch_mask_fluid(fs_ctx *c, CF3 in, F3 out)
+{
+    const Layout &L = c->L;
+    dim3 grid(grid_blocks(c, L.S, TH), 3);
+    k_mask_fluid<<<grid, TH, 0, c->stream>>>(in, out, c->fflag, L);
+    FS_CUDA(cudaGetLastError());
+    return FS_OK;
+}
+
+int launch_to_face_space(fs_ctx *c, CF3 in)
+{
+    const Layout &L = c->L;
+    dim3 grid(grid_blocks(c, L.S, TH), 3);
+    k_to_face_space<<<grid, TH, 0, c->stream>>>(in, c->vx, c->fflag, L);
+    FS_CUDA(cudaGetLastError());
+    return FS_OK;
+}
+
+int launch_nu_grad(fs_ctx *c, CF3 uv, double *dot)
+{
+    const Layout &L = c->L;
+    k_nu_grad<<<grid_blocks(c, L.S, TH), TH, 0, c->stream>>>(c->vx, uv, c->fflag, L, c->scal + 3, c->partials);
+    FS_CUDA(cudaGetLastError());
+    SolveScal m;
+    int rc = read_scal(c, 3, &m);
+    if (rc) return rc;
+    *dot = m.aux[0] / (c->prm.dx * c->prm.dx);
+    return FS_OK;
+}
+
+int launch_loss(fs_ctx *c, CF3 u, CF3 t, int kind, double alpha, double beta, F3 g, double *loss)
+{
+    const Layout &L = c->L;
+    const uint8_t bandbit = kind == FS_MASK_SURFACE ? CF_BAND : CF_LIQ;
+    const long long nbc = c->n_band_cells[kind], nbf = c->n_band_faces[kind];
+    const bool use_cos = alpha != 0.0 && nbc > 0;
+    const int bs = grid_blocks(c, L.S, TH);
+    F3 gcw{{c->gc[0], c->gc[1], c->gc[2]}};
+    CF3 gcr{{c->gc[0], c->gc[1], c->gc[2]}};
+    if (use_cos)
+        k_loss_cell<<<bs, TH, 0, c->stream>>>(u, t, c->cflag, bandbit, gcw, L, (float)(alpha / (double)nbc),
+                                             c->scal + 3, c->partials);
+    const float bo = nbf > 0 ? (float)(beta / (double)nbf) : 0.f;
+    k_loss_face<<<bs, TH, 0, c->stream>>>(u, t, c->cflag, c->fflag, bandbit, gcr, use_cos ? 1 : 0, g, L, bo,
+                                         c->scal + 2, c->partials);
+    FS_CUDA(cudaGetLastError());
+    SolveScal a, b;
+    int rc = read_scal(c, 2, &a);
+    if (rc) return rc;
+    double l = nbf > 0 ? beta * a.aux[0] / (double)nbf : 0.0;
+    if (use_cos) {
+        rc = read_scal(c, 3, &b);
+        if (rc) return rc;
+        l += alpha * b.aux[1] / (double)nbc;
+    }
+    *loss += l;
+    return FS_OK;
+}
+
+}  // namespace fs

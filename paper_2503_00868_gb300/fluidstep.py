@@ -1,0 +1,291 @@
+"""Thin ctypes binding of libfluidstep.so, the C ABI of include/fluidstep.h.
+
+Argument marshalling only: every step of the fluid step runs in the library's
+CUDA kernels. PyTorch provides device memory and the stream. The functions
+``fs_*`` mirror the C entry points one to one; ``Grid`` is a small convenience
+wrapper used by the tests, the rollout and the benchmark.
+
+Fields are ``Mac`` triples of float32 CUDA tensors of shape (planes, rows, pitch)
+in the library layout; ``pack``/``unpack`` convert from/to the dense staggered
+shapes (nz, ny, nx+1), (nz, ny+1, nx), (nz+1, ny, nx).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import NamedTuple, Optional
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfluidstep.so")
+
+FS_OK, FS_EINVAL, FS_ENOMEM, FS_ECUDA, FS_ENOCONV, FS_ENONFINITE, FS_ESTATE, FS_ETIMEOUT, FS_EBREAKDOWN = range(9)
+STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_ENOMEM", 3: "FS_ECUDA", 4: "FS_ENOCONV",
+                5: "FS_ENONFINITE", 6: "FS_ESTATE", 7: "FS_ETIMEOUT", 8: "FS_EBREAKDOWN"}
+FS_AIR, FS_LIQUID, FS_SOLID = 0, 1, 2
+FS_PRECOND_JACOBI, FS_PRECOND_MIC0, FS_PRECOND_LEARNED = 0, 1, 2
+FS_MASK_SURFACE, FS_MASK_OCCUPIED = 0, 1
+SOFT_STATUS = (FS_OK, FS_ENOCONV)
+
+
+class FluidStepError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class fs_params(C.Structure):
+    _fields_ = [("dx", C.c_double), ("dt", C.c_double), ("nu", C.c_double), ("rho", C.c_double),
+                ("g", C.c_double * 3), ("precond", C.c_int), ("maxit_p", C.c_int), ("maxit_v", C.c_int),
+                ("tol_p", C.c_double), ("tol_v", C.c_double), ("check_every", C.c_int),
+                ("spin_limit", C.c_int), ("mic_tau", C.c_double), ("mic_sigma", C.c_double)]
+
+
+class fs_stats(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters_p", C.c_int), ("iters_v", C.c_int),
+                ("relres_p", C.c_double), ("relres_v", C.c_double), ("true_relres_p", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class fs_layout_t(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("pitch", C.c_int),
+                ("rows", C.c_int), ("planes", C.c_int), ("nelems", C.c_longlong)]
+
+
+class fs_mac(C.Structure):
+    _fields_ = [("u", C.c_void_p), ("v", C.c_void_p), ("w", C.c_void_p)]
+
+
+_lib = None
+
+_SIGS = {
+    "fs_default_params": ([C.POINTER(fs_params)], None),
+    "fs_init_grid": ([C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.POINTER(fs_params), C.c_void_p], C.c_int),
+    "fs_destroy": ([C.c_void_p], C.c_int),
+    "fs_layout": ([C.c_void_p, C.POINTER(fs_layout_t)], C.c_int),
+    "fs_set_stream": ([C.c_void_p, C.c_void_p], C.c_int),
+    "fs_set_params": ([C.c_void_p, C.POINTER(fs_params)], C.c_int),
+    "fs_set_mask": ([C.c_void_p, C.c_void_p, C.POINTER(fs_mac)], C.c_int),
+    "fs_step": ([C.c_void_p, C.POINTER(fs_mac), C.POINTER(fs_mac), C.POINTER(fs_mac), C.POINTER(fs_stats)], C.c_int),
+    "fs_project": ([C.c_void_p, C.POINTER(fs_mac), C.c_void_p, C.POINTER(fs_stats)], C.c_int),
+    "fs_adjoint_step": ([C.c_void_p, C.POINTER(fs_mac), C.POINTER(fs_mac), C.POINTER(fs_mac), C.POINTER(fs_mac),
+                         C.POINTER(C.c_double), C.POINTER(fs_stats)], C.c_int),
+    "fs_loss_grad": ([C.c_void_p, C.POINTER(fs_mac), C.POINTER(fs_mac), C.c_int, C.c_double, C.c_double,
+                      C.POINTER(C.c_double), C.POINTER(fs_mac)], C.c_int),
+    "fs_last_error": ([], C.c_char_p),
+}
+
+
+def exported_symbols():
+    """Names of the C entry points this binding expects the library to export."""
+    return list(_SIGS)
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library; raises if it has not been built (no CPU fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FileNotFoundError(f"{path} is missing: build it with paper_2503_00868_gb300.build.build()")
+    L = C.CDLL(path)
+    for name, (args, res) in _SIGS.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _check(rc: int, soft=SOFT_STATUS) -> int:
+    if rc not in soft:
+        raise FluidStepError(rc, load().fs_last_error().decode())
+    return rc
+
+
+# ---- one-to-one wrappers of the C entry points ------------------------------
+
+def fs_default_params() -> fs_params:
+    p = fs_params()
+    load().fs_default_params(C.byref(p))
+    return p
+
+
+def fs_init_grid(nx: int, ny: int, nz: int, params: fs_params, stream: int = 0) -> int:
+    h = C.c_void_p()
+    _check(load().fs_init_grid(C.byref(h), nx, ny, nz, C.byref(params), C.c_void_p(stream)), (FS_OK,))
+    return h.value
+
+
+def fs_destroy(ctx: int) -> None:
+    load().fs_destroy(C.c_void_p(ctx))
+
+
+def fs_layout(ctx: int) -> fs_layout_t:
+    out = fs_layout_t()
+    _check(load().fs_layout(C.c_void_p(ctx), C.byref(out)), (FS_OK,))
+    return out
+
+
+def fs_set_stream(ctx: int, stream: int) -> None:
+    _check(load().fs_set_stream(C.c_void_p(ctx), C.c_void_p(stream)), (FS_OK,))
+
+
+def fs_set_params(ctx: int, params: fs_params) -> None:
+    _check(load().fs_set_params(C.c_void_p(ctx), C.byref(params)), (FS_OK,))
+
+
+class Mac(NamedTuple):
+    u: torch.Tensor
+    v: torch.Tensor
+    w: torch.Tensor
+
+
+def _mac(m: Optional[Mac]):
+    if m is None:
+        return None
+    for t in m:
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("fields must be contiguous float32 CUDA tensors")
+    return fs_mac(m.u.data_ptr(), m.v.data_ptr(), m.w.data_ptr())
+
+
+def _ref(s):
+    return C.byref(s) if s is not None else None
+
+
+def fs_set_mask(ctx: int, cell_type_dense: torch.Tensor, bc: Optional[Mac] = None) -> None:
+    if cell_type_dense.dtype != torch.uint8 or not cell_type_dense.is_cuda:
+        raise ValueError("cell types must be a uint8 CUDA tensor")
+    t = cell_type_dense.contiguous()
+    _check(load().fs_set_mask(C.c_void_p(ctx), C.c_void_p(t.data_ptr()), _ref(_mac(bc))), (FS_OK,))
+
+
+def fs_step(ctx: int, u_in: Mac, u_out: Mac, u_visc: Optional[Mac] = None):
+    st = fs_stats()
+    rc = _check(load().fs_step(C.c_void_p(ctx), _ref(_mac(u_in)), _ref(_mac(u_out)), _ref(_mac(u_visc)),
+                               C.byref(st)))
+    return rc, st.as_dict()
+
+
+def fs_project(ctx: int, u: Mac, q_out: Optional[torch.Tensor] = None):
+    st = fs_stats()
+    q = C.c_void_p(q_out.data_ptr()) if q_out is not None else None
+    rc = _check(load().fs_project(C.c_void_p(ctx), _ref(_mac(u)), q, C.byref(st)))
+    return rc, st.as_dict()
+
+
+def fs_adjoint_step(ctx: int, u_in: Mac, u_visc: Optional[Mac], g_out: Mac, g_in: Mac):
+    st = fs_stats()
+    gnu = C.c_double(0.0)
+    rc = _check(load().fs_adjoint_step(C.c_void_p(ctx), _ref(_mac(u_in)), _ref(_mac(u_visc)), _ref(_mac(g_out)),
+                                       _ref(_mac(g_in)), C.byref(gnu), C.byref(st)))
+    return rc, gnu.value, st.as_dict()
+
+
+def fs_loss_grad(ctx: int, u: Mac, target: Mac, mask_kind: int = FS_MASK_SURFACE, alpha: float = 0.0,
+                 beta: float = 1.0, g: Optional[Mac] = None) -> float:
+    loss = C.c_double(0.0)
+    _check(load().fs_loss_grad(C.c_void_p(ctx), _ref(_mac(u)), _ref(_mac(target)), mask_kind, alpha, beta,
+                               C.byref(loss), _ref(_mac(g))), (FS_OK,))
+    return loss.value
+
+
+def fs_last_error() -> str:
+    return load().fs_last_error().decode()
+
+
+# ---- convenience wrapper -----------------------------------------------------
+
+def make_params(**kw) -> fs_params:
+    p = fs_default_params()
+    for k, v in kw.items():
+        if k == "g":
+            for c in range(3):
+                p.g[c] = float(v[c])
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class Grid:
+    """A context plus layout helpers. Fields live on `device` in the library layout."""
+
+    def __init__(self, nx, ny, nz, params: Optional[fs_params] = None, device="cuda", stream=None, **kw):
+        self.device = torch.device(device)
+        self.params = params if params is not None else make_params(**kw)
+        with torch.cuda.device(self.device):
+            s = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.stream = s
+            self.ctx = fs_init_grid(nx, ny, nz, self.params, s.cuda_stream)
+        lay = fs_layout(self.ctx)
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.pitch, self.rows, self.planes, self.nelems = lay.pitch, lay.rows, lay.planes, lay.nelems
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            fs_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, **kw):
+        for k, v in kw.items():
+            if k == "g":
+                for c in range(3):
+                    self.params.g[c] = float(v[c])
+            else:
+                setattr(self.params, k, v)
+        fs_set_params(self.ctx, self.params)
+
+    # layout
+    def empty_cell(self):
+        return torch.zeros((self.planes, self.rows, self.pitch), dtype=torch.float32, device=self.device)
+
+    def zeros(self) -> Mac:
+        return Mac(self.empty_cell(), self.empty_cell(), self.empty_cell())
+
+    def dense_shapes(self):
+        nx, ny, nz = self.nx, self.ny, self.nz
+        return (nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx)
+
+    def pack(self, dense) -> Mac:
+        out = self.zeros()
+        for t, a, s in zip(out, dense, self.dense_shapes()):
+            a = torch.as_tensor(np.ascontiguousarray(a) if isinstance(a, np.ndarray) else a)
+            assert tuple(a.shape) == s, (tuple(a.shape), s)
+            t[: s[0], : s[1], : s[2]] = a.to(device=self.device, dtype=torch.float32)
+        return out
+
+    def unpack(self, m: Mac, dtype=np.float64):
+        return tuple(t[: s[0], : s[1], : s[2]].detach().cpu().numpy().astype(dtype)
+                     for t, s in zip(m, self.dense_shapes()))
+
+    def unpack_cell(self, q: torch.Tensor, dtype=np.float64):
+        return q[: self.nz, : self.ny, : self.nx].detach().cpu().numpy().astype(dtype)
+
+    # calls
+    def set_mask(self, types, bc: Optional[Mac] = None):
+        t = torch.as_tensor(np.ascontiguousarray(types, dtype=np.uint8)) if isinstance(types, np.ndarray) else types
+        fs_set_mask(self.ctx, t.to(self.device), bc)
+
+    def step(self, u_in: Mac, u_out: Mac, u_visc: Optional[Mac] = None):
+        return fs_step(self.ctx, u_in, u_out, u_visc)
+
+    def project(self, u: Mac, q: Optional[torch.Tensor] = None):
+        return fs_project(self.ctx, u, q)
+
+    def adjoint_step(self, u_in: Mac, g_out: Mac, g_in: Mac, u_visc: Optional[Mac] = None):
+        return fs_adjoint_step(self.ctx, u_in, u_visc, g_out, g_in)
+
+    def loss_grad(self, u: Mac, target: Mac, mask_kind=FS_MASK_SURFACE, alpha=0.0, beta=1.0,
+                  g: Optional[Mac] = None) -> float:
+        return fs_loss_grad(self.ctx, u, target, mask_kind, alpha, beta, g)
