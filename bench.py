@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark of the differentiable MAC-grid fluid step (arXiv 2503.00868, Sec. 3.4).
+
+Metric: forward + adjoint cell-steps per second at 256^3. One benchmark step is
+one pass of the whole hot path over one synthetic scene: a checkpointed rollout
+of FRAMES steps (advection, body force, implicit viscosity, pressure projection),
+the Eq. eq::optLoss loss on the surface band at the last frame, and the reverse
+pass (segment recompute + adjoint steps) giving dL/du0 and dL/dnu.
+cell-steps/s = nx * ny * nz * FRAMES / (time of the step).
+
+Scene (stand-in for the paper's video-derived liquid blob): an ellipsoid of
+liquid resting on the floor, 40 % occupancy, air elsewhere, box walls solid;
+initial velocity = seeded N(0,1) noise blurred by a sigma = 3 cell Gaussian;
+target = an independent blurred field (seed + 100); nu = 0.01, dt = 1/30,
+dx = 1/256, Jacobi-PCG to relative residual 1e-6 for both solves.
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Multi-GPU runs are independent replicas (one scene per rank, no collective on
+the data path); the timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FRAMES = 8
+CHECKPOINT = 4
+PROFILE_PERIOD = 8   # time every 8th CG iteration inside the timed region
+METRIC = "fwd+adjoint cell-steps/s at 256^3"
+UNIT = "cell-steps/s"
+
+# ncu DRAM traffic per launch (bytes) of the kernels, keyed by kernel name; each
+# entry holds the hash of the CUDA source it was measured on and is reported only
+# while the source is unchanged (capture commands in profiles/).
+NCU_TRAFFIC = {}
+
+
+def args_parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--frames", type=int, default=FRAMES)
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "mic0"])
+    ap.add_argument("--cpu-sample-n", type=int, default=64)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2503_00868_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                maxs.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sms:
+            return None
+        sms.sort()
+        return {"sm_mhz": sms[len(sms) // 2], "sm_max_mhz": max(maxs), "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def make_scene(n, seed):
+    from paper_2503_00868_gb300 import workloads as W
+    types, info = W.ellipsoid_blob(n, n, n, seed)
+    u0 = W.blurred_noise_mac(n, n, n, seed)
+    tgt = W.blurred_noise_mac(n, n, n, seed + 100)
+    return types, u0, tgt, info
+
+
+def params_for(n, precond):
+    from paper_2503_00868_gb300 import fluidstep as F
+    return dict(dx=1.0 / n, dt=1.0 / 30.0, nu=0.01, g=(0.0, 0.0, 0.0), tol_p=1e-6, tol_v=1e-6,
+                precond=F.FS_PRECOND_MIC0 if precond == "mic0" else F.FS_PRECOND_JACOBI, check_every=16,
+                maxit_p=20000, maxit_v=4000)
+
+
+def cpu_oracle_sample(n, frames=1):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload: the
+    same scene recipe at n^3, one forward step + loss + one adjoint step."""
+    import oracle as O
+    types, u0, tgt, _ = make_scene(n, 0)
+    kw = params_for(n, "jacobi")
+    g = O.Grid(types, kw["dx"], kw["dt"], kw["nu"], g=kw["g"], tol_p=kw["tol_p"], tol_v=kw["tol_v"],
+               precond=O.PC_JACOBI)
+    t0 = time.perf_counter()
+    states = [u0]
+    for _ in range(frames):
+        states.append(O.step(g, states[-1])[0])
+    loss, gbar = O.loss_grad(g, states[-1], tgt)
+    for k in range(frames - 1, -1, -1):
+        gbar, _ = O.adjoint_step(g, states[k], gbar)
+    dt = time.perf_counter() - t0
+    return n ** 3 * frames / dt, dt
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle as O
+    O.build()
+    n = a.cpu_sample_n
+    for _ in range(a.warmup):
+        cpu_oracle_sample(n)
+    vals, total = [], 0.0
+    for _ in range(a.steps):
+        v, dt = cpu_oracle_sample(n)
+        vals.append(v)
+        total += dt
+    value = a.steps * n ** 3 / total
+    sample = (f"oracle fwd+adjoint of 1 step of the same scene recipe at {n}^3 (iteration counts grow with n, "
+              f"so this overstates the oracle's throughput at 256^3)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(a),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(a):
+    return {"workload": f"fwd+adjoint checkpointed rollout on a {a.n}^3 MAC grid: ellipsoid liquid blob "
+                        f"(40% occupancy) on the floor, {a.frames} frames, checkpoint every {CHECKPOINT}, "
+                        f"surface-band L2 loss at the last frame, gradients w.r.t. nu and u0",
+            "grid": [a.n, a.n, a.n], "frames": a.frames, "checkpoint_every": CHECKPOINT,
+            "precond": a.precond, "tol": 1e-6, "nu": 0.01, "dt": 1.0 / 30.0,
+            "l2_between_steps": "inputs larger than L2 (working set > 1 GB per replica)",
+            "parallelism": "replicas" if a.gpus > 1 else "single"}
+
+
+def main():
+    a = args_parse()
+    if a.impl == "reference":
+        return run_reference(a)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2503_00868_gb300 import build as B
+    from paper_2503_00868_gb300 import fluidstep as F
+    from paper_2503_00868_gb300.rollout import rollout_loss
+    B.build()
+    F.load()
+
+    n, frames = a.n, a.frames
+    types, u0_np, tgt_np, info = make_scene(n, rank)
+    grid = F.Grid(n, n, n, **params_for(n, a.precond))
+    grid.set_mask(types)
+    u0 = grid.pack(u0_np)
+    tgt = grid.pack(tgt_np)
+    nu_t = torch.tensor(0.01, dtype=torch.float32)
+    stats = []
+
+    def one_step(u0m, tgtm):
+        leaves = [t.detach().requires_grad_(True) for t in u0m]
+        nu = nu_t.detach().clone().requires_grad_(True)
+        loss = rollout_loss(grid, F.Mac(*leaves), nu, frames, {frames: tgtm}, CHECKPOINT, stats=stats)
+        loss.backward()
+        return loss, nu.grad, leaves
+
+    stream = torch.cuda.current_stream()
+    for _ in range(max(a.warmup, 0)):
+        one_step(u0, tgt)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # ---- device-resident timing -------------------------------------------
+    stats.clear()
+    grid.profile(PROFILE_PERIOD)
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(a.steps):
+        loss, gnu, leaves = one_step(u0, tgt)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    prof = grid.profile_read()
+    grid.profile(0)
+    if world > 1:
+        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    cells = n ** 3
+    value = world * a.steps * cells * frames / elapsed
+    ms_per_step = 1e3 * elapsed / a.steps
+    iters_p = [s[2]["iters_p"] for s in stats if s[0] == "fwd"]
+    iters_v = [s[2]["iters_v"] for s in stats if s[0] == "fwd"]
+
+    # ---- end to end through the public API with host buffers ---------------
+    e2e = None
+    if not a.no_e2e:
+        host_u0 = [t.cpu().pin_memory() for t in u0]
+        host_t = [t.cpu().pin_memory() for t in tgt]
+        hb = sum(t.numel() * 4 for t in host_u0) + sum(t.numel() * 4 for t in host_t)
+        results = []
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            du = F.Mac(*(h.to("cuda", non_blocking=True) for h in host_u0))
+            dtg = F.Mac(*(h.to("cuda", non_blocking=True) for h in host_t))
+            loss, gnu, _ = one_step(du, dtg)
+            # the step's result read back on the host: loss and dL/dnu (2 doubles)
+            results.append((float(loss.detach().cpu()), float(gnu.detach().cpu())))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        t_e2e = e0.elapsed_time(e1) / 1e3
+        if world > 1:
+            t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": world * a.steps * cells * frames / t_e2e, "unit": UNIT, "h2d_bytes_per_step": hb,
+               "d2h_bytes_per_step": 16}
+
+    # ---- roofline of the dominant kernel -----------------------------------
+    peaks = measured_peaks()
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    top = max((k for k in prof.items() if k[1][2] > 0), key=lambda kv: kv[1][1], default=None)
+    roofline = None
+    if top:
+        name, (launches, ms, by) = top
+        achieved = (by / launches) / (ms / launches * 1e-3) / 1e9
+        src = source_hash()
+        tr = NCU_TRAFFIC.get(name)
+        traffic = tr["bytes_per_launch"] if tr and tr.get("source") == src else None
+        roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm, "traffic": traffic,
+                    "algorithmic_bytes_per_launch": by / launches, "launches": launches,
+                    "avg_launch_us": 1e3 * ms / launches,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback"}
+    total_ms = sum(v[1] for v in prof.values())
+    kernels = {k: {"launches": v[0], "ms": round(v[1], 3), "share_of_timed": round(v[1] / (1e3 * elapsed), 4)}
+               for k, v in prof.items()}
+    gpu_launches = None
+    if "all_kernels" in prof:
+        gpu_launches = prof["all_kernels"][0]
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        import oracle as O
+        O.build()
+        v, dt = cpu_oracle_sample(a.cpu_sample_n)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"oracle fwd+adjoint of 1 step of the same scene recipe at {a.cpu_sample_n}^3 "
+                         f"({dt:.1f} s; iteration counts grow with n, so this overstates the oracle at 256^3)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(a),
+                "clocks": clocks, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline,
+                "cpu_baseline": cpu, "kernels": kernels, "occupancy": info["occupancy"],
+                "pcg_iters_per_step": {"pressure_mean": sum(iters_p) / max(len(iters_p), 1),
+                                       "viscosity_mean": sum(iters_v) / max(len(iters_v), 1)},
+                "loss": float(loss.detach()), "dL_dnu": float(gnu)}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    grid.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -197,6 +197,28 @@ int fs_adjoint_step(fs_ctx *c, const fs_mac *u_in, const fs_mac *u_visc,
 int fs_loss_grad(fs_ctx *c, const fs_mac *u, const fs_mac *target, int mask_kind,
                  double alpha, double beta, double *loss, fs_mac *g);
 
+/* Per-kernel timing. fs_profile(c, k) with k >= 1 resets the counters and from
+ * then on brackets launches of the solver kernels (every k-th CG iteration of
+ * each batch), the advection kernels and the preconditioners with CUDA events on
+ * the context's stream; fs_profile(c, 0) stops. It also counts every kernel the
+ * context launches (reported as the entry "all_kernels"). Timing is collected when a call synchronises, so it adds no host
+ * round trip. fs_profile_read copies up to `max` entries (one per kernel kind
+ * that ran) into `out` and sets *count. `bytes` is the ALGORITHMIC traffic summed
+ * over the launches: for the CG kernels the flag byte of every element of the
+ * launch range plus, per active element (liquid cell or fluid face), 16 bytes for
+ * the fused direction update and operator apply (read r or z and p, write p and
+ * Ap) and 24 bytes for the iterate update (read x, r, p, Ap, write x, r); zero for
+ * kernels without a stated figure. */
+typedef struct {
+    char name[32];
+    long long launches;
+    double total_ms;
+    double bytes;
+} fs_kernel_time;
+
+int fs_profile(fs_ctx *c, int enable);
+int fs_profile_read(fs_ctx *c, fs_kernel_time *out, int max, int *count);
+
 /* The per-thread message of the last failing call ("" if none). */
 const char *fs_last_error(void);
 

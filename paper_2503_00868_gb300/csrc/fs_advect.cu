@@ -154,9 +154,12 @@ int launch_advect(fs_ctx *c, CF3 u)
     const Layout &L = c->L;
     const float h = (float)(c->prm.dt / c->prm.dx);
     dim3 grid((L.P + 127) / 128, L.R, L.Z);
+    cudaEvent_t e0 = prof_mark(c);
     for (int comp = 0; comp < 3; comp++)
         k_advect<<<grid, 128, 0, c->stream>>>(u, c->vx, c->fflag, L, comp, h,
                                              (float)(c->prm.dt * c->prm.g[comp]));
+    prof_add(c, K_ADVECT, e0, prof_mark(c), 0.0);
+    c->n_launches += 3;
     FS_CUDA(cudaGetLastError());
     return FS_OK;
 }
@@ -168,8 +171,11 @@ int launch_advect_adjoint(fs_ctx *c, CF3 u, F3 g)
     dim3 gz(grid_blocks(c, L.S / 4, 256), 3);
     k_zero3<<<gz, 256, 0, c->stream>>>(g, L.S);
     dim3 grid((L.P + 127) / 128, L.R, L.Z);
+    cudaEvent_t e0 = prof_mark(c);
     for (int comp = 0; comp < 3; comp++)
         k_advect_adj<<<grid, 128, 0, c->stream>>>(u, c->vx, g, c->fflag, L, comp, h);
+    prof_add(c, K_ADVECT_ADJ, e0, prof_mark(c), 0.0);
+    c->n_launches += 4;
     FS_CUDA(cudaGetLastError());
     return FS_OK;
 }

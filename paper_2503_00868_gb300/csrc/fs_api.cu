@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "fs_internal.cuh"
 
@@ -81,9 +82,74 @@ static int alloc_zero(void **p, size_t bytes)
     return check_cuda(cudaMemset(*p, 0, bytes), "cudaMemset");
 }
 
+// ---- per-kernel timing ---------------------------------------------------------
+static const char *kKernelNames[K_COUNT] = {"pressure_spmv", "pressure_update", "visc_spmv", "visc_update",
+                                            "advect", "advect_adjoint", "mic0_apply", "net_apply"};
+
+struct Prof {
+    std::vector<cudaEvent_t> free_ev, all_ev;
+    struct Pending { int id; cudaEvent_t a, b; double bytes; };
+    std::vector<Pending> pending;
+    double ms[K_COUNT] = {};
+    double bytes[K_COUNT] = {};
+    long long n[K_COUNT] = {};
+};
+
+cudaEvent_t prof_mark(fs_ctx *c)
+{
+    if (!c->prof_on) return nullptr;
+    Prof *p = static_cast<Prof *>(c->prof);
+    if (p->free_ev.empty()) return nullptr;
+    cudaEvent_t e = p->free_ev.back();
+    p->free_ev.pop_back();
+    cudaEventRecord(e, c->stream);
+    return e;
+}
+
+void prof_add(fs_ctx *c, int id, cudaEvent_t a, cudaEvent_t b, double bytes)
+{
+    if (!c->prof_on) return;
+    Prof *p = static_cast<Prof *>(c->prof);
+    if (!a || !b) {
+        if (a) p->free_ev.push_back(a);
+        if (b) p->free_ev.push_back(b);
+        return;
+    }
+    p->pending.push_back({id, a, b, bytes});
+}
+
+void prof_flush(fs_ctx *c)
+{
+    if (!c->prof) return;
+    Prof *p = static_cast<Prof *>(c->prof);
+    for (auto &q : p->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
+            p->ms[q.id] += ms;
+            p->bytes[q.id] += q.bytes;
+            p->n[q.id] += 1;
+        } else {
+            cudaGetLastError();
+        }
+        p->free_ev.push_back(q.a);
+        p->free_ev.push_back(q.b);
+    }
+    p->pending.clear();
+}
+
+static void prof_destroy(fs_ctx *c)
+{
+    if (!c->prof) return;
+    Prof *p = static_cast<Prof *>(c->prof);
+    for (cudaEvent_t e : p->all_ev) cudaEventDestroy(e);
+    delete p;
+    c->prof = nullptr;
+}
+
 static void free_ctx(fs_ctx *c)
 {
     if (!c) return;
+    prof_destroy(c);
     void *ptrs[] = {c->cflag, c->fflag, c->bc, c->dsum, c->pb, c->pr, c->pp[0], c->pp[1], c->pq, c->px, c->pz,
                     c->vx, c->vr, c->vp[0], c->vp[1], c->vq, c->fu[0], c->fu[1], c->fu[2], c->fg[0], c->fg[1],
                     c->fg[2], c->gc[0], c->gc[1], c->gc[2], c->mic_prec, c->scal, c->partials, c->err_word};
@@ -119,6 +185,65 @@ void fs_default_params(fs_params *p)
 }
 
 const char *fs_last_error(void) { return g_err; }
+
+int fs_profile(fs_ctx *c, int enable)
+{
+    if (!c) return set_error(FS_EINVAL, "NULL context");
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    prof_flush(c);
+    if (enable && !c->prof) {
+        Prof *p = new (std::nothrow) Prof();
+        if (!p) return set_error(FS_ENOMEM, "host allocation failed");
+        for (int k = 0; k < 8192; k++) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                break;
+            }
+            p->all_ev.push_back(e);
+            p->free_ev.push_back(e);
+        }
+        c->prof = p;
+    }
+    if (c->prof) {
+        Prof *p = static_cast<Prof *>(c->prof);
+        for (int k = 0; k < K_COUNT; k++) {
+            p->ms[k] = 0.0;
+            p->bytes[k] = 0.0;
+            p->n[k] = 0;
+        }
+    }
+    c->prof_on = enable > 0 ? 1 : 0;
+    c->prof_period = enable > 0 ? enable : 1;
+    c->n_launches = 0;
+    return FS_OK;
+}
+
+int fs_profile_read(fs_ctx *c, fs_kernel_time *out, int max, int *count)
+{
+    if (!c || !count || (max > 0 && !out)) return set_error(FS_EINVAL, "NULL argument");
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    prof_flush(c);
+    *count = 0;
+    if (!c->prof) return FS_OK;
+    Prof *p = static_cast<Prof *>(c->prof);
+    for (int k = 0; k < K_COUNT && *count < max; k++) {
+        if (!p->n[k]) continue;
+        fs_kernel_time &e = out[(*count)++];
+        std::memset(&e, 0, sizeof(e));
+        std::snprintf(e.name, sizeof(e.name), "%s", kKernelNames[k]);
+        e.launches = p->n[k];
+        e.total_ms = p->ms[k];
+        e.bytes = p->bytes[k];
+    }
+    if (*count < max) {
+        fs_kernel_time &e = out[(*count)++];
+        std::memset(&e, 0, sizeof(e));
+        std::snprintf(e.name, sizeof(e.name), "all_kernels");
+        e.launches = c->n_launches;
+    }
+    return FS_OK;
+}
 
 int fs_init_grid(fs_ctx **out, int nx, int ny, int nz, const fs_params *p, void *cuda_stream)
 {
@@ -273,6 +398,7 @@ int fs_step(fs_ctx *c, const fs_mac *u_in, fs_mac *u_out, fs_mac *u_visc, fs_sta
     if (rp == FS_ECUDA || rp == FS_EINVAL) return rp;
     if ((rc = launch_grad_subtract(c, cf3(uv), f3(u_out), nullptr))) return rc;
     FS_CUDA(cudaStreamSynchronize(c->stream));
+    prof_flush(c);
     return s->status;
 }
 
@@ -290,6 +416,7 @@ int fs_project(fs_ctx *c, fs_mac *u, float *q_out, fs_stats *st)
     if (rp == FS_ECUDA || rp == FS_EINVAL) return rp;
     if ((rc = launch_grad_subtract(c, cf3(u), f3(u), q_out))) return rc;
     FS_CUDA(cudaStreamSynchronize(c->stream));
+    prof_flush(c);
     return s->status;
 }
 
@@ -339,6 +466,7 @@ int fs_adjoint_step(fs_ctx *c, const fs_mac *u_in, const fs_mac *u_visc, const f
     // advection adjoint (the body force adds a constant)
     if ((rc = launch_advect_adjoint(c, cf3(u_in), f3(g_in)))) return rc;
     FS_CUDA(cudaStreamSynchronize(c->stream));
+    prof_flush(c);
     return s->status;
 }
 

@@ -105,6 +105,13 @@ struct fs_ctx {
     double *partials;           // device [max_blocks * 8]
     int max_blocks;
     unsigned *err_word;         // device error word of bounded waits
+    long long n_fluid;          // fluid faces
+
+    // per-kernel timing (fs_profile)
+    int prof_on;
+    int prof_period;            // time every prof_period-th CG iteration
+    void *prof;                 // fs::Prof
+    long long n_launches;       // kernels launched by this context since fs_profile(c, 1)
 };
 
 namespace fs {
@@ -225,5 +232,21 @@ int mic0_factor(fs_ctx *c);
 int mic0_apply(fs_ctx *c, const float *r, float *z);
 
 int read_scal(fs_ctx *c, int which, SolveScal *out);
+
+// ---- per-kernel timing -------------------------------------------------------
+enum KernelId : int {
+    K_P_SPMV = 0,
+    K_P_UPDATE,
+    K_V_SPMV,
+    K_V_UPDATE,
+    K_ADVECT,
+    K_ADVECT_ADJ,
+    K_MIC_APPLY,
+    K_NET_APPLY,
+    K_COUNT
+};
+cudaEvent_t prof_mark(fs_ctx *c);   // records an event on the stream (nullptr when off)
+void prof_add(fs_ctx *c, int id, cudaEvent_t a, cudaEvent_t b, double bytes);
+void prof_flush(fs_ctx *c);         // call after the stream has been synchronised
 
 }  // namespace fs

@@ -110,7 +110,8 @@ __global__ void k_face_count(Layout L, uint8_t *fflag, CF3 bc_user, float *bc, f
     }
 }
 
-// counts: 0 liquid cells, 1 surface band cells, 2 surface band faces, 3 occupied band faces
+// counts: 0 liquid cells, 1 surface band cells, 2 surface band faces, 3 occupied
+// band faces (= fluid faces)
 __global__ void k_counts(Layout L, const uint8_t *__restrict__ cflag, const uint8_t *__restrict__ fflag,
                          unsigned long long *cnt)
 {
@@ -180,6 +181,7 @@ int build_mask(fs_ctx *c, const uint8_t *types_dense, const fs_mac *bc)
     c->n_band_cells[FS_MASK_OCCUPIED] = (long long)h[0];
     c->n_band_faces[FS_MASK_SURFACE] = (long long)h[2];
     c->n_band_faces[FS_MASK_OCCUPIED] = (long long)h[3];
+    c->n_fluid = (long long)h[3];
     // The pressure operator has the constant on the liquid as null vector when no
     // liquid cell touches air (a closed box full of liquid).
     c->singular = (h[0] > 0 && h[1] == 0) ? 1 : 0;

@@ -49,19 +49,19 @@ __global__ void __launch_bounds__(TH) k_spmv(const float *__restrict__ src, cons
     if (s->done) return;
     const float beta = (float)s->beta;
     KSum acc;
+    // Inactive elements keep p = q = 0 (set when the solve starts), so they are
+    // neither read nor written here: only their flag byte is touched.
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
         const uint8_t f = fl[t];
-        float pc = 0.f, qv = 0.f;
-        if (f & Op::ACTIVE) {
-            auto pn = [&](int u) -> float {
-                float z = JAC ? __ldg(src + u) * inv_diag<Op>(__ldg(fl + u), cc) : __ldg(src + u);
-                return z + beta * __ldg(pold + u);
-            };
-            pc = pn(t);
-            float nb = (pn(t - 1) + pn(t + 1)) + (pn(t - P) + pn(t + P)) + (pn(t - PL) + pn(t + PL));
-            qv = Op::diag(f, cc) * pc - Op::offc(cc) * nb;
-            acc.add(pc * qv);
-        }
+        if (!(f & Op::ACTIVE)) continue;
+        auto pn = [&](int u) -> float {
+            float z = JAC ? __ldg(src + u) * inv_diag<Op>(__ldg(fl + u), cc) : __ldg(src + u);
+            return z + beta * __ldg(pold + u);
+        };
+        const float pc = pn(t);
+        const float nb = (pn(t - 1) + pn(t + 1)) + (pn(t - P) + pn(t + P)) + (pn(t - PL) + pn(t + PL));
+        const float qv = Op::diag(f, cc) * pc - Op::offc(cc) * nb;
+        acc.add(pc * qv);
         pnew[t] = pc;
         q[t] = qv;
     }
@@ -92,6 +92,9 @@ __global__ void __launch_bounds__(TH) k_update(float *__restrict__ x, float *__r
     const float4 *q4 = reinterpret_cast<const float4 *>(q);
     const uchar4 *f4 = reinterpret_cast<const uchar4 *>(fl);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += gridDim.x * blockDim.x) {
+        const uchar4 fv = f4[t];
+        // four inactive elements: p = q = 0 there, nothing changes
+        if (!((fv.x | fv.y | fv.z | fv.w) & Op::ACTIVE)) continue;
         float4 xv = x4[t], rv = r4[t];
         const float4 pv = __ldg(p4 + t), qv = __ldg(q4 + t);
         xv.x += alpha * pv.x; xv.y += alpha * pv.y; xv.z += alpha * pv.z; xv.w += alpha * pv.w;
@@ -99,11 +102,9 @@ __global__ void __launch_bounds__(TH) k_update(float *__restrict__ x, float *__r
         x4[t] = xv;
         r4[t] = rv;
         rr.add(rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w);
-        if (JAC) {
-            const uchar4 fv = f4[t];
+        if (JAC)
             rz.add(rv.x * rv.x * inv_diag<Op>(fv.x, cc) + rv.y * rv.y * inv_diag<Op>(fv.y, cc) +
                    rv.z * rv.z * inv_diag<Op>(fv.z, cc) + rv.w * rv.w * inv_diag<Op>(fv.w, cc));
-        }
     }
     double v[2] = {rr.value(), rz.value()}, tot[2];
     if (grid_reduce<2>(v, partials, &s->ticket, tot) && threadIdx.x == 0) {
@@ -429,6 +430,7 @@ int read_scal(fs_ctx *c, int which, SolveScal *out)
     FS_CUDA(cudaMemcpyAsync(c->scal_host + which, c->scal + which, sizeof(SolveScal), cudaMemcpyDeviceToHost,
                             c->stream));
     FS_CUDA(cudaStreamSynchronize(c->stream));
+    prof_flush(c);
     *out = c->scal_host[which];
     return FS_OK;
 }
@@ -447,7 +449,9 @@ int launch_divergence(fs_ctx *c, CF3 u)
         k_liquid_sum<<<grid_blocks(c, L.nC, TH), TH, 0, c->stream>>>(c->pb, c->cflag, L.nC, c->scal + 2,
                                                                      c->partials);
         k_sub_liquid_mean<<<grid_blocks(c, L.nC, TH), TH, 0, c->stream>>>(c->pb, c->cflag, L.nC, c->scal + 2);
+        c->n_launches += 2;
     }
+    c->n_launches += 1;
     FS_CUDA(cudaGetLastError());
     return FS_OK;
 }
@@ -472,28 +476,43 @@ int solve_pressure(fs_ctx *c, fs_stats *st)
         int rc = mic0_apply(c, c->pr, c->pz);
         if (rc) return rc;
         k_rz<<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(c->pr, c->pz, n4, 1, s, c->partials);
+        c->n_launches += 1;
     }
+    c->n_launches += 1;
     FS_CUDA(cudaGetLastError());
     const int bs = grid_blocks(c, L.nC, TH);
     const int b4 = grid_blocks(c, n4, TH);
     int cur = 0;
     long long launched = 0;
     SolveScal h;
+    const double by_spmv = (double)L.nC + 16.0 * (double)c->n_liquid;
+    const double by_upd = (double)L.nC + 24.0 * (double)c->n_liquid;
     for (;;) {
         for (int b = 0; b < c->prm.check_every; b++) {
-            if (jac) {
+            const bool samp = c->prof_on && (b % c->prof_period) == 0;
+            cudaEvent_t e0 = samp ? prof_mark(c) : nullptr;
+            if (jac)
                 k_spmv<PoisOp, true><<<bs, TH, 0, c->stream>>>(c->pr, c->pp[cur], c->pp[cur ^ 1], c->pq, c->cflag,
                                                                L.nC, L.P, L.PL, 0.f, s, c->partials);
-                k_update<PoisOp, true><<<b4, TH, 0, c->stream>>>(c->px, c->pr, c->pp[cur ^ 1], c->pq, c->cflag,
-                                                                 n4, 0.f, s, c->partials);
-            } else {
+            else
                 k_spmv<PoisOp, false><<<bs, TH, 0, c->stream>>>(c->pz, c->pp[cur], c->pp[cur ^ 1], c->pq,
                                                                 c->cflag, L.nC, L.P, L.PL, 0.f, s, c->partials);
+            cudaEvent_t e1 = samp ? prof_mark(c) : nullptr, e2 = samp ? prof_mark(c) : nullptr;
+            if (jac)
+                k_update<PoisOp, true><<<b4, TH, 0, c->stream>>>(c->px, c->pr, c->pp[cur ^ 1], c->pq, c->cflag,
+                                                                 n4, 0.f, s, c->partials);
+            else
                 k_update<PoisOp, false><<<b4, TH, 0, c->stream>>>(c->px, c->pr, c->pp[cur ^ 1], c->pq, c->cflag,
                                                                   n4, 0.f, s, c->partials);
+            cudaEvent_t e3 = samp ? prof_mark(c) : nullptr;
+            prof_add(c, K_P_SPMV, e0, e1, by_spmv);
+            prof_add(c, K_P_UPDATE, e2, e3, by_upd);
+            c->n_launches += 2;
+            if (!jac) {
                 int rc = mic0_apply(c, c->pr, c->pz);
                 if (rc) return rc;
                 k_rz<<<b4, TH, 0, c->stream>>>(c->pr, c->pz, n4, 0, s, c->partials);
+                c->n_launches += 1;
             }
             cur ^= 1;
         }
@@ -507,9 +526,11 @@ int solve_pressure(fs_ctx *c, fs_stats *st)
     }
     // true residual, then the mean-free representative of a singular solve
     k_pois_true_res<<<bs, TH, 0, c->stream>>>(c->pb, c->px, c->cflag, L.nC, L.P, L.PL, c->scal + 2, c->partials);
+    c->n_launches += 1;
     if (c->singular) {
         k_liquid_sum<<<bs, TH, 0, c->stream>>>(c->px, c->cflag, L.nC, c->scal + 3, c->partials);
         k_sub_liquid_mean<<<bs, TH, 0, c->stream>>>(c->px, c->cflag, L.nC, c->scal + 3);
+        c->n_launches += 2;
     }
     FS_CUDA(cudaGetLastError());
     SolveScal m;
@@ -536,16 +557,26 @@ int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st)
     k_helm_init<<<bs, TH, 0, c->stream>>>(c->vx, (dirichlet && c->has_bc) ? c->dsum : nullptr, c->vr, c->vp[0],
                                          c->vp[1], c->fflag, L.nF, L.P, L.PL, cc, tol2, c->prm.maxit_v, s,
                                          c->partials);
+    c->n_launches += 1;
     FS_CUDA(cudaGetLastError());
     int cur = 0;
     long long launched = 0;
     SolveScal h;
+    const double by_spmv = (double)L.nF + 16.0 * (double)c->n_fluid;
+    const double by_upd = (double)L.nF + 24.0 * (double)c->n_fluid;
     for (;;) {
         for (int b = 0; b < c->prm.check_every; b++) {
+            const bool samp = c->prof_on && (b % c->prof_period) == 0;
+            cudaEvent_t e0 = samp ? prof_mark(c) : nullptr;
             k_spmv<HelmOp, true><<<bs, TH, 0, c->stream>>>(c->vr, c->vp[cur], c->vp[cur ^ 1], c->vq, c->fflag,
                                                            L.nF, L.P, L.PL, cc, s, c->partials);
+            cudaEvent_t e1 = samp ? prof_mark(c) : nullptr, e2 = samp ? prof_mark(c) : nullptr;
             k_update<HelmOp, true><<<b4, TH, 0, c->stream>>>(c->vx, c->vr, c->vp[cur ^ 1], c->vq, c->fflag, n4,
                                                              cc, s, c->partials);
+            cudaEvent_t e3 = samp ? prof_mark(c) : nullptr;
+            prof_add(c, K_V_SPMV, e0, e1, by_spmv);
+            prof_add(c, K_V_UPDATE, e2, e3, by_upd);
+            c->n_launches += 2;
             cur ^= 1;
         }
         launched += c->prm.check_every;
@@ -569,6 +600,7 @@ int launch_grad_subtract(fs_ctx *c, CF3 in, F3 out, float *q_out)
     const Layout &L = c->L;
     dim3 grid(grid_blocks(c, L.S, TH), 4);
     k_grad_subtract<<<grid, TH, 0, c->stream>>>(in, out, c->px, q_out, c->fflag, L, (float)(1.0 / c->prm.dx));
+    c->n_launches += 1;
     FS_CUDA(cudaGetLastError());
     return FS_OK;
 }
@@ -578,6 +610,7 @@ int launch_compose(fs_ctx *c, F3 out)
     const Layout &L = c->L;
     dim3 grid(grid_blocks(c, L.S, TH), 3);
     k_compose<<<grid, TH, 0, c->stream>>>(c->vx, c->bc, c->fflag, out, L);
+    c->n_launches += 1;
     FS_CUDA(cudaGetLastError());
     return FS_OK;
 }
@@ -587,6 +620,7 @@ int launch_mask_fluid(fs_ctx *c, CF3 in, F3 out)
     const Layout &L = c->L;
     dim3 grid(grid_blocks(c, L.S, TH), 3);
     k_mask_fluid<<<grid, TH, 0, c->stream>>>(in, out, c->fflag, L);
+    c->n_launches += 1;
     FS_CUDA(cudaGetLastError());
     return FS_OK;
 }
@@ -596,6 +630,7 @@ int launch_to_face_space(fs_ctx *c, CF3 in)
     const Layout &L = c->L;
     dim3 grid(grid_blocks(c, L.S, TH), 3);
     k_to_face_space<<<grid, TH, 0, c->stream>>>(in, c->vx, c->fflag, L);
+    c->n_launches += 1;
     FS_CUDA(cudaGetLastError());
     return FS_OK;
 }
@@ -604,6 +639,7 @@ int launch_nu_grad(fs_ctx *c, CF3 uv, double *dot)
 {
     const Layout &L = c->L;
     k_nu_grad<<<grid_blocks(c, L.S, TH), TH, 0, c->stream>>>(c->vx, uv, c->fflag, L, c->scal + 3, c->partials);
+    c->n_launches += 1;
     FS_CUDA(cudaGetLastError());
     SolveScal m;
     int rc = read_scal(c, 3, &m);
@@ -627,6 +663,7 @@ int launch_loss(fs_ctx *c, CF3 u, CF3 t, int kind, double alpha, double beta, F3
     const float bo = nbf > 0 ? (float)(beta / (double)nbf) : 0.f;
     k_loss_face<<<bs, TH, 0, c->stream>>>(u, t, c->cflag, c->fflag, bandbit, gcr, use_cos ? 1 : 0, g, L, bo,
                                          c->scal + 2, c->partials);
+    c->n_launches += use_cos ? 2 : 1;
     FS_CUDA(cudaGetLastError());
     SolveScal a, b;
     int rc = read_scal(c, 2, &a);

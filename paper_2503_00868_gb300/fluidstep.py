@@ -56,6 +56,11 @@ class fs_layout_t(C.Structure):
                 ("rows", C.c_int), ("planes", C.c_int), ("nelems", C.c_longlong)]
 
 
+class fs_kernel_time(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_longlong), ("total_ms", C.c_double),
+                ("bytes", C.c_double)]
+
+
 class fs_mac(C.Structure):
     _fields_ = [("u", C.c_void_p), ("v", C.c_void_p), ("w", C.c_void_p)]
 
@@ -76,6 +81,8 @@ _SIGS = {
                          C.POINTER(C.c_double), C.POINTER(fs_stats)], C.c_int),
     "fs_loss_grad": ([C.c_void_p, C.POINTER(fs_mac), C.POINTER(fs_mac), C.c_int, C.c_double, C.c_double,
                       C.POINTER(C.c_double), C.POINTER(fs_mac)], C.c_int),
+    "fs_profile": ([C.c_void_p, C.c_int], C.c_int),
+    "fs_profile_read": ([C.c_void_p, C.POINTER(fs_kernel_time), C.c_int, C.POINTER(C.c_int)], C.c_int),
     "fs_last_error": ([], C.c_char_p),
 }
 
@@ -195,6 +202,19 @@ def fs_loss_grad(ctx: int, u: Mac, target: Mac, mask_kind: int = FS_MASK_SURFACE
     return loss.value
 
 
+def fs_profile(ctx: int, period: int) -> None:
+    """period >= 1: time every period-th CG iteration (and count launches); 0: off."""
+    _check(load().fs_profile(C.c_void_p(ctx), int(period)), (FS_OK,))
+
+
+def fs_profile_read(ctx: int):
+    """Per-kernel timing since fs_profile(ctx, True): {name: (launches, total_ms, bytes)}."""
+    buf = (fs_kernel_time * 16)()
+    n = C.c_int(0)
+    _check(load().fs_profile_read(C.c_void_p(ctx), buf, 16, C.byref(n)), (FS_OK,))
+    return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms, buf[i].bytes) for i in range(n.value)}
+
+
 def fs_last_error() -> str:
     return load().fs_last_error().decode()
 
@@ -285,6 +305,12 @@ class Grid:
 
     def adjoint_step(self, u_in: Mac, g_out: Mac, g_in: Mac, u_visc: Optional[Mac] = None):
         return fs_adjoint_step(self.ctx, u_in, u_visc, g_out, g_in)
+
+    def profile(self, period: int = 1):
+        fs_profile(self.ctx, period)
+
+    def profile_read(self):
+        return fs_profile_read(self.ctx)
 
     def loss_grad(self, u: Mac, target: Mac, mask_kind=FS_MASK_SURFACE, alpha=0.0, beta=1.0,
                   g: Optional[Mac] = None) -> float:
