@@ -219,6 +219,33 @@ typedef struct {
 int fs_profile(fs_ctx *c, int enable);
 int fs_profile_read(fs_ctx *c, fs_kernel_time *out, int max, int *count);
 
+/* Pressure projection that allocates nothing. The paper has no counterpart: this
+ * serves callers that cannot allocate device memory (code running where a CUDA
+ * allocation is forbidden or would break a fixed memory budget, such as a plugin
+ * inside an application that owns the device allocator, or a real-time loop that
+ * must not call cudaMalloc after start-up).
+ *
+ * It computes what fs_project computes with the Jacobi preconditioner, without a
+ * context: u (DEVICE field in the layout fs_init_grid would use for this size:
+ * pitch = nx + 1 rounded up to a multiple of 4, rows = ny + 1, planes = nz + 1)
+ * is projected in place; q_out (nullable DEVICE cell array, same layout)
+ * receives q; cell_type_dense is as in fs_set_mask; every fixed face keeps the
+ * value it holds in u. tol is the relative residual target, maxit the iteration
+ * cap, dx the cell size (it scales q only). All scratch lives in one static
+ * device array of 16 MiB that every GPU loading the library holds until the
+ * process exits; every grid up to 64 x 64 x 64 fits, a larger one is rejected
+ * with FS_EINVAL (and a message giving the bytes it needs) before any work.
+ * The call never calls cudaMalloc, cudaFree or any other allocating routine.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture. Every call shares the one array, and each clears the parts
+ * that must start at zero: calls that overlap on the GPU (on different streams or
+ * host threads, for the same device) race and corrupt each other's results.
+ * The call synchronises `cuda_stream` before it returns. */
+int fs_project_noalloc(int nx, int ny, int nz, const uint8_t *cell_type_dense, fs_mac *u, float *q_out,
+                       double dx, double tol, int maxit, void *cuda_stream, fs_stats *st);
+
 /* The per-thread message of the last failing call ("" if none). */
 const char *fs_last_error(void);
 

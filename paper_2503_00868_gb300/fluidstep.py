@@ -83,6 +83,8 @@ _SIGS = {
                       C.POINTER(C.c_double), C.POINTER(fs_mac)], C.c_int),
     "fs_profile": ([C.c_void_p, C.c_int], C.c_int),
     "fs_profile_read": ([C.c_void_p, C.POINTER(fs_kernel_time), C.c_int, C.POINTER(C.c_int)], C.c_int),
+    "fs_project_noalloc": ([C.c_int, C.c_int, C.c_int, C.c_void_p, C.POINTER(fs_mac), C.c_void_p, C.c_double,
+                            C.c_double, C.c_int, C.c_void_p, C.POINTER(fs_stats)], C.c_int),
     "fs_last_error": ([], C.c_char_p),
 }
 
@@ -213,6 +215,22 @@ def fs_profile_read(ctx: int):
     n = C.c_int(0)
     _check(load().fs_profile_read(C.c_void_p(ctx), buf, 16, C.byref(n)), (FS_OK,))
     return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms, buf[i].bytes) for i in range(n.value)}
+
+
+def fs_project_noalloc(nx: int, ny: int, nz: int, cell_type_dense: torch.Tensor, u: Mac,
+                       q_out: Optional[torch.Tensor] = None, dx: float = 1.0, tol: float = 1e-6,
+                       maxit: int = 20000, stream: Optional[int] = None):
+    """Projection for callers that cannot allocate device memory: the library
+    uses a fixed static scratch array (grids up to 64^3) instead of a context.
+    The tensors passed in are the caller's; this wrapper allocates nothing."""
+    if cell_type_dense.dtype != torch.uint8 or not cell_type_dense.is_cuda or not cell_type_dense.is_contiguous():
+        raise ValueError("cell types must be a contiguous uint8 CUDA tensor")
+    st = fs_stats()
+    s = torch.cuda.current_stream().cuda_stream if stream is None else stream
+    q = C.c_void_p(q_out.data_ptr()) if q_out is not None else None
+    rc = _check(load().fs_project_noalloc(nx, ny, nz, C.c_void_p(cell_type_dense.data_ptr()), _ref(_mac(u)), q,
+                                          dx, tol, maxit, C.c_void_p(s), C.byref(st)))
+    return rc, st.as_dict()
 
 
 def fs_last_error() -> str:
