@@ -2,6 +2,7 @@
 // context memory and the order of kernels for one step, its adjoint and the loss
 // (arXiv 2503.00868: Eq. eq::v split as in Sec. 3.2.2, back-traced convection of
 // Sec. 3.4.1, loss of Eq. eq::optLoss in Sec. 3.4.2).
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -152,7 +153,8 @@ static void free_ctx(fs_ctx *c)
     prof_destroy(c);
     void *ptrs[] = {c->cflag, c->fflag, c->bc, c->dsum, c->pb, c->pr, c->pp[0], c->pp[1], c->pq, c->px, c->pz,
                     c->vx, c->vr, c->vp[0], c->vp[1], c->vq, c->fu[0], c->fu[1], c->fu[2], c->fg[0], c->fg[1],
-                    c->fg[2], c->gc[0], c->gc[1], c->gc[2], c->mic_prec, c->scal, c->partials, c->err_word};
+                    c->fg[2], c->gc[0], c->gc[1], c->gc[2], c->mic_prec, c->scal, c->partials, c->err_word,
+                    c->act_cell, c->act_face, c->list_cell, c->list_face};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->scal_host) cudaFreeHost(c->scal_host);
@@ -304,8 +306,15 @@ int fs_init_grid(fs_ctx **out, int nx, int ny, int nz, const fs_params *p, void 
         ALLOC(c->gc[k], cb);
     }
     ALLOC(c->mic_prec, cb);
+    c->tm_cell = make_tilemap(L, 1, c->num_sms);
+    c->tm_face = make_tilemap(L, 3, c->num_sms);
+    ALLOC(c->act_cell, (size_t)c->tm_cell.nblocks);
+    ALLOC(c->act_face, (size_t)c->tm_face.nblocks);
+    ALLOC(c->list_cell, (size_t)c->tm_cell.nblocks * sizeof(int));
+    ALLOC(c->list_face, (size_t)c->tm_face.nblocks * sizeof(int));
+    const int red_blocks = std::max(c->max_blocks, std::max(c->tm_cell.nblocks, c->tm_face.nblocks));
     ALLOC(c->scal, 4 * sizeof(SolveScal));
-    ALLOC(c->partials, (size_t)c->max_blocks * 8 * sizeof(double));
+    ALLOC(c->partials, (size_t)red_blocks * 8 * sizeof(double));
     ALLOC(c->err_word, 16);
 #undef ALLOC
     if (cudaHostAlloc((void **)&c->scal_host, 4 * sizeof(SolveScal), cudaHostAllocDefault) != cudaSuccess) {

@@ -61,6 +61,29 @@ struct Layout {
     __host__ __device__ int face_origin(int c) const { return PL + c * (S + PL); }
 };
 
+// Tiling of a guarded space for the z-marching stencil kernels: `nvol` volumes
+// (1 for cell space, 3 for face space) of P x R x Z elements starting at
+// origin0 + v * vstride; tiles of TILE_X x TILE_Y columns, `tz` planes per chunk.
+// Block b covers tile (tx, ty) of chunk ch of volume v, x fastest.
+constexpr int TILE_X = 128;  // elements (32 threads x 4)
+constexpr int TILE_Y = 8;
+
+struct TileMap {
+    int ntx, nty, tz, nch, nvol;
+    int P, R, Z, PL;
+    int origin0, vstride;
+    int nblocks;
+    __host__ __device__ void decode(int b, int &v, int &ch, int &ty, int &tx) const
+    {
+        tx = b % ntx;
+        b /= ntx;
+        ty = b % nty;
+        b /= nty;
+        ch = b % nch;
+        v = b / nch;
+    }
+};
+
 struct F3 {
     float *c[3];
 };
@@ -106,6 +129,10 @@ struct fs_ctx {
     int max_blocks;
     unsigned *err_word;         // device error word of bounded waits
     long long n_fluid;          // fluid faces
+    fs::TileMap tm_cell, tm_face;    // z-marching tilings of cell and face space
+    uint8_t *act_cell, *act_face;    // per tile block: 1 if it holds an active element
+    int *list_cell, *list_face;      // the active tiles, in tile order
+    int nact_cell, nact_face;
 
     // per-kernel timing (fs_profile)
     int prof_on;
@@ -156,14 +183,16 @@ struct KSum {
 // Sums K doubles over the grid. Each block writes its partials; the last block
 // to arrive adds the partials in block order (so the result does not depend on
 // scheduling) and returns true in all its threads with the totals in `tot`
-// (valid in thread 0). Requires blockDim.x a multiple of 32, <= 1024.
+// (valid in thread 0). Requires blockDim.x * blockDim.y a multiple of 32,
+// <= 1024, and a one-dimensional grid.
 template <int K>
 __device__ __forceinline__ bool grid_reduce(double (&v)[K], double *partials, unsigned *ticket,
                                             double (&tot)[K])
 {
     __shared__ double sh[32][K];
     __shared__ int last;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x, nthr = blockDim.x * blockDim.y;
+    const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
 #pragma unroll
     for (int k = 0; k < K; k++) v[k] = warp_sum(v[k]);
     if (lane == 0)
@@ -189,7 +218,7 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[K], double *partials, un
 #pragma unroll
     for (int k = 0; k < K; k++) {
         double t = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+        for (int b = tid; b < (int)gridDim.x; b += nthr)
             t += __ldcg(&partials[(size_t)b * K + k]);
         tot[k] = warp_sum(t);
     }
@@ -198,7 +227,7 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[K], double *partials, un
 #pragma unroll
         for (int k = 0; k < K; k++) sh[wid][k] = tot[k];
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
 #pragma unroll
         for (int k = 0; k < K; k++) {
             double t = 0.0;
@@ -213,6 +242,7 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[K], double *partials, un
 // ---- launchers implemented in the .cu files --------------------------------
 // fs_mask.cu
 int build_mask(fs_ctx *c, const uint8_t *types_dense, const fs_mac *bc);
+TileMap make_tilemap(const Layout &L, int nvol, int num_sms);
 // fs_pcg.cu
 int solve_pressure(fs_ctx *c, fs_stats *st);             // pb -> px
 int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st);  // vx (guess, rhs) -> vx

@@ -2,6 +2,8 @@
 // face values, Dirichlet sums of the viscosity operator, band and singularity
 // counts. Runs once per mask (Sec. 3.4.2: "grid types of surface, occupation,
 // or empty").
+#include <vector>
+
 #include "fs_internal.cuh"
 
 namespace fs {
@@ -147,7 +149,45 @@ __global__ void k_counts(Layout L, const uint8_t *__restrict__ cflag, const uint
     }
 }
 
+// act[b] = 1 for every tile block of `m` that holds an element with a bit of
+// `mask` set in its flag byte.
+__global__ void k_tile_activity(const uint8_t *__restrict__ fl, uint8_t mask, TileMap m, uint8_t *act)
+{
+    const long long per_vol = (long long)m.PL * m.Z;
+    const long long total = per_vol * m.nvol;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int v = (int)(t / per_vol);
+        const int idx = (int)(t - (long long)v * per_vol);
+        if (!(fl[m.origin0 + (long long)v * m.vstride + idx] & mask)) continue;
+        const int i = idx % m.P, row = idx / m.P, j = row % m.R, k = row / m.R;
+        const int b = ((v * m.nch + k / m.tz) * m.nty + j / TILE_Y) * m.ntx + i / TILE_X;
+        act[b] = 1;
+    }
+}
+
 }  // namespace
+
+TileMap make_tilemap(const Layout &L, int nvol, int num_sms)
+{
+    TileMap m;
+    m.P = L.P;
+    m.R = L.R;
+    m.Z = L.Z;
+    m.PL = L.PL;
+    m.nvol = nvol;
+    m.origin0 = L.PL;
+    m.vstride = L.S + L.PL;
+    m.ntx = (L.P + TILE_X - 1) / TILE_X;
+    m.nty = (L.R + TILE_Y - 1) / TILE_Y;
+    // one plane per block: many small independent blocks
+    (void)num_sms;
+    const long long cols = (long long)m.ntx * m.nty * nvol;
+    m.tz = 1;
+    m.nch = L.Z;
+    m.nblocks = (int)(cols * m.nch);
+    return m;
+}
 
 int build_mask(fs_ctx *c, const uint8_t *types_dense, const fs_mac *bc)
 {
@@ -169,6 +209,13 @@ int build_mask(fs_ctx *c, const uint8_t *types_dense, const fs_mac *bc)
     k_face_count<<<grid_blocks(c, L.nF, th), th, 0, c->stream>>>(L, c->fflag, bcu, c->bc,
                                                                   bc ? c->dsum : nullptr);
     k_counts<<<grid_blocks(c, L.nF, th), th, 0, c->stream>>>(L, c->cflag, c->fflag, cnt);
+    if (c->act_cell && c->act_face) {
+        FS_CUDA(cudaMemsetAsync(c->act_cell, 0, (size_t)c->tm_cell.nblocks, c->stream));
+        FS_CUDA(cudaMemsetAsync(c->act_face, 0, (size_t)c->tm_face.nblocks, c->stream));
+        k_tile_activity<<<grid_blocks(c, L.S, th), th, 0, c->stream>>>(c->cflag, CF_LIQ, c->tm_cell, c->act_cell);
+        k_tile_activity<<<grid_blocks(c, 3LL * L.S, th), th, 0, c->stream>>>(c->fflag, FF_FLUID, c->tm_face,
+                                                                             c->act_face);
+    }
     FS_CUDA(cudaGetLastError());
     unsigned long long h[4];
     unsigned herr = 0;
@@ -176,6 +223,23 @@ int build_mask(fs_ctx *c, const uint8_t *types_dense, const fs_mac *bc)
     FS_CUDA(cudaMemcpyAsync(&herr, c->err_word, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     FS_CUDA(cudaStreamSynchronize(c->stream));
     if (herr) return set_error(FS_EINVAL, "fs_set_mask: a cell type is not 0 (air), 1 (liquid) or 2 (solid)");
+    if (c->act_cell && c->act_face) {
+        // ordered lists of the active tiles (set-up work, on the host)
+        struct Space { const uint8_t *act; int *list; int n; int *nact; } sp[2] = {
+            {c->act_cell, c->list_cell, c->tm_cell.nblocks, &c->nact_cell},
+            {c->act_face, c->list_face, c->tm_face.nblocks, &c->nact_face}};
+        for (auto &s : sp) {
+            std::vector<uint8_t> act((size_t)s.n);
+            FS_CUDA(cudaMemcpy(act.data(), s.act, (size_t)s.n, cudaMemcpyDeviceToHost));
+            std::vector<int> list;
+            list.reserve((size_t)s.n);
+            for (int b = 0; b < s.n; b++)
+                if (act[(size_t)b]) list.push_back(b);
+            *s.nact = (int)list.size();
+            if (!list.empty())
+                FS_CUDA(cudaMemcpy(s.list, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice));
+        }
+    }
     c->n_liquid = (long long)h[0];
     c->n_band_cells[FS_MASK_SURFACE] = (long long)h[1];
     c->n_band_cells[FS_MASK_OCCUPIED] = (long long)h[0];

@@ -9,6 +9,7 @@
 // each reducing kernel updates them, so a batch of iterations runs without a
 // host round trip; the host reads the convergence flag every `check_every`
 // iterations. Once `done` is set every later kernel of the batch returns at once.
+#include <algorithm>
 #include <cmath>
 
 #include "fs_internal.cuh"
@@ -38,9 +39,11 @@ __device__ __forceinline__ float inv_diag(uint8_t f, float cc)
     return d > 0.f ? __frcp_rn(d) : 0.f;
 }
 
-// p_new = z + beta p_old (z = r / diag for Jacobi, else the stored z), then
-// q = A p_new and the partial sums of p_new . q. alpha = r.z / p.q at the end.
-template <class Op, bool JAC>
+// Flat versions of the two CG kernels, for a context without tile maps.
+// p_new = z + beta p_old (z the stored preconditioned residual; for Jacobi the
+// solver keeps z = D^-1 r itself), then q = A p_new and the partial sums of
+// p_new . q. alpha = r.z / p.q at the end.
+template <class Op>
 __global__ void __launch_bounds__(TH) k_spmv(const float *__restrict__ src, const float *__restrict__ pold,
                                              float *__restrict__ pnew, float *__restrict__ q,
                                              const uint8_t *__restrict__ fl, int n, int P, int PL, float cc,
@@ -54,10 +57,7 @@ __global__ void __launch_bounds__(TH) k_spmv(const float *__restrict__ src, cons
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
         const uint8_t f = fl[t];
         if (!(f & Op::ACTIVE)) continue;
-        auto pn = [&](int u) -> float {
-            float z = JAC ? __ldg(src + u) * inv_diag<Op>(__ldg(fl + u), cc) : __ldg(src + u);
-            return z + beta * __ldg(pold + u);
-        };
+        auto pn = [&](int u) -> float { return __ldg(src + u) + beta * __ldg(pold + u); };
         const float pc = pn(t);
         const float nb = (pn(t - 1) + pn(t + 1)) + (pn(t - P) + pn(t + P)) + (pn(t - PL) + pn(t + PL));
         const float qv = Op::diag(f, cc) * pc - Op::offc(cc) * nb;
@@ -98,13 +98,20 @@ __global__ void __launch_bounds__(TH) k_update(float *__restrict__ x, float *__r
         float4 xv = x4[t], rv = r4[t];
         const float4 pv = __ldg(p4 + t), qv = __ldg(q4 + t);
         xv.x += alpha * pv.x; xv.y += alpha * pv.y; xv.z += alpha * pv.z; xv.w += alpha * pv.w;
-        rv.x -= alpha * qv.x; rv.y -= alpha * qv.y; rv.z -= alpha * qv.z; rv.w -= alpha * qv.w;
+        if (JAC) {
+            // scaled residual z = D^-1 r: z -= alpha D^-1 Ap; r.z = sum d z^2, r.r = sum (d z)^2
+            rv.x -= alpha * inv_diag<Op>(fv.x, cc) * qv.x; rv.y -= alpha * inv_diag<Op>(fv.y, cc) * qv.y;
+            rv.z -= alpha * inv_diag<Op>(fv.z, cc) * qv.z; rv.w -= alpha * inv_diag<Op>(fv.w, cc) * qv.w;
+            const float ax = Op::diag(fv.x, cc) * rv.x, ay = Op::diag(fv.y, cc) * rv.y;
+            const float az = Op::diag(fv.z, cc) * rv.z, aw = Op::diag(fv.w, cc) * rv.w;
+            rz.add(ax * rv.x + ay * rv.y + az * rv.z + aw * rv.w);
+            rr.add(ax * ax + ay * ay + az * az + aw * aw);
+        } else {
+            rv.x -= alpha * qv.x; rv.y -= alpha * qv.y; rv.z -= alpha * qv.z; rv.w -= alpha * qv.w;
+            rr.add(rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w);
+        }
         x4[t] = xv;
         r4[t] = rv;
-        rr.add(rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w);
-        if (JAC)
-            rz.add(rv.x * rv.x * inv_diag<Op>(fv.x, cc) + rv.y * rv.y * inv_diag<Op>(fv.y, cc) +
-                   rv.z * rv.z * inv_diag<Op>(fv.z, cc) + rv.w * rv.w * inv_diag<Op>(fv.w, cc));
     }
     double v[2] = {rr.value(), rz.value()}, tot[2];
     if (grid_reduce<2>(v, partials, &s->ticket, tot) && threadIdx.x == 0) {
@@ -172,15 +179,19 @@ __global__ void __launch_bounds__(TH) k_pois_init(const float *__restrict__ b, f
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += gridDim.x * blockDim.x) {
         const float4 v = __ldg(b4 + t);
-        reinterpret_cast<float4 *>(r)[t] = v;
         reinterpret_cast<float4 *>(x)[t] = zero;
         reinterpret_cast<float4 *>(p0)[t] = zero;
         reinterpret_cast<float4 *>(p1)[t] = zero;
         bb.add(v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w);
         if (JAC) {
+            // Jacobi keeps the scaled residual z = D^-1 r
             const uchar4 fv = f4[t];
-            rz.add(v.x * v.x * inv_diag<PoisOp>(fv.x, 0.f) + v.y * v.y * inv_diag<PoisOp>(fv.y, 0.f) +
-                   v.z * v.z * inv_diag<PoisOp>(fv.z, 0.f) + v.w * v.w * inv_diag<PoisOp>(fv.w, 0.f));
+            const float4 z = make_float4(v.x * inv_diag<PoisOp>(fv.x, 0.f), v.y * inv_diag<PoisOp>(fv.y, 0.f),
+                                         v.z * inv_diag<PoisOp>(fv.z, 0.f), v.w * inv_diag<PoisOp>(fv.w, 0.f));
+            reinterpret_cast<float4 *>(r)[t] = z;
+            rz.add(v.x * z.x + v.y * z.y + v.z * z.z + v.w * z.w);
+        } else {
+            reinterpret_cast<float4 *>(r)[t] = v;
         }
     }
     double v[2] = {bb.value(), rz.value()}, tot[2];
@@ -210,7 +221,7 @@ __global__ void __launch_bounds__(TH) k_helm_init(const float *__restrict__ x, c
             rr.add(rv * rv);
             rz.add(rv * rv * inv_diag<HelmOp>(f, cc));
         }
-        r[t] = rv;
+        r[t] = rv * inv_diag<HelmOp>(f, cc);  // Jacobi keeps the scaled residual z = D^-1 r
         p0[t] = 0.f;
         p1[t] = 0.f;
     }
@@ -424,6 +435,22 @@ __global__ void __launch_bounds__(TH) k_loss_face(CF3 u, CF3 tg, const uint8_t *
 }
 
 }  // namespace
+}  // namespace fs
+
+#include "fs_stencil.cuh"
+
+namespace fs {
+
+// Resident 256-thread blocks per SM of a tiled kernel (the persistent grid).
+static int resident_blocks(const void *fn)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, 0) != cudaSuccess || nb < 1) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    return nb;
+}
 
 int read_scal(fs_ctx *c, int which, SolveScal *out)
 {
@@ -487,18 +514,31 @@ int solve_pressure(fs_ctx *c, fs_stats *st)
     SolveScal h;
     const double by_spmv = (double)L.nC + 16.0 * (double)c->n_liquid;
     const double by_upd = (double)L.nC + 24.0 * (double)c->n_liquid;
+    const bool tiled = c->act_cell != nullptr;
+    const TileMap &tm = c->tm_cell;
+    const dim3 tdim(TILE_X / 4, TILE_Y);
+    const int tgrid = std::max(1, std::min(c->nact_cell, c->num_sms * resident_blocks((const void *)k_spmv_p<PoisOp>)));
+    const int ugrid = std::max(1, std::min(c->nact_cell, c->num_sms * resident_blocks((const void *)k_update_p<PoisOp, true>)));
     for (;;) {
         for (int b = 0; b < c->prm.check_every; b++) {
             const bool samp = c->prof_on && (b % c->prof_period) == 0;
             cudaEvent_t e0 = samp ? prof_mark(c) : nullptr;
-            if (jac)
-                k_spmv<PoisOp, true><<<bs, TH, 0, c->stream>>>(c->pr, c->pp[cur], c->pp[cur ^ 1], c->pq, c->cflag,
-                                                               L.nC, L.P, L.PL, 0.f, s, c->partials);
+            const float *zsrc = jac ? c->pr : c->pz;
+            if (tiled)
+                k_spmv_p<PoisOp><<<tgrid, tdim, 0, c->stream>>>(zsrc, c->pp[cur], c->pp[cur ^ 1], c->pq,
+                                                                     c->cflag, c->list_cell, c->nact_cell, tm, 0.f, s, c->partials);
             else
-                k_spmv<PoisOp, false><<<bs, TH, 0, c->stream>>>(c->pz, c->pp[cur], c->pp[cur ^ 1], c->pq,
-                                                                c->cflag, L.nC, L.P, L.PL, 0.f, s, c->partials);
+                k_spmv<PoisOp><<<bs, TH, 0, c->stream>>>(zsrc, c->pp[cur], c->pp[cur ^ 1], c->pq, c->cflag, L.nC,
+                                                         L.P, L.PL, 0.f, s, c->partials);
             cudaEvent_t e1 = samp ? prof_mark(c) : nullptr, e2 = samp ? prof_mark(c) : nullptr;
-            if (jac)
+            if (tiled) {
+                if (jac)
+                    k_update_p<PoisOp, true><<<ugrid, tdim, 0, c->stream>>>(
+                        c->px, c->pr, c->pp[cur ^ 1], c->pq, c->cflag, c->list_cell, c->nact_cell, tm, 0.f, s, c->partials);
+                else
+                    k_update_p<PoisOp, false><<<ugrid, tdim, 0, c->stream>>>(
+                        c->px, c->pr, c->pp[cur ^ 1], c->pq, c->cflag, c->list_cell, c->nact_cell, tm, 0.f, s, c->partials);
+            } else if (jac)
                 k_update<PoisOp, true><<<b4, TH, 0, c->stream>>>(c->px, c->pr, c->pp[cur ^ 1], c->pq, c->cflag,
                                                                  n4, 0.f, s, c->partials);
             else
@@ -564,15 +604,28 @@ int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st)
     SolveScal h;
     const double by_spmv = (double)L.nF + 16.0 * (double)c->n_fluid;
     const double by_upd = (double)L.nF + 24.0 * (double)c->n_fluid;
+    const bool tiled = c->act_face != nullptr;
+    const TileMap &tm = c->tm_face;
+    const dim3 tdim(TILE_X / 4, TILE_Y);
+    const int tgrid = std::max(1, std::min(c->nact_face, c->num_sms * resident_blocks((const void *)k_spmv_p<HelmOp>)));
+    const int ugrid = std::max(1, std::min(c->nact_face, c->num_sms * resident_blocks((const void *)k_update_p<HelmOp, true>)));
     for (;;) {
         for (int b = 0; b < c->prm.check_every; b++) {
             const bool samp = c->prof_on && (b % c->prof_period) == 0;
             cudaEvent_t e0 = samp ? prof_mark(c) : nullptr;
-            k_spmv<HelmOp, true><<<bs, TH, 0, c->stream>>>(c->vr, c->vp[cur], c->vp[cur ^ 1], c->vq, c->fflag,
-                                                           L.nF, L.P, L.PL, cc, s, c->partials);
+            if (tiled)
+                k_spmv_p<HelmOp><<<tgrid, tdim, 0, c->stream>>>(c->vr, c->vp[cur], c->vp[cur ^ 1], c->vq,
+                                                                     c->fflag, c->list_face, c->nact_face, tm, cc, s, c->partials);
+            else
+                k_spmv<HelmOp><<<bs, TH, 0, c->stream>>>(c->vr, c->vp[cur], c->vp[cur ^ 1], c->vq, c->fflag, L.nF,
+                                                         L.P, L.PL, cc, s, c->partials);
             cudaEvent_t e1 = samp ? prof_mark(c) : nullptr, e2 = samp ? prof_mark(c) : nullptr;
-            k_update<HelmOp, true><<<b4, TH, 0, c->stream>>>(c->vx, c->vr, c->vp[cur ^ 1], c->vq, c->fflag, n4,
-                                                             cc, s, c->partials);
+            if (tiled)
+                k_update_p<HelmOp, true><<<ugrid, tdim, 0, c->stream>>>(
+                    c->vx, c->vr, c->vp[cur ^ 1], c->vq, c->fflag, c->list_face, c->nact_face, tm, cc, s, c->partials);
+            else
+                k_update<HelmOp, true><<<b4, TH, 0, c->stream>>>(c->vx, c->vr, c->vp[cur ^ 1], c->vq, c->fflag, n4,
+                                                                 cc, s, c->partials);
             cudaEvent_t e3 = samp ? prof_mark(c) : nullptr;
             prof_add(c, K_V_SPMV, e0, e1, by_spmv);
             prof_add(c, K_V_UPDATE, e2, e3, by_upd);
