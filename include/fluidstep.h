@@ -197,6 +197,15 @@ int fs_adjoint_step(fs_ctx *c, const fs_mac *u_in, const fs_mac *u_visc,
 int fs_loss_grad(fs_ctx *c, const fs_mac *u, const fs_mac *target, int mask_kind,
                  double alpha, double beta, double *loss, fs_mac *g);
 
+/* Apply the pressure preconditioner selected in the parameters to one vector:
+ * z = M^-1 r on the liquid cells (zero elsewhere). Jacobi: M = diag(L_p);
+ * MIC(0): M = L L^T with the modified incomplete Cholesky factor of L_p (Bridson,
+ * cited by the paper for its pressure projection, Sec. 3.2.2), factored on first
+ * use after fs_set_mask, computed in lexicographic order (x fastest).
+ * r, z: DEVICE cell arrays in the library layout, must not alias.
+ * Returns FS_ETIMEOUT if a bounded device wait of the MIC(0) wavefront ran out. */
+int fs_precond_apply(fs_ctx *c, const float *r, float *z);
+
 /* Per-kernel timing. fs_profile(c, k) with k >= 1 resets the counters and from
  * then on brackets launches of the solver kernels (every k-th CG iteration of
  * each batch), the advection kernels and the preconditioners with CUDA events on

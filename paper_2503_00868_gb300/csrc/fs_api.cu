@@ -154,7 +154,8 @@ static void free_ctx(fs_ctx *c)
     void *ptrs[] = {c->cflag, c->fflag, c->bc, c->dsum, c->pb, c->pr, c->pp[0], c->pp[1], c->pq, c->px, c->pz,
                     c->vx, c->vr, c->vp[0], c->vp[1], c->vq, c->fu[0], c->fu[1], c->fu[2], c->fg[0], c->fg[1],
                     c->fg[2], c->gc[0], c->gc[1], c->gc[2], c->mic_prec, c->scal, c->partials, c->err_word,
-                    c->act_cell, c->act_face, c->list_cell, c->list_face};
+                    c->act_cell, c->act_face, c->list_cell, c->list_face, c->py, c->mic_order,
+                    c->mic_tact, c->mic_tflag, c->mic_next};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->scal_host) cudaFreeHost(c->scal_host);
@@ -306,6 +307,12 @@ int fs_init_grid(fs_ctx **out, int nx, int ny, int nz, const fs_params *p, void 
         ALLOC(c->gc[k], cb);
     }
     ALLOC(c->mic_prec, cb);
+    ALLOC(c->py, cb);
+    c->mic_ntiles = ((nx + 7) / 8) * ((ny + 7) / 8) * ((nz + 7) / 8);
+    ALLOC(c->mic_order, (size_t)c->mic_ntiles * sizeof(int));
+    ALLOC(c->mic_tact, (size_t)c->mic_ntiles);
+    ALLOC(c->mic_tflag, (size_t)c->mic_ntiles * sizeof(int));
+    ALLOC(c->mic_next, 16);
     c->tm_cell = make_tilemap(L, 1, c->num_sms);
     c->tm_face = make_tilemap(L, 3, c->num_sms);
     ALLOC(c->act_cell, (size_t)c->tm_cell.nblocks);
@@ -477,6 +484,16 @@ int fs_adjoint_step(fs_ctx *c, const fs_mac *u_in, const fs_mac *u_visc, const f
     FS_CUDA(cudaStreamSynchronize(c->stream));
     prof_flush(c);
     return s->status;
+}
+
+int fs_precond_apply(fs_ctx *c, const float *r, float *z)
+{
+    int rc = need_mask(c);
+    if (rc) return rc;
+    g_err[0] = 0;
+    if (!r || !z) return set_error(FS_EINVAL, "NULL argument");
+    if (r == z) return set_error(FS_EINVAL, "r and z must not alias");
+    return precond_apply_public(c, r, z);
 }
 
 int fs_loss_grad(fs_ctx *c, const fs_mac *u, const fs_mac *target, int mask_kind, double alpha, double beta,

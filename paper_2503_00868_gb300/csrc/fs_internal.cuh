@@ -120,7 +120,14 @@ struct fs_ctx {
 
     // MIC(0)
     float *mic_prec;      // cell space
-    int mic_ready;
+    float *py;            // cell space: forward-substitution result
+    int mic_ready;        // factor valid for the current mask and tau, sigma
+    int mic_sched_ready;  // tile order valid for the current mask
+    int *mic_order;       // liquid 8^3 tiles by tile level
+    uint8_t *mic_tact;    // per tile: holds liquid
+    int *mic_tflag;       // per tile: epoch of its last completed sweep
+    int *mic_next;        // work counter of the running sweep
+    int mic_n, mic_epoch, mic_ntiles;
 
     // reductions
     fs::SolveScal *scal;        // device [4]: 0 pressure, 1 viscosity, 2 misc, 3 misc
@@ -246,6 +253,7 @@ TileMap make_tilemap(const Layout &L, int nvol, int num_sms);
 // fs_pcg.cu
 int solve_pressure(fs_ctx *c, fs_stats *st);             // pb -> px
 int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st);  // vx (guess, rhs) -> vx
+int precond_apply_public(fs_ctx *c, const float *r, float *z);  // public cell arrays
 int launch_divergence(fs_ctx *c, CF3 u);                 // u -> pb, with bb/mean handling
 int launch_grad_subtract(fs_ctx *c, CF3 in, F3 out, float *q_out);
 int launch_compose(fs_ctx *c, F3 out);                   // vx + bc -> full field

@@ -483,6 +483,22 @@ int launch_divergence(fs_ctx *c, CF3 u)
     return FS_OK;
 }
 
+// When the pressure operator is singular (liquid touching no air), the
+// preconditioned residual is made mean-free over the liquid, so every search
+// direction stays in the range of the operator (the preconditioner becomes
+// P M^-1 P with P the mean-removing projector, still SPD on that range).
+static int remove_null_mode(fs_ctx *c, float *z)
+{
+    if (!c->singular) return FS_OK;
+    const Layout &L = c->L;
+    const int bs = grid_blocks(c, L.nC, TH);
+    k_liquid_sum<<<bs, TH, 0, c->stream>>>(z, c->cflag, L.nC, c->scal + 3, c->partials);
+    k_sub_liquid_mean<<<bs, TH, 0, c->stream>>>(z, c->cflag, L.nC, c->scal + 3);
+    c->n_launches += 2;
+    FS_CUDA(cudaGetLastError());
+    return FS_OK;
+}
+
 int solve_pressure(fs_ctx *c, fs_stats *st)
 {
     const Layout &L = c->L;
@@ -490,7 +506,10 @@ int solve_pressure(fs_ctx *c, fs_stats *st)
     const bool jac = c->prm.precond == FS_PRECOND_JACOBI;
     const int n4 = L.nC / 4;
     const double tol2 = c->prm.tol_p * c->prm.tol_p;
-    if (!jac && c->prm.precond == FS_PRECOND_MIC0 && !c->mic_ready) {
+    if (c->prm.precond == FS_PRECOND_LEARNED)
+        return set_error(FS_ESTATE, "the learned preconditioner has no network loaded");
+    if (!jac) FS_CUDA(cudaMemsetAsync(c->err_word, 0, sizeof(unsigned), c->stream));
+    if (!jac && !c->mic_ready) {
         int rc = mic0_factor(c);
         if (rc) return rc;
     }
@@ -502,6 +521,7 @@ int solve_pressure(fs_ctx *c, fs_stats *st)
             c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, n4, tol2, c->prm.maxit_p, s, c->partials);
         int rc = mic0_apply(c, c->pr, c->pz);
         if (rc) return rc;
+        if ((rc = remove_null_mode(c, c->pz))) return rc;
         k_rz<<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(c->pr, c->pz, n4, 1, s, c->partials);
         c->n_launches += 1;
     }
@@ -551,6 +571,7 @@ int solve_pressure(fs_ctx *c, fs_stats *st)
             if (!jac) {
                 int rc = mic0_apply(c, c->pr, c->pz);
                 if (rc) return rc;
+                if ((rc = remove_null_mode(c, c->pz))) return rc;
                 k_rz<<<b4, TH, 0, c->stream>>>(c->pr, c->pz, n4, 0, s, c->partials);
                 c->n_launches += 1;
             }
@@ -563,6 +584,17 @@ int solve_pressure(fs_ctx *c, fs_stats *st)
         if (h.done) break;
         if (launched > (long long)c->prm.maxit_p + c->prm.check_every)
             return set_error(FS_ECUDA, "pressure solve: iteration flag never set");
+    }
+    if (!jac) {
+        // a bounded wait of the MIC(0) wavefront that ran out leaves a flag
+        unsigned herr = 0;
+        FS_CUDA(cudaMemcpyAsync(&herr, c->err_word, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+        FS_CUDA(cudaStreamSynchronize(c->stream));
+        if (herr) {
+            c->mic_ready = 0;  // the factor may be incomplete: refactor on the next use
+            return set_error(FS_ETIMEOUT, "MIC(0) sweep: a wait on a predecessor tile ran out (spin_limit %d)",
+                             c->prm.spin_limit);
+        }
     }
     // true residual, then the mean-free representative of a singular solve
     k_pois_true_res<<<bs, TH, 0, c->stream>>>(c->pb, c->px, c->cflag, L.nC, L.P, L.PL, c->scal + 2, c->partials);
@@ -646,6 +678,58 @@ int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st)
         if (h.status != FS_OK && st->status == FS_OK) st->status = h.status;
     }
     return finish_status(h.status);
+}
+
+namespace {
+// public cell array -> cell space (zero off liquid), and back
+__global__ void k_cell_in(const float *__restrict__ src, float *dst, const uint8_t *__restrict__ cf, Layout L)
+{
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < L.S; idx += gridDim.x * blockDim.x)
+        dst[L.PL + idx] = (cf[L.PL + idx] & CF_LIQ) ? src[idx] : 0.f;
+}
+__global__ void k_cell_out(const float *__restrict__ src, float *dst, Layout L)
+{
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < L.S; idx += gridDim.x * blockDim.x)
+        dst[idx] = src[L.PL + idx];
+}
+__global__ void k_jacobi(const float *__restrict__ r, float *z, const uint8_t *__restrict__ cf, int n)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+        z[t] = r[t] * inv_diag<PoisOp>(cf[t], 0.f);
+}
+}  // namespace
+
+int precond_apply_public(fs_ctx *c, const float *r, float *z)
+{
+    const Layout &L = c->L;
+    const int bs = grid_blocks(c, L.S, TH);
+    k_cell_in<<<bs, TH, 0, c->stream>>>(r, c->pr, c->cflag, L);
+    c->n_launches += 1;
+    if (c->prm.precond == FS_PRECOND_JACOBI) {
+        k_jacobi<<<grid_blocks(c, L.nC, TH), TH, 0, c->stream>>>(c->pr, c->pz, c->cflag, L.nC);
+        c->n_launches += 1;
+    } else if (c->prm.precond == FS_PRECOND_MIC0) {
+        FS_CUDA(cudaMemsetAsync(c->err_word, 0, sizeof(unsigned), c->stream));
+        if (!c->mic_ready) {
+            int rc = mic0_factor(c);
+            if (rc) return rc;
+        }
+        int rc = mic0_apply(c, c->pr, c->pz);
+        if (rc) return rc;
+    } else {
+        return set_error(FS_ESTATE, "the learned preconditioner has no network loaded");
+    }
+    k_cell_out<<<bs, TH, 0, c->stream>>>(c->pz, z, L);
+    c->n_launches += 1;
+    FS_CUDA(cudaGetLastError());
+    unsigned herr = 0;
+    FS_CUDA(cudaMemcpyAsync(&herr, c->err_word, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->prm.precond == FS_PRECOND_MIC0 && herr) {
+        c->mic_ready = 0;  // the factor may be incomplete: refactor on the next use
+        return set_error(FS_ETIMEOUT, "MIC(0) sweep: a wait on a predecessor tile ran out");
+    }
+    return FS_OK;
 }
 
 int launch_grad_subtract(fs_ctx *c, CF3 in, F3 out, float *q_out)

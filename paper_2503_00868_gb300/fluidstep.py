@@ -83,6 +83,7 @@ _SIGS = {
                       C.POINTER(C.c_double), C.POINTER(fs_mac)], C.c_int),
     "fs_profile": ([C.c_void_p, C.c_int], C.c_int),
     "fs_profile_read": ([C.c_void_p, C.POINTER(fs_kernel_time), C.c_int, C.POINTER(C.c_int)], C.c_int),
+    "fs_precond_apply": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "fs_project_noalloc": ([C.c_int, C.c_int, C.c_int, C.c_void_p, C.POINTER(fs_mac), C.c_void_p, C.c_double,
                             C.c_double, C.c_int, C.c_void_p, C.POINTER(fs_stats)], C.c_int),
     "fs_last_error": ([], C.c_char_p),
@@ -217,6 +218,13 @@ def fs_profile_read(ctx: int):
     return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms, buf[i].bytes) for i in range(n.value)}
 
 
+def fs_precond_apply(ctx: int, r: torch.Tensor, z: torch.Tensor) -> None:
+    for t in (r, z):
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("r and z must be contiguous float32 CUDA tensors")
+    _check(load().fs_precond_apply(C.c_void_p(ctx), C.c_void_p(r.data_ptr()), C.c_void_p(z.data_ptr())), (FS_OK,))
+
+
 def fs_project_noalloc(nx: int, ny: int, nz: int, cell_type_dense: torch.Tensor, u: Mac,
                        q_out: Optional[torch.Tensor] = None, dx: float = 1.0, tol: float = 1e-6,
                        maxit: int = 20000, stream: Optional[int] = None):
@@ -323,6 +331,14 @@ class Grid:
 
     def adjoint_step(self, u_in: Mac, g_out: Mac, g_in: Mac, u_visc: Optional[Mac] = None):
         return fs_adjoint_step(self.ctx, u_in, u_visc, g_out, g_in)
+
+    def precond_apply(self, r: torch.Tensor, z: torch.Tensor):
+        fs_precond_apply(self.ctx, r, z)
+
+    def pack_cell(self, a) -> torch.Tensor:
+        out = self.empty_cell()
+        out[: self.nz, : self.ny, : self.nx] = torch.as_tensor(np.ascontiguousarray(a)).to(self.device, torch.float32)
+        return out
 
     def profile(self, period: int = 1):
         fs_profile(self.ctx, period)
