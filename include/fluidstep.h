@@ -118,6 +118,7 @@ typedef struct {
     double relres_p;       /* last pressure solve: recursive |r|/|b| at exit */
     double relres_v;       /* last viscosity solve: recursive |r|/|b| at exit */
     double true_relres_p;  /* last pressure solve: |b - A q|/|b| recomputed at exit */
+    int fallbacks;         /* pressure solves redone with MIC(0) after the learned one failed */
 } fs_stats;
 
 typedef struct {
@@ -205,6 +206,49 @@ int fs_loss_grad(fs_ctx *c, const fs_mac *u, const fs_mac *target, int mask_kind
  * r, z: DEVICE cell arrays in the library layout, must not alias.
  * Returns FS_ETIMEOUT if a bounded device wait of the MIC(0) wavefront ran out. */
 int fs_precond_apply(fs_ctx *c, const float *r, float *z);
+
+/* ---- learned preconditioner (Sec. 3.4.1, Fig. percnn_str_fit: a network of
+ * 3x3x3 convolutions fitted to implicit-solver output stands in for the
+ * pressure solve; here it serves as the preconditioner of flexible CG) ----------
+ * Five 3x3x3 convolutions, channels 2 -> 16 -> 16 -> 16 -> 16 -> 1, zero padding,
+ * ReLU after the first four; input channel 0 = r / s on liquid cells (s = max |r|
+ * over the liquid), channel 1 = cell type code (liquid 1, air 0, solid -1);
+ * output z = s * y on liquid cells. bf16 weights and activations, FP32 sums.
+ * Parameters are one flat FP32 vector in PyTorch Conv3d order: W1 [16][2][3][3][3],
+ * b1 [16], W2, b2, W3, b3, W4, b4 (each [16][16][3][3][3], [16]), W5 [1][16][3][3][3],
+ * b5 [1]; fs_net_param_count() gives its length. With precond = FS_PRECOND_LEARNED
+ * the pressure solve runs flexible CG (beta = -z'.Ap / p.Ap); if that does not
+ * reach the tolerance it is redone with MIC(0) and fs_stats.fallbacks counts it. */
+int fs_net_param_count(void);
+
+/* Load parameters (FP32, `count` values; HOST memory if params_on_host, else
+ * DEVICE). Allocates the network's buffers on first use (FS_ENOMEM). */
+int fs_net_load(fs_ctx *c, const float *params, int count, int params_on_host);
+
+/* Copy the current FP32 master parameters to HOST memory (`count` values). */
+int fs_net_read(fs_ctx *c, float *params_host, int count);
+
+/* z = Net(r) on liquid cells; r, z DEVICE cell arrays (library layout). */
+int fs_net_forward(fs_ctx *c, const float *r, float *z);
+
+/* Training on one (b, q) pair with L_p q = b on the context's mask (DEVICE cell
+ * arrays): loss = sum_liq (Net(b/s) - q/s)^2 / sum_liq (q/s)^2 is ADDED to *loss
+ * (host) and its gradient ADDED to the context's gradient accumulator. */
+int fs_net_grad(fs_ctx *c, const float *b, const float *q, double *loss);
+
+/* Copy the accumulated gradient to HOST memory (`count` values). */
+int fs_net_grad_read(fs_ctx *c, float *grad_host, int count);
+
+/* One Adam step (bias-corrected, `step` >= 1) on the FP32 master parameters with
+ * the accumulated gradient times grad_scale; clears the accumulator and refreshes
+ * the bf16 working copies. */
+int fs_net_adam(fs_ctx *c, double lr, double beta1, double beta2, double eps, int step, double grad_scale);
+
+/* fs_net_grad over `batch` pairs stored back to back (each `nelems` floats of the
+ * library layout) followed by fs_net_adam with grad_scale = 1/batch (beta1 0.9,
+ * beta2 0.999, eps 1e-8). *loss receives the mean loss of the batch. */
+int fs_net_train_step(fs_ctx *c, const float *b_batch, const float *q_batch, int batch, double lr, int step,
+                      double *loss);
 
 /* Per-kernel timing. fs_profile(c, k) with k >= 1 resets the counters and from
  * then on brackets launches of the solver kernels (every k-th CG iteration of

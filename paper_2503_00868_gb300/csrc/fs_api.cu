@@ -151,6 +151,7 @@ static void free_ctx(fs_ctx *c)
 {
     if (!c) return;
     prof_destroy(c);
+    net_free(c);
     void *ptrs[] = {c->cflag, c->fflag, c->bc, c->dsum, c->pb, c->pr, c->pp[0], c->pp[1], c->pq, c->px, c->pz,
                     c->vx, c->vr, c->vp[0], c->vp[1], c->vq, c->fu[0], c->fu[1], c->fu[2], c->fg[0], c->fg[1],
                     c->fg[2], c->gc[0], c->gc[1], c->gc[2], c->mic_prec, c->scal, c->partials, c->err_word,
@@ -484,6 +485,75 @@ int fs_adjoint_step(fs_ctx *c, const fs_mac *u_in, const fs_mac *u_visc, const f
     FS_CUDA(cudaStreamSynchronize(c->stream));
     prof_flush(c);
     return s->status;
+}
+
+int fs_net_param_count(void) { return net_param_count(); }
+
+int fs_net_load(fs_ctx *c, const float *params, int count, int params_on_host)
+{
+    if (!c || !params) return set_error(FS_EINVAL, "NULL argument");
+    g_err[0] = 0;
+    return net_load(c, params, count, params_on_host != 0);
+}
+
+int fs_net_read(fs_ctx *c, float *params_host, int count)
+{
+    if (!c || !params_host) return set_error(FS_EINVAL, "NULL argument");
+    if (count != net_param_count()) return set_error(FS_EINVAL, "expected %d values", net_param_count());
+    return net_read(c, params_host);
+}
+
+int fs_net_forward(fs_ctx *c, const float *r, float *z)
+{
+    int rc = need_mask(c);
+    if (rc) return rc;
+    if (!r || !z || r == z) return set_error(FS_EINVAL, "bad r / z");
+    if (!net_loaded(c)) return set_error(FS_ESTATE, "no network loaded");
+    const int saved = c->prm.precond;
+    c->prm.precond = FS_PRECOND_LEARNED;
+    rc = precond_apply_public(c, r, z);
+    c->prm.precond = saved;
+    return rc;
+}
+
+int fs_net_grad(fs_ctx *c, const float *b, const float *q, double *loss)
+{
+    int rc = need_mask(c);
+    if (rc) return rc;
+    if (!b || !q) return set_error(FS_EINVAL, "NULL argument");
+    g_err[0] = 0;
+    return net_grad(c, b, q, loss);
+}
+
+int fs_net_grad_read(fs_ctx *c, float *grad_host, int count)
+{
+    if (!c || !grad_host) return set_error(FS_EINVAL, "NULL argument");
+    if (count != net_param_count()) return set_error(FS_EINVAL, "expected %d values", net_param_count());
+    return net_grad_read(c, grad_host);
+}
+
+int fs_net_adam(fs_ctx *c, double lr, double beta1, double beta2, double eps, int step, double grad_scale)
+{
+    if (!c) return set_error(FS_EINVAL, "NULL context");
+    if (!(lr >= 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0))
+        return set_error(FS_EINVAL, "bad Adam hyper-parameters");
+    return net_adam(c, lr, beta1, beta2, eps, step, grad_scale);
+}
+
+int fs_net_train_step(fs_ctx *c, const float *b_batch, const float *q_batch, int batch, double lr, int step,
+                      double *loss)
+{
+    int rc = need_mask(c);
+    if (rc) return rc;
+    if (!b_batch || !q_batch || batch < 1) return set_error(FS_EINVAL, "bad batch");
+    double l = 0.0;
+    for (int k = 0; k < batch; k++) {
+        rc = net_grad(c, b_batch + (size_t)k * c->L.S, q_batch + (size_t)k * c->L.S, &l);
+        if (rc) return rc;
+    }
+    rc = net_adam(c, lr, 0.9, 0.999, 1e-8, step, 1.0 / batch);
+    if (loss) *loss = l / batch;
+    return rc;
 }
 
 int fs_precond_apply(fs_ctx *c, const float *r, float *z)

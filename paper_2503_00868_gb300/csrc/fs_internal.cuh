@@ -129,6 +129,9 @@ struct fs_ctx {
     int *mic_next;        // work counter of the running sweep
     int mic_n, mic_epoch, mic_ntiles;
 
+    // learned preconditioner (fs_net.cu), allocated on first use
+    void *net;
+
     // reductions
     fs::SolveScal *scal;        // device [4]: 0 pressure, 1 viscosity, 2 misc, 3 misc
     fs::SolveScal *scal_host;   // pinned mirror
@@ -268,6 +271,20 @@ int launch_advect_adjoint(fs_ctx *c, CF3 u, F3 g);       // vx cotangent -> g (+
 // fs_mic0.cu
 int mic0_factor(fs_ctx *c);
 int mic0_apply(fs_ctx *c, const float *r, float *z);
+// fs_net.cu
+int net_alloc(fs_ctx *c, bool training);
+void net_free(fs_ctx *c);
+int net_load(fs_ctx *c, const float *params, int count, bool host);
+int net_read(fs_ctx *c, float *params_host);
+int net_apply(fs_ctx *c, const float *r, float *z);   // cell space
+int net_grad(fs_ctx *c, const float *b, const float *q, double *loss);  // public layout
+int net_adam(fs_ctx *c, double lr, double beta1, double beta2, double eps, int step, double gscale);
+int net_grad_read(fs_ctx *c, float *grad_host);
+int net_grad_clear(fs_ctx *c);
+int net_param_count();
+bool net_loaded(const fs_ctx *c);
+// public cell array -> cell space, zero off liquid
+int cell_in(fs_ctx *c, const float *src, float *dst);
 
 int read_scal(fs_ctx *c, int which, SolveScal *out);
 

@@ -1,0 +1,688 @@
+// fs_net.cu -- the learned pressure preconditioner (arXiv 2503.00868, Sec. 3.4.1,
+// Fig. percnn_str_fit: a convolutional network with fitted 3x3x3 kernels that
+// maps a pressure right-hand side to a pressure, fitted to solver output).
+//
+// Network: five 3x3x3 convolutions, channels 2 -> 16 -> 16 -> 16 -> 16 -> 1, zero
+// padding at the grid boundary, ReLU after the first four. Input channel 0 is
+// r / s on liquid cells rounded to bf16 (s = max |r| over the liquid), channel 1
+// the cell type code (liquid 1, air 0, solid -1). Output z = s * y on liquid
+// cells. Weights are bf16 (FP32 master copies for training), every hidden
+// activation is stored as bf16, every sum accumulates in FP32.
+//
+// Kernels:
+//   k_conv_first   layer 1 (2 -> 16) on CUDA cores, input formed on the fly;
+//   k_conv_mid     layers 2-4 (16 -> 16) as an implicit GEMM per 3x3x3 tap on the
+//                  tensor cores (mma.sync m16n8k16 bf16 x bf16 -> f32, operands
+//                  via ldmatrix from a swizzled shared-memory tile); the same
+//                  kernel runs the backward-data pass with flipped, transposed
+//                  weights and a ReLU-derivative epilogue;
+//   k_conv_last    layer 5 (16 -> 1) on CUDA cores; scales by s and masks;
+//   k_bwd_last     gradient through layer 5 to its input;
+//   k_wgrad<CIN,COUT>  weight and bias gradients (FP32 CUDA cores, per-block
+//                  partial sums, one atomicAdd per weight per block);
+//   k_adam         Adam on the FP32 master weights, then the bf16 copies.
+// Layout: activations are channel-last, [cell][16] bf16 (32 bytes per cell) in
+// cell space; a neighbour outside the grid reads zero (checked per cell).
+#include <cuda_bf16.h>
+
+#include <new>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "fs_internal.cuh"
+
+namespace fs {
+
+// parameter offsets in the flat FP32 vector (PyTorch conv3d layout [co][ci][kd][kh][kw])
+constexpr int NW1 = 16 * 2 * 27, NB1 = 16, NWM = 16 * 16 * 27, NBM = 16, NW5 = 16 * 27, NB5 = 1;
+constexpr int OW1 = 0, OB1 = OW1 + NW1;
+constexpr int OW2 = OB1 + NB1, OB2 = OW2 + NWM;
+constexpr int OW3 = OB2 + NBM, OB3 = OW3 + NWM;
+constexpr int OW4 = OB3 + NBM, OB4 = OW4 + NWM;
+constexpr int OW5 = OB4 + NBM, OB5 = OW5 + NW5;
+constexpr int NPARAM = OB5 + NB5;
+
+struct NetState {
+    float *master;        // FP32 parameters, flat
+    float *grad;          // FP32 gradient accumulator, flat
+    float *m, *v;         // Adam moments
+    float *w1f, *w5f;     // bf16-rounded layer-1 / layer-5 weights as float
+    __nv_bfloat16 *wf;    // layers 2-4 forward: [3][27 tap][16 co][16 ci]
+    __nv_bfloat16 *wt;    // layers 2-4 backward-data: [3][27 tap][16 ci][16 co], tap flipped
+    __nv_bfloat16 *act;   // [6][nC][16]: x (2 ch used), a1, a2, a3, a4, spare
+    __nv_bfloat16 *gact;  // [2][nC][16] gradient ping-pong
+    float *y;             // [nC] network output (training) / scratch
+    float *gy;            // [nC] dL/dy
+    unsigned *smax;       // device max |r| (float bits)
+    int loaded;
+};
+
+namespace {
+
+constexpr int NT_X = 32, NT_Y = 8;  // conv tile: 32 x 8 cells of one plane
+
+__device__ __forceinline__ int tap_index(int dz, int dy, int dx) { return (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1); }
+
+__device__ __forceinline__ bool in_grid(const Layout &L, int i, int j, int k)
+{
+    return i >= 0 && j >= 0 && k >= 0 && i < L.nx && j < L.ny && k < L.nz;
+}
+
+__device__ __forceinline__ int cell_t(const Layout &L, int i, int j, int k) { return L.PL + (k * L.R + j) * L.P + i; }
+
+__device__ __forceinline__ float type_code(uint8_t f) { return (f & CF_LIQ) ? 1.f : ((f & CF_AIR) ? 0.f : -1.f); }
+
+__device__ __forceinline__ float bfr(float x) { return __bfloat162float(__float2bfloat16(x)); }
+
+// ---- layer 1 (2 -> 16), CUDA cores; also stores the bf16 input x ----------------
+__global__ void __launch_bounds__(256) k_conv_first(const float *__restrict__ r, const uint8_t *__restrict__ cf,
+                                                    const unsigned *__restrict__ smax,
+                                                    const float *__restrict__ w1f, const float *__restrict__ b1,
+                                                    __nv_bfloat16 *xin, __nv_bfloat16 *out, Layout L)
+{
+    __shared__ float w[NW1], b[16];
+    for (int t = threadIdx.x; t < NW1; t += blockDim.x) w[t] = w1f[t];
+    if (threadIdx.x < 16) b[threadIdx.x] = b1[threadIdx.x];
+    __syncthreads();
+    const float s = __uint_as_float(*smax);
+    const float inv = s > 0.f ? 1.f / s : 0.f;
+    const int ncell = L.nx * L.ny * L.nz;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+        const int i = c % L.nx, j = (c / L.nx) % L.ny, k = c / (L.nx * L.ny);
+        float acc[16];
+#pragma unroll
+        for (int o = 0; o < 16; o++) acc[o] = b[o];
+        for (int dz = -1; dz <= 1; dz++)
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    if (!in_grid(L, i + dx, j + dy, k + dz)) continue;
+                    const int tn = cell_t(L, i + dx, j + dy, k + dz);
+                    const uint8_t f = cf[tn];
+                    const float x0 = (f & CF_LIQ) ? bfr(r[tn] * inv) : 0.f;
+                    const float x1 = type_code(f);
+                    const int tp = tap_index(dz, dy, dx);
+#pragma unroll
+                    for (int o = 0; o < 16; o++) acc[o] += w[(o * 2 + 0) * 27 + tp] * x0 + w[(o * 2 + 1) * 27 + tp] * x1;
+                }
+        const int t = cell_t(L, i, j, k);
+        if (xin) {
+            const uint8_t f = cf[t];
+            xin[(size_t)t * 16 + 0] = __float2bfloat16((f & CF_LIQ) ? bfr(r[t] * inv) : 0.f);
+            xin[(size_t)t * 16 + 1] = __float2bfloat16(type_code(f));
+        }
+        __nv_bfloat162 *o2 = reinterpret_cast<__nv_bfloat162 *>(out + (size_t)t * 16);
+#pragma unroll
+        for (int o = 0; o < 8; o++)
+            o2[o] = __floats2bfloat162_rn(fmaxf(acc[2 * o], 0.f), fmaxf(acc[2 * o + 1], 0.f));
+    }
+}
+
+// ---- layers 2-4 (16 -> 16), tensor cores ------------------------------------------
+// Shared tile: 3 planes x (NT_Y + 2) rows x (NT_X + 2) cells x 16 bf16. The two
+// 16-byte halves of a cell are swapped when bit 2 of its tile index is set, so
+// the 8 rows of an ldmatrix phase fall in distinct banks.
+constexpr int TZ3 = 3, TYH = NT_Y + 2, TXH = NT_X + 2;
+constexpr int TCELLS = TZ3 * TYH * TXH;
+
+__device__ __forceinline__ uint32_t swz_off(int cidx, int half)  // byte offset of a cell half
+{
+    return (uint32_t)(cidx * 32 + ((half ^ ((cidx >> 2) & 1)) << 4));
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// MODE 0: out = relu(conv(in) + bias).  MODE 1 (backward data): out = conv(in)
+// * [aref > 0], the ReLU derivative of the layer input. Output only on grid cells.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_conv_mid(const __nv_bfloat16 *__restrict__ in,
+                                                  const __nv_bfloat16 *__restrict__ wts,  // [27][16 n][16 k]
+                                                  const float *__restrict__ bias,
+                                                  const __nv_bfloat16 *__restrict__ aref, __nv_bfloat16 *out,
+                                                  Layout L)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char *tile = smem;                          // TCELLS * 32 bytes
+    unsigned char *wsm = smem + TCELLS * 32;             // 27 * 16 rows * 32 bytes
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // weights once per block (rows n = tap * 16 + co, swizzled like the tile)
+    for (int e = tid; e < 27 * 16 * 2; e += blockDim.x) {
+        const int row = e >> 1, half = e & 1;
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(wts) + row * 2 + half);
+        *reinterpret_cast<uint4 *>(wsm + swz_off(row, half)) = v;
+    }
+    float bv[4] = {0.f, 0.f, 0.f, 0.f};  // bias of this lane's output channels
+    if (MODE == 0) {
+        const int co = (lane & 3) * 2;
+        bv[0] = bias[co];
+        bv[1] = bias[co + 1];
+        bv[2] = bias[8 + co];
+        bv[3] = bias[8 + co + 1];
+    }
+    const uint32_t tile_s = (uint32_t)__cvta_generic_to_shared(tile);
+    const uint32_t w_s = (uint32_t)__cvta_generic_to_shared(wsm);
+    const int ntx = (L.nx + NT_X - 1) / NT_X, nty = (L.ny + NT_Y - 1) / NT_Y;
+    const int ntiles = ntx * nty * L.nz;
+    for (int tb = blockIdx.x; tb < ntiles; tb += gridDim.x) {
+        const int tx = tb % ntx, ty = (tb / ntx) % nty, tk = tb / (ntx * nty);
+        const int i0 = tx * NT_X, j0 = ty * NT_Y;
+        __syncthreads();  // previous tile done with the shared tile (and weights stored)
+        for (int e = tid; e < TCELLS * 2; e += blockDim.x) {
+            const int cidx = e >> 1, half = e & 1;
+            const int xx = cidx % TXH, yy = (cidx / TXH) % TYH, zz = cidx / (TXH * TYH);
+            const int gi = i0 - 1 + xx, gj = j0 - 1 + yy, gk = tk - 1 + zz;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (in_grid(L, gi, gj, gk))
+                v = __ldg(reinterpret_cast<const uint4 *>(in + (size_t)cell_t(L, gi, gj, gk) * 16) + half);
+            *reinterpret_cast<uint4 *>(tile + swz_off(cidx, half)) = v;
+        }
+        __syncthreads();
+        // warp w: row y = w of the tile, two M-tiles of 16 cells (x 0-15, 16-31)
+        for (int mt = 0; mt < 2; mt++) {
+            float acc0[4] = {0.f, 0.f, 0.f, 0.f}, acc1[4] = {0.f, 0.f, 0.f, 0.f};
+            const int row = lane & 15, khalf = lane >> 4;
+            for (int dz = 0; dz < 3; dz++)
+                for (int dy = 0; dy < 3; dy++)
+                    for (int dx = 0; dx < 3; dx++) {
+                        const int cidx = (dz * TYH + warp + dy) * TXH + mt * 16 + dx + row;
+                        uint32_t a0, a1, a2, a3;
+                        ldsm_x4(tile_s + swz_off(cidx, khalf), a0, a1, a2, a3);
+                        const int tp = dz * 9 + dy * 3 + dx;
+                        const int wrow = tp * 16 + (lane & 7) + ((lane >> 4) << 3);
+                        const int wh = (lane >> 3) & 1;
+                        uint32_t b0, b1, b2, b3;
+                        ldsm_x4(w_s + swz_off(wrow, wh), b0, b1, b2, b3);
+                        mma_bf16(acc0, a0, a1, a2, a3, b0, b1);
+                        mma_bf16(acc1, a0, a1, a2, a3, b2, b3);
+                    }
+            // epilogue: cells (lane/4) and (lane/4 + 8); channels (lane%4)*2 (+1), +8
+            const int gj = j0 + warp;
+            for (int hr = 0; hr < 2; hr++) {
+                const int gi = i0 + mt * 16 + (lane >> 2) + hr * 8;
+                if (gi >= L.nx || gj >= L.ny) continue;
+                const size_t t = (size_t)cell_t(L, gi, gj, tk);
+                const int co = (lane & 3) * 2;
+                float v0 = acc0[hr * 2], v1 = acc0[hr * 2 + 1], v2 = acc1[hr * 2], v3 = acc1[hr * 2 + 1];
+                if (MODE == 0) {
+                    v0 = fmaxf(v0 + bv[0], 0.f);
+                    v1 = fmaxf(v1 + bv[1], 0.f);
+                    v2 = fmaxf(v2 + bv[2], 0.f);
+                    v3 = fmaxf(v3 + bv[3], 0.f);
+                } else {
+                    const __nv_bfloat162 r0 = *reinterpret_cast<const __nv_bfloat162 *>(aref + t * 16 + co);
+                    const __nv_bfloat162 r1 = *reinterpret_cast<const __nv_bfloat162 *>(aref + t * 16 + 8 + co);
+                    v0 = __bfloat162float(r0.x) > 0.f ? v0 : 0.f;
+                    v1 = __bfloat162float(r0.y) > 0.f ? v1 : 0.f;
+                    v2 = __bfloat162float(r1.x) > 0.f ? v2 : 0.f;
+                    v3 = __bfloat162float(r1.y) > 0.f ? v3 : 0.f;
+                }
+                *reinterpret_cast<__nv_bfloat162 *>(out + t * 16 + co) = __floats2bfloat162_rn(v0, v1);
+                *reinterpret_cast<__nv_bfloat162 *>(out + t * 16 + 8 + co) = __floats2bfloat162_rn(v2, v3);
+            }
+        }
+    }
+}
+
+// ---- layer 5 (16 -> 1), CUDA cores ---------------------------------------------------
+__global__ void __launch_bounds__(256) k_conv_last(const __nv_bfloat16 *__restrict__ in,
+                                                   const float *__restrict__ w5f, const float *__restrict__ b5,
+                                                   const uint8_t *__restrict__ cf,
+                                                   const unsigned *__restrict__ smax, float *y, float *z, Layout L)
+{
+    __shared__ float w[NW5];
+    for (int t = threadIdx.x; t < NW5; t += blockDim.x) w[t] = w5f[t];
+    __syncthreads();
+    const float s = __uint_as_float(*smax);
+    const float bias = b5[0];
+    const int ncell = L.nx * L.ny * L.nz;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+        const int i = c % L.nx, j = (c / L.nx) % L.ny, k = c / (L.nx * L.ny);
+        float acc = bias;
+        for (int dz = -1; dz <= 1; dz++)
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    if (!in_grid(L, i + dx, j + dy, k + dz)) continue;
+                    const __nv_bfloat162 *a =
+                        reinterpret_cast<const __nv_bfloat162 *>(in + (size_t)cell_t(L, i + dx, j + dy, k + dz) * 16);
+                    const int tp = tap_index(dz, dy, dx);
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        const float2 v = __bfloat1622float2(a[q]);
+                        acc += w[(2 * q) * 27 + tp] * v.x + w[(2 * q + 1) * 27 + tp] * v.y;
+                    }
+                }
+        const int t = cell_t(L, i, j, k);
+        if (y) y[t] = acc;
+        if (z) z[t] = (cf[t] & CF_LIQ) ? s * acc : 0.f;
+    }
+}
+
+// max |r| over the liquid, as float bits (non-negative floats order like ints)
+__global__ void k_absmax(const float *__restrict__ r, const uint8_t *__restrict__ cf, int n, unsigned *smax)
+{
+    float m = 0.f;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+        if (cf[t] & CF_LIQ) m = fmaxf(m, fabsf(r[t]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(smax, __float_as_uint(m));
+}
+
+// s is rounded to bf16 (the oracle rounds x = r/s, not s; keep s exact)
+// ---- training: loss, gradients -----------------------------------------------------
+
+// loss terms: sum_liq (y - q/s)^2 and sum_liq (q/s)^2 -> scal aux[0], aux[1]
+__global__ void __launch_bounds__(256) k_net_loss(const float *__restrict__ y, const float *__restrict__ q,
+                                                  const uint8_t *__restrict__ cf, const unsigned *__restrict__ smax,
+                                                  int n, SolveScal *s, double *partials)
+{
+    const float sc = __uint_as_float(*smax);
+    const float inv = sc > 0.f ? 1.f / sc : 0.f;
+    double num = 0.0, den = 0.0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        if (!(cf[t] & CF_LIQ)) continue;
+        const double tq = (double)q[t] * inv;
+        const double e = (double)y[t] - tq;
+        num += e * e;
+        den += tq * tq;
+    }
+    double v[2] = {num, den}, tot[2];
+    if (grid_reduce<2>(v, partials, &s->ticket, tot) && threadIdx.x == 0) {
+        s->aux[0] = tot[0];
+        s->aux[1] = tot[1];
+    }
+}
+
+__global__ void k_net_gy(const float *__restrict__ y, const float *__restrict__ q, const uint8_t *__restrict__ cf,
+                         const unsigned *__restrict__ smax, const SolveScal *s, float *gy, int n)
+{
+    const float sc = __uint_as_float(*smax);
+    const float inv = sc > 0.f ? 1.f / sc : 0.f;
+    const double den = s->aux[1];
+    const float g = den > 0.0 ? (float)(2.0 / den) : 0.f;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+        gy[t] = (cf[t] & CF_LIQ) ? g * (y[t] - q[t] * inv) : 0.f;
+}
+
+// dL/d(layer-5 input) = sum_tap w5[ci][tap] gy[cell - tap], times [a4 > 0]
+__global__ void __launch_bounds__(256) k_bwd_last(const float *__restrict__ gy, const float *__restrict__ w5f,
+                                                  const __nv_bfloat16 *__restrict__ a4, __nv_bfloat16 *g4, Layout L)
+{
+    __shared__ float w[NW5];
+    for (int t = threadIdx.x; t < NW5; t += blockDim.x) w[t] = w5f[t];
+    __syncthreads();
+    const int ncell = L.nx * L.ny * L.nz;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+        const int i = c % L.nx, j = (c / L.nx) % L.ny, k = c / (L.nx * L.ny);
+        float acc[16];
+#pragma unroll
+        for (int o = 0; o < 16; o++) acc[o] = 0.f;
+        for (int dz = -1; dz <= 1; dz++)
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    // output cell (i - d) saw this cell through tap d
+                    if (!in_grid(L, i - dx, j - dy, k - dz)) continue;
+                    const float g = gy[cell_t(L, i - dx, j - dy, k - dz)];
+                    if (g == 0.f) continue;
+                    const int tp = tap_index(dz, dy, dx);
+#pragma unroll
+                    for (int o = 0; o < 16; o++) acc[o] += w[o * 27 + tp] * g;
+                }
+        const size_t t = (size_t)cell_t(L, i, j, k);
+        const __nv_bfloat162 *a = reinterpret_cast<const __nv_bfloat162 *>(a4 + t * 16);
+        __nv_bfloat162 *o2 = reinterpret_cast<__nv_bfloat162 *>(g4 + t * 16);
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const float2 av = __bfloat1622float2(a[q]);
+            o2[q] = __floats2bfloat162_rn(av.x > 0.f ? acc[2 * q] : 0.f, av.y > 0.f ? acc[2 * q + 1] : 0.f);
+        }
+    }
+}
+
+// Weight and bias gradients of one layer: gW[co][ci][tap] += sum_cells
+// g[cell][co] * a[cell + tap][ci]; gB[co] += sum_cells g[cell][co]. g is bf16
+// [cell][16] (COUT = 16) or FP32 [cell] (COUT = 1); a is bf16 [cell][16].
+template <int CIN, int COUT, bool GF32>
+__global__ void __launch_bounds__(256) k_wgrad(const void *__restrict__ gptr, const __nv_bfloat16 *__restrict__ a,
+                                               float *gW, float *gB, Layout L)
+{
+    constexpr int NOUT = COUT * CIN * 27;
+    extern __shared__ float wg_smem[];
+    float(*sg)[COUT] = reinterpret_cast<float(*)[COUT]>(wg_smem);
+    float(*sa)[CIN] = reinterpret_cast<float(*)[CIN]>(wg_smem + NT_X * NT_Y * COUT);
+    float part[(NOUT + 255) / 256];
+    float bpart = 0.f;
+#pragma unroll
+    for (int u = 0; u < (NOUT + 255) / 256; u++) part[u] = 0.f;
+    const int tid = threadIdx.x;
+    const int ntx = (L.nx + NT_X - 1) / NT_X, nty = (L.ny + NT_Y - 1) / NT_Y;
+    const int ntiles = ntx * nty * L.nz;
+    for (int tb = blockIdx.x; tb < ntiles; tb += gridDim.x) {
+        const int tx = tb % ntx, ty = (tb / ntx) % nty, tk = tb / (ntx * nty);
+        const int i0 = tx * NT_X, j0 = ty * NT_Y;
+        __syncthreads();
+        for (int e = tid; e < NT_X * NT_Y * COUT; e += blockDim.x) {
+            const int cl = e / COUT, o = e % COUT;
+            const int gi = i0 + cl % NT_X, gj = j0 + cl / NT_X;
+            float v = 0.f;
+            if (gi < L.nx && gj < L.ny) {
+                const size_t t = (size_t)cell_t(L, gi, gj, tk);
+                v = GF32 ? static_cast<const float *>(gptr)[t]
+                         : __bfloat162float(static_cast<const __nv_bfloat16 *>(gptr)[t * 16 + o]);
+            }
+            sg[cl][o] = v;
+        }
+        for (int e = tid; e < TCELLS * CIN; e += blockDim.x) {
+            const int cidx = e / CIN, ci = e % CIN;
+            const int xx = cidx % TXH, yy = (cidx / TXH) % TYH, zz = cidx / (TXH * TYH);
+            const int gi = i0 - 1 + xx, gj = j0 - 1 + yy, gk = tk - 1 + zz;
+            sa[cidx][ci] = in_grid(L, gi, gj, gk) ? __bfloat162float(a[(size_t)cell_t(L, gi, gj, gk) * 16 + ci]) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < (NOUT + 255) / 256; u++) {
+            const int o = tid + u * 256;
+            if (o >= NOUT) break;
+            const int tp = o % 27, ci = (o / 27) % CIN, co = o / (27 * CIN);
+            const int dz = tp / 9, dy = (tp / 3) % 3, dx = tp % 3;
+            float acc = 0.f;
+            for (int cl = 0; cl < NT_X * NT_Y; cl++) {
+                const float g = sg[cl][co];
+                const int cx = cl % NT_X, cy = cl / NT_X;
+                acc += g * sa[(dz * TYH + cy + dy) * TXH + cx + dx][ci];
+            }
+            part[u] += acc;
+        }
+        if (tid < COUT)
+            for (int cl = 0; cl < NT_X * NT_Y; cl++) bpart += sg[cl][tid];
+    }
+#pragma unroll
+    for (int u = 0; u < (NOUT + 255) / 256; u++) {
+        const int o = tid + u * 256;
+        if (o < NOUT) atomicAdd(gW + o, part[u]);
+    }
+    if (tid < COUT) atomicAdd(gB + tid, bpart);
+}
+
+// Adam on the FP32 master copy; the gradient buffer is cleared.
+__global__ void k_adam(float *p, float *g, float *m, float *v, int n, float lr, float b1, float b2, float eps,
+                       float c1, float c2, float gscale)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const float gr = g[t] * gscale;
+        const float mm = b1 * m[t] + (1.f - b1) * gr;
+        const float vv = b2 * v[t] + (1.f - b2) * gr * gr;
+        m[t] = mm;
+        v[t] = vv;
+        p[t] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+        g[t] = 0.f;
+    }
+}
+
+// bf16 working copies from the master copy
+__global__ void k_net_refresh(const float *__restrict__ p, float *w1f, float *w5f, __nv_bfloat16 *wf,
+                              __nv_bfloat16 *wt)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < NPARAM; t += gridDim.x * blockDim.x) {
+        if (t < OB1) w1f[t] = bfr(p[t]);
+        if (t >= OW5 && t < OB5) w5f[t - OW5] = bfr(p[t]);
+        const int offs[3] = {OW2, OW3, OW4};
+        for (int l = 0; l < 3; l++) {
+            if (t < offs[l] || t >= offs[l] + NWM) continue;
+            const int e = t - offs[l];
+            const int tp = e % 27, ci = (e / 27) % 16, co = e / (27 * 16);
+            const __nv_bfloat16 v = __float2bfloat16(p[t]);
+            wf[(size_t)l * NWM + (tp * 16 + co) * 16 + ci] = v;            // [tap][n = co][k = ci]
+            wt[(size_t)l * NWM + ((26 - tp) * 16 + ci) * 16 + co] = v;     // [tap'][n = ci][k = co]
+        }
+    }
+}
+
+__global__ void k_fill_zero(float *p, int n)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) p[t] = 0.f;
+}
+
+}  // namespace
+
+static NetState *net(fs_ctx *c) { return static_cast<NetState *>(c->net); }
+
+static size_t conv_mid_smem() { return (size_t)TCELLS * 32 + 27 * 16 * 32; }
+
+template <int CIN, int COUT>
+static size_t wgrad_smem() { return ((size_t)NT_X * NT_Y * COUT + (size_t)TCELLS * CIN) * 4; }
+
+int net_alloc(fs_ctx *c, bool training)
+{
+    if (c->net && (!training || net(c)->gact)) return FS_OK;
+    NetState *n = net(c);
+    if (!n) {
+        n = new (std::nothrow) NetState();
+        if (!n) return set_error(FS_ENOMEM, "host allocation failed");
+        c->net = n;
+    }
+    auto alloc = [&](void **p, size_t bytes) -> int {
+        if (*p) return FS_OK;
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) {
+            *p = nullptr;
+            cudaGetLastError();
+            return set_error(FS_ENOMEM, "cudaMalloc of %zu bytes failed", bytes);
+        }
+        return check_cuda(cudaMemset(*p, 0, bytes), "cudaMemset");
+    };
+    const size_t nC = (size_t)c->L.nC;
+    int rc;
+    if ((rc = alloc((void **)&n->master, NPARAM * 4)) || (rc = alloc((void **)&n->grad, NPARAM * 4)) ||
+        (rc = alloc((void **)&n->m, NPARAM * 4)) || (rc = alloc((void **)&n->v, NPARAM * 4)) ||
+        (rc = alloc((void **)&n->w1f, NW1 * 4)) || (rc = alloc((void **)&n->w5f, NW5 * 4)) ||
+        (rc = alloc((void **)&n->wf, 3 * NWM * 2)) || (rc = alloc((void **)&n->wt, 3 * NWM * 2)) ||
+        (rc = alloc((void **)&n->smax, 16)) || (rc = alloc((void **)&n->y, nC * 4)))
+        return rc;
+    // inference needs two activation buffers; training keeps all five layer inputs
+    const int nact = training ? 6 : 2;
+    if (training && n->act && !n->gact) {
+        cudaFree(n->act);
+        n->act = nullptr;
+    }
+    if ((rc = alloc((void **)&n->act, nact * nC * 32))) return rc;
+    if (training) {
+        if ((rc = alloc((void **)&n->gact, 2 * nC * 32)) || (rc = alloc((void **)&n->gy, nC * 4))) return rc;
+    }
+    static bool attr_done = false;
+    if (!attr_done) {
+        FS_CUDA(cudaFuncSetAttribute(k_conv_mid<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_mid_smem()));
+        FS_CUDA(cudaFuncSetAttribute(k_conv_mid<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_mid_smem()));
+        FS_CUDA(cudaFuncSetAttribute(k_wgrad<16, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)wgrad_smem<16, 16>()));
+        FS_CUDA(cudaFuncSetAttribute(k_wgrad<16, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)wgrad_smem<16, 1>()));
+        FS_CUDA(cudaFuncSetAttribute(k_wgrad<2, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)wgrad_smem<2, 16>()));
+        attr_done = true;
+    }
+    return FS_OK;
+}
+
+void net_free(fs_ctx *c)
+{
+    NetState *n = net(c);
+    if (!n) return;
+    void *ptrs[] = {n->master, n->grad, n->m, n->v, n->w1f, n->w5f, n->wf, n->wt, n->act, n->gact, n->y, n->gy, n->smax};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete n;
+    c->net = nullptr;
+}
+
+int net_load(fs_ctx *c, const float *params, int count, bool host)
+{
+    if (count != NPARAM) return set_error(FS_EINVAL, "the network has %d parameters, got %d", NPARAM, count);
+    int rc = net_alloc(c, false);
+    if (rc) return rc;
+    NetState *n = net(c);
+    FS_CUDA(cudaMemcpyAsync(n->master, params, NPARAM * 4, host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                            c->stream));
+    k_net_refresh<<<(NPARAM + 255) / 256, 256, 0, c->stream>>>(n->master, n->w1f, n->w5f, n->wf, n->wt);
+    FS_CUDA(cudaGetLastError());
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    n->loaded = 1;
+    return FS_OK;
+}
+
+int net_read(fs_ctx *c, float *params_host)
+{
+    NetState *n = net(c);
+    if (!n || !n->loaded) return set_error(FS_ESTATE, "no network loaded");
+    FS_CUDA(cudaMemcpyAsync(params_host, n->master, NPARAM * 4, cudaMemcpyDeviceToHost, c->stream));
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    return FS_OK;
+}
+
+static int conv_grid(const fs_ctx *c)
+{
+    const Layout &L = c->L;
+    const int ntiles = ((L.nx + NT_X - 1) / NT_X) * ((L.ny + NT_Y - 1) / NT_Y) * L.nz;
+    return std::max(1, std::min(ntiles, c->num_sms * 2));
+}
+
+// z = s Net(r / s) on liquid cells (cell space), forward activations kept in
+// act[0..4] when `keep` (training), else ping-pong in act[0..1].
+static int net_forward(fs_ctx *c, const float *r, float *z, float *y, bool keep)
+{
+    NetState *n = net(c);
+    const Layout &L = c->L;
+    const size_t nC = (size_t)L.nC;
+    const int ncell = L.nx * L.ny * L.nz;
+    const int gb = std::max(1, std::min((ncell + 255) / 256, c->num_sms * 8));
+    FS_CUDA(cudaMemsetAsync(n->smax, 0, sizeof(unsigned), c->stream));
+    k_absmax<<<grid_blocks(c, L.nC, 256), 256, 0, c->stream>>>(r, c->cflag, L.nC, n->smax);
+    __nv_bfloat16 *A[6];
+    for (int l = 0; l < 6; l++) A[l] = n->act + (keep ? (size_t)l : (size_t)(l & 1)) * nC * 16;
+    // keep: x -> A[0], a1 -> A[1], ..., a4 -> A[4]; else a1 -> A[0]/A[1] ping-pong
+    __nv_bfloat16 *xin = keep ? A[0] : nullptr;
+    __nv_bfloat16 *a1 = keep ? A[1] : A[0];
+    k_conv_first<<<gb, 256, 0, c->stream>>>(r, c->cflag, n->smax, n->w1f, n->master + OB1, xin, a1, L);
+    __nv_bfloat16 *cur = a1;
+    const int bias_off[3] = {OB2, OB3, OB4};
+    for (int l = 0; l < 3; l++) {
+        __nv_bfloat16 *nxt = keep ? A[2 + l] : (cur == A[0] ? A[1] : A[0]);
+        k_conv_mid<0><<<conv_grid(c), 256, conv_mid_smem(), c->stream>>>(cur, n->wf + (size_t)l * NWM,
+                                                                         n->master + bias_off[l], nullptr, nxt, L);
+        cur = nxt;
+    }
+    k_conv_last<<<gb, 256, 0, c->stream>>>(cur, n->w5f, n->master + OB5, c->cflag, n->smax, y, z, L);
+    c->n_launches += 6;
+    FS_CUDA(cudaGetLastError());
+    return FS_OK;
+}
+
+int net_apply(fs_ctx *c, const float *r, float *z)
+{
+    NetState *n = net(c);
+    if (!n || !n->loaded) return set_error(FS_ESTATE, "the learned preconditioner has no network loaded");
+    cudaEvent_t e0 = prof_mark(c);
+    int rc = net_forward(c, r, z, nullptr, false);
+    prof_add(c, K_NET_APPLY, e0, prof_mark(c), 0.0);
+    return rc;
+}
+
+// Forward + backward for one (b, q) pair (public-layout cell arrays); adds the
+// gradient to the accumulator and the loss to *loss.
+int net_grad(fs_ctx *c, const float *b, const float *q, double *loss)
+{
+    int rc = net_alloc(c, true);
+    if (rc) return rc;
+    NetState *n = net(c);
+    if (!n->loaded) return set_error(FS_ESTATE, "load initial network parameters first");
+    const Layout &L = c->L;
+    const size_t nC = (size_t)L.nC;
+    const int ncell = L.nx * L.ny * L.nz;
+    const int gb = std::max(1, std::min((ncell + 255) / 256, c->num_sms * 8));
+    // b, q into cell space (zero off liquid): pb <- b, px <- q
+    if ((rc = cell_in(c, b, c->pb)) || (rc = cell_in(c, q, c->px))) return rc;
+    if ((rc = net_forward(c, c->pb, nullptr, n->y, true))) return rc;
+    __nv_bfloat16 *A[5];
+    for (int l = 0; l < 5; l++) A[l] = n->act + (size_t)l * nC * 16;
+    SolveScal *s = c->scal + 3;
+    k_net_loss<<<grid_blocks(c, L.nC, 256), 256, 0, c->stream>>>(n->y, c->px, c->cflag, n->smax, L.nC, s, c->partials);
+    k_net_gy<<<grid_blocks(c, L.nC, 256), 256, 0, c->stream>>>(n->y, c->px, c->cflag, n->smax, s, n->gy, L.nC);
+    // layer 5
+    const int wg = std::max(1, std::min(((L.nx + NT_X - 1) / NT_X) * ((L.ny + NT_Y - 1) / NT_Y) * L.nz, c->num_sms * 2));
+    k_wgrad<16, 1, true><<<wg, 256, wgrad_smem<16, 1>(), c->stream>>>(n->gy, A[4], n->grad + OW5, n->grad + OB5, L);
+    __nv_bfloat16 *G[2] = {n->gact, n->gact + nC * 16};
+    k_bwd_last<<<gb, 256, 0, c->stream>>>(n->gy, n->w5f, A[4], G[0], L);
+    // layers 4, 3, 2: weight gradient, then the gradient of the layer input
+    const int woff[3] = {OW2, OW3, OW4}, boff[3] = {OB2, OB3, OB4};
+    int gi = 0;
+    for (int l = 2; l >= 0; l--) {
+        // G[gi] = dL/d(output of layer l+2) (post-ReLU mask applied); input = A[l+1]
+        k_wgrad<16, 16, false><<<wg, 256, wgrad_smem<16, 16>(), c->stream>>>(G[gi], A[l + 1], n->grad + woff[l], n->grad + boff[l], L);
+        k_conv_mid<1><<<conv_grid(c), 256, conv_mid_smem(), c->stream>>>(G[gi], n->wt + (size_t)l * NWM, nullptr,
+                                                                        A[l + 1], G[gi ^ 1], L);
+        gi ^= 1;
+    }
+    // layer 1: gradient w.r.t. W1 from the stored input x (2 channels used)
+    k_wgrad<2, 16, false><<<wg, 256, wgrad_smem<2, 16>(), c->stream>>>(G[gi], A[0], n->grad + OW1, n->grad + OB1, L);
+    c->n_launches += 2 + 2 + 6 + 1;
+    FS_CUDA(cudaGetLastError());
+    SolveScal h;
+    if ((rc = read_scal(c, 3, &h))) return rc;
+    if (loss) *loss += h.aux[1] > 0.0 ? h.aux[0] / h.aux[1] : 0.0;
+    return FS_OK;
+}
+
+int net_adam(fs_ctx *c, double lr, double beta1, double beta2, double eps, int step, double gscale)
+{
+    NetState *n = net(c);
+    if (!n || !n->loaded || !n->gact) return set_error(FS_ESTATE, "no gradients accumulated");
+    if (step < 1) return set_error(FS_EINVAL, "step must be >= 1");
+    const float c1 = (float)(1.0 - std::pow(beta1, step)), c2 = (float)(1.0 - std::pow(beta2, step));
+    k_adam<<<(NPARAM + 255) / 256, 256, 0, c->stream>>>(n->master, n->grad, n->m, n->v, NPARAM, (float)lr,
+                                                        (float)beta1, (float)beta2, (float)eps, c1, c2,
+                                                        (float)gscale);
+    k_net_refresh<<<(NPARAM + 255) / 256, 256, 0, c->stream>>>(n->master, n->w1f, n->w5f, n->wf, n->wt);
+    c->n_launches += 2;
+    FS_CUDA(cudaGetLastError());
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    return FS_OK;
+}
+
+int net_grad_read(fs_ctx *c, float *grad_host)
+{
+    NetState *n = net(c);
+    if (!n || !n->gact) return set_error(FS_ESTATE, "no gradients accumulated");
+    FS_CUDA(cudaMemcpyAsync(grad_host, n->grad, NPARAM * 4, cudaMemcpyDeviceToHost, c->stream));
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    return FS_OK;
+}
+
+int net_grad_clear(fs_ctx *c)
+{
+    NetState *n = net(c);
+    if (!n) return FS_OK;
+    k_fill_zero<<<(NPARAM + 255) / 256, 256, 0, c->stream>>>(n->grad, NPARAM);
+    c->n_launches += 1;
+    FS_CUDA(cudaGetLastError());
+    return FS_OK;
+}
+
+int net_param_count() { return NPARAM; }
+
+bool net_loaded(const fs_ctx *c) { return c->net && static_cast<const NetState *>(c->net)->loaded; }
+
+}  // namespace fs

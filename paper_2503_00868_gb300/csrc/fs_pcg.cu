@@ -147,6 +147,30 @@ __global__ void __launch_bounds__(TH) k_rz(const float *__restrict__ r, const fl
     }
 }
 
+// Flexible CG with a nonlinear preconditioner (the network): after z_{k+1} =
+// M(r_{k+1}), beta = -z_{k+1}.A p_k / p_k.A p_k (one step of A-orthogonalisation
+// against the previous direction, Notay's flexible CG) and r.z for the next alpha.
+__global__ void __launch_bounds__(TH) k_fcg(const float *__restrict__ r, const float *__restrict__ z,
+                                            const float *__restrict__ q, int n4, SolveScal *s, double *partials)
+{
+    if (s->done) return;
+    KSum rz, zq;
+    const float4 *r4 = reinterpret_cast<const float4 *>(r);
+    const float4 *z4 = reinterpret_cast<const float4 *>(z);
+    const float4 *q4 = reinterpret_cast<const float4 *>(q);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += gridDim.x * blockDim.x) {
+        const float4 a = __ldg(r4 + t), b = __ldg(z4 + t), c = __ldg(q4 + t);
+        rz.add(a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w);
+        zq.add(b.x * c.x + b.y * c.y + b.z * c.z + b.w * c.w);
+    }
+    double v[2] = {rz.value(), zq.value()}, tot[2];
+    if (grid_reduce<2>(v, partials, &s->ticket, tot) && threadIdx.x == 0) {
+        if (!isfinite(tot[0]) || !isfinite(tot[1])) { s->done = 1; s->status = FS_ENONFINITE; return; }
+        s->beta = -tot[1] / s->pq;
+        s->rz = tot[0];
+    }
+}
+
 __device__ __forceinline__ void init_scalars(SolveScal *s, double bb, double rr, double rz, double tol2,
                                              int maxit)
 {
@@ -499,27 +523,30 @@ static int remove_null_mode(fs_ctx *c, float *z)
     return FS_OK;
 }
 
-int solve_pressure(fs_ctx *c, fs_stats *st)
+static int solve_pressure_once(fs_ctx *c, fs_stats *st)
 {
     const Layout &L = c->L;
     SolveScal *s = c->scal + 0;
     const bool jac = c->prm.precond == FS_PRECOND_JACOBI;
     const int n4 = L.nC / 4;
     const double tol2 = c->prm.tol_p * c->prm.tol_p;
-    if (c->prm.precond == FS_PRECOND_LEARNED)
+    const bool learned = c->prm.precond == FS_PRECOND_LEARNED;
+    if (learned && !net_loaded(c))
         return set_error(FS_ESTATE, "the learned preconditioner has no network loaded");
     if (!jac) FS_CUDA(cudaMemsetAsync(c->err_word, 0, sizeof(unsigned), c->stream));
-    if (!jac && !c->mic_ready) {
+    if (c->prm.precond == FS_PRECOND_MIC0 && !c->mic_ready) {
         int rc = mic0_factor(c);
         if (rc) return rc;
     }
+    // z = M r for the stored-z preconditioners (MIC(0) or the network)
+    auto apply_m = [&]() -> int { return learned ? net_apply(c, c->pr, c->pz) : mic0_apply(c, c->pr, c->pz); };
     if (jac)
         k_pois_init<true><<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(
             c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, n4, tol2, c->prm.maxit_p, s, c->partials);
     else {
         k_pois_init<false><<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(
             c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, n4, tol2, c->prm.maxit_p, s, c->partials);
-        int rc = mic0_apply(c, c->pr, c->pz);
+        int rc = apply_m();
         if (rc) return rc;
         if ((rc = remove_null_mode(c, c->pz))) return rc;
         k_rz<<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(c->pr, c->pz, n4, 1, s, c->partials);
@@ -569,10 +596,13 @@ int solve_pressure(fs_ctx *c, fs_stats *st)
             prof_add(c, K_P_UPDATE, e2, e3, by_upd);
             c->n_launches += 2;
             if (!jac) {
-                int rc = mic0_apply(c, c->pr, c->pz);
+                int rc = apply_m();
                 if (rc) return rc;
                 if ((rc = remove_null_mode(c, c->pz))) return rc;
-                k_rz<<<b4, TH, 0, c->stream>>>(c->pr, c->pz, n4, 0, s, c->partials);
+                if (learned)
+                    k_fcg<<<b4, TH, 0, c->stream>>>(c->pr, c->pz, c->pq, n4, s, c->partials);
+                else
+                    k_rz<<<b4, TH, 0, c->stream>>>(c->pr, c->pz, n4, 0, s, c->partials);
                 c->n_launches += 1;
             }
             cur ^= 1;
@@ -615,6 +645,25 @@ int solve_pressure(fs_ctx *c, fs_stats *st)
         if (h.status != FS_OK && st->status == FS_OK) st->status = h.status;
     }
     return finish_status(h.status);
+}
+
+// The learned preconditioner is judged by the true residual: if flexible CG with
+// it does not reach the tolerance (or breaks down), the solve is redone from
+// scratch with MIC(0)-PCG.
+int solve_pressure(fs_ctx *c, fs_stats *st)
+{
+    int rc = solve_pressure_once(c, st);
+    if (c->prm.precond != FS_PRECOND_LEARNED || rc == FS_OK || rc == FS_ECUDA || rc == FS_EINVAL ||
+        rc == FS_ESTATE || rc == FS_ETIMEOUT)
+        return rc;
+    c->prm.precond = FS_PRECOND_MIC0;
+    if (st) {
+        st->status = FS_OK;
+        st->fallbacks += 1;
+    }
+    rc = solve_pressure_once(c, st);
+    c->prm.precond = FS_PRECOND_LEARNED;
+    return rc;
 }
 
 int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st)
@@ -699,6 +748,14 @@ __global__ void k_jacobi(const float *__restrict__ r, float *z, const uint8_t *_
 }
 }  // namespace
 
+int cell_in(fs_ctx *c, const float *src, float *dst)
+{
+    k_cell_in<<<grid_blocks(c, c->L.S, TH), TH, 0, c->stream>>>(src, dst, c->cflag, c->L);
+    c->n_launches += 1;
+    FS_CUDA(cudaGetLastError());
+    return FS_OK;
+}
+
 int precond_apply_public(fs_ctx *c, const float *r, float *z)
 {
     const Layout &L = c->L;
@@ -717,7 +774,8 @@ int precond_apply_public(fs_ctx *c, const float *r, float *z)
         int rc = mic0_apply(c, c->pr, c->pz);
         if (rc) return rc;
     } else {
-        return set_error(FS_ESTATE, "the learned preconditioner has no network loaded");
+        int rc = net_apply(c, c->pr, c->pz);
+        if (rc) return rc;
     }
     k_cell_out<<<bs, TH, 0, c->stream>>>(c->pz, z, L);
     c->n_launches += 1;

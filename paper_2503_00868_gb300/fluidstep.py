@@ -45,7 +45,8 @@ class fs_params(C.Structure):
 
 class fs_stats(C.Structure):
     _fields_ = [("status", C.c_int), ("iters_p", C.c_int), ("iters_v", C.c_int),
-                ("relres_p", C.c_double), ("relres_v", C.c_double), ("true_relres_p", C.c_double)]
+                ("relres_p", C.c_double), ("relres_v", C.c_double), ("true_relres_p", C.c_double),
+                ("fallbacks", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -84,6 +85,15 @@ _SIGS = {
     "fs_profile": ([C.c_void_p, C.c_int], C.c_int),
     "fs_profile_read": ([C.c_void_p, C.POINTER(fs_kernel_time), C.c_int, C.POINTER(C.c_int)], C.c_int),
     "fs_precond_apply": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "fs_net_param_count": ([], C.c_int),
+    "fs_net_load": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int], C.c_int),
+    "fs_net_read": ([C.c_void_p, C.c_void_p, C.c_int], C.c_int),
+    "fs_net_forward": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "fs_net_grad": ([C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)], C.c_int),
+    "fs_net_grad_read": ([C.c_void_p, C.c_void_p, C.c_int], C.c_int),
+    "fs_net_adam": ([C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.c_double], C.c_int),
+    "fs_net_train_step": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int,
+                           C.POINTER(C.c_double)], C.c_int),
     "fs_project_noalloc": ([C.c_int, C.c_int, C.c_int, C.c_void_p, C.POINTER(fs_mac), C.c_void_p, C.c_double,
                             C.c_double, C.c_int, C.c_void_p, C.POINTER(fs_stats)], C.c_int),
     "fs_last_error": ([], C.c_char_p),
@@ -223,6 +233,59 @@ def fs_precond_apply(ctx: int, r: torch.Tensor, z: torch.Tensor) -> None:
         if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
             raise ValueError("r and z must be contiguous float32 CUDA tensors")
     _check(load().fs_precond_apply(C.c_void_p(ctx), C.c_void_p(r.data_ptr()), C.c_void_p(z.data_ptr())), (FS_OK,))
+
+
+def _cell(t: torch.Tensor) -> C.c_void_p:
+    if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("cell arrays must be contiguous float32 CUDA tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+def fs_net_param_count() -> int:
+    return load().fs_net_param_count()
+
+
+def fs_net_load(ctx: int, params) -> None:
+    """params: 1-D float32 array (numpy, CPU or CUDA tensor) in PyTorch Conv3d order."""
+    if isinstance(params, torch.Tensor) and params.is_cuda:
+        p = params.detach().to(torch.float32).contiguous()
+        _check(load().fs_net_load(C.c_void_p(ctx), C.c_void_p(p.data_ptr()), p.numel(), 0), (FS_OK,))
+    else:
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float32).ravel())
+        _check(load().fs_net_load(C.c_void_p(ctx), p.ctypes.data_as(C.c_void_p), p.size, 1), (FS_OK,))
+
+
+def fs_net_read(ctx: int) -> np.ndarray:
+    out = np.zeros(fs_net_param_count(), dtype=np.float32)
+    _check(load().fs_net_read(C.c_void_p(ctx), out.ctypes.data_as(C.c_void_p), out.size), (FS_OK,))
+    return out
+
+
+def fs_net_forward(ctx: int, r: torch.Tensor, z: torch.Tensor) -> None:
+    _check(load().fs_net_forward(C.c_void_p(ctx), _cell(r), _cell(z)), (FS_OK,))
+
+
+def fs_net_grad(ctx: int, b: torch.Tensor, q: torch.Tensor) -> float:
+    loss = C.c_double(0.0)
+    _check(load().fs_net_grad(C.c_void_p(ctx), _cell(b), _cell(q), C.byref(loss)), (FS_OK,))
+    return loss.value
+
+
+def fs_net_grad_read(ctx: int) -> np.ndarray:
+    out = np.zeros(fs_net_param_count(), dtype=np.float32)
+    _check(load().fs_net_grad_read(C.c_void_p(ctx), out.ctypes.data_as(C.c_void_p), out.size), (FS_OK,))
+    return out
+
+
+def fs_net_adam(ctx: int, lr: float, step: int, beta1=0.9, beta2=0.999, eps=1e-8, grad_scale=1.0) -> None:
+    _check(load().fs_net_adam(C.c_void_p(ctx), lr, beta1, beta2, eps, step, grad_scale), (FS_OK,))
+
+
+def fs_net_train_step(ctx: int, b_batch: torch.Tensor, q_batch: torch.Tensor, lr: float, step: int) -> float:
+    loss = C.c_double(0.0)
+    _check(load().fs_net_train_step(C.c_void_p(ctx), _cell(b_batch), _cell(q_batch), b_batch.shape[0], lr, step,
+                                    C.byref(loss)), (FS_OK,))
+    return loss.value
 
 
 def fs_project_noalloc(nx: int, ny: int, nz: int, cell_type_dense: torch.Tensor, u: Mac,

@@ -1,0 +1,120 @@
+"""GPU learned preconditioner: the BF16 tensor-core network against the FP64
+oracle (which rounds weights, the input and every hidden activation to bf16
+like the GPU stores them), its gradients against the oracle's backpropagation,
+training reducing the loss, and flexible CG with the network."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2503_00868_gb300 import fluidstep as F
+from paper_2503_00868_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+CH = (2, 16, 16, 16, 16, 1)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2503_00868_gb300 import build as B
+    B.build()
+    O.build()
+    torch.cuda.set_device(0)
+
+
+def rand_params(seed, scale=1.0):
+    """Flat FP32 parameters (PyTorch Conv3d order) with bf16-representable values,
+    and the same as per-layer float64 arrays for the oracle."""
+    rng = np.random.default_rng(seed)
+    Ws, Bs, flat = [], [], []
+    for l in range(5):
+        fan = CH[l] * 27
+        w = rng.standard_normal((CH[l + 1], CH[l], 3, 3, 3)) * np.sqrt(2.0 / fan) * scale
+        w = torch.from_numpy(w).to(torch.bfloat16).to(torch.float64).numpy()
+        b = rng.standard_normal(CH[l + 1]) * 0.05
+        b = torch.from_numpy(b).to(torch.float32).to(torch.float64).numpy()
+        Ws.append(w)
+        Bs.append(b)
+        flat += [w.ravel(), b.ravel()]
+    return np.concatenate(flat).astype(np.float32), Ws, Bs
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def setup(nx, ny, nz, seed=2):
+    types, _ = W.ellipsoid_blob(nx, ny, nz, seed)
+    types[0, 0, :3] = 2  # a few solid cells: the type channel takes all three codes
+    og = O.Grid(types, 1.0 / ny, 1 / 30, 0.01)
+    gg = F.Grid(nx, ny, nz, dx=1.0 / ny, tol_p=1e-6, maxit_p=3000)
+    gg.set_mask(types)
+    return types, og, gg
+
+
+def test_param_count_matches_layout():
+    assert F.fs_net_param_count() == sum(CH[l] * CH[l + 1] * 27 + CH[l + 1] for l in range(5))
+
+
+def test_forward_matches_oracle():
+    types, og, gg = setup(37, 21, 26)   # ragged against the 32 x 8 conv tiles
+    flat, Ws, Bs = rand_params(1)
+    F.fs_net_load(gg.ctx, flat)
+    r = np.where(types == 1, np.random.default_rng(5).standard_normal(types.shape), 0.0)
+    z = gg.empty_cell()
+    F.fs_net_forward(gg.ctx, gg.pack_cell(r), z)
+    zo = O.net_forward(og, Ws, Bs, r)
+    assert rel(gg.unpack_cell(z), zo) < 5e-3
+    assert np.all(gg.unpack_cell(z)[types != 1] == 0.0)
+    np.testing.assert_allclose(F.fs_net_read(gg.ctx), flat, rtol=0, atol=0)
+
+
+def test_gradients_match_oracle():
+    types, og, gg = setup(30, 17, 19, seed=5)
+    flat, Ws, Bs = rand_params(3)
+    F.fs_net_load(gg.ctx, flat)
+    rng = np.random.default_rng(7)
+    b = np.where(types == 1, rng.standard_normal(types.shape), 0.0)
+    q = np.where(types == 1, rng.standard_normal(types.shape), 0.0)
+    loss = F.fs_net_grad(gg.ctx, gg.pack_cell(b), gg.pack_cell(q))
+    g = F.fs_net_grad_read(gg.ctx)
+    lo, gW, gB = O.net_loss_grad(og, Ws, Bs, b, q)
+    assert abs(loss - lo) <= 5e-3 * abs(lo)
+    off = 0
+    for l in range(5):
+        nw, nb = gW[l].size, gB[l].size
+        assert rel(g[off:off + nw], gW[l].ravel()) < 2e-2, f"layer {l + 1} weights"
+        off += nw
+        assert rel(g[off:off + nb], gB[l].ravel()) < 2e-2, f"layer {l + 1} bias"
+        off += nb
+
+
+def test_training_reduces_loss_and_fcg_converges():
+    types, og, gg = setup(24, 24, 24, seed=8)
+    flat, _, _ = rand_params(11, scale=0.5)
+    F.fs_net_load(gg.ctx, flat)
+    # training pairs: random right-hand sides, labels from the solver (MIC(0)-PCG)
+    gm = F.Grid(24, 24, 24, dx=1 / 24, tol_p=1e-7, precond=F.FS_PRECOND_MIC0)
+    gm.set_mask(types)
+    pairs = []
+    for s in range(6):
+        u = gm.pack(W.random_mac(24, 24, 24, 100 + s))
+        q = gm.empty_cell()
+        gm.project(u, q)                       # L_p q = b, b = -dx div(u) on liquid cells
+        bn = O.divergence(og, W.random_mac(24, 24, 24, 100 + s))
+        pairs.append((gm.pack_cell(bn), q))
+    losses = []
+    for step in range(1, 41):
+        l = 0.0
+        for b, q in pairs:
+            l += F.fs_net_grad(gg.ctx, b, q)
+        F.fs_net_adam(gg.ctx, 2e-3, step, grad_scale=1.0 / len(pairs))
+        losses.append(l / len(pairs))
+    assert losses[-1] < 0.8 * losses[0], losses[::8]
+    # flexible CG with the trained network reaches the tolerance (true residual)
+    gg.set_params(precond=F.FS_PRECOND_LEARNED)
+    u = gg.pack(W.random_mac(24, 24, 24, 999))
+    rc, st = gg.project(u)
+    assert rc == F.FS_OK and st["true_relres_p"] < 1e-5, st
