@@ -198,6 +198,11 @@ int fs_adjoint_step(fs_ctx *c, const fs_mac *u_in, const fs_mac *u_visc,
 int fs_loss_grad(fs_ctx *c, const fs_mac *u, const fs_mac *target, int mask_kind,
                  double alpha, double beta, double *loss, fs_mac *g);
 
+/* The right-hand side of the pressure equation for a field u (Sec. 3.2.2):
+ * b = -dx * div(u) on liquid cells (the liquid mean removed when the operator is
+ * singular), zero elsewhere. u: DEVICE field; b_out: DEVICE cell array. */
+int fs_divergence(fs_ctx *c, const fs_mac *u, float *b_out);
+
 /* Apply the pressure preconditioner selected in the parameters to one vector:
  * z = M^-1 r on the liquid cells (zero elsewhere). Jacobi: M = diag(L_p);
  * MIC(0): M = L L^T with the modified incomplete Cholesky factor of L_p (Bridson,
@@ -232,8 +237,11 @@ int fs_net_read(fs_ctx *c, float *params_host, int count);
 int fs_net_forward(fs_ctx *c, const float *r, float *z);
 
 /* Training on one (b, q) pair with L_p q = b on the context's mask (DEVICE cell
- * arrays): loss = sum_liq (Net(b/s) - q/s)^2 / sum_liq (q/s)^2 is ADDED to *loss
- * (host) and its gradient ADDED to the context's gradient accumulator. */
+ * arrays): with y = Net(b/s) and e = y - q/s on liquid cells, the relative error
+ * in the energy norm of the pressure operator, loss = e.L_p e / (q/s).L_p (q/s)
+ * (the fitted network should give the pressure of the Laplacian scheme,
+ * Sec. 3.4.1), is ADDED to *loss (host) and its gradient ADDED to the context's
+ * gradient accumulator. */
 int fs_net_grad(fs_ctx *c, const float *b, const float *q, double *loss);
 
 /* Copy the accumulated gradient to HOST memory (`count` values). */
@@ -241,12 +249,16 @@ int fs_net_grad_read(fs_ctx *c, float *grad_host, int count);
 
 /* One Adam step (bias-corrected, `step` >= 1) on the FP32 master parameters with
  * the accumulated gradient times grad_scale; clears the accumulator and refreshes
- * the bf16 working copies. */
-int fs_net_adam(fs_ctx *c, double lr, double beta1, double beta2, double eps, int step, double grad_scale);
+ * the bf16 working copies. fix_offsets = 1 keeps every bias and the weights of the
+ * cell-type input channel at their current values: when those are zero the
+ * network is positively homogeneous, Net(a x) = a Net(x) for a >= 0, so the
+ * preconditioner responds to a shrinking residual in proportion. */
+int fs_net_adam(fs_ctx *c, double lr, double beta1, double beta2, double eps, int step, double grad_scale,
+                int fix_offsets);
 
 /* fs_net_grad over `batch` pairs stored back to back (each `nelems` floats of the
  * library layout) followed by fs_net_adam with grad_scale = 1/batch (beta1 0.9,
- * beta2 0.999, eps 1e-8). *loss receives the mean loss of the batch. */
+ * beta2 0.999, eps 1e-8, fix_offsets 1). *loss receives the mean loss of the batch. */
 int fs_net_train_step(fs_ctx *c, const float *b_batch, const float *q_batch, int batch, double lr, int step,
                       double *loss);
 

@@ -1016,9 +1016,12 @@ double or_net_forward(const or_grid *g, const double *const W[NET_LAYERS],
     return s;
 }
 
-/* Training loss for one (b, q) pair with A q = b:
- *   s = max |b| over liquid;  y = Net(b / s);
- *   loss = sum_liquid (y - q/s)^2 / sum_liquid (q/s)^2.
+/* Training loss for one (b, q) pair with A q = b (A the pressure operator):
+ *   s = max |b| over liquid;  y = Net(b / s);  e = y - q/s on liquid cells;
+ *   loss = e^T A e / ((q/s)^T A (q/s)),
+ * the relative error of the predicted pressure in the energy norm of the
+ * discrete Laplacian (Sec. 3.4.1: the fitted network should give the pressure of
+ * the second-order Laplacian scheme). dloss/dy = 2 A e / ((q/s)^T A (q/s)).
  * Returns the loss and ADDS its gradient to gW, gB (same layouts as W, B). */
 double or_net_loss_grad(const or_grid *g, const double *const W[NET_LAYERS],
                         const double *const B[NET_LAYERS], const double *b, const double *q,
@@ -1035,17 +1038,23 @@ double or_net_loss_grad(const or_grid *g, const double *const W[NET_LAYERS],
     offs[0] = 0;
     for (int l = 1; l <= NET_LAYERS; l++) offs[l] = offs[l - 1] + (long)net_ch[l - 1] * n;
     const double *y = acts + offs[NET_LAYERS];
-    double den = 0.0, num = 0.0;
+    double *ev = (double *)calloc((size_t)n, sizeof(double));
+    double *tq = (double *)calloc((size_t)n, sizeof(double));
+    double *Aev = (double *)calloc((size_t)n, sizeof(double));
+    double *Atq = (double *)calloc((size_t)n, sizeof(double));
     for (long t = 0; t < n; t++)
-        if (g->type[t] == LIQUID) { double tq = q[t] / s; den += tq * tq; }
+        if (g->type[t] == LIQUID) {
+            tq[t] = q[t] / s;
+            ev[t] = y[t] - tq[t];
+        }
+    or_poisson_apply(g, ev, Aev);
+    or_poisson_apply(g, tq, Atq);
+    double den = dot(tq, Atq, n), num = dot(ev, Aev, n);
     double *gy = (double *)calloc((size_t)n * 16, sizeof(double));
     double *gx = (double *)calloc((size_t)n * 16, sizeof(double));
     for (long t = 0; t < n; t++)
-        if (g->type[t] == LIQUID) {
-            double e = y[t] - q[t] / s;
-            num += e * e;
-            gy[t] = 2.0 * e / den;
-        }
+        if (g->type[t] == LIQUID) gy[t] = 2.0 * Aev[t] / den;
+    free(ev); free(tq); free(Aev); free(Atq);
     int nx = g->nx, ny = g->ny, nz = g->nz;
     for (int l = NET_LAYERS - 1; l >= 0; l--) {
         int ci_n = net_ch[l], co_n = net_ch[l + 1];

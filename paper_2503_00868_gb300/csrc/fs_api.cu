@@ -85,7 +85,7 @@ static int alloc_zero(void **p, size_t bytes)
 
 // ---- per-kernel timing ---------------------------------------------------------
 static const char *kKernelNames[K_COUNT] = {"pressure_spmv", "pressure_update", "visc_spmv", "visc_update",
-                                            "advect", "advect_adjoint", "mic0_apply", "net_apply"};
+                                            "advect", "advect_adjoint", "mic0_apply", "net_apply", "fcg_vectors"};
 
 struct Prof {
     std::vector<cudaEvent_t> free_ev, all_ev;
@@ -152,6 +152,7 @@ static void free_ctx(fs_ctx *c)
     if (!c) return;
     prof_destroy(c);
     net_free(c);
+    fcg_release(c);
     void *ptrs[] = {c->cflag, c->fflag, c->bc, c->dsum, c->pb, c->pr, c->pp[0], c->pp[1], c->pq, c->px, c->pz,
                     c->vx, c->vr, c->vp[0], c->vp[1], c->vq, c->fu[0], c->fu[1], c->fu[2], c->fg[0], c->fg[1],
                     c->fg[2], c->gc[0], c->gc[1], c->gc[2], c->mic_prec, c->scal, c->partials, c->err_word,
@@ -487,6 +488,18 @@ int fs_adjoint_step(fs_ctx *c, const fs_mac *u_in, const fs_mac *u_visc, const f
     return s->status;
 }
 
+int fs_divergence(fs_ctx *c, const fs_mac *u, float *b_out)
+{
+    int rc = need_mask(c);
+    if (rc) return rc;
+    if ((rc = check_field(u, "u", false))) return rc;
+    if (!b_out) return set_error(FS_EINVAL, "b_out is NULL");
+    if ((rc = launch_divergence(c, cf3(u)))) return rc;
+    if ((rc = cell_out(c, c->pb, b_out))) return rc;
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    return FS_OK;
+}
+
 int fs_net_param_count(void) { return net_param_count(); }
 
 int fs_net_load(fs_ctx *c, const float *params, int count, int params_on_host)
@@ -532,12 +545,13 @@ int fs_net_grad_read(fs_ctx *c, float *grad_host, int count)
     return net_grad_read(c, grad_host);
 }
 
-int fs_net_adam(fs_ctx *c, double lr, double beta1, double beta2, double eps, int step, double grad_scale)
+int fs_net_adam(fs_ctx *c, double lr, double beta1, double beta2, double eps, int step, double grad_scale,
+                int fix_offsets)
 {
     if (!c) return set_error(FS_EINVAL, "NULL context");
     if (!(lr >= 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0))
         return set_error(FS_EINVAL, "bad Adam hyper-parameters");
-    return net_adam(c, lr, beta1, beta2, eps, step, grad_scale);
+    return net_adam(c, lr, beta1, beta2, eps, step, grad_scale, fix_offsets);
 }
 
 int fs_net_train_step(fs_ctx *c, const float *b_batch, const float *q_batch, int batch, double lr, int step,
@@ -551,7 +565,7 @@ int fs_net_train_step(fs_ctx *c, const float *b_batch, const float *q_batch, int
         rc = net_grad(c, b_batch + (size_t)k * c->L.S, q_batch + (size_t)k * c->L.S, &l);
         if (rc) return rc;
     }
-    rc = net_adam(c, lr, 0.9, 0.999, 1e-8, step, 1.0 / batch);
+    rc = net_adam(c, lr, 0.9, 0.999, 1e-8, step, 1.0 / batch, 1);
     if (loss) *loss = l / batch;
     return rc;
 }

@@ -129,8 +129,10 @@ struct fs_ctx {
     int *mic_next;        // work counter of the running sweep
     int mic_n, mic_epoch, mic_ntiles;
 
-    // learned preconditioner (fs_net.cu), allocated on first use
+    // learned preconditioner (fs_net.cu) and its flexible-CG direction ring
+    // (fs_fcg.cu), allocated on first use
     void *net;
+    void *fcg;
 
     // reductions
     fs::SolveScal *scal;        // device [4]: 0 pressure, 1 viscosity, 2 misc, 3 misc
@@ -278,15 +280,22 @@ int net_load(fs_ctx *c, const float *params, int count, bool host);
 int net_read(fs_ctx *c, float *params_host);
 int net_apply(fs_ctx *c, const float *r, float *z);   // cell space
 int net_grad(fs_ctx *c, const float *b, const float *q, double *loss);  // public layout
-int net_adam(fs_ctx *c, double lr, double beta1, double beta2, double eps, int step, double gscale);
+int net_adam(fs_ctx *c, double lr, double beta1, double beta2, double eps, int step, double gscale,
+             int fix_offsets);
 int net_grad_read(fs_ctx *c, float *grad_host);
 int net_grad_clear(fs_ctx *c);
 int net_param_count();
 bool net_loaded(const fs_ctx *c);
 // public cell array -> cell space, zero off liquid
 int cell_in(fs_ctx *c, const float *src, float *dst);
+int cell_out(fs_ctx *c, const float *src, float *dst);  // cell space -> public cell array
 
 int read_scal(fs_ctx *c, int which, SolveScal *out);
+// mean-free preconditioned residual over the liquid when the operator is singular
+int remove_null_mode(fs_ctx *c, float *z);
+// fs_fcg.cu: flexible CG with the network, pb -> px; final scalars in *h
+int solve_pressure_fcg(fs_ctx *c, SolveScal *h);
+void fcg_release(fs_ctx *c);
 
 // ---- per-kernel timing -------------------------------------------------------
 enum KernelId : int {
@@ -298,6 +307,7 @@ enum KernelId : int {
     K_ADVECT_ADJ,
     K_MIC_APPLY,
     K_NET_APPLY,
+    K_FCG_VEC,
     K_COUNT
 };
 cudaEvent_t prof_mark(fs_ctx *c);   // records an event on the stream (nullptr when off)

@@ -285,20 +285,37 @@ __global__ void k_absmax(const float *__restrict__ r, const uint8_t *__restrict_
 // s is rounded to bf16 (the oracle rounds x = r/s, not s; keep s exact)
 // ---- training: loss, gradients -----------------------------------------------------
 
-// loss terms: sum_liq (y - q/s)^2 and sum_liq (q/s)^2 -> scal aux[0], aux[1]
-__global__ void __launch_bounds__(256) k_net_loss(const float *__restrict__ y, const float *__restrict__ q,
-                                                  const uint8_t *__restrict__ cf, const unsigned *__restrict__ smax,
-                                                  int n, SolveScal *s, double *partials)
+// Energy-norm loss (y - q/s)^T A (y - q/s) / ((q/s)^T A (q/s)), A the pressure
+// operator. Pass 1: e = y - q/s and t = q/s on liquid cells (zero elsewhere).
+__global__ void k_net_err(const float *__restrict__ y, const float *__restrict__ q, const uint8_t *__restrict__ cf,
+                          const unsigned *__restrict__ smax, float *e, float *tq, int n)
 {
     const float sc = __uint_as_float(*smax);
     const float inv = sc > 0.f ? 1.f / sc : 0.f;
-    double num = 0.0, den = 0.0;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        if (!(cf[t] & CF_LIQ)) continue;
-        const double tq = (double)q[t] * inv;
-        const double e = (double)y[t] - tq;
-        num += e * e;
-        den += tq * tq;
+        const bool liq = (cf[t] & CF_LIQ) != 0;
+        const float tv = liq ? q[t] * inv : 0.f;
+        tq[t] = tv;
+        e[t] = liq ? y[t] - tv : 0.f;
+    }
+}
+
+// Pass 2: Ae (kept for the gradient), e.Ae and t.At -> aux[0], aux[1].
+__global__ void __launch_bounds__(256) k_net_energy(const float *__restrict__ e, const float *__restrict__ tq,
+                                                    float *ae, const uint8_t *__restrict__ cf, Layout L,
+                                                    SolveScal *s, double *partials)
+{
+    double num = 0.0, den = 0.0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < L.nC; t += gridDim.x * blockDim.x) {
+        const uint8_t f = cf[t];
+        if (!(f & CF_LIQ)) continue;
+        const float d = (float)(f & CF_D);
+        const float av = d * e[t] - ((e[t - 1] + e[t + 1]) + (e[t - L.P] + e[t + L.P]) + (e[t - L.PL] + e[t + L.PL]));
+        const float at = d * tq[t] - ((tq[t - 1] + tq[t + 1]) + (tq[t - L.P] + tq[t + L.P]) +
+                                      (tq[t - L.PL] + tq[t + L.PL]));
+        ae[t] = av;
+        num += (double)e[t] * av;
+        den += (double)tq[t] * at;
     }
     double v[2] = {num, den}, tot[2];
     if (grid_reduce<2>(v, partials, &s->ticket, tot) && threadIdx.x == 0) {
@@ -307,15 +324,14 @@ __global__ void __launch_bounds__(256) k_net_loss(const float *__restrict__ y, c
     }
 }
 
-__global__ void k_net_gy(const float *__restrict__ y, const float *__restrict__ q, const uint8_t *__restrict__ cf,
-                         const unsigned *__restrict__ smax, const SolveScal *s, float *gy, int n)
+// Pass 3: dloss/dy = 2 A e / den on liquid cells.
+__global__ void k_net_gy(const float *__restrict__ ae, const uint8_t *__restrict__ cf, const SolveScal *s, float *gy,
+                         int n)
 {
-    const float sc = __uint_as_float(*smax);
-    const float inv = sc > 0.f ? 1.f / sc : 0.f;
     const double den = s->aux[1];
     const float g = den > 0.0 ? (float)(2.0 / den) : 0.f;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
-        gy[t] = (cf[t] & CF_LIQ) ? g * (y[t] - q[t] * inv) : 0.f;
+        gy[t] = (cf[t] & CF_LIQ) ? g * ae[t] : 0.f;
 }
 
 // dL/d(layer-5 input) = sum_tap w5[ci][tap] gy[cell - tap], times [a4 > 0]
@@ -418,11 +434,25 @@ __global__ void __launch_bounds__(256) k_wgrad(const void *__restrict__ gptr, co
     if (tid < COUT) atomicAdd(gB + tid, bpart);
 }
 
-// Adam on the FP32 master copy; the gradient buffer is cleared.
+// A parameter that does not depend on the residual: a bias, or a weight of the
+// cell-type input channel (W1[co][1][tap]).
+__device__ __forceinline__ bool offset_param(int t)
+{
+    if (t < OB1) return (t / 27) % 2 == 1;
+    return (t >= OB1 && t < OW2) || (t >= OB2 && t < OW3) || (t >= OB3 && t < OW4) || (t >= OB4 && t < OW5) ||
+           t >= OB5;
+}
+
+// Adam on the FP32 master copy; the gradient buffer is cleared. With
+// `fix_offsets` the offset parameters keep their values.
 __global__ void k_adam(float *p, float *g, float *m, float *v, int n, float lr, float b1, float b2, float eps,
-                       float c1, float c2, float gscale)
+                       float c1, float c2, float gscale, int fix_offsets)
 {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        if (fix_offsets && offset_param(t)) {
+            g[t] = 0.f;
+            continue;
+        }
         const float gr = g[t] * gscale;
         const float mm = b1 * m[t] + (1.f - b1) * gr;
         const float vv = b2 * v[t] + (1.f - b2) * gr * gr;
@@ -619,8 +649,10 @@ int net_grad(fs_ctx *c, const float *b, const float *q, double *loss)
     __nv_bfloat16 *A[5];
     for (int l = 0; l < 5; l++) A[l] = n->act + (size_t)l * nC * 16;
     SolveScal *s = c->scal + 3;
-    k_net_loss<<<grid_blocks(c, L.nC, 256), 256, 0, c->stream>>>(n->y, c->px, c->cflag, n->smax, L.nC, s, c->partials);
-    k_net_gy<<<grid_blocks(c, L.nC, 256), 256, 0, c->stream>>>(n->y, c->px, c->cflag, n->smax, s, n->gy, L.nC);
+    // energy-norm loss; scratch: pr = e, pz = q/s, pq = A e (no solve runs meanwhile)
+    k_net_err<<<grid_blocks(c, L.nC, 256), 256, 0, c->stream>>>(n->y, c->px, c->cflag, n->smax, c->pr, c->pz, L.nC);
+    k_net_energy<<<grid_blocks(c, L.nC, 256), 256, 0, c->stream>>>(c->pr, c->pz, c->pq, c->cflag, L, s, c->partials);
+    k_net_gy<<<grid_blocks(c, L.nC, 256), 256, 0, c->stream>>>(c->pq, c->cflag, s, n->gy, L.nC);
     // layer 5
     const int wg = std::max(1, std::min(((L.nx + NT_X - 1) / NT_X) * ((L.ny + NT_Y - 1) / NT_Y) * L.nz, c->num_sms * 2));
     k_wgrad<16, 1, true><<<wg, 256, wgrad_smem<16, 1>(), c->stream>>>(n->gy, A[4], n->grad + OW5, n->grad + OB5, L);
@@ -638,7 +670,7 @@ int net_grad(fs_ctx *c, const float *b, const float *q, double *loss)
     }
     // layer 1: gradient w.r.t. W1 from the stored input x (2 channels used)
     k_wgrad<2, 16, false><<<wg, 256, wgrad_smem<2, 16>(), c->stream>>>(G[gi], A[0], n->grad + OW1, n->grad + OB1, L);
-    c->n_launches += 2 + 2 + 6 + 1;
+    c->n_launches += 3 + 2 + 6 + 1;
     FS_CUDA(cudaGetLastError());
     SolveScal h;
     if ((rc = read_scal(c, 3, &h))) return rc;
@@ -646,7 +678,7 @@ int net_grad(fs_ctx *c, const float *b, const float *q, double *loss)
     return FS_OK;
 }
 
-int net_adam(fs_ctx *c, double lr, double beta1, double beta2, double eps, int step, double gscale)
+int net_adam(fs_ctx *c, double lr, double beta1, double beta2, double eps, int step, double gscale, int fix_offsets)
 {
     NetState *n = net(c);
     if (!n || !n->loaded || !n->gact) return set_error(FS_ESTATE, "no gradients accumulated");
@@ -654,7 +686,7 @@ int net_adam(fs_ctx *c, double lr, double beta1, double beta2, double eps, int s
     const float c1 = (float)(1.0 - std::pow(beta1, step)), c2 = (float)(1.0 - std::pow(beta2, step));
     k_adam<<<(NPARAM + 255) / 256, 256, 0, c->stream>>>(n->master, n->grad, n->m, n->v, NPARAM, (float)lr,
                                                         (float)beta1, (float)beta2, (float)eps, c1, c2,
-                                                        (float)gscale);
+                                                        (float)gscale, fix_offsets);
     k_net_refresh<<<(NPARAM + 255) / 256, 256, 0, c->stream>>>(n->master, n->w1f, n->w5f, n->wf, n->wt);
     c->n_launches += 2;
     FS_CUDA(cudaGetLastError());

@@ -11,6 +11,8 @@
 // iterations. Once `done` is set every later kernel of the batch returns at once.
 #include <algorithm>
 #include <cmath>
+#include <utility>
+#include <vector>
 
 #include "fs_internal.cuh"
 
@@ -143,30 +145,6 @@ __global__ void __launch_bounds__(TH) k_rz(const float *__restrict__ r, const fl
     if (grid_reduce<1>(v, partials, &s->ticket, tot) && threadIdx.x == 0) {
         if (!isfinite(tot[0])) { s->done = 1; s->status = FS_ENONFINITE; return; }
         s->beta = first ? 0.0 : tot[0] / s->rz;
-        s->rz = tot[0];
-    }
-}
-
-// Flexible CG with a nonlinear preconditioner (the network): after z_{k+1} =
-// M(r_{k+1}), beta = -z_{k+1}.A p_k / p_k.A p_k (one step of A-orthogonalisation
-// against the previous direction, Notay's flexible CG) and r.z for the next alpha.
-__global__ void __launch_bounds__(TH) k_fcg(const float *__restrict__ r, const float *__restrict__ z,
-                                            const float *__restrict__ q, int n4, SolveScal *s, double *partials)
-{
-    if (s->done) return;
-    KSum rz, zq;
-    const float4 *r4 = reinterpret_cast<const float4 *>(r);
-    const float4 *z4 = reinterpret_cast<const float4 *>(z);
-    const float4 *q4 = reinterpret_cast<const float4 *>(q);
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += gridDim.x * blockDim.x) {
-        const float4 a = __ldg(r4 + t), b = __ldg(z4 + t), c = __ldg(q4 + t);
-        rz.add(a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w);
-        zq.add(b.x * c.x + b.y * c.y + b.z * c.z + b.w * c.w);
-    }
-    double v[2] = {rz.value(), zq.value()}, tot[2];
-    if (grid_reduce<2>(v, partials, &s->ticket, tot) && threadIdx.x == 0) {
-        if (!isfinite(tot[0]) || !isfinite(tot[1])) { s->done = 1; s->status = FS_ENONFINITE; return; }
-        s->beta = -tot[1] / s->pq;
         s->rz = tot[0];
     }
 }
@@ -511,7 +489,7 @@ int launch_divergence(fs_ctx *c, CF3 u)
 // preconditioned residual is made mean-free over the liquid, so every search
 // direction stays in the range of the operator (the preconditioner becomes
 // P M^-1 P with P the mean-removing projector, still SPD on that range).
-static int remove_null_mode(fs_ctx *c, float *z)
+int remove_null_mode(fs_ctx *c, float *z)
 {
     if (!c->singular) return FS_OK;
     const Layout &L = c->L;
@@ -522,6 +500,8 @@ static int remove_null_mode(fs_ctx *c, float *z)
     FS_CUDA(cudaGetLastError());
     return FS_OK;
 }
+
+static int pressure_tail(fs_ctx *c, const SolveScal &h, fs_stats *st);
 
 static int solve_pressure_once(fs_ctx *c, fs_stats *st)
 {
@@ -538,8 +518,14 @@ static int solve_pressure_once(fs_ctx *c, fs_stats *st)
         int rc = mic0_factor(c);
         if (rc) return rc;
     }
-    // z = M r for the stored-z preconditioners (MIC(0) or the network)
-    auto apply_m = [&]() -> int { return learned ? net_apply(c, c->pr, c->pz) : mic0_apply(c, c->pr, c->pz); };
+    SolveScal h;
+    if (learned) {
+        int rc = solve_pressure_fcg(c, &h);
+        if (rc) return rc;
+        return pressure_tail(c, h, st);
+    }
+    // z = M r for MIC(0), the stored-z preconditioner
+    auto apply_m = [&]() -> int { return mic0_apply(c, c->pr, c->pz); };
     if (jac)
         k_pois_init<true><<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(
             c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, n4, tol2, c->prm.maxit_p, s, c->partials);
@@ -558,7 +544,6 @@ static int solve_pressure_once(fs_ctx *c, fs_stats *st)
     const int b4 = grid_blocks(c, n4, TH);
     int cur = 0;
     long long launched = 0;
-    SolveScal h;
     const double by_spmv = (double)L.nC + 16.0 * (double)c->n_liquid;
     const double by_upd = (double)L.nC + 24.0 * (double)c->n_liquid;
     const bool tiled = c->act_cell != nullptr;
@@ -599,10 +584,7 @@ static int solve_pressure_once(fs_ctx *c, fs_stats *st)
                 int rc = apply_m();
                 if (rc) return rc;
                 if ((rc = remove_null_mode(c, c->pz))) return rc;
-                if (learned)
-                    k_fcg<<<b4, TH, 0, c->stream>>>(c->pr, c->pz, c->pq, n4, s, c->partials);
-                else
-                    k_rz<<<b4, TH, 0, c->stream>>>(c->pr, c->pz, n4, 0, s, c->partials);
+                k_rz<<<b4, TH, 0, c->stream>>>(c->pr, c->pz, n4, 0, s, c->partials);
                 c->n_launches += 1;
             }
             cur ^= 1;
@@ -626,6 +608,15 @@ static int solve_pressure_once(fs_ctx *c, fs_stats *st)
                              c->prm.spin_limit);
         }
     }
+    return pressure_tail(c, h, st);
+}
+
+// After the iterations: the true residual b - A x, the mean-free representative
+// of a singular solve, and the statistics.
+static int pressure_tail(fs_ctx *c, const SolveScal &h, fs_stats *st)
+{
+    const Layout &L = c->L;
+    const int bs = grid_blocks(c, L.nC, TH);
     // true residual, then the mean-free representative of a singular solve
     k_pois_true_res<<<bs, TH, 0, c->stream>>>(c->pb, c->px, c->cflag, L.nC, L.P, L.PL, c->scal + 2, c->partials);
     c->n_launches += 1;
@@ -751,6 +742,14 @@ __global__ void k_jacobi(const float *__restrict__ r, float *z, const uint8_t *_
 int cell_in(fs_ctx *c, const float *src, float *dst)
 {
     k_cell_in<<<grid_blocks(c, c->L.S, TH), TH, 0, c->stream>>>(src, dst, c->cflag, c->L);
+    c->n_launches += 1;
+    FS_CUDA(cudaGetLastError());
+    return FS_OK;
+}
+
+int cell_out(fs_ctx *c, const float *src, float *dst)
+{
+    k_cell_out<<<grid_blocks(c, c->L.S, TH), TH, 0, c->stream>>>(src, dst, c->L);
     c->n_launches += 1;
     FS_CUDA(cudaGetLastError());
     return FS_OK;

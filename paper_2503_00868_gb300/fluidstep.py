@@ -85,13 +85,15 @@ _SIGS = {
     "fs_profile": ([C.c_void_p, C.c_int], C.c_int),
     "fs_profile_read": ([C.c_void_p, C.POINTER(fs_kernel_time), C.c_int, C.POINTER(C.c_int)], C.c_int),
     "fs_precond_apply": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "fs_divergence": ([C.c_void_p, C.POINTER(fs_mac), C.c_void_p], C.c_int),
     "fs_net_param_count": ([], C.c_int),
     "fs_net_load": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int], C.c_int),
     "fs_net_read": ([C.c_void_p, C.c_void_p, C.c_int], C.c_int),
     "fs_net_forward": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "fs_net_grad": ([C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)], C.c_int),
     "fs_net_grad_read": ([C.c_void_p, C.c_void_p, C.c_int], C.c_int),
-    "fs_net_adam": ([C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.c_double], C.c_int),
+    "fs_net_adam": ([C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int],
+                    C.c_int),
     "fs_net_train_step": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int,
                            C.POINTER(C.c_double)], C.c_int),
     "fs_project_noalloc": ([C.c_int, C.c_int, C.c_int, C.c_void_p, C.POINTER(fs_mac), C.c_void_p, C.c_double,
@@ -241,6 +243,10 @@ def _cell(t: torch.Tensor) -> C.c_void_p:
     return C.c_void_p(t.data_ptr())
 
 
+def fs_divergence(ctx: int, u: Mac, b_out: torch.Tensor) -> None:
+    _check(load().fs_divergence(C.c_void_p(ctx), _ref(_mac(u)), _cell(b_out)), (FS_OK,))
+
+
 def fs_net_param_count() -> int:
     return load().fs_net_param_count()
 
@@ -277,8 +283,10 @@ def fs_net_grad_read(ctx: int) -> np.ndarray:
     return out
 
 
-def fs_net_adam(ctx: int, lr: float, step: int, beta1=0.9, beta2=0.999, eps=1e-8, grad_scale=1.0) -> None:
-    _check(load().fs_net_adam(C.c_void_p(ctx), lr, beta1, beta2, eps, step, grad_scale), (FS_OK,))
+def fs_net_adam(ctx: int, lr: float, step: int, beta1=0.9, beta2=0.999, eps=1e-8, grad_scale=1.0,
+                fix_offsets=True) -> None:
+    _check(load().fs_net_adam(C.c_void_p(ctx), lr, beta1, beta2, eps, step, grad_scale, 1 if fix_offsets else 0),
+           (FS_OK,))
 
 
 def fs_net_train_step(ctx: int, b_batch: torch.Tensor, q_batch: torch.Tensor, lr: float, step: int) -> float:
