@@ -156,7 +156,8 @@ static void free_ctx(fs_ctx *c)
     void *ptrs[] = {c->cflag, c->fflag, c->bc, c->dsum, c->pb, c->pr, c->pp[0], c->pp[1], c->pq, c->px, c->pz,
                     c->vx, c->vr, c->vp[0], c->vp[1], c->vq, c->fu[0], c->fu[1], c->fu[2], c->fg[0], c->fg[1],
                     c->fg[2], c->gc[0], c->gc[1], c->gc[2], c->mic_prec, c->scal, c->partials, c->err_word,
-                    c->act_cell, c->act_face, c->list_cell, c->list_face, c->py, c->mic_order,
+                    c->act_cell, c->act_face, c->list_cell, c->list_face, c->items_cell, c->items_face, c->qmask_cell, c->qmask_face,
+                    c->py, c->mic_order,
                     c->mic_tact, c->mic_tflag, c->mic_next};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -321,6 +322,10 @@ int fs_init_grid(fs_ctx **out, int nx, int ny, int nz, const fs_params *p, void 
     ALLOC(c->act_face, (size_t)c->tm_face.nblocks);
     ALLOC(c->list_cell, (size_t)c->tm_cell.nblocks * sizeof(int));
     ALLOC(c->list_face, (size_t)c->tm_face.nblocks * sizeof(int));
+    ALLOC(c->qmask_cell, (size_t)c->tm_cell.nblocks * 8 * sizeof(unsigned));
+    ALLOC(c->qmask_face, (size_t)c->tm_face.nblocks * 8 * sizeof(unsigned));
+    ALLOC(c->items_cell, (size_t)c->tm_cell.nblocks * sizeof(int4));
+    ALLOC(c->items_face, (size_t)c->tm_face.nblocks * sizeof(int4));
     const int red_blocks = std::max(c->max_blocks, std::max(c->tm_cell.nblocks, c->tm_face.nblocks));
     ALLOC(c->scal, 4 * sizeof(SolveScal));
     ALLOC(c->partials, (size_t)red_blocks * 8 * sizeof(double));
@@ -331,6 +336,10 @@ int fs_init_grid(fs_ctx **out, int nx, int ny, int nz, const fs_params *p, void 
         c->scal_host = nullptr;
         free_ctx(c);
         return set_error(FS_ENOMEM, "pinned allocation failed");
+    }
+    if (int rc = make_tensor_maps(c)) {
+        free_ctx(c);
+        return rc;
     }
     *out = c;
     return FS_OK;

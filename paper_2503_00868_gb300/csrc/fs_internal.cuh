@@ -11,6 +11,7 @@
 // neighbour outside the grid contributes nothing.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -145,6 +146,15 @@ struct fs_ctx {
     uint8_t *act_cell, *act_face;    // per tile block: 1 if it holds an active element
     int *list_cell, *list_face;      // the active tiles, in tile order
     int nact_cell, nact_face;
+    // per listed tile, 8 words (one per tile row) with bit q set when quad q of
+    // that row holds an active element
+    unsigned *qmask_cell, *qmask_face;
+    // z-marching work of the operator apply: {column, k0, k1, 0} chunks of active planes
+    int4 *items_cell, *items_face;
+    int nitems_cell, nitems_face;
+    // tensor maps of the vectors the operator apply reads (3-D: pitch x rows x
+    // planes of the guarded space, 136 x 10 x 1 boxes)
+    CUtensorMap tmz_pr, tmz_pz, tmz_pp[2], tmz_vr, tmz_vp[2];
 
     // per-kernel timing (fs_profile)
     int prof_on;
@@ -255,6 +265,8 @@ __device__ __forceinline__ bool grid_reduce(double (&v)[K], double *partials, un
 // fs_mask.cu
 int build_mask(fs_ctx *c, const uint8_t *types_dense, const fs_mac *bc);
 TileMap make_tilemap(const Layout &L, int nvol, int num_sms);
+int make_tensor_maps(fs_ctx *c);   // fs_mask.cu, once per context
+int zmarch_slots(const fs_ctx *c, bool face);  // fs_pcg.cu: resident blocks of the operator apply
 // fs_pcg.cu
 int solve_pressure(fs_ctx *c, fs_stats *st);             // pb -> px
 int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st);  // vx (guess, rhs) -> vx

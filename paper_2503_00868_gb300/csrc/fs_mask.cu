@@ -1,8 +1,11 @@
 // fs_mask.cu -- grid-type mask set-up: cell and face flag bytes, prescribed
 // face values, Dirichlet sums of the viscosity operator, band and singularity
-// counts. Runs once per mask (Sec. 3.4.2: "grid types of surface, occupation,
-// or empty").
+// counts. Runs once per mask (Sec. 3.4.2: the loss is restricted by a mask
+// derived from the cell types of the grid).
+#include <algorithm>
 #include <vector>
+
+#include <cudaTypedefs.h>
 
 #include "fs_internal.cuh"
 
@@ -166,7 +169,103 @@ __global__ void k_tile_activity(const uint8_t *__restrict__ fl, uint8_t mask, Ti
     }
 }
 
+// Quad-activity words of the listed tiles: block = one listed tile, thread
+// (x, y) = quad x of tile row y; word y of the tile is the ballot of row y.
+__global__ void k_quad_mask(const uint8_t *__restrict__ fl, uint8_t mask, const int *__restrict__ list, TileMap m,
+                            unsigned *qmask)
+{
+    int v, k, tyi, txi;
+    m.decode(list[blockIdx.x], v, k, tyi, txi);
+    const int i = txi * TILE_X + 4 * threadIdx.x, j = tyi * TILE_Y + threadIdx.y;
+    bool act = false;
+    if (i < m.P && j < m.R) {
+        const uchar4 f = *reinterpret_cast<const uchar4 *>(fl + m.origin0 + v * m.vstride + k * m.PL + j * m.P + i);
+        act = ((f.x | f.y | f.z | f.w) & mask) != 0;
+    }
+    const unsigned w = __ballot_sync(0xffffffffu, act);
+    if (threadIdx.x == 0) qmask[(size_t)blockIdx.x * TILE_Y + threadIdx.y] = w;
+}
+
 }  // namespace
+
+// The driver's tensor-map encoder, found through the runtime (no link to libcuda).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// A guarded space as a 3-D FP32 tensor: x = pitch, y = rows, z = planes (guard
+// planes included), with a box of bx x by x 1 elements. Out-of-range elements
+// of a box read as zero.
+static int encode_map(CUtensorMap *m, float *base, const Layout &L, long long len, int bx, int by)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return set_error(FS_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint64_t dims[3] = {(cuuint64_t)L.P, (cuuint64_t)L.R, (cuuint64_t)(len / L.PL)};
+    const cuuint64_t strides[2] = {(cuuint64_t)L.P * 4, (cuuint64_t)L.PL * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(FS_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return FS_OK;
+}
+
+int make_tensor_maps(fs_ctx *c)
+{
+    const Layout &L = c->L;
+    const int zx = TILE_X + 8, zy = TILE_Y + 2;  // the operator apply's halo box
+    struct M { CUtensorMap *m; float *p; long long len; int bx, by; } maps[] = {
+        {&c->tmz_pr, c->pr, L.nC, zx, zy},         {&c->tmz_pz, c->pz, L.nC, zx, zy},
+        {&c->tmz_pp[0], c->pp[0], L.nC, zx, zy},   {&c->tmz_pp[1], c->pp[1], L.nC, zx, zy},
+        {&c->tmz_vr, c->vr, L.nF, zx, zy},         {&c->tmz_vp[0], c->vp[0], L.nF, zx, zy},
+        {&c->tmz_vp[1], c->vp[1], L.nF, zx, zy}};
+    for (auto &e : maps) {
+        int rc = encode_map(e.m, e.p, L, e.len, e.bx, e.by);
+        if (rc) return rc;
+    }
+    return FS_OK;
+}
+
+// Work of the z-marching operator apply: for every column (volume, tile row,
+// tile column) the runs of planes whose tile holds an active element (gaps of
+// up to two planes are bridged), cut into chunks of at most zc planes, in
+// column order so that neighbouring chunks run at about the same time.
+static std::vector<int4> zmarch_items(const std::vector<uint8_t> &act, const TileMap &m, int zc)
+{
+    std::vector<int4> items;
+    const int ncol = m.ntx * m.nty * m.nvol;
+    for (int col = 0; col < ncol; col++) {
+        const int txi = col % m.ntx, tyi = (col / m.ntx) % m.nty, v = col / (m.ntx * m.nty);
+        auto active = [&](int k) { return act[(size_t)(((v * m.nch + k) * m.nty + tyi) * m.ntx + txi)] != 0; };
+        int k = 0;
+        while (k < m.Z) {
+            while (k < m.Z && !active(k)) k++;
+            if (k >= m.Z) break;
+            int e = k + 1, last = k;
+            while (e < m.Z && e - last <= 3) {
+                if (active(e)) last = e;
+                e++;
+            }
+            const int k1 = last + 1;  // run [k, k1)
+            for (int a = k; a < k1; a += zc) items.push_back(make_int4(col, a, std::min(a + zc, k1), 0));
+            k = k1;
+        }
+    }
+    return items;
+}
 
 TileMap make_tilemap(const Layout &L, int nvol, int num_sms)
 {
@@ -228,7 +327,11 @@ int build_mask(fs_ctx *c, const uint8_t *types_dense, const fs_mac *bc)
         struct Space { const uint8_t *act; int *list; int n; int *nact; } sp[2] = {
             {c->act_cell, c->list_cell, c->tm_cell.nblocks, &c->nact_cell},
             {c->act_face, c->list_face, c->tm_face.nblocks, &c->nact_face}};
-        for (auto &s : sp) {
+        int4 *items_dev[2] = {c->items_cell, c->items_face};
+        int *nitems[2] = {&c->nitems_cell, &c->nitems_face};
+        const TileMap *tms[2] = {&c->tm_cell, &c->tm_face};
+        for (int si = 0; si < 2; si++) {
+            auto &s = sp[si];
             std::vector<uint8_t> act((size_t)s.n);
             FS_CUDA(cudaMemcpy(act.data(), s.act, (size_t)s.n, cudaMemcpyDeviceToHost));
             std::vector<int> list;
@@ -236,8 +339,25 @@ int build_mask(fs_ctx *c, const uint8_t *types_dense, const fs_mac *bc)
             for (int b = 0; b < s.n; b++)
                 if (act[(size_t)b]) list.push_back(b);
             *s.nact = (int)list.size();
-            if (!list.empty())
+            if (!list.empty()) {
                 FS_CUDA(cudaMemcpy(s.list, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice));
+                k_quad_mask<<<(unsigned)list.size(), dim3(TILE_X / 4, TILE_Y), 0, c->stream>>>(
+                    si == 0 ? c->cflag : c->fflag, si == 0 ? CF_LIQ : FF_FLUID, s.list, *tms[si],
+                    si == 0 ? c->qmask_cell : c->qmask_face);
+                FS_CUDA(cudaGetLastError());
+            }
+            // at most one chunk per resident block of the operator apply (a second
+            // chunk on some blocks would double the launch), 8 planes at least
+            const long long slots = (long long)zmarch_slots(c, si == 1);
+            int zc = (int)std::max<long long>(8, ((long long)list.size() + slots - 1) / slots);
+            std::vector<int4> items = zmarch_items(act, *tms[si], zc);
+            while ((long long)items.size() > slots && zc < c->L.Z) {
+                zc += std::max(1, zc / 8);
+                items = zmarch_items(act, *tms[si], zc);
+            }
+            *nitems[si] = (int)items.size();
+            if (!items.empty())
+                FS_CUDA(cudaMemcpy(items_dev[si], items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
         }
     }
     c->n_liquid = (long long)h[0];

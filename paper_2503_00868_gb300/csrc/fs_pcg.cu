@@ -440,18 +440,59 @@ __global__ void __launch_bounds__(TH) k_loss_face(CF3 u, CF3 tg, const uint8_t *
 }  // namespace fs
 
 #include "fs_stencil.cuh"
+#include "fs_tma.cuh"
 
 namespace fs {
 
-// Resident 256-thread blocks per SM of a tiled kernel (the persistent grid).
-static int resident_blocks(const void *fn)
+// Resident 256-thread blocks per SM of a kernel with `dyn` bytes of dynamic
+// shared memory (the persistent grids); raises the kernel's dynamic shared
+// memory limit to `dyn` on first use.
+static int resident_blocks(const void *fn, size_t dyn)
 {
+    if (dyn > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, 0) != cudaSuccess || nb < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, dyn) != cudaSuccess || nb < 1) {
         cudaGetLastError();
         nb = 1;
     }
     return nb;
+}
+
+// Persistent grid sizes of the two CG kernels for one operator.
+template <class Op>
+struct TmaGrids {
+    int spmv, upd;
+    TmaGrids(const fs_ctx *c, int nitems, int nact)
+    {
+        static const int rs = resident_blocks((const void *)k_spmv_z<Op>, zmarch_smem());
+        static const int ru = resident_blocks((const void *)k_update_q<Op, true>, 0);
+        static const int ru2 = resident_blocks((const void *)k_update_q<Op, false>, 0);
+        spmv = std::max(1, std::min(nitems, c->num_sms * rs));
+        upd = std::max(1, std::min(nact, c->num_sms * std::min(ru, ru2)));
+    }
+};
+
+int zmarch_slots(const fs_ctx *c, bool face)
+{
+    const int r = face ? resident_blocks((const void *)k_spmv_z<HelmOp>, zmarch_smem())
+                       : resident_blocks((const void *)k_spmv_z<PoisOp>, zmarch_smem());
+    return c->num_sms * r;
+}
+
+// A bounded wait of a TMA-fed kernel or of the MIC(0) wavefront that ran out
+// leaves a bit in the error word.
+static int check_wait_error(fs_ctx *c, const char *what)
+{
+    unsigned herr = 0;
+    FS_CUDA(cudaMemcpyAsync(&herr, c->err_word, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    if (herr & 1u) {
+        c->mic_ready = 0;  // the factor may be incomplete: refactor on the next use
+        return set_error(FS_ETIMEOUT, "MIC(0) sweep: a wait on a predecessor tile ran out (spin_limit %d)",
+                         c->prm.spin_limit);
+    }
+    if (herr & ERR_TMA) return set_error(FS_ETIMEOUT, "%s: a wait for a tensor copy ran out", what);
+    return FS_OK;
 }
 
 int read_scal(fs_ctx *c, int which, SolveScal *out)
@@ -513,7 +554,7 @@ static int solve_pressure_once(fs_ctx *c, fs_stats *st)
     const bool learned = c->prm.precond == FS_PRECOND_LEARNED;
     if (learned && !net_loaded(c))
         return set_error(FS_ESTATE, "the learned preconditioner has no network loaded");
-    if (!jac) FS_CUDA(cudaMemsetAsync(c->err_word, 0, sizeof(unsigned), c->stream));
+    FS_CUDA(cudaMemsetAsync(c->err_word, 0, sizeof(unsigned), c->stream));
     if (c->prm.precond == FS_PRECOND_MIC0 && !c->mic_ready) {
         int rc = mic0_factor(c);
         if (rc) return rc;
@@ -549,27 +590,29 @@ static int solve_pressure_once(fs_ctx *c, fs_stats *st)
     const bool tiled = c->act_cell != nullptr;
     const TileMap &tm = c->tm_cell;
     const dim3 tdim(TILE_X / 4, TILE_Y);
-    const int tgrid = std::max(1, std::min(c->nact_cell, c->num_sms * resident_blocks((const void *)k_spmv_p<PoisOp>)));
-    const int ugrid = std::max(1, std::min(c->nact_cell, c->num_sms * resident_blocks((const void *)k_update_p<PoisOp, true>)));
+    const TmaGrids<PoisOp> tg(c, c->nitems_cell, c->nact_cell);
     for (;;) {
         for (int b = 0; b < c->prm.check_every; b++) {
             const bool samp = c->prof_on && (b % c->prof_period) == 0;
             cudaEvent_t e0 = samp ? prof_mark(c) : nullptr;
             const float *zsrc = jac ? c->pr : c->pz;
             if (tiled)
-                k_spmv_p<PoisOp><<<tgrid, tdim, 0, c->stream>>>(zsrc, c->pp[cur], c->pp[cur ^ 1], c->pq,
-                                                                     c->cflag, c->list_cell, c->nact_cell, tm, 0.f, s, c->partials);
+                k_spmv_z<PoisOp><<<tg.spmv, tdim, zmarch_smem(), c->stream>>>(
+                    jac ? c->tmz_pr : c->tmz_pz, c->tmz_pp[cur], c->pp[cur ^ 1], c->pq, c->cflag, c->items_cell,
+                    c->nitems_cell, tm, 0.f, s, c->partials, c->err_word);
             else
                 k_spmv<PoisOp><<<bs, TH, 0, c->stream>>>(zsrc, c->pp[cur], c->pp[cur ^ 1], c->pq, c->cflag, L.nC,
                                                          L.P, L.PL, 0.f, s, c->partials);
             cudaEvent_t e1 = samp ? prof_mark(c) : nullptr, e2 = samp ? prof_mark(c) : nullptr;
             if (tiled) {
                 if (jac)
-                    k_update_p<PoisOp, true><<<ugrid, tdim, 0, c->stream>>>(
-                        c->px, c->pr, c->pp[cur ^ 1], c->pq, c->cflag, c->list_cell, c->nact_cell, tm, 0.f, s, c->partials);
+                    k_update_q<PoisOp, true><<<tg.upd, tdim, 0, c->stream>>>(
+                        c->px, c->pr, c->pp[cur ^ 1], c->pq, c->cflag, c->list_cell, c->qmask_cell, c->nact_cell, tm,
+                        0.f, s, c->partials);
                 else
-                    k_update_p<PoisOp, false><<<ugrid, tdim, 0, c->stream>>>(
-                        c->px, c->pr, c->pp[cur ^ 1], c->pq, c->cflag, c->list_cell, c->nact_cell, tm, 0.f, s, c->partials);
+                    k_update_q<PoisOp, false><<<tg.upd, tdim, 0, c->stream>>>(
+                        c->px, c->pr, c->pp[cur ^ 1], c->pq, c->cflag, c->list_cell, c->qmask_cell, c->nact_cell, tm,
+                        0.f, s, c->partials);
             } else if (jac)
                 k_update<PoisOp, true><<<b4, TH, 0, c->stream>>>(c->px, c->pr, c->pp[cur ^ 1], c->pq, c->cflag,
                                                                  n4, 0.f, s, c->partials);
@@ -597,17 +640,7 @@ static int solve_pressure_once(fs_ctx *c, fs_stats *st)
         if (launched > (long long)c->prm.maxit_p + c->prm.check_every)
             return set_error(FS_ECUDA, "pressure solve: iteration flag never set");
     }
-    if (!jac) {
-        // a bounded wait of the MIC(0) wavefront that ran out leaves a flag
-        unsigned herr = 0;
-        FS_CUDA(cudaMemcpyAsync(&herr, c->err_word, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
-        FS_CUDA(cudaStreamSynchronize(c->stream));
-        if (herr) {
-            c->mic_ready = 0;  // the factor may be incomplete: refactor on the next use
-            return set_error(FS_ETIMEOUT, "MIC(0) sweep: a wait on a predecessor tile ran out (spin_limit %d)",
-                             c->prm.spin_limit);
-        }
-    }
+    if (int rc = check_wait_error(c, "pressure solve")) return rc;
     return pressure_tail(c, h, st);
 }
 
@@ -666,6 +699,7 @@ int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st)
     const double tol2 = c->prm.tol_v * c->prm.tol_v;
     const int bs = grid_blocks(c, L.nF, TH);
     const int b4 = grid_blocks(c, n4, TH);
+    FS_CUDA(cudaMemsetAsync(c->err_word, 0, sizeof(unsigned), c->stream));
     k_helm_init<<<bs, TH, 0, c->stream>>>(c->vx, (dirichlet && c->has_bc) ? c->dsum : nullptr, c->vr, c->vp[0],
                                          c->vp[1], c->fflag, L.nF, L.P, L.PL, cc, tol2, c->prm.maxit_v, s,
                                          c->partials);
@@ -679,22 +713,23 @@ int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st)
     const bool tiled = c->act_face != nullptr;
     const TileMap &tm = c->tm_face;
     const dim3 tdim(TILE_X / 4, TILE_Y);
-    const int tgrid = std::max(1, std::min(c->nact_face, c->num_sms * resident_blocks((const void *)k_spmv_p<HelmOp>)));
-    const int ugrid = std::max(1, std::min(c->nact_face, c->num_sms * resident_blocks((const void *)k_update_p<HelmOp, true>)));
+    const TmaGrids<HelmOp> tg(c, c->nitems_face, c->nact_face);
     for (;;) {
         for (int b = 0; b < c->prm.check_every; b++) {
             const bool samp = c->prof_on && (b % c->prof_period) == 0;
             cudaEvent_t e0 = samp ? prof_mark(c) : nullptr;
             if (tiled)
-                k_spmv_p<HelmOp><<<tgrid, tdim, 0, c->stream>>>(c->vr, c->vp[cur], c->vp[cur ^ 1], c->vq,
-                                                                     c->fflag, c->list_face, c->nact_face, tm, cc, s, c->partials);
+                k_spmv_z<HelmOp><<<tg.spmv, tdim, zmarch_smem(), c->stream>>>(
+                    c->tmz_vr, c->tmz_vp[cur], c->vp[cur ^ 1], c->vq, c->fflag, c->items_face, c->nitems_face, tm,
+                    cc, s, c->partials, c->err_word);
             else
                 k_spmv<HelmOp><<<bs, TH, 0, c->stream>>>(c->vr, c->vp[cur], c->vp[cur ^ 1], c->vq, c->fflag, L.nF,
                                                          L.P, L.PL, cc, s, c->partials);
             cudaEvent_t e1 = samp ? prof_mark(c) : nullptr, e2 = samp ? prof_mark(c) : nullptr;
             if (tiled)
-                k_update_p<HelmOp, true><<<ugrid, tdim, 0, c->stream>>>(
-                    c->vx, c->vr, c->vp[cur ^ 1], c->vq, c->fflag, c->list_face, c->nact_face, tm, cc, s, c->partials);
+                k_update_q<HelmOp, true><<<tg.upd, tdim, 0, c->stream>>>(
+                    c->vx, c->vr, c->vp[cur ^ 1], c->vq, c->fflag, c->list_face, c->qmask_face, c->nact_face, tm, cc,
+                    s, c->partials);
             else
                 k_update<HelmOp, true><<<b4, TH, 0, c->stream>>>(c->vx, c->vr, c->vp[cur ^ 1], c->vq, c->fflag, n4,
                                                                  cc, s, c->partials);
@@ -712,6 +747,7 @@ int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st)
         if (launched > (long long)c->prm.maxit_v + c->prm.check_every)
             return set_error(FS_ECUDA, "viscosity solve: iteration flag never set");
     }
+    if (int rc = check_wait_error(c, "viscosity solve")) return rc;
     if (st) {
         st->iters_v += h.iter;
         st->relres_v = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
