@@ -119,6 +119,9 @@ typedef struct {
     double relres_v;       /* last viscosity solve: recursive |r|/|b| at exit */
     double true_relres_p;  /* last pressure solve: |b - A q|/|b| recomputed at exit */
     int fallbacks;         /* pressure solves redone with MIC(0) after the learned one failed */
+    int restarts_p;        /* pressure CG restarts from the current iterate with the true
+                              residual (taken when the recursive residual meets tol_p but
+                              |b - A q| > 2 tol_p |b|; at most two per solve) */
 } fs_stats;
 
 typedef struct {

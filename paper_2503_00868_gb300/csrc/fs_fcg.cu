@@ -230,10 +230,11 @@ void fcg_release(fs_ctx *c)
     c->fcg = nullptr;
 }
 
-// Flexible CG on pb -> px with the loaded network. Leaves the final scalars in
-// *h (status FS_ENOCONV also when |r| stagnates: no tenfold drop over 200
-// iterations); the caller computes the true residual.
-int solve_pressure_fcg(fs_ctx *c, SolveScal *h)
+// Flexible CG on pb -> px with the loaded network, from x = 0 or (warm) from
+// the current x with the true residual. Leaves the final scalars in *h (status
+// FS_ENOCONV also when |r| stagnates: no tenfold drop over 200 iterations); the
+// caller computes the true residual.
+int solve_pressure_fcg(fs_ctx *c, SolveScal *h, bool warm)
 {
     int rc = fcg_alloc(c);
     if (rc) return rc;
@@ -244,8 +245,12 @@ int solve_pressure_fcg(fs_ctx *c, SolveScal *h)
     const int b4 = grid_blocks(c, n4, TH), bs = grid_blocks(c, L.nC, TH);
     const double tol2 = c->prm.tol_p * c->prm.tol_p;
     const double by_vec = (double)L.nC * 4.0;
-    k_fcg_init<<<b4, TH, 0, c->stream>>>(c->pb, c->px, c->pr, n4, tol2, c->prm.maxit_p, s, c->partials);
-    c->n_launches += 1;
+    if (warm) {
+        if ((rc = pressure_restart(c))) return rc;  // r = b - A x, iteration count kept
+    } else {
+        k_fcg_init<<<b4, TH, 0, c->stream>>>(c->pb, c->px, c->pr, n4, tol2, c->prm.maxit_p, s, c->partials);
+        c->n_launches += 1;
+    }
     FS_CUDA(cudaGetLastError());
     long long k = 0;
     std::vector<std::pair<int, double>> hist;  // (iteration, r.r) at the host checks

@@ -305,8 +305,10 @@ int cell_out(fs_ctx *c, const float *src, float *dst);  // cell space -> public 
 int read_scal(fs_ctx *c, int which, SolveScal *out);
 // mean-free preconditioned residual over the liquid when the operator is singular
 int remove_null_mode(fs_ctx *c, float *z);
-// fs_fcg.cu: flexible CG with the network, pb -> px; final scalars in *h
-int solve_pressure_fcg(fs_ctx *c, SolveScal *h);
+// fs_fcg.cu: flexible CG with the network, pb -> px (warm: from the current x);
+// final scalars in *h
+int solve_pressure_fcg(fs_ctx *c, SolveScal *h, bool warm);
+int pressure_restart(fs_ctx *c);  // fs_pcg.cu: r = b - A x, p = 0 (scalars of slot 0)
 void fcg_release(fs_ctx *c);
 
 // ---- per-kernel timing -------------------------------------------------------

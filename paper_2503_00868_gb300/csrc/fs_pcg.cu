@@ -233,11 +233,14 @@ __global__ void __launch_bounds__(TH) k_helm_init(const float *__restrict__ x, c
 }
 
 // |b - A x|^2 of the pressure system -> s->aux[0].
+// |b - A x|^2 over the liquid -> s->aux[0]. For a singular operator (liquid
+// touching no air) the component along the null vector (the constant), which
+// no iterate can change, is left out: sum e^2 - (sum e)^2 / N.
 __global__ void __launch_bounds__(TH) k_pois_true_res(const float *__restrict__ b, const float *__restrict__ x,
                                                       const uint8_t *__restrict__ fl, int n, int P, int PL,
-                                                      SolveScal *s, double *partials)
+                                                      int singular, SolveScal *s, double *partials)
 {
-    double acc = 0.0;
+    double acc = 0.0, sum = 0.0, cnt = 0.0;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
         const uint8_t f = fl[t];
         if (!(f & CF_LIQ)) continue;
@@ -245,9 +248,50 @@ __global__ void __launch_bounds__(TH) k_pois_true_res(const float *__restrict__ 
         const float ax = PoisOp::diag(f, 0.f) * x[t] - nb;
         const double e = (double)b[t] - (double)ax;
         acc += e * e;
+        sum += e;
+        cnt += 1.0;
     }
-    double v[1] = {acc}, tot[1];
-    if (grid_reduce<1>(v, partials, &s->ticket, tot) && threadIdx.x == 0) s->aux[0] = tot[0];
+    double v[3] = {acc, sum, cnt}, tot[3];
+    if (grid_reduce<3>(v, partials, &s->ticket, tot) && threadIdx.x == 0)
+        s->aux[0] = (singular && tot[2] > 0.0) ? fmax(0.0, tot[0] - tot[1] * tot[1] / tot[2]) : tot[0];
+}
+
+// Residual replacement: restart CG from the current x with the true residual
+// r = b - A x (Jacobi: stored as z = D^-1 r), both p buffers zero; r.r (and
+// for Jacobi r.z) recomputed, the iteration count kept.
+template <bool JAC>
+__global__ void __launch_bounds__(TH) k_pois_restart(const float *__restrict__ b, const float *__restrict__ x,
+                                                     float *__restrict__ r, float *__restrict__ p0,
+                                                     float *__restrict__ p1, const uint8_t *__restrict__ fl, int n,
+                                                     int P, int PL, SolveScal *s, double *partials)
+{
+    KSum rr, rz;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const uint8_t f = fl[t];
+        float v = 0.f;
+        if (f & CF_LIQ) {
+            const float nb = (x[t - 1] + x[t + 1]) + (x[t - P] + x[t + P]) + (x[t - PL] + x[t + PL]);
+            const float res = b[t] - (PoisOp::diag(f, 0.f) * x[t] - nb);
+            v = JAC ? res * inv_diag<PoisOp>(f, 0.f) : res;
+            rr.add(res * res);
+            rz.add(res * v);
+        }
+        r[t] = v;
+        p0[t] = 0.f;
+        p1[t] = 0.f;
+    }
+    double v[2] = {rr.value(), rz.value()}, tot[2];
+    if (grid_reduce<2>(v, partials, &s->ticket, tot) && threadIdx.x == 0) {
+        s->rr = tot[0];
+        s->rz = tot[1];
+        s->alpha = 0.0;
+        s->beta = 0.0;
+        s->pq = 0.0;
+        s->status = FS_OK;
+        s->done = 0;
+        if (!isfinite(tot[0])) { s->done = 1; s->status = FS_ENONFINITE; }
+        else if (tot[0] <= s->tol2 * s->bb) s->done = 1;
+    }
 }
 
 // Sum and count of a cell vector over the liquid -> s->aux[0], s->aux[1].
@@ -544,35 +588,43 @@ int remove_null_mode(fs_ctx *c, float *z)
 
 static int pressure_tail(fs_ctx *c, const SolveScal &h, fs_stats *st);
 
-static int solve_pressure_once(fs_ctx *c, fs_stats *st)
+// r = b - A x in pr (unscaled) for a warm restart of flexible CG.
+int pressure_restart(fs_ctx *c)
+{
+    const Layout &L = c->L;
+    k_pois_restart<false><<<grid_blocks(c, L.nC, TH), TH, 0, c->stream>>>(
+        c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, L.nC, L.P, L.PL, c->scal + 0, c->partials);
+    c->n_launches += 1;
+    FS_CUDA(cudaGetLastError());
+    return FS_OK;
+}
+
+// Jacobi- or MIC(0)-PCG on pb -> px: from x = 0, or (warm) from the current x
+// with the true residual (residual replacement). Final scalars in h.
+static int pcg_iterate(fs_ctx *c, SolveScal &h, bool warm)
 {
     const Layout &L = c->L;
     SolveScal *s = c->scal + 0;
     const bool jac = c->prm.precond == FS_PRECOND_JACOBI;
     const int n4 = L.nC / 4;
     const double tol2 = c->prm.tol_p * c->prm.tol_p;
-    const bool learned = c->prm.precond == FS_PRECOND_LEARNED;
-    if (learned && !net_loaded(c))
-        return set_error(FS_ESTATE, "the learned preconditioner has no network loaded");
-    FS_CUDA(cudaMemsetAsync(c->err_word, 0, sizeof(unsigned), c->stream));
-    if (c->prm.precond == FS_PRECOND_MIC0 && !c->mic_ready) {
-        int rc = mic0_factor(c);
-        if (rc) return rc;
-    }
-    SolveScal h;
-    if (learned) {
-        int rc = solve_pressure_fcg(c, &h);
-        if (rc) return rc;
-        return pressure_tail(c, h, st);
-    }
     // z = M r for MIC(0), the stored-z preconditioner
     auto apply_m = [&]() -> int { return mic0_apply(c, c->pr, c->pz); };
-    if (jac)
+    if (warm) {
+        if (jac)
+            k_pois_restart<true><<<grid_blocks(c, L.nC, TH), TH, 0, c->stream>>>(
+                c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, L.nC, L.P, L.PL, s, c->partials);
+        else
+            k_pois_restart<false><<<grid_blocks(c, L.nC, TH), TH, 0, c->stream>>>(
+                c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, L.nC, L.P, L.PL, s, c->partials);
+    } else if (jac) {
         k_pois_init<true><<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(
             c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, n4, tol2, c->prm.maxit_p, s, c->partials);
-    else {
+    } else {
         k_pois_init<false><<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(
             c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, n4, tol2, c->prm.maxit_p, s, c->partials);
+    }
+    if (!jac) {
         int rc = apply_m();
         if (rc) return rc;
         if ((rc = remove_null_mode(c, c->pz))) return rc;
@@ -640,7 +692,40 @@ static int solve_pressure_once(fs_ctx *c, fs_stats *st)
         if (launched > (long long)c->prm.maxit_p + c->prm.check_every)
             return set_error(FS_ECUDA, "pressure solve: iteration flag never set");
     }
-    if (int rc = check_wait_error(c, "pressure solve")) return rc;
+    return check_wait_error(c, "pressure solve");
+}
+
+static int solve_pressure_once(fs_ctx *c, fs_stats *st)
+{
+    const bool learned = c->prm.precond == FS_PRECOND_LEARNED;
+    if (learned && !net_loaded(c))
+        return set_error(FS_ESTATE, "the learned preconditioner has no network loaded");
+    FS_CUDA(cudaMemsetAsync(c->err_word, 0, sizeof(unsigned), c->stream));
+    if (c->prm.precond == FS_PRECOND_MIC0 && !c->mic_ready) {
+        int rc = mic0_factor(c);
+        if (rc) return rc;
+    }
+    const Layout &L = c->L;
+    const int bs = grid_blocks(c, L.nC, TH);
+    SolveScal h;
+    // The recursively updated FP32 residual drifts from b - A x over many
+    // iterations; when it meets the tolerance but the true residual is above
+    // twice the tolerance, CG restarts from x with the true residual (at most
+    // twice).
+    for (int restart = 0;; restart++) {
+        int rc = learned ? solve_pressure_fcg(c, &h, restart > 0) : pcg_iterate(c, h, restart > 0);
+        if (rc) return rc;
+        // (a singular system keeps its iterates in the operator's range: no restart)
+        if (h.status != FS_OK || restart == 2 || !(h.bb > 0.0) || c->singular) break;
+        k_pois_true_res<<<bs, TH, 0, c->stream>>>(c->pb, c->px, c->cflag, L.nC, L.P, L.PL, c->singular,
+                                                  c->scal + 2, c->partials);
+        c->n_launches += 1;
+        FS_CUDA(cudaGetLastError());
+        SolveScal m;
+        if ((rc = read_scal(c, 2, &m))) return rc;
+        if (m.aux[0] <= 4.0 * h.tol2 * h.bb) break;
+        if (st) st->restarts_p += 1;
+    }
     return pressure_tail(c, h, st);
 }
 
@@ -651,7 +736,8 @@ static int pressure_tail(fs_ctx *c, const SolveScal &h, fs_stats *st)
     const Layout &L = c->L;
     const int bs = grid_blocks(c, L.nC, TH);
     // true residual, then the mean-free representative of a singular solve
-    k_pois_true_res<<<bs, TH, 0, c->stream>>>(c->pb, c->px, c->cflag, L.nC, L.P, L.PL, c->scal + 2, c->partials);
+    k_pois_true_res<<<bs, TH, 0, c->stream>>>(c->pb, c->px, c->cflag, L.nC, L.P, L.PL, c->singular, c->scal + 2,
+                                              c->partials);
     c->n_launches += 1;
     if (c->singular) {
         k_liquid_sum<<<bs, TH, 0, c->stream>>>(c->px, c->cflag, L.nC, c->scal + 3, c->partials);

@@ -46,7 +46,7 @@ class fs_params(C.Structure):
 class fs_stats(C.Structure):
     _fields_ = [("status", C.c_int), ("iters_p", C.c_int), ("iters_v", C.c_int),
                 ("relres_p", C.c_double), ("relres_v", C.c_double), ("true_relres_p", C.c_double),
-                ("fallbacks", C.c_int)]
+                ("fallbacks", C.c_int), ("restarts_p", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
