@@ -38,10 +38,12 @@ PROFILE_PERIOD = 8   # time every 8th CG iteration inside the timed region
 METRIC = "fwd+adjoint cell-steps/s at 256^3"
 UNIT = "cell-steps/s"
 
-# ncu DRAM traffic per launch (bytes) of the kernels, keyed by kernel name; each
-# entry holds the hash of the CUDA source it was measured on and is reported only
-# while the source is unchanged (capture commands in profiles/).
+# ncu DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum,
+# bytes) of the kernels, keyed by the profile name; each entry holds the hash of
+# the files that define the kernel and the data layout it reads, and is reported
+# only while those files are unchanged (capture commands in profiles/).
 NCU_TRAFFIC = {}
+KERNEL_FILES = ("fs_stencil.cuh", "fs_tma.cuh", "fs_internal.cuh", "fs_mask.cu")
 
 
 def args_parse():
@@ -56,15 +58,17 @@ def args_parse():
     ap.add_argument("--cpu-sample-n", type=int, default=64)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the Jacobi / MIC(0) / learned projection comparison")
+    ap.add_argument("--compare-n", type=int, default=256)
     return ap.parse_args()
 
 
-def source_hash():
+def source_hash(files=KERNEL_FILES):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2503_00868_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, name), "rb").read())
+    for name in files:
+        h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -192,6 +196,44 @@ def workload_config(a):
             "precond": a.precond, "tol": 1e-6, "nu": 0.01, "dt": 1.0 / 30.0,
             "l2_between_steps": "inputs larger than L2 (working set > 1 GB per replica)",
             "parallelism": "replicas" if a.gpus > 1 else "single"}
+
+
+def precond_compare(n, seeds=(0,)):
+    """Projection of an unblurred N(0,1) MAC field (the stress right-hand side) on
+    a union of 8 spheres at n^3, to relative residual 1e-6, with Jacobi, MIC(0)
+    and the shipped learned network (flexible CG): device wall time of fs_project
+    (CUDA events, after one warm-up solve), iterations, true residual."""
+    import torch
+    from paper_2503_00868_gb300 import fluidstep as F
+    from paper_2503_00868_gb300 import train_precond as T
+    from paper_2503_00868_gb300 import workloads as W
+    out = {"workload": f"projection of a divergent N(0,1) MAC field on a union of 8 spheres at {n}^3, "
+                       "tol 1e-6, maxit 20000", "rows": []}
+    pcs = (("jacobi", F.FS_PRECOND_JACOBI), ("mic0", F.FS_PRECOND_MIC0), ("learned", F.FS_PRECOND_LEARNED))
+    for seed in seeds:
+        types, info = W.sphere_union(n, n, n, seed)
+        row = {"seed": seed, "occupancy": info["occupancy"]}
+        for name, pc in pcs:
+            g = F.Grid(n, n, n, dx=1.0 / n, tol_p=1e-6, maxit_p=20000, precond=pc)
+            g.set_mask(types)
+            if pc == F.FS_PRECOND_LEARNED:
+                F.fs_net_load(g.ctx, T.default_weights())
+            u0 = g.pack(W.random_mac(n, n, n, 500 + seed))
+            ts = []
+            for rep in range(2):
+                u = F.Mac(*(t.clone() for t in u0))
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                rc, st = g.project(u)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            row[name] = {"ms": round(ts[-1], 3), "iters": st["iters_p"], "true_relres": st["true_relres_p"],
+                         "fallbacks": st["fallbacks"], "restarts": st["restarts_p"], "status": rc}
+            g.close()
+        out["rows"].append(row)
+    return out
 
 
 def main():
@@ -328,6 +370,10 @@ def main():
                "sample": f"oracle fwd+adjoint of 1 step of the same scene recipe at {a.cpu_sample_n}^3 "
                          f"({dt:.1f} s; iteration counts grow with n, so this overstates the oracle at 256^3)"}
 
+    compare = None
+    if rank == 0 and not a.no_compare:
+        compare = precond_compare(a.compare_n)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -336,7 +382,7 @@ def main():
                 "cpu_baseline": cpu, "kernels": kernels, "occupancy": info["occupancy"],
                 "pcg_iters_per_step": {"pressure_mean": sum(iters_p) / max(len(iters_p), 1),
                                        "viscosity_mean": sum(iters_v) / max(len(iters_v), 1)},
-                "loss": float(loss.detach()), "dL_dnu": float(gnu)}
+                "loss": float(loss.detach()), "dL_dnu": float(gnu), "precond_compare": compare}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

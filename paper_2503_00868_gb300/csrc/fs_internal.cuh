@@ -101,6 +101,7 @@ struct fs_ctx {
     int device;
     int num_sms;
     int mask_set;
+    long long mask_epoch;  // incremented by every fs_set_mask (caches keyed to the mask)
     int singular;
     int has_bc;
     long long n_liquid, n_band_cells[2], n_band_faces[2];

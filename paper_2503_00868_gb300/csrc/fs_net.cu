@@ -10,13 +10,17 @@
 // activation is stored as bf16, every sum accumulates in FP32.
 //
 // Kernels:
-//   k_conv_first   layer 1 (2 -> 16) on CUDA cores, input formed on the fly;
-//   k_conv_mid     layers 2-4 (16 -> 16) as an implicit GEMM per 3x3x3 tap on the
-//                  tensor cores (mma.sync m16n8k16 bf16 x bf16 -> f32, operands
-//                  via ldmatrix from a swizzled shared-memory tile); the same
-//                  kernel runs the backward-data pass with flipped, transposed
-//                  weights and a ReLU-derivative epilogue;
-//   k_conv_last    layer 5 (16 -> 1) on CUDA cores; scales by s and masks;
+//   k_conv<IN, OUT>  every layer as an implicit GEMM per 3x3x3 tap on the tensor
+//                  cores (mma.sync m16n8k16 bf16 x bf16 -> f32, operands via
+//                  ldmatrix from a swizzled shared-memory tile); layer 1 builds
+//                  its (r/s, cell type) input tile on the fly with the weights
+//                  zero-padded to 16 input channels, layer 5 uses one 8-wide
+//                  n-tile and writes z = s y on liquid cells; the same kernel
+//                  runs the backward-data pass of layers 2-4 with flipped,
+//                  transposed weights and a ReLU-derivative epilogue. For
+//                  inference layer l visits only the conv tiles within 5 - l
+//                  cells of the liquid (the output on liquid cells depends on
+//                  nothing farther), from a tile list sorted by that distance;
 //   k_bwd_last     gradient through layer 5 to its input;
 //   k_wgrad<CIN,COUT>  weight and bias gradients (FP32 CUDA cores, per-block
 //                  partial sums, one atomicAdd per weight per block);
@@ -50,6 +54,12 @@ struct NetState {
     float *m, *v;         // Adam moments
     float *w1f, *w5f;     // bf16-rounded layer-1 / layer-5 weights as float
     __nv_bfloat16 *wf;    // layers 2-4 forward: [3][27 tap][16 co][16 ci]
+    __nv_bfloat16 *wf1;   // layer 1 forward: [27 tap][16 co][16 ci], ci >= 2 zero
+    __nv_bfloat16 *wf5;   // layer 5 forward: [27 tap][16 co][16 ci], co >= 1 zero
+    int *tlist;           // conv tiles sorted by distance to the liquid (0 .. 5 = farther)
+    uint8_t *tdist;       // per conv tile: Chebyshev distance to the nearest liquid cell, capped at 5
+    int tcount[6];        // tiles within distance d of the liquid
+    long long tlist_epoch;  // mask epoch the list was built for (-1: none)
     __nv_bfloat16 *wt;    // layers 2-4 backward-data: [3][27 tap][16 ci][16 co], tap flipped
     __nv_bfloat16 *act;   // [6][nC][16]: x (2 ch used), a1, a2, a3, a4, spare
     __nv_bfloat16 *gact;  // [2][nC][16] gradient ping-pong
@@ -75,49 +85,6 @@ __device__ __forceinline__ int cell_t(const Layout &L, int i, int j, int k) { re
 __device__ __forceinline__ float type_code(uint8_t f) { return (f & CF_LIQ) ? 1.f : ((f & CF_AIR) ? 0.f : -1.f); }
 
 __device__ __forceinline__ float bfr(float x) { return __bfloat162float(__float2bfloat16(x)); }
-
-// ---- layer 1 (2 -> 16), CUDA cores; also stores the bf16 input x ----------------
-__global__ void __launch_bounds__(256) k_conv_first(const float *__restrict__ r, const uint8_t *__restrict__ cf,
-                                                    const unsigned *__restrict__ smax,
-                                                    const float *__restrict__ w1f, const float *__restrict__ b1,
-                                                    __nv_bfloat16 *xin, __nv_bfloat16 *out, Layout L)
-{
-    __shared__ float w[NW1], b[16];
-    for (int t = threadIdx.x; t < NW1; t += blockDim.x) w[t] = w1f[t];
-    if (threadIdx.x < 16) b[threadIdx.x] = b1[threadIdx.x];
-    __syncthreads();
-    const float s = __uint_as_float(*smax);
-    const float inv = s > 0.f ? 1.f / s : 0.f;
-    const int ncell = L.nx * L.ny * L.nz;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
-        const int i = c % L.nx, j = (c / L.nx) % L.ny, k = c / (L.nx * L.ny);
-        float acc[16];
-#pragma unroll
-        for (int o = 0; o < 16; o++) acc[o] = b[o];
-        for (int dz = -1; dz <= 1; dz++)
-            for (int dy = -1; dy <= 1; dy++)
-                for (int dx = -1; dx <= 1; dx++) {
-                    if (!in_grid(L, i + dx, j + dy, k + dz)) continue;
-                    const int tn = cell_t(L, i + dx, j + dy, k + dz);
-                    const uint8_t f = cf[tn];
-                    const float x0 = (f & CF_LIQ) ? bfr(r[tn] * inv) : 0.f;
-                    const float x1 = type_code(f);
-                    const int tp = tap_index(dz, dy, dx);
-#pragma unroll
-                    for (int o = 0; o < 16; o++) acc[o] += w[(o * 2 + 0) * 27 + tp] * x0 + w[(o * 2 + 1) * 27 + tp] * x1;
-                }
-        const int t = cell_t(L, i, j, k);
-        if (xin) {
-            const uint8_t f = cf[t];
-            xin[(size_t)t * 16 + 0] = __float2bfloat16((f & CF_LIQ) ? bfr(r[t] * inv) : 0.f);
-            xin[(size_t)t * 16 + 1] = __float2bfloat16(type_code(f));
-        }
-        __nv_bfloat162 *o2 = reinterpret_cast<__nv_bfloat162 *>(out + (size_t)t * 16);
-#pragma unroll
-        for (int o = 0; o < 8; o++)
-            o2[o] = __floats2bfloat162_rn(fmaxf(acc[2 * o], 0.f), fmaxf(acc[2 * o + 1], 0.f));
-    }
-}
 
 // ---- layers 2-4 (16 -> 16), tensor cores ------------------------------------------
 // Shared tile: 3 planes x (NT_Y + 2) rows x (NT_X + 2) cells x 16 bf16. The two
@@ -147,38 +114,64 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1
                  : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-// MODE 0: out = relu(conv(in) + bias).  MODE 1 (backward data): out = conv(in)
-// * [aref > 0], the ReLU derivative of the layer input. Output only on grid cells.
-template <int MODE>
-__global__ void __launch_bounds__(256) k_conv_mid(const __nv_bfloat16 *__restrict__ in,
-                                                  const __nv_bfloat16 *__restrict__ wts,  // [27][16 n][16 k]
-                                                  const float *__restrict__ bias,
-                                                  const __nv_bfloat16 *__restrict__ aref, __nv_bfloat16 *out,
-                                                  Layout L)
+enum : int { IN_ACT = 0, IN_R = 1 };                  // input: bf16 activations / built from r
+enum : int { OUT_RELU = 0, OUT_BWD = 1, OUT_Z = 2 };  // epilogue
+
+struct ConvArgs {
+    const __nv_bfloat16 *in;    // IN_ACT: [cell][16]
+    const float *r;             // IN_R: right-hand side (cell space)
+    const uint8_t *cf;          // cell flags
+    const unsigned *smax;       // max |r| over the liquid (float bits)
+    const __nv_bfloat16 *wts;   // [27 tap][16 n][16 k]
+    const float *bias;          // OUT_RELU: [16]; OUT_Z: [1]
+    const __nv_bfloat16 *aref;  // OUT_BWD: the layer input whose ReLU derivative masks
+    __nv_bfloat16 *out;         // OUT_RELU, OUT_BWD: [cell][16]
+    __nv_bfloat16 *xin;         // IN_R (optional): the bf16 input, channels 0 and 1
+    float *y, *z;               // OUT_Z (each optional): network output; z = s y on liquid, else 0
+    const int *tiles;           // optional list of conv tiles (else every tile)
+    int ntiles;                 // entries of `tiles`
+    Layout L;
+};
+
+// IN_ACT/OUT_RELU: out = relu(conv(in) + bias). OUT_BWD (backward data):
+// out = conv(in) * [aref > 0]. OUT_Z: y = conv(in) + bias, z = s y on liquid
+// cells. IN_R: the input is (bf16(r/s) on liquid, cell-type code), channels 2-15
+// zero. Outputs only on grid cells.
+template <int IN, int OUT>
+__global__ void __launch_bounds__(256) k_conv(ConvArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned char *tile = smem;                          // TCELLS * 32 bytes
     unsigned char *wsm = smem + TCELLS * 32;             // 27 * 16 rows * 32 bytes
+    const Layout &L = a.L;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // weights once per block (rows n = tap * 16 + co, swizzled like the tile)
     for (int e = tid; e < 27 * 16 * 2; e += blockDim.x) {
         const int row = e >> 1, half = e & 1;
-        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(wts) + row * 2 + half);
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(a.wts) + row * 2 + half);
         *reinterpret_cast<uint4 *>(wsm + swz_off(row, half)) = v;
     }
     float bv[4] = {0.f, 0.f, 0.f, 0.f};  // bias of this lane's output channels
-    if (MODE == 0) {
+    if (OUT == OUT_RELU) {
         const int co = (lane & 3) * 2;
-        bv[0] = bias[co];
-        bv[1] = bias[co + 1];
-        bv[2] = bias[8 + co];
-        bv[3] = bias[8 + co + 1];
+        bv[0] = a.bias[co];
+        bv[1] = a.bias[co + 1];
+        bv[2] = a.bias[8 + co];
+        bv[3] = a.bias[8 + co + 1];
+    } else if (OUT == OUT_Z) {
+        bv[0] = a.bias[0];
+    }
+    float sc = 1.f, inv = 0.f;
+    if (IN == IN_R || OUT == OUT_Z) {
+        sc = __uint_as_float(*a.smax);
+        inv = sc > 0.f ? 1.f / sc : 0.f;
     }
     const uint32_t tile_s = (uint32_t)__cvta_generic_to_shared(tile);
     const uint32_t w_s = (uint32_t)__cvta_generic_to_shared(wsm);
     const int ntx = (L.nx + NT_X - 1) / NT_X, nty = (L.ny + NT_Y - 1) / NT_Y;
-    const int ntiles = ntx * nty * L.nz;
-    for (int tb = blockIdx.x; tb < ntiles; tb += gridDim.x) {
+    const int total = a.tiles ? a.ntiles : ntx * nty * L.nz;
+    for (int idx = blockIdx.x; idx < total; idx += gridDim.x) {
+        const int tb = a.tiles ? __ldg(a.tiles + idx) : idx;
         const int tx = tb % ntx, ty = (tb / ntx) % nty, tk = tb / (ntx * nty);
         const int i0 = tx * NT_X, j0 = ty * NT_Y;
         __syncthreads();  // previous tile done with the shared tile (and weights stored)
@@ -187,8 +180,16 @@ __global__ void __launch_bounds__(256) k_conv_mid(const __nv_bfloat16 *__restric
             const int xx = cidx % TXH, yy = (cidx / TXH) % TYH, zz = cidx / (TXH * TYH);
             const int gi = i0 - 1 + xx, gj = j0 - 1 + yy, gk = tk - 1 + zz;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (in_grid(L, gi, gj, gk))
-                v = __ldg(reinterpret_cast<const uint4 *>(in + (size_t)cell_t(L, gi, gj, gk) * 16) + half);
+            if (in_grid(L, gi, gj, gk)) {
+                const int t = cell_t(L, gi, gj, gk);
+                if (IN == IN_ACT) {
+                    v = __ldg(reinterpret_cast<const uint4 *>(a.in + (size_t)t * 16) + half);
+                } else if (half == 0) {
+                    const uint8_t f = a.cf[t];
+                    const __nv_bfloat162 x = __floats2bfloat162_rn((f & CF_LIQ) ? a.r[t] * inv : 0.f, type_code(f));
+                    v.x = *reinterpret_cast<const uint32_t *>(&x);
+                }
+            }
             *reinterpret_cast<uint4 *>(tile + swz_off(cidx, half)) = v;
         }
         __syncthreads();
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(256) k_conv_mid(const __nv_bfloat16 *__restric
                         uint32_t b0, b1, b2, b3;
                         ldsm_x4(w_s + swz_off(wrow, wh), b0, b1, b2, b3);
                         mma_bf16(acc0, a0, a1, a2, a3, b0, b1);
-                        mma_bf16(acc1, a0, a1, a2, a3, b2, b3);
+                        if (OUT != OUT_Z) mma_bf16(acc1, a0, a1, a2, a3, b2, b3);
                     }
             // epilogue: cells (lane/4) and (lane/4 + 8); channels (lane%4)*2 (+1), +8
             const int gj = j0 + warp;
@@ -217,59 +218,64 @@ __global__ void __launch_bounds__(256) k_conv_mid(const __nv_bfloat16 *__restric
                 if (gi >= L.nx || gj >= L.ny) continue;
                 const size_t t = (size_t)cell_t(L, gi, gj, tk);
                 const int co = (lane & 3) * 2;
+                if (OUT == OUT_Z) {
+                    if (co == 0) {
+                        const float yv = acc0[hr * 2] + bv[0];
+                        if (a.y) a.y[t] = yv;
+                        if (a.z) a.z[t] = (a.cf[t] & CF_LIQ) ? sc * yv : 0.f;
+                    }
+                    continue;
+                }
+                if (IN == IN_R && a.xin && co == 0) {
+                    const uint8_t f = a.cf[t];
+                    *reinterpret_cast<__nv_bfloat162 *>(a.xin + t * 16) =
+                        __floats2bfloat162_rn((f & CF_LIQ) ? a.r[t] * inv : 0.f, type_code(f));
+                }
                 float v0 = acc0[hr * 2], v1 = acc0[hr * 2 + 1], v2 = acc1[hr * 2], v3 = acc1[hr * 2 + 1];
-                if (MODE == 0) {
+                if (OUT == OUT_RELU) {
                     v0 = fmaxf(v0 + bv[0], 0.f);
                     v1 = fmaxf(v1 + bv[1], 0.f);
                     v2 = fmaxf(v2 + bv[2], 0.f);
                     v3 = fmaxf(v3 + bv[3], 0.f);
                 } else {
-                    const __nv_bfloat162 r0 = *reinterpret_cast<const __nv_bfloat162 *>(aref + t * 16 + co);
-                    const __nv_bfloat162 r1 = *reinterpret_cast<const __nv_bfloat162 *>(aref + t * 16 + 8 + co);
+                    const __nv_bfloat162 r0 = *reinterpret_cast<const __nv_bfloat162 *>(a.aref + t * 16 + co);
+                    const __nv_bfloat162 r1 = *reinterpret_cast<const __nv_bfloat162 *>(a.aref + t * 16 + 8 + co);
                     v0 = __bfloat162float(r0.x) > 0.f ? v0 : 0.f;
                     v1 = __bfloat162float(r0.y) > 0.f ? v1 : 0.f;
                     v2 = __bfloat162float(r1.x) > 0.f ? v2 : 0.f;
                     v3 = __bfloat162float(r1.y) > 0.f ? v3 : 0.f;
                 }
-                *reinterpret_cast<__nv_bfloat162 *>(out + t * 16 + co) = __floats2bfloat162_rn(v0, v1);
-                *reinterpret_cast<__nv_bfloat162 *>(out + t * 16 + 8 + co) = __floats2bfloat162_rn(v2, v3);
+                *reinterpret_cast<__nv_bfloat162 *>(a.out + t * 16 + co) = __floats2bfloat162_rn(v0, v1);
+                *reinterpret_cast<__nv_bfloat162 *>(a.out + t * 16 + 8 + co) = __floats2bfloat162_rn(v2, v3);
             }
         }
     }
 }
 
-// ---- layer 5 (16 -> 1), CUDA cores ---------------------------------------------------
-__global__ void __launch_bounds__(256) k_conv_last(const __nv_bfloat16 *__restrict__ in,
-                                                   const float *__restrict__ w5f, const float *__restrict__ b5,
-                                                   const uint8_t *__restrict__ cf,
-                                                   const unsigned *__restrict__ smax, float *y, float *z, Layout L)
+// Chebyshev distance from each conv tile (32 x 8 cells of one plane) to the
+// nearest liquid cell, capped at 5: one block per tile scans the tile grown by 5.
+__global__ void __launch_bounds__(256) k_conv_tile_dist(const uint8_t *__restrict__ cf, Layout L, uint8_t *dist)
 {
-    __shared__ float w[NW5];
-    for (int t = threadIdx.x; t < NW5; t += blockDim.x) w[t] = w5f[t];
+    __shared__ int best;
+    const int ntx = (L.nx + NT_X - 1) / NT_X, nty = (L.ny + NT_Y - 1) / NT_Y;
+    const int tb = blockIdx.x;
+    const int tx = tb % ntx, ty = (tb / ntx) % nty, tk = tb / (ntx * nty);
+    const int i0 = tx * NT_X, j0 = ty * NT_Y;
+    if (threadIdx.x == 0) best = 5;
     __syncthreads();
-    const float s = __uint_as_float(*smax);
-    const float bias = b5[0];
-    const int ncell = L.nx * L.ny * L.nz;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
-        const int i = c % L.nx, j = (c / L.nx) % L.ny, k = c / (L.nx * L.ny);
-        float acc = bias;
-        for (int dz = -1; dz <= 1; dz++)
-            for (int dy = -1; dy <= 1; dy++)
-                for (int dx = -1; dx <= 1; dx++) {
-                    if (!in_grid(L, i + dx, j + dy, k + dz)) continue;
-                    const __nv_bfloat162 *a =
-                        reinterpret_cast<const __nv_bfloat162 *>(in + (size_t)cell_t(L, i + dx, j + dy, k + dz) * 16);
-                    const int tp = tap_index(dz, dy, dx);
-#pragma unroll
-                    for (int q = 0; q < 8; q++) {
-                        const float2 v = __bfloat1622float2(a[q]);
-                        acc += w[(2 * q) * 27 + tp] * v.x + w[(2 * q + 1) * 27 + tp] * v.y;
-                    }
-                }
-        const int t = cell_t(L, i, j, k);
-        if (y) y[t] = acc;
-        if (z) z[t] = (cf[t] & CF_LIQ) ? s * acc : 0.f;
+    const int bx = NT_X + 10, by = NT_Y + 10, bz = 11;
+    int d = 5;
+    for (int e = threadIdx.x; e < bx * by * bz; e += blockDim.x) {
+        const int gi = i0 - 5 + e % bx, gj = j0 - 5 + (e / bx) % by, gk = tk - 5 + e / (bx * by);
+        if (!in_grid(L, gi, gj, gk) || !(cf[cell_t(L, gi, gj, gk)] & CF_LIQ)) continue;
+        const int dx = max(0, max(i0 - gi, gi - (i0 + NT_X - 1)));
+        const int dy = max(0, max(j0 - gj, gj - (j0 + NT_Y - 1)));
+        const int dz = abs(gk - tk);
+        d = min(d, max(dx, max(dy, dz)));
     }
+    if (d < 5) atomicMin(&best, d);
+    __syncthreads();
+    if (threadIdx.x == 0) dist[tb] = (uint8_t)best;
 }
 
 // max |r| over the liquid, as float bits (non-negative floats order like ints)
@@ -465,11 +471,19 @@ __global__ void k_adam(float *p, float *g, float *m, float *v, int n, float lr, 
 
 // bf16 working copies from the master copy
 __global__ void k_net_refresh(const float *__restrict__ p, float *w1f, float *w5f, __nv_bfloat16 *wf,
-                              __nv_bfloat16 *wt)
+                              __nv_bfloat16 *wt, __nv_bfloat16 *wf1, __nv_bfloat16 *wf5)
 {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < NPARAM; t += gridDim.x * blockDim.x) {
-        if (t < OB1) w1f[t] = bfr(p[t]);
-        if (t >= OW5 && t < OB5) w5f[t - OW5] = bfr(p[t]);
+        if (t < OB1) {
+            w1f[t] = bfr(p[t]);
+            const int tp = t % 27, ci = (t / 27) % 2, co = t / 54;  // [co][ci][tap]
+            wf1[(tp * 16 + co) * 16 + ci] = __float2bfloat16(p[t]);
+        }
+        if (t >= OW5 && t < OB5) {
+            w5f[t - OW5] = bfr(p[t]);
+            const int tp = (t - OW5) % 27, ci = (t - OW5) / 27;    // [1][ci][tap]
+            wf5[(tp * 16 + 0) * 16 + ci] = __float2bfloat16(p[t]);
+        }
         const int offs[3] = {OW2, OW3, OW4};
         for (int l = 0; l < 3; l++) {
             if (t < offs[l] || t >= offs[l] + NWM) continue;
@@ -491,7 +505,9 @@ __global__ void k_fill_zero(float *p, int n)
 
 static NetState *net(fs_ctx *c) { return static_cast<NetState *>(c->net); }
 
-static size_t conv_mid_smem() { return (size_t)TCELLS * 32 + 27 * 16 * 32; }
+static size_t conv_smem() { return (size_t)TCELLS * 32 + 27 * 16 * 32; }
+
+static int conv_tiles(const Layout &L) { return ((L.nx + NT_X - 1) / NT_X) * ((L.ny + NT_Y - 1) / NT_Y) * L.nz; }
 
 template <int CIN, int COUT>
 static size_t wgrad_smem() { return ((size_t)NT_X * NT_Y * COUT + (size_t)TCELLS * CIN) * 4; }
@@ -503,6 +519,7 @@ int net_alloc(fs_ctx *c, bool training)
     if (!n) {
         n = new (std::nothrow) NetState();
         if (!n) return set_error(FS_ENOMEM, "host allocation failed");
+        n->tlist_epoch = -1;
         c->net = n;
     }
     auto alloc = [&](void **p, size_t bytes) -> int {
@@ -521,7 +538,10 @@ int net_alloc(fs_ctx *c, bool training)
         (rc = alloc((void **)&n->m, NPARAM * 4)) || (rc = alloc((void **)&n->v, NPARAM * 4)) ||
         (rc = alloc((void **)&n->w1f, NW1 * 4)) || (rc = alloc((void **)&n->w5f, NW5 * 4)) ||
         (rc = alloc((void **)&n->wf, 3 * NWM * 2)) || (rc = alloc((void **)&n->wt, 3 * NWM * 2)) ||
-        (rc = alloc((void **)&n->smax, 16)) || (rc = alloc((void **)&n->y, nC * 4)))
+        (rc = alloc((void **)&n->smax, 16)) || (rc = alloc((void **)&n->y, nC * 4)) ||
+        (rc = alloc((void **)&n->wf1, 27 * 16 * 16 * 2)) || (rc = alloc((void **)&n->wf5, 27 * 16 * 16 * 2)) ||
+        (rc = alloc((void **)&n->tdist, (size_t)conv_tiles(c->L))) ||
+        (rc = alloc((void **)&n->tlist, (size_t)conv_tiles(c->L) * sizeof(int))))
         return rc;
     // inference needs two activation buffers; training keeps all five layer inputs
     const int nact = training ? 6 : 2;
@@ -535,8 +555,11 @@ int net_alloc(fs_ctx *c, bool training)
     }
     static bool attr_done = false;
     if (!attr_done) {
-        FS_CUDA(cudaFuncSetAttribute(k_conv_mid<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_mid_smem()));
-        FS_CUDA(cudaFuncSetAttribute(k_conv_mid<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_mid_smem()));
+        const int cs = (int)conv_smem();
+        FS_CUDA(cudaFuncSetAttribute(k_conv<IN_R, OUT_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs));
+        FS_CUDA(cudaFuncSetAttribute(k_conv<IN_ACT, OUT_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs));
+        FS_CUDA(cudaFuncSetAttribute(k_conv<IN_ACT, OUT_Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs));
+        FS_CUDA(cudaFuncSetAttribute(k_conv<IN_ACT, OUT_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs));
         FS_CUDA(cudaFuncSetAttribute(k_wgrad<16, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)wgrad_smem<16, 16>()));
         FS_CUDA(cudaFuncSetAttribute(k_wgrad<16, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -552,7 +575,8 @@ void net_free(fs_ctx *c)
 {
     NetState *n = net(c);
     if (!n) return;
-    void *ptrs[] = {n->master, n->grad, n->m, n->v, n->w1f, n->w5f, n->wf, n->wt, n->act, n->gact, n->y, n->gy, n->smax};
+    void *ptrs[] = {n->master, n->grad, n->m, n->v, n->w1f, n->w5f, n->wf, n->wt, n->act, n->gact,
+                    n->y, n->gy, n->smax, n->wf1, n->wf5, n->tdist, n->tlist};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete n;
@@ -567,7 +591,8 @@ int net_load(fs_ctx *c, const float *params, int count, bool host)
     NetState *n = net(c);
     FS_CUDA(cudaMemcpyAsync(n->master, params, NPARAM * 4, host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
                             c->stream));
-    k_net_refresh<<<(NPARAM + 255) / 256, 256, 0, c->stream>>>(n->master, n->w1f, n->w5f, n->wf, n->wt);
+    k_net_refresh<<<(NPARAM + 255) / 256, 256, 0, c->stream>>>(n->master, n->w1f, n->w5f, n->wf, n->wt, n->wf1,
+                                                                n->wf5);
     FS_CUDA(cudaGetLastError());
     FS_CUDA(cudaStreamSynchronize(c->stream));
     n->loaded = 1;
@@ -583,40 +608,115 @@ int net_read(fs_ctx *c, float *params_host)
     return FS_OK;
 }
 
-static int conv_grid(const fs_ctx *c)
+// Persistent grid of the conv kernel: as many blocks as fit on the SMs.
+static int conv_grid(const fs_ctx *c, int tiles)
 {
-    const Layout &L = c->L;
-    const int ntiles = ((L.nx + NT_X - 1) / NT_X) * ((L.ny + NT_Y - 1) / NT_Y) * L.nz;
-    return std::max(1, std::min(ntiles, c->num_sms * 2));
+    static int per_sm = 0;
+    if (!per_sm) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv<IN_ACT, OUT_RELU>, 256, conv_smem()) !=
+                cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+    }
+    return std::max(1, std::min(tiles, c->num_sms * per_sm));
 }
 
-// z = s Net(r / s) on liquid cells (cell space), forward activations kept in
-// act[0..4] when `keep` (training), else ping-pong in act[0..1].
+// The conv tiles sorted by their distance to the liquid, for the current mask.
+static int net_tile_list(fs_ctx *c)
+{
+    NetState *n = net(c);
+    if (n->tlist_epoch == c->mask_epoch) return FS_OK;
+    const Layout &L = c->L;
+    const int nt = conv_tiles(L);
+    k_conv_tile_dist<<<nt, 256, 0, c->stream>>>(c->cflag, L, n->tdist);
+    c->n_launches += 1;
+    FS_CUDA(cudaGetLastError());
+    std::vector<uint8_t> d((size_t)nt);
+    FS_CUDA(cudaMemcpyAsync(d.data(), n->tdist, (size_t)nt, cudaMemcpyDeviceToHost, c->stream));
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    std::vector<int> list;
+    list.reserve((size_t)nt);
+    for (int dd = 0; dd <= 5; dd++) {
+        for (int t = 0; t < nt; t++)
+            if (d[(size_t)t] == dd) list.push_back(t);
+        n->tcount[dd] = (int)list.size();
+    }
+    FS_CUDA(cudaMemcpy(n->tlist, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice));
+    n->tlist_epoch = c->mask_epoch;
+    return FS_OK;
+}
+
+static void conv_launch(fs_ctx *c, int in, int out, const ConvArgs &a, int tiles)
+{
+    const int g = conv_grid(c, tiles);
+    const size_t sm = conv_smem();
+    if (in == IN_R)
+        k_conv<IN_R, OUT_RELU><<<g, 256, sm, c->stream>>>(a);
+    else if (out == OUT_RELU)
+        k_conv<IN_ACT, OUT_RELU><<<g, 256, sm, c->stream>>>(a);
+    else if (out == OUT_Z)
+        k_conv<IN_ACT, OUT_Z><<<g, 256, sm, c->stream>>>(a);
+    else
+        k_conv<IN_ACT, OUT_BWD><<<g, 256, sm, c->stream>>>(a);
+    c->n_launches += 1;
+}
+
+// z = s Net(r / s) on liquid cells, 0 elsewhere (cell space). Training (`keep`)
+// runs every layer on every tile and keeps the layer inputs in act[0..4] and the
+// output in y; inference runs layer l on the tiles within 5 - l cells of the
+// liquid, with activations ping-ponging in act[0..1].
 static int net_forward(fs_ctx *c, const float *r, float *z, float *y, bool keep)
 {
     NetState *n = net(c);
     const Layout &L = c->L;
     const size_t nC = (size_t)L.nC;
-    const int ncell = L.nx * L.ny * L.nz;
-    const int gb = std::max(1, std::min((ncell + 255) / 256, c->num_sms * 8));
+    int rc;
+    if (!keep && (rc = net_tile_list(c))) return rc;
     FS_CUDA(cudaMemsetAsync(n->smax, 0, sizeof(unsigned), c->stream));
     k_absmax<<<grid_blocks(c, L.nC, 256), 256, 0, c->stream>>>(r, c->cflag, L.nC, n->smax);
+    c->n_launches += 1;
+    if (z) FS_CUDA(cudaMemsetAsync(z, 0, nC * sizeof(float), c->stream));
     __nv_bfloat16 *A[6];
     for (int l = 0; l < 6; l++) A[l] = n->act + (keep ? (size_t)l : (size_t)(l & 1)) * nC * 16;
-    // keep: x -> A[0], a1 -> A[1], ..., a4 -> A[4]; else a1 -> A[0]/A[1] ping-pong
-    __nv_bfloat16 *xin = keep ? A[0] : nullptr;
-    __nv_bfloat16 *a1 = keep ? A[1] : A[0];
-    k_conv_first<<<gb, 256, 0, c->stream>>>(r, c->cflag, n->smax, n->w1f, n->master + OB1, xin, a1, L);
-    __nv_bfloat16 *cur = a1;
+    const int all = conv_tiles(L);
+    auto tiles_for = [&](int layer) { return keep ? all : n->tcount[5 - layer]; };  // layer 1 .. 5
+    ConvArgs a{};
+    a.cf = c->cflag;
+    a.smax = n->smax;
+    a.tiles = keep ? nullptr : n->tlist;
+    a.L = L;
+    // layer 1: input built from r; keep: x -> A[0], a1 -> A[1]
+    a.r = r;
+    a.wts = n->wf1;
+    a.bias = n->master + OB1;
+    a.xin = keep ? A[0] : nullptr;
+    a.out = keep ? A[1] : A[0];
+    a.ntiles = tiles_for(1);
+    conv_launch(c, IN_R, OUT_RELU, a, a.ntiles);
+    __nv_bfloat16 *cur = a.out;
+    a.xin = nullptr;
+    a.r = nullptr;
     const int bias_off[3] = {OB2, OB3, OB4};
     for (int l = 0; l < 3; l++) {
         __nv_bfloat16 *nxt = keep ? A[2 + l] : (cur == A[0] ? A[1] : A[0]);
-        k_conv_mid<0><<<conv_grid(c), 256, conv_mid_smem(), c->stream>>>(cur, n->wf + (size_t)l * NWM,
-                                                                         n->master + bias_off[l], nullptr, nxt, L);
+        a.in = cur;
+        a.wts = n->wf + (size_t)l * NWM;
+        a.bias = n->master + bias_off[l];
+        a.out = nxt;
+        a.ntiles = tiles_for(2 + l);
+        conv_launch(c, IN_ACT, OUT_RELU, a, a.ntiles);
         cur = nxt;
     }
-    k_conv_last<<<gb, 256, 0, c->stream>>>(cur, n->w5f, n->master + OB5, c->cflag, n->smax, y, z, L);
-    c->n_launches += 6;
+    a.in = cur;
+    a.wts = n->wf5;
+    a.bias = n->master + OB5;
+    a.out = nullptr;
+    a.y = y;
+    a.z = z;
+    a.ntiles = tiles_for(5);
+    conv_launch(c, IN_ACT, OUT_Z, a, a.ntiles);
     FS_CUDA(cudaGetLastError());
     return FS_OK;
 }
@@ -664,8 +764,13 @@ int net_grad(fs_ctx *c, const float *b, const float *q, double *loss)
     for (int l = 2; l >= 0; l--) {
         // G[gi] = dL/d(output of layer l+2) (post-ReLU mask applied); input = A[l+1]
         k_wgrad<16, 16, false><<<wg, 256, wgrad_smem<16, 16>(), c->stream>>>(G[gi], A[l + 1], n->grad + woff[l], n->grad + boff[l], L);
-        k_conv_mid<1><<<conv_grid(c), 256, conv_mid_smem(), c->stream>>>(G[gi], n->wt + (size_t)l * NWM, nullptr,
-                                                                        A[l + 1], G[gi ^ 1], L);
+        ConvArgs bw{};
+        bw.in = G[gi];
+        bw.wts = n->wt + (size_t)l * NWM;
+        bw.aref = A[l + 1];
+        bw.out = G[gi ^ 1];
+        bw.L = L;
+        conv_launch(c, IN_ACT, OUT_BWD, bw, conv_tiles(L));
         gi ^= 1;
     }
     // layer 1: gradient w.r.t. W1 from the stored input x (2 channels used)
@@ -687,7 +792,8 @@ int net_adam(fs_ctx *c, double lr, double beta1, double beta2, double eps, int s
     k_adam<<<(NPARAM + 255) / 256, 256, 0, c->stream>>>(n->master, n->grad, n->m, n->v, NPARAM, (float)lr,
                                                         (float)beta1, (float)beta2, (float)eps, c1, c2,
                                                         (float)gscale, fix_offsets);
-    k_net_refresh<<<(NPARAM + 255) / 256, 256, 0, c->stream>>>(n->master, n->w1f, n->w5f, n->wf, n->wt);
+    k_net_refresh<<<(NPARAM + 255) / 256, 256, 0, c->stream>>>(n->master, n->w1f, n->w5f, n->wf, n->wt, n->wf1,
+                                                                n->wf5);
     c->n_launches += 2;
     FS_CUDA(cudaGetLastError());
     FS_CUDA(cudaStreamSynchronize(c->stream));
