@@ -42,8 +42,13 @@ UNIT = "cell-steps/s"
 # bytes) of the kernels, keyed by the profile name; each entry holds the hash of
 # the files that define the kernel and the data layout it reads, and is reported
 # only while those files are unchanged (capture commands in profiles/).
-NCU_TRAFFIC = {}
-KERNEL_FILES = ("fs_stencil.cuh", "fs_tma.cuh", "fs_internal.cuh", "fs_mask.cu")
+NCU_TRAFFIC = {
+    # ncu --set full on the benchmark's 256^3 blob (profiles/cg_kernels_256_ncu.md); DRAM writes
+    # still held dirty in L2 when the kernel ends are not counted
+    "pressure_spmv": {"bytes_per_launch": 122095872 + 24217344, "source": "c05aabbc521428b2"},
+    "pressure_update": {"bytes_per_launch": 139048448 + 19815168, "source": "c05aabbc521428b2"},
+}
+KERNEL_FILES = ("fs_stencil.cuh", "fs_tma.cuh", "fs_mask.cu")
 
 
 def args_parse():
@@ -354,9 +359,15 @@ def main():
                     "algorithmic_bytes_per_launch": by / launches, "launches": launches,
                     "avg_launch_us": 1e3 * ms / launches,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback"}
-    total_ms = sum(v[1] for v in prof.values())
-    kernels = {k: {"launches": v[0], "ms": round(v[1], 3), "share_of_timed": round(v[1] / (1e3 * elapsed), 4)}
-               for k, v in prof.items()}
+    # CG kernels are timed every PROFILE_PERIOD-th iteration, the others at every launch
+    sampled = ("pressure_spmv", "pressure_update", "visc_spmv", "visc_update", "fcg_vectors")
+    kernels = {}
+    for k, v in prof.items():
+        if k == "all_kernels" or not v[0]:
+            continue
+        scale = PROFILE_PERIOD if k in sampled else 1
+        kernels[k] = {"timed_launches": v[0], "mean_us": round(1e3 * v[1] / v[0], 2),
+                      "est_share_of_step": round(scale * v[1] / (1e3 * elapsed), 4)}
     gpu_launches = None
     if "all_kernels" in prof:
         gpu_launches = prof["all_kernels"][0]

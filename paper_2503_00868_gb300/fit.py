@@ -1,0 +1,141 @@
+"""Parameter fit through the differentiable step (Sec. 3.4.2).
+
+The paper fits simulation parameters (among them the viscosity) and a correction of
+the initial velocity by minimising the masked loss of Eq. eq::optLoss between
+simulated and observed surface velocities over the frames, with each parameter
+mapped to its physical scale through exp or a sigmoid (Sec. 3.4.2). This module
+runs that fit on the library:
+  * theta = log nu and a per-face correction delta of the initial velocity;
+  * the loss at every frame on the surface band, its gradient w.r.t. nu and the
+    initial velocity from the checkpointed rollout's hand-written adjoint;
+  * Adam on both (torch.optim on the parameter tensors: the optimiser update is
+    plumbing around the library, every step and adjoint runs in its kernels).
+The scene is a liquid blob on the floor with a shallow liquid layer fed by an
+inflow patch on the x = 0 wall, gravity along -y. Targets are synthetic: a
+forward run with nu_true and a seeded smooth delta_true, observed every frame.
+
+    python -m paper_2503_00868_gb300.fit --nx 192 --ny 128 --nz 192 --frames 60 \\
+        --iters 50 --precond learned
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+from typing import Callable, Dict, Optional
+
+import numpy as np
+import torch
+
+from . import fluidstep as F
+from . import workloads as W
+from .rollout import forward_states, rollout_loss
+
+PRECONDS = {"jacobi": F.FS_PRECOND_JACOBI, "mic0": F.FS_PRECOND_MIC0, "learned": F.FS_PRECOND_LEARNED}
+
+
+def river_scene(nx: int, ny: int, nz: int, seed: int, inflow_speed: float = 0.5, depth: float = 0.25):
+    """Cell types, prescribed face values (inflow on the x = 0 wall faces of liquid
+    cells below `depth` m, zero on the other fixed faces) and scene info."""
+    types, inflow, info = W.river_with_blob(nx, ny, nz, seed, depth)
+    bc = [np.zeros(s) for s in W.face_shapes(nx, ny, nz)]
+    bc[0] = np.where(inflow == 1, inflow_speed, 0.0)
+    return types, bc, info
+
+
+def make_grid(nx: int, ny: int, nz: int, types, bc, precond: str = "jacobi", nu: float = 1e-2,
+              weights: Optional[np.ndarray] = None, **kw) -> F.Grid:
+    g = F.Grid(nx, ny, nz, dx=1.0 / ny, dt=1.0 / 30.0, nu=nu, g=(0.0, -9.81, 0.0), precond=PRECONDS[precond],
+               **kw)
+    g.set_mask(types, g.pack(bc))
+    if precond == "learned":
+        if weights is None:
+            from .train_precond import default_weights
+            weights = default_weights()
+        F.fs_net_load(g.ctx, weights)
+    return g
+
+
+def synthetic_targets(grid: F.Grid, u_base: F.Mac, delta_true: F.Mac, nu_true: float, frames: int):
+    """Band observations of a forward run from u_base + delta_true with nu_true:
+    {frame: state} for frames 1..frames."""
+    grid.set_params(nu=nu_true)
+    u0 = F.Mac(*(b + d for b, d in zip(u_base, delta_true)))
+    states = forward_states(grid, u0, frames)
+    return {n: states[n] for n in range(1, frames + 1)}
+
+
+def fit(grid: F.Grid, u_base: F.Mac, targets: Dict[int, F.Mac], frames: int, iters: int = 50,
+        nu0: float = 1e-3, lr_theta: float = 0.05, lr_delta: float = 1e-3, checkpoint_every: int = 4,
+        fit_delta: bool = True, cosine: bool = False, betas=(0.9, 0.999),
+        callback: Optional[Callable[[int, float, float], None]] = None) -> dict:
+    """Adam on theta = log nu (and delta when `fit_delta`) against `targets`, with
+    the learning rates decayed to zero along a cosine when `cosine`. Returns the
+    fitted nu, delta and the (loss, nu) history before each update."""
+    theta = torch.tensor(math.log(nu0), dtype=torch.float32, requires_grad=True)
+    delta = [torch.zeros_like(t, requires_grad=fit_delta) for t in u_base]
+    groups = [{"params": [theta], "lr": lr_theta}]
+    if fit_delta:
+        groups.append({"params": delta, "lr": lr_delta})
+    opt = torch.optim.Adam(groups, betas=betas)
+    sched = (torch.optim.lr_scheduler.LambdaLR(opt, lambda i: 0.5 * (1.0 + math.cos(math.pi * i / iters)))
+             if cosine else None)
+    history = []
+    for it in range(iters):
+        opt.zero_grad()
+        u0 = F.Mac(*(b + d for b, d in zip(u_base, delta)))
+        nu = torch.exp(theta)
+        loss = rollout_loss(grid, u0, nu, frames, targets, checkpoint_every)
+        loss.backward()
+        history.append((float(loss.detach()), float(nu.detach())))
+        if callback:
+            callback(it, history[-1][0], history[-1][1])
+        opt.step()
+        if sched:
+            sched.step()
+    return {"nu": float(torch.exp(theta).detach()), "delta": [d.detach() for d in delta], "history": history}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--nx", type=int, default=192)
+    ap.add_argument("--ny", type=int, default=128)
+    ap.add_argument("--nz", type=int, default=192)
+    ap.add_argument("--frames", type=int, default=60)
+    ap.add_argument("--iters", type=int, default=50)
+    ap.add_argument("--precond", default="learned", choices=sorted(PRECONDS))
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--nu-true", type=float, default=1e-2)
+    ap.add_argument("--nu0", type=float, default=1e-3)
+    ap.add_argument("--delta-sigma", type=float, default=0.05, help="std of the true correction, m/s")
+    a = ap.parse_args()
+    torch.cuda.set_device(0)
+    types, bc, info = river_scene(a.nx, a.ny, a.nz, a.seed)
+    grid = make_grid(a.nx, a.ny, a.nz, types, bc, a.precond, maxit_p=20000)
+    u_base = grid.pack(bc)
+    dt_np = W.blurred_noise_mac(a.nx, a.ny, a.nz, a.seed + 7)
+    scale = a.delta_sigma / max(float(np.std(np.concatenate([x.ravel() for x in dt_np]))), 1e-12)
+    delta_true = grid.pack([x * scale for x in dt_np])
+    t0 = time.time()
+    targets = synthetic_targets(grid, u_base, delta_true, a.nu_true, a.frames)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    log = []
+    res = fit(grid, u_base, targets, a.frames, a.iters, a.nu0,
+              callback=lambda it, l, nu: (log.append((it, l, nu)), print(f"iter {it:3d} loss {l:.6e} nu {nu:.5e}",
+                                                                          flush=True)))
+    torch.cuda.synchronize()
+    t2 = time.time()
+    cells = a.nx * a.ny * a.nz
+    steps = a.iters * a.frames * 3  # forward, recompute, adjoint
+    print(json.dumps({"grid": [a.nx, a.ny, a.nz], "frames": a.frames, "iters": a.iters, "precond": a.precond,
+                      "occupancy": info["occupancy"], "nu_true": a.nu_true, "nu_fit": res["nu"],
+                      "loss_first": res["history"][0][0], "loss_last": res["history"][-1][0],
+                      "targets_s": t1 - t0, "fit_s": t2 - t1, "s_per_iter": (t2 - t1) / max(a.iters, 1),
+                      "cell_steps_per_s": cells * steps / (t2 - t1)}), flush=True)
+    grid.close()
+
+
+if __name__ == "__main__":
+    main()
