@@ -66,6 +66,8 @@ def args_parse():
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the Jacobi / MIC(0) / learned projection comparison")
     ap.add_argument("--compare-n", type=int, default=256)
+    ap.add_argument("--cold-start", action="store_true",
+                    help="every pressure solve from q = 0 (default: warm start from the previous solve)")
     return ap.parse_args()
 
 
@@ -140,11 +142,11 @@ def make_scene(n, seed):
     return types, u0, tgt, info
 
 
-def params_for(n, precond):
+def params_for(n, precond, warm_start=1):
     from paper_2503_00868_gb300 import fluidstep as F
     return dict(dx=1.0 / n, dt=1.0 / 30.0, nu=0.01, g=(0.0, 0.0, 0.0), tol_p=1e-6, tol_v=1e-6,
                 precond=F.FS_PRECOND_MIC0 if precond == "mic0" else F.FS_PRECOND_JACOBI, check_every=16,
-                maxit_p=20000, maxit_v=4000)
+                maxit_p=20000, maxit_v=4000, warm_start=warm_start)
 
 
 def cpu_oracle_sample(n, frames=1):
@@ -199,6 +201,7 @@ def workload_config(a):
                         f"surface-band L2 loss at the last frame, gradients w.r.t. nu and u0",
             "grid": [a.n, a.n, a.n], "frames": a.frames, "checkpoint_every": CHECKPOINT,
             "precond": a.precond, "tol": 1e-6, "nu": 0.01, "dt": 1.0 / 30.0,
+            "warm_start": not a.cold_start,
             "l2_between_steps": "inputs larger than L2 (working set > 1 GB per replica)",
             "parallelism": "replicas" if a.gpus > 1 else "single"}
 
@@ -264,7 +267,7 @@ def main():
 
     n, frames = a.n, a.frames
     types, u0_np, tgt_np, info = make_scene(n, rank)
-    grid = F.Grid(n, n, n, **params_for(n, a.precond))
+    grid = F.Grid(n, n, n, **params_for(n, a.precond, 0 if a.cold_start else 1))
     grid.set_mask(types)
     u0 = grid.pack(u0_np)
     tgt = grid.pack(tgt_np)

@@ -109,6 +109,13 @@ typedef struct {
     int spin_limit;    /* cap on every device-side spin-wait (iterations), >= 1 */
     double mic_tau;    /* MIC(0) modification, in [0, 1] */
     double mic_sigma;  /* MIC(0) safety threshold, in [0, 1) */
+    int warm_start;    /* 0: every pressure solve starts from q = 0. 1: a forward projection
+                          (fs_step, fs_project) starts from the last converged pressure of a
+                          forward projection on this context, an adjoint projection
+                          (fs_adjoint_step) from the last adjoint one, whenever that gives a
+                          smaller initial residual than q = 0; the stopping test is unchanged,
+                          so only the iteration count differs. fs_set_mask and
+                          fs_set_params reset the kept pressures. */
 } fs_params;
 
 typedef struct {
@@ -134,7 +141,7 @@ typedef struct {
 
 /* Default parameters: dx = 1/ny is left to the caller (set to 1), dt = 1/30,
  * nu = 0.01, rho = 1000, g = 0, Jacobi, tolerances 1e-6, caps 20000/2000,
- * check_every 8, spin_limit 1<<22, MIC(0) tau = 0.97, sigma = 0.25. */
+ * check_every 8, spin_limit 1<<22, MIC(0) tau = 0.97, sigma = 0.25, no warm start. */
 void fs_default_params(fs_params *p);
 
 /* Create a context for an nx * ny * nz grid (each >= 2) bound to `cuda_stream`
@@ -152,7 +159,8 @@ int fs_layout(const fs_ctx *c, fs_layout_t *out);
 /* Rebind the context to another stream. */
 int fs_set_stream(fs_ctx *c, void *cuda_stream);
 
-/* Replace the step parameters (e.g. a new nu during a fit). Same checks as init. */
+/* Replace the step parameters (e.g. a new nu during a fit). Same checks as init.
+ * Drops the pressures kept for warm starts. */
 int fs_set_params(fs_ctx *c, const fs_params *p);
 
 /* Set the grid-type mask (Sec. 3.4.2, "grid types of surface, occupation, or

@@ -49,6 +49,7 @@ static int check_params(const fs_params *p)
     if (p->spin_limit < 1) return set_error(FS_EINVAL, "spin_limit must be >= 1");
     if (!(p->mic_tau >= 0.0 && p->mic_tau <= 1.0)) return set_error(FS_EINVAL, "mic_tau must be in [0, 1]");
     if (!(p->mic_sigma >= 0.0 && p->mic_sigma < 1.0)) return set_error(FS_EINVAL, "mic_sigma must be in [0, 1)");
+    if (p->warm_start != 0 && p->warm_start != 1) return set_error(FS_EINVAL, "warm_start must be 0 or 1");
     return FS_OK;
 }
 
@@ -155,7 +156,7 @@ static void free_ctx(fs_ctx *c)
     fcg_release(c);
     void *ptrs[] = {c->cflag, c->fflag, c->bc, c->dsum, c->pb, c->pr, c->pp[0], c->pp[1], c->pq, c->px, c->pz,
                     c->vx, c->vr, c->vp[0], c->vp[1], c->vq, c->fu[0], c->fu[1], c->fu[2], c->fg[0], c->fg[1],
-                    c->fg[2], c->gc[0], c->gc[1], c->gc[2], c->mic_prec, c->scal, c->partials, c->err_word,
+                    c->fg[2], c->gc[0], c->gc[1], c->gc[2], c->mic_prec, c->scal, c->partials, c->err_word, c->pw[0], c->pw[1],
                     c->act_cell, c->act_face, c->list_cell, c->list_face, c->items_cell, c->items_face, c->qmask_cell, c->qmask_face,
                     c->py, c->mic_order,
                     c->mic_tact, c->mic_tflag, c->mic_next};
@@ -188,6 +189,7 @@ void fs_default_params(fs_params *p)
     p->spin_limit = 1 << 22;
     p->mic_tau = 0.97;
     p->mic_sigma = 0.25;
+    p->warm_start = 0;
 }
 
 const char *fs_last_error(void) { return g_err; }
@@ -380,6 +382,7 @@ int fs_set_params(fs_ctx *c, const fs_params *p)
     if (rc) return rc;
     if (p->mic_tau != c->prm.mic_tau || p->mic_sigma != c->prm.mic_sigma) c->mic_ready = 0;
     c->prm = *p;
+    c->pw_valid[0] = c->pw_valid[1] = 0;  // a new problem: no warm start from earlier solves
     return FS_OK;
 }
 
@@ -421,6 +424,7 @@ int fs_step(fs_ctx *c, const fs_mac *u_in, fs_mac *u_out, fs_mac *u_visc, fs_sta
     fs_mac *uv = u_visc ? u_visc : u_out;
     if ((rc = launch_compose(c, f3(uv)))) return rc;
     if ((rc = launch_divergence(c, cf3(uv)))) return rc;
+    c->solve_kind = 0;
     int rp = solve_pressure(c, s);
     if (rp == FS_ECUDA || rp == FS_EINVAL) return rp;
     if ((rc = launch_grad_subtract(c, cf3(uv), f3(u_out), nullptr))) return rc;
@@ -439,6 +443,7 @@ int fs_project(fs_ctx *c, fs_mac *u, float *q_out, fs_stats *st)
     fs_stats *s = st ? st : &local;
     std::memset(s, 0, sizeof(*s));
     if ((rc = launch_divergence(c, cf3(u)))) return rc;
+    c->solve_kind = 0;
     int rp = solve_pressure(c, s);
     if (rp == FS_ECUDA || rp == FS_EINVAL) return rp;
     if ((rc = launch_grad_subtract(c, cf3(u), f3(u), q_out))) return rc;
@@ -478,6 +483,7 @@ int fs_adjoint_step(fs_ctx *c, const fs_mac *u_in, const fs_mac *u_visc, const f
     CF3 fgc{{c->fg[0], c->fg[1], c->fg[2]}};
     if ((rc = launch_mask_fluid(c, cf3(g_out), fg))) return rc;
     if ((rc = launch_divergence(c, fgc))) return rc;
+    c->solve_kind = 1;
     int rp = solve_pressure(c, s);
     if (rp == FS_ECUDA || rp == FS_EINVAL) return rp;
     if ((rc = launch_grad_subtract(c, fgc, fg, nullptr))) return rc;

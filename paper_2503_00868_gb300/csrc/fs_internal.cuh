@@ -113,6 +113,11 @@ struct fs_ctx {
 
     // pressure solve (cell space)
     float *pb, *pr, *pp[2], *pq, *px, *pz;
+    // warm start: last converged pressure of a forward (0) / adjoint (1) projection,
+    // allocated on first use, invalidated by set_mask
+    float *pw[2];
+    int pw_valid[2];
+    int solve_kind;       // kind of the pressure solve being run
     // viscosity solve (face space)
     float *vx, *vr, *vp[2], *vq;
     // full-layout scratch fields (3 * S each, public layout)

@@ -371,6 +371,7 @@ int build_mask(fs_ctx *c, const uint8_t *types_dense, const fs_mac *bc)
     c->singular = (h[0] > 0 && h[1] == 0) ? 1 : 0;
     c->mask_set = 1;
     c->mask_epoch += 1;
+    c->pw_valid[0] = c->pw_valid[1] = 0;
     c->mic_ready = 0;
     c->mic_sched_ready = 0;
     return FS_OK;

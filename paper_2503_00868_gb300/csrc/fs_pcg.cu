@@ -588,6 +588,53 @@ int remove_null_mode(fs_ctx *c, float *z)
 
 static int pressure_tail(fs_ctx *c, const SolveScal &h, fs_stats *st);
 
+// Warm start (fs_params.warm_start): after the x = 0 initialisation, start
+// instead from the last converged pressure of the same kind of projection when
+// its residual is below half of |b|^2; r = b - A x, p = 0, iteration count 0.
+static int try_warm_start(fs_ctx *c, bool jac)
+{
+    const int k = c->solve_kind;
+    if (!c->prm.warm_start || !c->pw_valid[k] || !c->pw[k]) return FS_OK;
+    const Layout &L = c->L;
+    const int bs = grid_blocks(c, L.nC, TH);
+    k_pois_true_res<<<bs, TH, 0, c->stream>>>(c->pb, c->pw[k], c->cflag, L.nC, L.P, L.PL, c->singular,
+                                              c->scal + 2, c->partials);
+    c->n_launches += 1;
+    FS_CUDA(cudaGetLastError());
+    SolveScal m, h0;
+    int rc;
+    if ((rc = read_scal(c, 2, &m)) || (rc = read_scal(c, 0, &h0))) return rc;
+    if (h0.done || !(m.aux[0] < 0.5 * h0.bb)) return FS_OK;
+    FS_CUDA(cudaMemcpyAsync(c->px, c->pw[k], (size_t)L.nC * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    if (jac)
+        k_pois_restart<true><<<bs, TH, 0, c->stream>>>(c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, L.nC,
+                                                       L.P, L.PL, c->scal + 0, c->partials);
+    else
+        k_pois_restart<false><<<bs, TH, 0, c->stream>>>(c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, L.nC,
+                                                        L.P, L.PL, c->scal + 0, c->partials);
+    c->n_launches += 1;
+    FS_CUDA(cudaGetLastError());
+    return FS_OK;
+}
+
+// Keep the converged pressure for the next warm start of this kind.
+static int save_warm_start(fs_ctx *c)
+{
+    const int k = c->solve_kind;
+    if (!c->prm.warm_start) return FS_OK;
+    const size_t bytes = (size_t)c->L.nC * sizeof(float);
+    if (!c->pw[k]) {
+        if (cudaMalloc(&c->pw[k], bytes) != cudaSuccess) {
+            cudaGetLastError();
+            c->pw[k] = nullptr;
+            return FS_OK;  // no warm start then; not an error of the solve
+        }
+    }
+    FS_CUDA(cudaMemcpyAsync(c->pw[k], c->px, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    c->pw_valid[k] = 1;
+    return FS_OK;
+}
+
 // r = b - A x in pr (unscaled) for a warm restart of flexible CG.
 int pressure_restart(fs_ctx *c)
 {
@@ -617,12 +664,14 @@ static int pcg_iterate(fs_ctx *c, SolveScal &h, bool warm)
         else
             k_pois_restart<false><<<grid_blocks(c, L.nC, TH), TH, 0, c->stream>>>(
                 c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, L.nC, L.P, L.PL, s, c->partials);
-    } else if (jac) {
-        k_pois_init<true><<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(
-            c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, n4, tol2, c->prm.maxit_p, s, c->partials);
     } else {
-        k_pois_init<false><<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(
-            c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, n4, tol2, c->prm.maxit_p, s, c->partials);
+        if (jac)
+            k_pois_init<true><<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(
+                c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, n4, tol2, c->prm.maxit_p, s, c->partials);
+        else
+            k_pois_init<false><<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(
+                c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, n4, tol2, c->prm.maxit_p, s, c->partials);
+        if (int rc = try_warm_start(c, jac)) return rc;
     }
     if (!jac) {
         int rc = apply_m();
@@ -726,7 +775,9 @@ static int solve_pressure_once(fs_ctx *c, fs_stats *st)
         if (m.aux[0] <= 4.0 * h.tol2 * h.bb) break;
         if (st) st->restarts_p += 1;
     }
-    return pressure_tail(c, h, st);
+    int rc = pressure_tail(c, h, st);
+    if (rc == FS_OK) rc = save_warm_start(c);
+    return rc;
 }
 
 // After the iterations: the true residual b - A x, the mean-free representative

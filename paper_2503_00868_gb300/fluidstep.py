@@ -40,7 +40,8 @@ class fs_params(C.Structure):
     _fields_ = [("dx", C.c_double), ("dt", C.c_double), ("nu", C.c_double), ("rho", C.c_double),
                 ("g", C.c_double * 3), ("precond", C.c_int), ("maxit_p", C.c_int), ("maxit_v", C.c_int),
                 ("tol_p", C.c_double), ("tol_v", C.c_double), ("check_every", C.c_int),
-                ("spin_limit", C.c_int), ("mic_tau", C.c_double), ("mic_sigma", C.c_double)]
+                ("spin_limit", C.c_int), ("mic_tau", C.c_double), ("mic_sigma", C.c_double),
+                ("warm_start", C.c_int)]
 
 
 class fs_stats(C.Structure):
