@@ -92,6 +92,8 @@ def lib():
                 "or_bf16_round": [C.c_double],
                 "or_net_forward": [G, _D * 5, _D * 5, _D, _D, _D],
                 "or_net_loss_grad": [G, _D * 5, _D * 5, _D, _D, _D * 5, _D * 5],
+                "or_wall_profile": [G, _D, _D, C.c_double, _P3],
+                "or_pbd_project": [G, _P3, C.c_int, C.c_int, C.c_double],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -101,6 +103,7 @@ def lib():
             L.or_bf16_round.restype = C.c_double
             L.or_net_forward.restype = C.c_double
             L.or_net_loss_grad.restype = C.c_double
+            L.or_pbd_project.restype = C.c_double
             _lib = L
     return _lib
 
@@ -328,3 +331,20 @@ def net_loss_grad(g: Grid, W, B, b, q):
     loss = lib().or_net_loss_grad(g.cstruct(), _net_ptrs(W), _net_ptrs(B), _ptr(_f64(b)),
                                   _ptr(_f64(q)), _net_ptrs(gW), _net_ptrs(gB))
     return loss, gW, gB
+
+
+def wall_profile(g: Grid, direction, vinf, delta):
+    """Base velocity of the volumetric initialisation (Sec. 3.3.3); vinf: (nz, nx)."""
+    out = g.zeros()
+    d = _f64(direction)
+    v = _f64(vinf)
+    assert v.shape == (g.nz, g.nx)
+    lib().or_wall_profile(g.cstruct(), _ptr(d), _ptr(v), float(delta), _p3(out))
+    return out
+
+
+def pbd_project(g: Grid, u, hold_surface=True, iters=100, eps=0.0):
+    """Constrained divergence projection (Eq. eq::divProj); returns (u, |div|_2)."""
+    u = [a.copy() for a in _field(g, u)]
+    norm = lib().or_pbd_project(g.cstruct(), _p3(u), int(bool(hold_surface)), int(iters), float(eps))
+    return u, norm

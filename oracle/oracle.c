@@ -1089,3 +1089,123 @@ double or_net_loss_grad(const or_grid *g, const double *const W[NET_LAYERS],
     free(acts); free(z); free(gy); free(gx);
     return num / den;
 }
+
+/* ------------------------------------------------------------------------ */
+/* volumetric-velocity initialisation (Sec. 3.3.3)                           */
+/* ------------------------------------------------------------------------ */
+
+/* Laminar boundary-layer profile of Sec. 3.3.3: |v| / V_inf = 3/2 e - 1/2 e^3 with
+ * e = y / delta below the boundary-layer thickness, 1 above it. */
+static double wall_factor(double y, double delta)
+{
+    if (!(delta > 0.0)) return 1.0;
+    double e = y / delta;
+    if (e >= 1.0) return 1.0;
+    if (e <= 0.0) return 0.0;
+    return 1.5 * e - 0.5 * e * e * e;
+}
+
+/* Surface speed of the column (i, k) of cells, clamped to the grid. */
+static double column_speed(const or_grid *g, const double *vinf, int i, int k)
+{
+    if (i < 0) i = 0;
+    if (i >= g->nx) i = g->nx - 1;
+    if (k < 0) k = 0;
+    if (k >= g->nz) k = g->nz - 1;
+    return vinf[(long)k * g->nx + i];
+}
+
+/* Base velocity: on every fluid face dir_c * V_inf * wall_factor(y / delta), y the
+ * height of the face centre above the floor (y = 0, the riverbed), V_inf the surface
+ * speed of the face's cell column (vinf, (nz, nx)); x and z faces between two
+ * columns take the mean of both. Fixed faces take their prescribed value, faces
+ * between air cells 0. */
+void or_wall_profile(const or_grid *g, const double dir[3], const double *vinf, double delta, double *const u[3])
+{
+    for (int c = 0; c < 3; c++) {
+        int d[3];
+        face_dims(g, c, d);
+        for (int k = 0; k < d[2]; k++)
+            for (int j = 0; j < d[1]; j++)
+                for (int i = 0; i < d[0]; i++) {
+                    long f = fidx(d, i, j, k);
+                    int cls = face_class(g, c, i, j, k);
+                    if (cls == FC_FIXED) { u[c][f] = bc_value(g, c, f); continue; }
+                    if (cls != FC_FLUID) { u[c][f] = 0.0; continue; }
+                    double y = (c == 1 ? (double)j : j + 0.5) * g->dx;
+                    double vi;
+                    if (c == 0) vi = 0.5 * (column_speed(g, vinf, i - 1, k) + column_speed(g, vinf, i, k));
+                    else if (c == 2) vi = 0.5 * (column_speed(g, vinf, i, k - 1) + column_speed(g, vinf, i, k));
+                    else vi = column_speed(g, vinf, i, k);
+                    u[c][f] = dir[c] * vi * wall_factor(y, delta);
+                }
+    }
+}
+
+/* A face the constrained projection may move: a fluid face that is not held. With
+ * hold_surface the faces between a liquid and an air cell (the free surface, which
+ * carries the observed surface velocity) are held. */
+static int pbd_free(const or_grid *g, int c, int i, int j, int k, int hold_surface)
+{
+    if (face_class(g, c, i, j, k) != FC_FLUID) return 0;
+    if (!hold_surface) return 1;
+    int o[3] = {0, 0, 0};
+    o[c] = 1;
+    int tl = cell_type(g, i - o[0], j - o[1], k - o[2]), tr = cell_type(g, i, j, k);
+    return !((tl == LIQUID && tr == AIR) || (tl == AIR && tr == LIQUID));
+}
+
+/* Constrained divergence projection (Eq. eq::divProj), Jacobi form: per iteration,
+ * for every liquid cell i the constraint C_i = (div u)_i = sum over its six faces of
+ * (u_hi - u_lo)/dx, lambda_i = -C_i / (sum over its free faces of (1/dx)^2 + eps);
+ * then every free face f moves by sum_i lambda_i dC_i/du_f = (lambda_lo - lambda_hi)/dx,
+ * lo and hi the cells on its two sides (lambda = 0 off the liquid). All lambda of an
+ * iteration come from the same field. Returns |C|_2 over the liquid after the last
+ * iteration. */
+double or_pbd_project(const or_grid *g, double *const u[3], int hold_surface, int iters, double eps)
+{
+    long n = ncells(g);
+    double *lam = (double *)calloc((size_t)n, sizeof(double));
+    double norm2 = 0.0;
+    for (int it = 0; it <= iters; it++) {
+        norm2 = 0.0;
+        for (int k = 0; k < g->nz; k++)
+            for (int j = 0; j < g->ny; j++)
+                for (int i = 0; i < g->nx; i++) {
+                    long ci = cidx(g, i, j, k);
+                    lam[ci] = 0.0;
+                    if (g->type[ci] != LIQUID) continue;
+                    double C = 0.0;
+                    int nfree = 0;
+                    for (int c = 0; c < 3; c++) {
+                        int d[3];
+                        face_dims(g, c, d);
+                        int hi[3] = {i, j, k};
+                        hi[c] += 1;
+                        C += (u[c][fidx(d, hi[0], hi[1], hi[2])] - u[c][fidx(d, i, j, k)]) / g->dx;
+                        nfree += pbd_free(g, c, i, j, k, hold_surface);
+                        nfree += pbd_free(g, c, hi[0], hi[1], hi[2], hold_surface);
+                    }
+                    norm2 += C * C;
+                    lam[ci] = -C / (nfree / (g->dx * g->dx) + eps);
+                }
+        if (it == iters) break;
+        for (int c = 0; c < 3; c++) {
+            int d[3];
+            face_dims(g, c, d);
+            int o[3] = {0, 0, 0};
+            o[c] = 1;
+            for (int k = 0; k < d[2]; k++)
+                for (int j = 0; j < d[1]; j++)
+                    for (int i = 0; i < d[0]; i++) {
+                        if (!pbd_free(g, c, i, j, k, hold_surface)) continue;
+                        int li = i - o[0], lj = j - o[1], lk = k - o[2];
+                        double ll = (cell_type(g, li, lj, lk) == LIQUID) ? lam[cidx(g, li, lj, lk)] : 0.0;
+                        double lh = (cell_type(g, i, j, k) == LIQUID) ? lam[cidx(g, i, j, k)] : 0.0;
+                        u[c][fidx(d, i, j, k)] += (ll - lh) / g->dx;
+                    }
+        }
+    }
+    free(lam);
+    return sqrt(norm2);
+}
