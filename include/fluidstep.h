@@ -214,6 +214,34 @@ int fs_loss_grad(fs_ctx *c, const fs_mac *u, const fs_mac *target, int mask_kind
  * singular), zero elsewhere. u: DEVICE field; b_out: DEVICE cell array. */
 int fs_divergence(fs_ctx *c, const fs_mac *u, float *b_out);
 
+/* Volumetric-velocity initialisation, base profile (Sec. 3.3.3: the laminar
+ * wall-function polynomial |v| / V_inf = 3/2 (y/delta) - 1/2 (y/delta)^3 below the
+ * boundary-layer thickness delta, 1 above). Every fluid face of component c gets
+ * dir[c] * V_inf * that factor, with y the height of the face centre above the
+ * floor (dx * j for y faces, dx * (j + 1/2) otherwise) and V_inf the surface speed
+ * of the face's cell column (the mean of the two columns for x and z faces between
+ * columns). Fixed faces get their prescribed values (fs_set_mask), all other faces
+ * and the padding 0.
+ *   dir:   HOST, 3 doubles (the mainstream direction; not normalised here)
+ *   vinf:  DEVICE, nz * nx floats, column (i, k) at k * nx + i
+ *   delta: boundary-layer thickness in metres, >= 0 (0: the factor is 1)
+ *   u_out: DEVICE field, overwritten.
+ * FS_EINVAL on a NULL pointer or a non-finite / negative delta. */
+int fs_wall_profile(fs_ctx *c, const double dir[3], const float *vinf, double delta, fs_mac *u_out);
+
+/* Constrained divergence projection (Sec. 3.3.3, Eq. eq::divProj), Jacobi form,
+ * in place on u. Per iteration every liquid cell i computes its constraint
+ * C_i = (div u)_i = sum over its six faces of (u_hi - u_lo)/dx and
+ * lambda_i = -C_i / (n_i / dx^2 + eps), n_i its number of free faces; then every
+ * free face moves by (lambda_lo - lambda_hi) / dx (lambda = 0 off the liquid).
+ * Free faces are fluid faces that are not held: fixed faces are always held, and
+ * with hold_surface != 0 the faces between a liquid and an air cell (the observed
+ * free surface) are held too.
+ *   iters: iterations, in [0, 10^7]; eps: relaxation, >= 0
+ *   div_norm (HOST, nullable): |C|_2 over the liquid after the last iteration.
+ * FS_EINVAL on bad arguments, FS_ENONFINITE if the divergence is not finite. */
+int fs_pbd_project(fs_ctx *c, fs_mac *u, int hold_surface, int iters, double eps, double *div_norm);
+
 /* Apply the pressure preconditioner selected in the parameters to one vector:
  * z = M^-1 r on the liquid cells (zero elsewhere). Jacobi: M = diag(L_p);
  * MIC(0): M = L L^T with the modified incomplete Cholesky factor of L_p (Bridson,

@@ -16,6 +16,8 @@
  *   - Sec. 3.4.2, Eq. (eq::optLoss): masked cosine + L2 loss on grid velocities.
  *   - Sec. 3.4.1, Fig. percnn_str_fit: a small 3D convolution network that maps a
  *     pressure right-hand side to a pressure (used as a PCG preconditioner).
+ *   - Sec. 3.3.3: the volumetric-velocity initialisation, a laminar wall-function
+ *     base profile and the constrained divergence projection of Eq. (eq::divProj).
  *
  * Readings where the paper is silent (each is restated where it is used):
  *   R1 split order: advect -> body force -> implicit viscosity -> projection, so

@@ -515,6 +515,30 @@ int fs_divergence(fs_ctx *c, const fs_mac *u, float *b_out)
     return FS_OK;
 }
 
+int fs_wall_profile(fs_ctx *c, const double dir[3], const float *vinf, double delta, fs_mac *u_out)
+{
+    int rc = need_mask(c);
+    if (rc) return rc;
+    if (!dir || !vinf) return set_error(FS_EINVAL, "dir / vinf is NULL");
+    if (!std::isfinite(dir[0]) || !std::isfinite(dir[1]) || !std::isfinite(dir[2]))
+        return set_error(FS_EINVAL, "dir must be finite");
+    if (!(delta >= 0.0) || !std::isfinite(delta)) return set_error(FS_EINVAL, "delta must be finite and >= 0");
+    if ((rc = check_field(u_out, "u_out", false))) return rc;
+    if ((rc = launch_wall_profile(c, dir, vinf, delta, f3(u_out)))) return rc;
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    return FS_OK;
+}
+
+int fs_pbd_project(fs_ctx *c, fs_mac *u, int hold_surface, int iters, double eps, double *div_norm)
+{
+    int rc = need_mask(c);
+    if (rc) return rc;
+    if ((rc = check_field(u, "u", false))) return rc;
+    if (iters < 0 || iters > 10000000) return set_error(FS_EINVAL, "iters must be in [0, 1e7]");
+    if (!(eps >= 0.0) || !std::isfinite(eps)) return set_error(FS_EINVAL, "eps must be finite and >= 0");
+    return launch_pbd_project(c, f3(u), hold_surface ? 1 : 0, iters, eps, div_norm);
+}
+
 int fs_net_param_count(void) { return net_param_count(); }
 
 int fs_net_load(fs_ctx *c, const float *params, int count, int params_on_host)

@@ -285,6 +285,9 @@ int launch_to_face_space(fs_ctx *c, CF3 in);             // full field (fluid) -
 int launch_nu_grad(fs_ctx *c, CF3 uv, double *dot);      // <vx, L~ uv>
 int launch_loss(fs_ctx *c, CF3 u, CF3 t, int kind, double alpha, double beta, F3 g,
                 double *loss);
+// fs_volume.cu
+int launch_wall_profile(fs_ctx *c, const double dir[3], const float *vinf, double delta, F3 u);
+int launch_pbd_project(fs_ctx *c, F3 u, int hold, int iters, double eps, double *norm);
 // fs_advect.cu
 int launch_advect(fs_ctx *c, CF3 u);                     // u -> vx (fluid faces)
 int launch_advect_adjoint(fs_ctx *c, CF3 u, F3 g);       // vx cotangent -> g (+=)

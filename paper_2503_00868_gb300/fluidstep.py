@@ -87,6 +87,9 @@ _SIGS = {
     "fs_profile_read": ([C.c_void_p, C.POINTER(fs_kernel_time), C.c_int, C.POINTER(C.c_int)], C.c_int),
     "fs_precond_apply": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "fs_divergence": ([C.c_void_p, C.POINTER(fs_mac), C.c_void_p], C.c_int),
+    "fs_wall_profile": ([C.c_void_p, C.POINTER(C.c_double), C.c_void_p, C.c_double, C.POINTER(fs_mac)], C.c_int),
+    "fs_pbd_project": ([C.c_void_p, C.POINTER(fs_mac), C.c_int, C.c_int, C.c_double, C.POINTER(C.c_double)],
+                       C.c_int),
     "fs_net_param_count": ([], C.c_int),
     "fs_net_load": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int], C.c_int),
     "fs_net_read": ([C.c_void_p, C.c_void_p, C.c_int], C.c_int),
@@ -246,6 +249,23 @@ def _cell(t: torch.Tensor) -> C.c_void_p:
 
 def fs_divergence(ctx: int, u: Mac, b_out: torch.Tensor) -> None:
     _check(load().fs_divergence(C.c_void_p(ctx), _ref(_mac(u)), _cell(b_out)), (FS_OK,))
+
+
+def fs_wall_profile(ctx: int, direction, vinf: torch.Tensor, delta: float, u_out: Mac) -> None:
+    """vinf: device float32 tensor of nz * nx column surface speeds ([k][i])."""
+    if vinf.dtype != torch.float32 or not vinf.is_cuda or not vinf.is_contiguous():
+        raise ValueError("vinf must be a contiguous float32 CUDA tensor")
+    d = (C.c_double * 3)(*[float(x) for x in direction])
+    _check(load().fs_wall_profile(C.c_void_p(ctx), d, C.c_void_p(vinf.data_ptr()), float(delta),
+                                  _ref(_mac(u_out))), (FS_OK,))
+
+
+def fs_pbd_project(ctx: int, u: Mac, hold_surface: bool = True, iters: int = 100, eps: float = 0.0) -> float:
+    """In place; returns |div u|_2 over the liquid after the last iteration."""
+    n = C.c_double(0.0)
+    _check(load().fs_pbd_project(C.c_void_p(ctx), _ref(_mac(u)), int(bool(hold_surface)), int(iters),
+                                 float(eps), C.byref(n)), (FS_OK,))
+    return n.value
 
 
 def fs_net_param_count() -> int:
