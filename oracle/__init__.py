@@ -48,7 +48,8 @@ class _Grid(C.Structure):
                 ("tol_p", C.c_double), ("tol_v", C.c_double),
                 ("maxit_p", C.c_int), ("maxit_v", C.c_int),
                 ("precond", C.c_int),
-                ("mic_tau", C.c_double), ("mic_sigma", C.c_double)]
+                ("mic_tau", C.c_double), ("mic_sigma", C.c_double),
+                ("percnn_w", C.POINTER(C.c_double)), ("percnn_k", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -94,6 +95,8 @@ def lib():
                 "or_net_loss_grad": [G, _D * 5, _D * 5, _D, _D, _D * 5, _D * 5],
                 "or_wall_profile": [G, _D, _D, C.c_double, _P3],
                 "or_pbd_project": [G, _P3, C.c_int, C.c_int, C.c_double],
+                "or_percnn_solve": [G, _D, C.c_int, _D, _D, C.POINTER(Stats)],
+                "or_percnn_loss_grad": [G, _D, C.c_int, _D, _D, _D],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -104,6 +107,7 @@ def lib():
             L.or_net_forward.restype = C.c_double
             L.or_net_loss_grad.restype = C.c_double
             L.or_pbd_project.restype = C.c_double
+            L.or_percnn_loss_grad.restype = C.c_double
             _lib = L
     return _lib
 
@@ -162,6 +166,9 @@ class Grid:
         s.maxit_p, s.maxit_v = self.maxit_p, self.maxit_v
         s.precond = self.precond
         s.mic_tau, s.mic_sigma = self.mic_tau, self.mic_sigma
+        pw = getattr(self, "percnn_w", None)
+        s.percnn_w = _ptr(pw) if pw is not None else _D()
+        s.percnn_k = int(getattr(self, "percnn_k", 0)) if pw is not None else 0
         self._keep = s
         return C.byref(s)
 
@@ -348,3 +355,25 @@ def pbd_project(g: Grid, u, hold_surface=True, iters=100, eps=0.0):
     u = [a.copy() for a in _field(g, u)]
     norm = lib().or_pbd_project(g.cstruct(), _p3(u), int(bool(hold_surface)), int(iters), float(eps))
     return u, norm
+
+
+def set_percnn(g: Grid, W, K: int):
+    """Make the grid's projection (project, step, adjoint_step) solve the pressure by
+    K recurrent sub-steps with the 27-tap kernel W (None: back to PCG)."""
+    g.percnn_w = None if W is None else _f64(np.asarray(W).ravel())
+    g.percnn_k = int(K)
+
+
+def percnn_solve(g: Grid, W, K, b):
+    p = np.zeros((g.nz, g.ny, g.nx))
+    st = Stats()
+    lib().or_percnn_solve(g.cstruct(), _ptr(_f64(np.asarray(W).ravel())), int(K), _ptr(_f64(b)), _ptr(p),
+                          C.byref(st))
+    return p, st.as_dict()
+
+
+def percnn_loss_grad(g: Grid, W, K, b, q):
+    dW = np.zeros(27)
+    loss = lib().or_percnn_loss_grad(g.cstruct(), _ptr(_f64(np.asarray(W).ravel())), int(K), _ptr(_f64(b)),
+                                     _ptr(_f64(q)), _ptr(dW))
+    return loss, dW

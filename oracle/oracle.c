@@ -60,6 +60,8 @@ typedef struct {
     int maxit_p, maxit_v;
     int precond;                /* pressure preconditioner: PC_NONE/JACOBI/MIC0 */
     double mic_tau, mic_sigma;
+    const double *percnn_w;     /* 27 taps [dz][dy][dx]; with percnn_k > 0 the projection */
+    int percnn_k;               /* solves the pressure by that many recurrent sub-steps */
 } or_grid;
 
 typedef struct {
@@ -746,13 +748,18 @@ void or_pcg(const or_grid *g, const double *b_in, double *x, int precond, or_sta
 
 /* Project u in place onto the discretely divergence-free fields: b = div RHS,
  * solve for q, subtract the pressure gradient. q_out (nullable) receives q. */
+void or_percnn_solve(const or_grid *g, const double *W, int K, const double *b, double *p, or_stats *st);
+
 void or_project(const or_grid *g, double *const u[3], double *q_out, or_stats *st)
 {
     long n = ncells(g);
     double *b = (double *)malloc((size_t)n * sizeof(double));
     double *q = (double *)calloc((size_t)n, sizeof(double));
     or_divergence(g, (const double *const *)u, b);
-    or_pcg(g, b, q, g->precond, st);
+    if (g->percnn_k > 0 && g->percnn_w)
+        or_percnn_solve(g, g->percnn_w, g->percnn_k, b, q, st);
+    else
+        or_pcg(g, b, q, g->precond, st);
     or_grad_subtract(g, q, u);
     if (q_out) memcpy(q_out, q, (size_t)n * sizeof(double));
     free(b);
@@ -1210,4 +1217,116 @@ double or_pbd_project(const or_grid *g, double *const u[3], int hold_surface, in
     }
     free(lam);
     return sqrt(norm2);
+}
+
+/* ------------------------------------------------------------------------ */
+/* recurrent convolutional pressure solver (Sec. 3.4.1, PeRCNN)              */
+/* ------------------------------------------------------------------------ */
+
+/* z = m (W * r): the 27-tap correlation of r with W (taps [dz][dy][dx], r zero off
+ * the liquid and outside the grid), kept on liquid cells (m) only. flip = 1 uses the
+ * point-reflected kernel W[26 - t], the transpose of the masked operator. */
+static void percnn_conv(const or_grid *g, const double *W, int flip, const double *r, double *z)
+{
+    for (int k = 0; k < g->nz; k++)
+        for (int j = 0; j < g->ny; j++)
+            for (int i = 0; i < g->nx; i++) {
+                long ci = cidx(g, i, j, k);
+                if (g->type[ci] != LIQUID) { z[ci] = 0.0; continue; }
+                double acc = 0.0;
+                for (int dz = -1; dz <= 1; dz++)
+                    for (int dy = -1; dy <= 1; dy++)
+                        for (int dxo = -1; dxo <= 1; dxo++) {
+                            if (cell_type(g, i + dxo, j + dy, k + dz) != LIQUID) continue;
+                            int t = (dz + 1) * 9 + (dy + 1) * 3 + (dxo + 1);
+                            acc += W[flip ? 26 - t : t] * r[cidx(g, i + dxo, j + dy, k + dz)];
+                        }
+                z[ci] = acc;
+            }
+}
+
+/* The pressure by K recurrent sub-steps (my reading of the PeRCNN layer of Sec.
+ * 3.4.1): the physics operator is the scheme's own 7-point L_p with the cell-type
+ * boundary conditions, the fitted part a 3x3x3 kernel W acting on the residual:
+ *   p_0 = 0,  r_k = b - L_p p_k,  p_{k+1} = p_k + m (W * r_k).
+ * Its fixed points solve L_p p = b. For a singular operator the liquid mean of the
+ * result is removed. st (nullable) gets K and |b - L_p p_K| / |b|. */
+void or_percnn_solve(const or_grid *g, const double *W, int K, const double *b, double *p, or_stats *st)
+{
+    long n = ncells(g);
+    double *r = (double *)malloc((size_t)n * sizeof(double));
+    double *z = (double *)malloc((size_t)n * sizeof(double));
+    for (long c = 0; c < n; c++) p[c] = 0.0;
+    for (int it = 0; it < K; it++) {
+        or_poisson_apply(g, p, r);
+        for (long c = 0; c < n; c++) r[c] = (g->type[c] == LIQUID) ? b[c] - r[c] : 0.0;
+        percnn_conv(g, W, 0, r, z);
+        for (long c = 0; c < n; c++) p[c] += z[c];
+    }
+    if (or_is_singular(g)) remove_liquid_mean(g, p);
+    if (st) {
+        or_poisson_apply(g, p, r);
+        double rr = 0.0, bb = 0.0;
+        for (long c = 0; c < n; c++)
+            if (g->type[c] == LIQUID) { rr += (b[c] - r[c]) * (b[c] - r[c]); bb += b[c] * b[c]; }
+        st->iters = K;
+        st->status = ST_OK;
+        st->relres = st->true_relres = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    }
+    free(r);
+    free(z);
+}
+
+/* Energy-norm fit loss of the recurrent solver on one pair L_p q = b:
+ *   e = p_K - q,  loss = e^T L_p e / q^T L_p q,
+ * and its gradient w.r.t. the 27 taps (added to dW) by the backward recurrence:
+ *   g_K = dloss/dp_K = 2 L_p e / (q^T L_p q);  for k = K-1 .. 0:
+ *   dW[t] += sum_i g_{k+1,i} m_i r_k(i + t);   g_k = g_{k+1} - L_p (m W^T * (m g_{k+1})).
+ * Stores every residual r_k. Returns the loss. */
+double or_percnn_loss_grad(const or_grid *g, const double *W, int K, const double *b, const double *q, double *dW)
+{
+    long n = ncells(g);
+    double *rs = (double *)malloc((size_t)n * (size_t)(K > 0 ? K : 1) * sizeof(double));
+    double *p = (double *)calloc((size_t)n, sizeof(double));
+    double *t1 = (double *)malloc((size_t)n * sizeof(double));
+    double *gk = (double *)malloc((size_t)n * sizeof(double));
+    for (int it = 0; it < K; it++) {
+        double *r = rs + (size_t)it * n;
+        or_poisson_apply(g, p, t1);
+        for (long c = 0; c < n; c++) r[c] = (g->type[c] == LIQUID) ? b[c] - t1[c] : 0.0;
+        percnn_conv(g, W, 0, r, t1);
+        for (long c = 0; c < n; c++) p[c] += t1[c];
+    }
+    /* loss and its gradient w.r.t. p_K */
+    double *e = (double *)malloc((size_t)n * sizeof(double));
+    double *Ae = (double *)malloc((size_t)n * sizeof(double));
+    for (long c = 0; c < n; c++) e[c] = (g->type[c] == LIQUID) ? p[c] - q[c] : 0.0;
+    or_poisson_apply(g, e, Ae);
+    or_poisson_apply(g, q, t1);
+    double num = 0.0, den = 0.0;
+    for (long c = 0; c < n; c++)
+        if (g->type[c] == LIQUID) { num += e[c] * Ae[c]; den += q[c] * t1[c]; }
+    double loss = den > 0.0 ? num / den : 0.0;
+    for (long c = 0; c < n; c++) gk[c] = den > 0.0 ? 2.0 * Ae[c] / den : 0.0;
+    for (int it = K - 1; it >= 0; it--) {
+        const double *r = rs + (size_t)it * n;
+        for (int k = 0; k < g->nz; k++)
+            for (int j = 0; j < g->ny; j++)
+                for (int i = 0; i < g->nx; i++) {
+                    long ci = cidx(g, i, j, k);
+                    if (g->type[ci] != LIQUID || gk[ci] == 0.0) continue;
+                    for (int dz = -1; dz <= 1; dz++)
+                        for (int dy = -1; dy <= 1; dy++)
+                            for (int dxo = -1; dxo <= 1; dxo++) {
+                                if (cell_type(g, i + dxo, j + dy, k + dz) != LIQUID) continue;
+                                int t = (dz + 1) * 9 + (dy + 1) * 3 + (dxo + 1);
+                                dW[t] += gk[ci] * r[cidx(g, i + dxo, j + dy, k + dz)];
+                            }
+                }
+        percnn_conv(g, W, 1, gk, t1);  /* m W^T * (m g) (gk is zero off the liquid) */
+        or_poisson_apply(g, t1, e);
+        for (long c = 0; c < n; c++) gk[c] = (g->type[c] == LIQUID) ? gk[c] - e[c] : 0.0;
+    }
+    free(rs); free(p); free(t1); free(gk); free(e); free(Ae);
+    return loss;
 }
