@@ -240,6 +240,24 @@ def precond_compare(n, seeds=(0,)):
             row[name] = {"ms": round(ts[-1], 3), "iters": st["iters_p"], "true_relres": st["true_relres_p"],
                          "fallbacks": st["fallbacks"], "restarts": st["restarts_p"], "status": rc}
             g.close()
+        # the recurrent convolutional solver with the shipped fitted kernel: a fixed
+        # 100 sub-steps, so its true residual is reported rather than reached
+        from paper_2503_00868_gb300 import train_percnn as TP
+        g = F.Grid(n, n, n, dx=1.0 / n, pressure_solver=F.FS_SOLVER_PERCNN)
+        g.set_mask(types)
+        F.fs_percnn_load(g.ctx, TP.default_kernel(), 100)
+        u0 = g.pack(W.random_mac(n, n, n, 500 + seed))
+        for rep in range(2):
+            u = F.Mac(*(t.clone() for t in u0))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            rc, st = g.project(u)
+            e1.record()
+            torch.cuda.synchronize()
+        row["percnn_k100"] = {"ms": round(e0.elapsed_time(e1), 3), "iters": st["iters_p"],
+                              "true_relres": st["true_relres_p"], "status": rc}
+        g.close()
         out["rows"].append(row)
     return out
 

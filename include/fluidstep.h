@@ -83,6 +83,11 @@ enum {
 };
 
 enum {
+    FS_SOLVER_PCG = 0,      /* preconditioned CG to tol_p (precond selects the preconditioner) */
+    FS_SOLVER_PERCNN = 1    /* K recurrent convolutional sub-steps (fs_percnn_load), Sec. 3.4.1 */
+};
+
+enum {
     FS_MASK_SURFACE = 0,   /* liquid cells with an air neighbour (the surface band) */
     FS_MASK_OCCUPIED = 1   /* every liquid cell */
 };
@@ -116,6 +121,10 @@ typedef struct {
                           smaller initial residual than q = 0; the stopping test is unchanged,
                           so only the iteration count differs. fs_set_mask and
                           fs_set_params reset the kept pressures. */
+    int pressure_solver;  /* FS_SOLVER_PCG (default) or FS_SOLVER_PERCNN: the pressure of every
+                             projection (fs_step, fs_project, fs_adjoint_step) by the recurrent
+                             convolutional solver; its map is symmetric, so the adjoint step
+                             applies the same projection to the cotangent */
 } fs_params;
 
 typedef struct {
@@ -241,6 +250,33 @@ int fs_wall_profile(fs_ctx *c, const double dir[3], const float *vinf, double de
  *   div_norm (HOST, nullable): |C|_2 over the liquid after the last iteration.
  * FS_EINVAL on bad arguments, FS_ENONFINITE if the divergence is not finite. */
 int fs_pbd_project(fs_ctx *c, fs_mac *u, int hold_surface, int iters, double eps, double *div_norm);
+
+/* Recurrent convolutional pressure solver (Sec. 3.4.1: the PeRCNN layer that
+ * replaces the implicit pressure solve during the optimisation). The scheme's own
+ * 7-point operator L_p with the cell-type boundary conditions is encoded; a fitted
+ * 3x3x3 kernel W acts on the residual, and `substeps` recurrent sub-steps emulate
+ * the iteration of an implicit solver:
+ *   p_0 = 0,  r_k = m (b - L_p p_k),  p_{k+1} = p_k + m (W * r_k),
+ * m the liquid mask, * the correlation over the 27 taps [dz][dy][dx] (neighbours
+ * off the liquid read 0). Fixed points solve L_p p = b. With
+ * fs_params.pressure_solver = FS_SOLVER_PERCNN every projection uses it; the
+ * statistics report K iterations and the true residual.
+ *   w27: HOST, 27 floats; stored point-symmetrised, (w[t] + w[26 - t]) / 2, which
+ *        makes the map b -> p_K symmetric (the adjoint step relies on it)
+ *   substeps: K in [1, 100000]. FS_EINVAL on a NULL or non-finite kernel. */
+int fs_percnn_load(fs_ctx *c, const float *w27, int substeps);
+
+/* The stored (symmetrised) kernel and K. w27: HOST, 27 floats. FS_ESTATE when none. */
+int fs_percnn_read(fs_ctx *c, float *w27, int *substeps);
+
+/* Fit of the kernel (Sec. 3.4.1: the recurrent solver should give the pressure of
+ * the second-order scheme on solver-generated pairs): for one pair L_p q = b
+ * (DEVICE public-layout cell arrays) ADDS the energy-norm loss
+ * (p_K - q)^T L_p (p_K - q) / q^T L_p q to *loss and its gradient w.r.t. the 27
+ * stored taps to dw27 (HOST, 27 floats), by the backward recurrence over the K
+ * stored residuals (K * cells floats of device memory). The gradient is w.r.t.
+ * the stored taps; a caller that fits the symmetric kernel symmetrises it. */
+int fs_percnn_grad(fs_ctx *c, const float *b, const float *q, double *loss, float *dw27);
 
 /* Apply the pressure preconditioner selected in the parameters to one vector:
  * z = M^-1 r on the liquid cells (zero elsewhere). Jacobi: M = diag(L_p);

@@ -50,6 +50,8 @@ static int check_params(const fs_params *p)
     if (!(p->mic_tau >= 0.0 && p->mic_tau <= 1.0)) return set_error(FS_EINVAL, "mic_tau must be in [0, 1]");
     if (!(p->mic_sigma >= 0.0 && p->mic_sigma < 1.0)) return set_error(FS_EINVAL, "mic_sigma must be in [0, 1)");
     if (p->warm_start != 0 && p->warm_start != 1) return set_error(FS_EINVAL, "warm_start must be 0 or 1");
+    if (p->pressure_solver != FS_SOLVER_PCG && p->pressure_solver != FS_SOLVER_PERCNN)
+        return set_error(FS_EINVAL, "unknown pressure solver %d", p->pressure_solver);
     return FS_OK;
 }
 
@@ -154,6 +156,7 @@ static void free_ctx(fs_ctx *c)
     prof_destroy(c);
     net_free(c);
     fcg_release(c);
+    percnn_free(c);
     void *ptrs[] = {c->cflag, c->fflag, c->bc, c->dsum, c->pb, c->pr, c->pp[0], c->pp[1], c->pq, c->px, c->pz,
                     c->vx, c->vr, c->vp[0], c->vp[1], c->vq, c->fu[0], c->fu[1], c->fu[2], c->fg[0], c->fg[1],
                     c->fg[2], c->gc[0], c->gc[1], c->gc[2], c->mic_prec, c->scal, c->partials, c->err_word, c->pw[0], c->pw[1],
@@ -190,6 +193,7 @@ void fs_default_params(fs_params *p)
     p->mic_tau = 0.97;
     p->mic_sigma = 0.25;
     p->warm_start = 0;
+    p->pressure_solver = FS_SOLVER_PCG;
 }
 
 const char *fs_last_error(void) { return g_err; }
@@ -537,6 +541,26 @@ int fs_pbd_project(fs_ctx *c, fs_mac *u, int hold_surface, int iters, double eps
     if (iters < 0 || iters > 10000000) return set_error(FS_EINVAL, "iters must be in [0, 1e7]");
     if (!(eps >= 0.0) || !std::isfinite(eps)) return set_error(FS_EINVAL, "eps must be finite and >= 0");
     return launch_pbd_project(c, f3(u), hold_surface ? 1 : 0, iters, eps, div_norm);
+}
+
+int fs_percnn_load(fs_ctx *c, const float *w27, int substeps)
+{
+    if (!c) return set_error(FS_EINVAL, "NULL context");
+    return percnn_load(c, w27, substeps);
+}
+
+int fs_percnn_read(fs_ctx *c, float *w27, int *substeps)
+{
+    if (!c || !w27) return set_error(FS_EINVAL, "NULL argument");
+    return percnn_read(c, w27, substeps);
+}
+
+int fs_percnn_grad(fs_ctx *c, const float *b, const float *q, double *loss, float *dw27)
+{
+    int rc = need_mask(c);
+    if (rc) return rc;
+    if (!b || !q || !loss || !dw27) return set_error(FS_EINVAL, "NULL argument");
+    return percnn_grad(c, b, q, loss, dw27);
 }
 
 int fs_net_param_count(void) { return net_param_count(); }

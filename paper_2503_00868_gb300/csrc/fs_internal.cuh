@@ -140,6 +140,7 @@ struct fs_ctx {
     // (fs_fcg.cu), allocated on first use
     void *net;
     void *fcg;
+    void *percnn;         // recurrent convolutional pressure solver (fs_percnn.cu)
 
     // reductions
     fs::SolveScal *scal;        // device [4]: 0 pressure, 1 viscosity, 2 misc, 3 misc
@@ -319,6 +320,13 @@ int remove_null_mode(fs_ctx *c, float *z);
 int solve_pressure_fcg(fs_ctx *c, SolveScal *h, bool warm);
 int pressure_restart(fs_ctx *c);  // fs_pcg.cu: r = b - A x, p = 0 (scalars of slot 0)
 void fcg_release(fs_ctx *c);
+// fs_percnn.cu: recurrent convolutional pressure solver, pb -> px
+int percnn_load(fs_ctx *c, const float *w27, int K);
+int percnn_read(fs_ctx *c, float *w27, int *K);
+bool percnn_loaded(const fs_ctx *c);
+void percnn_free(fs_ctx *c);
+int solve_pressure_percnn(fs_ctx *c, SolveScal *h);
+int percnn_grad(fs_ctx *c, const float *b, const float *q, double *loss, float *dw_host);
 
 // ---- per-kernel timing -------------------------------------------------------
 enum KernelId : int {

@@ -746,6 +746,13 @@ static int pcg_iterate(fs_ctx *c, SolveScal &h, bool warm)
 
 static int solve_pressure_once(fs_ctx *c, fs_stats *st)
 {
+    if (c->prm.pressure_solver == FS_SOLVER_PERCNN) {
+        // K recurrent sub-steps: no convergence test, the true residual is reported
+        SolveScal h;
+        int rc = solve_pressure_percnn(c, &h);
+        if (rc) return rc;
+        return pressure_tail(c, h, st);
+    }
     const bool learned = c->prm.precond == FS_PRECOND_LEARNED;
     if (learned && !net_loaded(c))
         return set_error(FS_ESTATE, "the learned preconditioner has no network loaded");

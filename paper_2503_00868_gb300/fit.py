@@ -45,10 +45,17 @@ def river_scene(nx: int, ny: int, nz: int, seed: int, inflow_speed: float = 0.5,
 
 
 def make_grid(nx: int, ny: int, nz: int, types, bc, precond: str = "jacobi", nu: float = 1e-2,
-              weights: Optional[np.ndarray] = None, **kw) -> F.Grid:
+              weights: Optional[np.ndarray] = None, percnn_kernel: Optional[np.ndarray] = None,
+              percnn_k: int = 100, **kw) -> F.Grid:
+    """A grid for the scene. With `percnn_kernel` every projection solves the
+    pressure by `percnn_k` recurrent sub-steps of that kernel (Sec. 3.4.1)
+    instead of PCG."""
+    solver = F.FS_SOLVER_PERCNN if percnn_kernel is not None else F.FS_SOLVER_PCG
     g = F.Grid(nx, ny, nz, dx=1.0 / ny, dt=1.0 / 30.0, nu=nu, g=(0.0, -9.81, 0.0), precond=PRECONDS[precond],
-               **kw)
+               pressure_solver=solver, **kw)
     g.set_mask(types, g.pack(bc))
+    if percnn_kernel is not None:
+        F.fs_percnn_load(g.ctx, percnn_kernel, percnn_k)
     if precond == "learned":
         if weights is None:
             from .train_precond import default_weights
@@ -97,6 +104,31 @@ def fit(grid: F.Grid, u_base: F.Mac, targets: Dict[int, F.Mac], frames: int, ite
     return {"nu": float(torch.exp(theta).detach()), "delta": [d.detach() for d in delta], "history": history}
 
 
+def compare_pressure_solvers(nx: int = 64, ny: int = 48, nz: int = 64, frames: int = 12, iters: int = 30,
+                             K: int = 100, seed: int = 0) -> dict:
+    """The optimisation with the pressure from the fitted recurrent solver, from K
+    Jacobi-like sub-steps (the same recurrence from its starting kernel) and from
+    PCG to 1e-6, against targets made with PCG (the analogue of the paper's
+    comparison of PeRCNN with Jacobi iterations in the optimisation): the loss
+    after each update and the fitted nu."""
+    from .train_percnn import default_kernel, jacobi_kernel
+    types, bc, info = river_scene(nx, ny, nz, seed)
+    ref = make_grid(nx, ny, nz, types, bc, "jacobi", tol_p=1e-6, maxit_p=20000)
+    u_base = ref.pack(bc)
+    d = W.blurred_noise_mac(nx, ny, nz, seed + 7)
+    sc = 0.05 / max(float(np.std(np.concatenate([x.ravel() for x in d]))), 1e-12)
+    targets = synthetic_targets(ref, u_base, ref.pack([x * sc for x in d]), 1e-2, frames)
+    out = {"grid": [nx, ny, nz], "frames": frames, "iters": iters, "K": K, "runs": {}}
+    for name, kern in (("pcg", None), ("percnn_fitted", default_kernel()), ("jacobi_substeps", jacobi_kernel())):
+        g = ref if kern is None else make_grid(nx, ny, nz, types, bc, "jacobi", percnn_kernel=kern, percnn_k=K)
+        t0 = time.time()
+        res = fit(g, u_base, targets, frames, iters, 1e-3)
+        torch.cuda.synchronize()
+        out["runs"][name] = {"loss": [round(h[0], 6) for h in res["history"]], "nu_fit": res["nu"],
+                             "s_per_iter": (time.time() - t0) / iters}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--nx", type=int, default=192)
@@ -109,8 +141,13 @@ def main():
     ap.add_argument("--nu-true", type=float, default=1e-2)
     ap.add_argument("--nu0", type=float, default=1e-3)
     ap.add_argument("--delta-sigma", type=float, default=0.05, help="std of the true correction, m/s")
+    ap.add_argument("--compare-pressure-solvers", action="store_true",
+                    help="run the PCG / fitted recurrent solver / Jacobi sub-step comparison instead")
     a = ap.parse_args()
     torch.cuda.set_device(0)
+    if a.compare_pressure_solvers:
+        print(json.dumps(compare_pressure_solvers(seed=a.seed)), flush=True)
+        return
     types, bc, info = river_scene(a.nx, a.ny, a.nz, a.seed)
     grid = make_grid(a.nx, a.ny, a.nz, types, bc, a.precond, maxit_p=20000)
     u_base = grid.pack(bc)
@@ -139,3 +176,4 @@ def main():
 
 if __name__ == "__main__":
     main()
+

@@ -27,6 +27,7 @@ STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_ENOMEM", 3: "FS_ECUDA", 4: "F
 FS_AIR, FS_LIQUID, FS_SOLID = 0, 1, 2
 FS_PRECOND_JACOBI, FS_PRECOND_MIC0, FS_PRECOND_LEARNED = 0, 1, 2
 FS_MASK_SURFACE, FS_MASK_OCCUPIED = 0, 1
+FS_SOLVER_PCG, FS_SOLVER_PERCNN = 0, 1
 SOFT_STATUS = (FS_OK, FS_ENOCONV)
 
 
@@ -41,7 +42,7 @@ class fs_params(C.Structure):
                 ("g", C.c_double * 3), ("precond", C.c_int), ("maxit_p", C.c_int), ("maxit_v", C.c_int),
                 ("tol_p", C.c_double), ("tol_v", C.c_double), ("check_every", C.c_int),
                 ("spin_limit", C.c_int), ("mic_tau", C.c_double), ("mic_sigma", C.c_double),
-                ("warm_start", C.c_int)]
+                ("warm_start", C.c_int), ("pressure_solver", C.c_int)]
 
 
 class fs_stats(C.Structure):
@@ -87,6 +88,10 @@ _SIGS = {
     "fs_profile_read": ([C.c_void_p, C.POINTER(fs_kernel_time), C.c_int, C.POINTER(C.c_int)], C.c_int),
     "fs_precond_apply": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "fs_divergence": ([C.c_void_p, C.POINTER(fs_mac), C.c_void_p], C.c_int),
+    "fs_percnn_load": ([C.c_void_p, C.POINTER(C.c_float), C.c_int], C.c_int),
+    "fs_percnn_read": ([C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_int)], C.c_int),
+    "fs_percnn_grad": ([C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_float)],
+                       C.c_int),
     "fs_wall_profile": ([C.c_void_p, C.POINTER(C.c_double), C.c_void_p, C.c_double, C.POINTER(fs_mac)], C.c_int),
     "fs_pbd_project": ([C.c_void_p, C.POINTER(fs_mac), C.c_int, C.c_int, C.c_double, C.POINTER(C.c_double)],
                        C.c_int),
@@ -249,6 +254,30 @@ def _cell(t: torch.Tensor) -> C.c_void_p:
 
 def fs_divergence(ctx: int, u: Mac, b_out: torch.Tensor) -> None:
     _check(load().fs_divergence(C.c_void_p(ctx), _ref(_mac(u)), _cell(b_out)), (FS_OK,))
+
+
+def fs_percnn_load(ctx: int, w27, substeps: int) -> None:
+    w = np.ascontiguousarray(np.asarray(w27, dtype=np.float32).ravel())
+    if w.size != 27:
+        raise ValueError("the recurrent-solver kernel has 27 taps")
+    _check(load().fs_percnn_load(C.c_void_p(ctx), w.ctypes.data_as(C.POINTER(C.c_float)), int(substeps)),
+           (FS_OK,))
+
+
+def fs_percnn_read(ctx: int):
+    w = np.zeros(27, np.float32)
+    k = C.c_int(0)
+    _check(load().fs_percnn_read(C.c_void_p(ctx), w.ctypes.data_as(C.POINTER(C.c_float)), C.byref(k)), (FS_OK,))
+    return w, k.value
+
+
+def fs_percnn_grad(ctx: int, b: torch.Tensor, q: torch.Tensor):
+    """(loss, dloss/dW over the 27 stored taps) for one pair L_p q = b."""
+    loss = C.c_double(0.0)
+    dw = np.zeros(27, np.float32)
+    _check(load().fs_percnn_grad(C.c_void_p(ctx), _cell(b), _cell(q), C.byref(loss),
+                                 dw.ctypes.data_as(C.POINTER(C.c_float))), (FS_OK,))
+    return loss.value, dw
 
 
 def fs_wall_profile(ctx: int, direction, vinf: torch.Tensor, delta: float, u_out: Mac) -> None:
