@@ -96,6 +96,8 @@ def lib():
                 "or_wall_profile": [G, _D, _D, C.c_double, _P3],
                 "or_pbd_project": [G, _P3, C.c_int, C.c_int, C.c_double],
                 "or_percnn_solve": [G, _D, C.c_int, _D, _D, C.POINTER(Stats)],
+                "or_p2g": [G, C.c_int, _D, _D, _D, _D, _P3, C.c_void_p],
+                "or_g2p": [G, C.c_int, _D, _D, _D, _D, _D, _D, _P3, C.c_double, C.c_int, C.c_double, C.c_double],
                 "or_percnn_loss_grad": [G, _D, C.c_int, _D, _D, _D],
             }
             for name, args in sig.items():
@@ -377,3 +379,29 @@ def percnn_loss_grad(g: Grid, W, K, b, q):
     loss = lib().or_percnn_loss_grad(g.cstruct(), _ptr(_f64(np.asarray(W).ravel())), int(K), _ptr(_f64(b)),
                                      _ptr(_f64(q)), _ptr(dW))
     return loss, dW
+
+
+def p2g(g: Grid, x, v, Cp, m, return_mass=False):
+    """APIC particle -> MAC grid (Eq. eq::particle_map). x, v: (np, 3); Cp: (np, 3, 3); m: (np,)."""
+    x, v, Cp, m = _f64(x), _f64(v), _f64(Cp), _f64(m)
+    n = x.shape[0]
+    u = g.zeros()
+    mass = g.zeros()
+    mp = _P3(*[_ptr(a) for a in mass])
+    lib().or_p2g(g.cstruct(), n, _ptr(x), _ptr(v), _ptr(Cp), _ptr(m), _p3(u), C.cast(C.pointer(mp), C.c_void_p))
+    return (u, mass) if return_mass else u
+
+
+def g2p(g: Grid, x, u, F=None, A0=None, dt=0.0, advance=False, lo=0.0, hi=1e30):
+    """MAC grid -> particles: returns (x, v, C, F, A) after the optional advance."""
+    x = _f64(x).copy()
+    n = x.shape[0]
+    v = np.zeros((n, 3))
+    Cm = np.zeros((n, 3, 3))
+    Fm = None if F is None else _f64(F).copy()
+    A = None if A0 is None else np.zeros((n, 3, 3))
+    u = _field(g, u)
+    lib().or_g2p(g.cstruct(), n, _ptr(x), _ptr(v), _ptr(Cm), _ptr(Fm) if Fm is not None else _D(),
+                 _ptr(_f64(A0)) if A0 is not None else _D(), _ptr(A) if A is not None else _D(), _p3(u),
+                 float(dt), int(bool(advance)), float(lo), float(hi))
+    return x, v, Cm, Fm, A

@@ -18,6 +18,10 @@
  *     pressure right-hand side to a pressure (used as a PCG preconditioner).
  *   - Sec. 3.3.3: the volumetric-velocity initialisation, a laminar wall-function
  *     base profile and the constrained divergence projection of Eq. (eq::divProj).
+ *   - Sec. 3.4.1: the recurrent convolutional (PeRCNN) pressure solver.
+ *   - Sec. 3.2.2, Sec. 3.4.3: APIC transfers (Eq. eq::particle_map, the G2P and C
+ *     update) per MAC face component, particle advection, and the deformation
+ *     gradient and covariance update of the Gaussians.
  *
  * Readings where the paper is silent (each is restated where it is used):
  *   R1 split order: advect -> body force -> implicit viscosity -> projection, so
@@ -1329,4 +1333,136 @@ double or_percnn_loss_grad(const or_grid *g, const double *W, int K, const doubl
     }
     free(rs); free(p); free(t1); free(gk); free(e); free(Ae);
     return loss;
+}
+
+/* ------------------------------------------------------------------------ */
+/* APIC transfers and Gaussian deformation (Sec. 3.2.2, Sec. 3.4.3)          */
+/* ------------------------------------------------------------------------ */
+
+/* Quadratic B-spline weights of the 3 nodes base, base+1, base+2 of one axis for a
+ * particle at continuous node coordinate s (nodes at integers): base = floor(s - 1/2),
+ * f = s - base in [1/2, 3/2). Returns base. */
+static int bspline2(double s, double w[3])
+{
+    int base = (int)floor(s - 0.5);
+    double f = s - base;
+    w[0] = 0.5 * (1.5 - f) * (1.5 - f);
+    w[1] = 0.75 - (f - 1.0) * (f - 1.0);
+    w[2] = 0.5 * (f - 0.5) * (f - 0.5);
+    return base;
+}
+
+/* Continuous node coordinate of position x along `axis` for face component c: the
+ * nodes of component c sit at index * dx along axis c and (index + 1/2) * dx along
+ * the others. */
+static double node_coord(const or_grid *g, int c, int axis, double x)
+{
+    return x / g->dx - (axis == c ? 0.0 : 0.5);
+}
+
+/* P2G (Eq. eq::particle_map) per face component c on the MAC grid:
+ *   (m v)_i = sum_p w_ip m_p [v_p,c + (C_p (x_i - x_p))_c],  v_i = (m v)_i / sum_p w_ip m_p,
+ * w_ip the product of quadratic B-spline weights, nodes outside the face arrays
+ * skipped, v_i = 0 where no particle contributes. x, v: [p][3]; C: [p][3][3]
+ * (row c = gradient of component c); m: [p]. mass (nullable) gets sum_p w_ip m_p. */
+void or_p2g(const or_grid *g, int np, const double *x, const double *v, const double *C, const double *m,
+            double *const u[3], double *const mass[3])
+{
+    for (int c = 0; c < 3; c++) {
+        int d[3];
+        face_dims(g, c, d);
+        long nf = (long)d[0] * d[1] * d[2];
+        double *mv = (double *)calloc((size_t)nf, sizeof(double));
+        double *ms = (double *)calloc((size_t)nf, sizeof(double));
+        for (int p = 0; p < np; p++) {
+            double w[3][3];
+            int base[3];
+            for (int a = 0; a < 3; a++) base[a] = bspline2(node_coord(g, c, a, x[3 * p + a]), w[a]);
+            for (int kz = 0; kz < 3; kz++)
+                for (int ky = 0; ky < 3; ky++)
+                    for (int kx = 0; kx < 3; kx++) {
+                        int i = base[0] + kx, j = base[1] + ky, k = base[2] + kz;
+                        if (i < 0 || j < 0 || k < 0 || i >= d[0] || j >= d[1] || k >= d[2]) continue;
+                        double wt = w[0][kx] * w[1][ky] * w[2][kz] * m[p];
+                        double xi[3] = {(i + (c == 0 ? 0.0 : 0.5)) * g->dx, (j + (c == 1 ? 0.0 : 0.5)) * g->dx,
+                                        (k + (c == 2 ? 0.0 : 0.5)) * g->dx};
+                        double aff = 0.0;
+                        for (int a = 0; a < 3; a++) aff += C[9 * p + 3 * c + a] * (xi[a] - x[3 * p + a]);
+                        long f = fidx(d, i, j, k);
+                        mv[f] += wt * (v[3 * p + c] + aff);
+                        ms[f] += wt;
+                    }
+        }
+        for (long f = 0; f < nf; f++) {
+            u[c][f] = ms[f] > 0.0 ? mv[f] / ms[f] : 0.0;
+            if (mass && mass[c]) mass[c][f] = ms[f];
+        }
+        free(mv);
+        free(ms);
+    }
+}
+
+/* G2P and the particle update (Sec. 3.2.2, Sec. 3.4.3), per particle:
+ *   v_p,c = sum_i w_ip u_c,i ;  C_p[c][a] = 4/dx^2 sum_i w_ip u_c,i (x_i - x_p)_a
+ * (nodes outside the face arrays contribute nothing), then when `advance`:
+ *   x_p += dt v_p (clamped to [lo, hi] per axis),  F_p = (I + dt C_p) F_p,
+ *   A_p = F_p A0_p F_p^T  (F, A0, A nullable; [p][3][3]). */
+void or_g2p(const or_grid *g, int np, double *x, double *v, double *C, double *F, const double *A0, double *A,
+            const double *const u[3], double dt, int advance, double lo, double hi)
+{
+    for (int p = 0; p < np; p++) {
+        double xp[3] = {x[3 * p], x[3 * p + 1], x[3 * p + 2]};
+        for (int c = 0; c < 3; c++) {
+            int d[3];
+            face_dims(g, c, d);
+            double w[3][3];
+            int base[3];
+            for (int a = 0; a < 3; a++) base[a] = bspline2(node_coord(g, c, a, xp[a]), w[a]);
+            double vc = 0.0, cc[3] = {0.0, 0.0, 0.0};
+            for (int kz = 0; kz < 3; kz++)
+                for (int ky = 0; ky < 3; ky++)
+                    for (int kx = 0; kx < 3; kx++) {
+                        int i = base[0] + kx, j = base[1] + ky, k = base[2] + kz;
+                        if (i < 0 || j < 0 || k < 0 || i >= d[0] || j >= d[1] || k >= d[2]) continue;
+                        double wt = w[0][kx] * w[1][ky] * w[2][kz];
+                        double uv = u[c][fidx(d, i, j, k)];
+                        double xi[3] = {(i + (c == 0 ? 0.0 : 0.5)) * g->dx, (j + (c == 1 ? 0.0 : 0.5)) * g->dx,
+                                        (k + (c == 2 ? 0.0 : 0.5)) * g->dx};
+                        vc += wt * uv;
+                        for (int a = 0; a < 3; a++) cc[a] += wt * uv * (xi[a] - xp[a]);
+                    }
+            v[3 * p + c] = vc;
+            for (int a = 0; a < 3; a++) C[9 * p + 3 * c + a] = 4.0 / (g->dx * g->dx) * cc[a];
+        }
+        if (!advance) continue;
+        for (int a = 0; a < 3; a++) {
+            double nx = xp[a] + dt * v[3 * p + a];
+            x[3 * p + a] = nx < lo ? lo : (nx > hi ? hi : nx);
+        }
+        if (F) {
+            double Fn[9];
+            for (int r = 0; r < 3; r++)
+                for (int s = 0; s < 3; s++) {
+                    double acc = F[9 * p + 3 * r + s];
+                    for (int t = 0; t < 3; t++) acc += dt * C[9 * p + 3 * r + t] * F[9 * p + 3 * t + s];
+                    Fn[3 * r + s] = acc;
+                }
+            memcpy(F + 9 * p, Fn, sizeof(Fn));
+            if (A0 && A) {
+                double T[9];
+                for (int r = 0; r < 3; r++)
+                    for (int s = 0; s < 3; s++) {
+                        double acc = 0.0;
+                        for (int t = 0; t < 3; t++) acc += Fn[3 * r + t] * A0[9 * p + 3 * t + s];
+                        T[3 * r + s] = acc;
+                    }
+                for (int r = 0; r < 3; r++)
+                    for (int s = 0; s < 3; s++) {
+                        double acc = 0.0;
+                        for (int t = 0; t < 3; t++) acc += T[3 * r + t] * Fn[3 * s + t];
+                        A[9 * p + 3 * r + s] = acc;
+                    }
+            }
+        }
+    }
 }
