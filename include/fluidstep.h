@@ -251,6 +251,30 @@ int fs_wall_profile(fs_ctx *c, const double dir[3], const float *vinf, double de
  * FS_EINVAL on bad arguments, FS_ENONFINITE if the divergence is not finite. */
 int fs_pbd_project(fs_ctx *c, fs_mac *u, int hold_surface, int iters, double eps, double *div_norm);
 
+/* APIC particle -> grid transfer (Sec. 3.2.2, Eq. eq::particle_map), per MAC face
+ * component c with quadratic B-spline weights w_ip over 3 x 3 x 3 nodes (the nodes
+ * of component c sit at index * dx along axis c and (index + 1/2) * dx along the
+ * others):  (m v)_i = sum_p w_ip m_p [v_p,c + (C_p (x_i - x_p))_c],
+ *           u_c,i = (m v)_i / sum_p w_ip m_p, 0 where no particle reaches.
+ * Does not depend on the mask. np >= 0 particles, all DEVICE arrays:
+ *   x, v: [np][3] metres and m/s; C: [np][3][3] row-major (row c = gradient of
+ *   component c); m: [np]; u_out: overwritten; mass_out (nullable): sum_p w_ip m_p.
+ * FP32 atomic accumulation: the last bits depend on the scheduling.
+ * FS_EINVAL on a NULL array or np < 0. */
+int fs_p2g(fs_ctx *c, int np, const float *x, const float *v, const float *C, const float *m, fs_mac *u_out,
+           fs_mac *mass_out);
+
+/* APIC grid -> particle transfer and particle update (Sec. 3.2.2, Sec. 3.4.3):
+ *   v_p,c = sum_i w_ip u_c,i,   C_p[c][a] = 4/dx^2 sum_i w_ip u_c,i (x_i - x_p)_a,
+ * then when advance != 0: x_p += dt v_p clamped to [lo, hi] per axis,
+ * F_p = (I + dt C_p) F_p (when F != NULL) and A_p = F_p A0_p F_p^T (when A0 and
+ * A_out != NULL), the deformation and covariance of the Gaussians. All DEVICE:
+ *   x [np][3] (updated when advancing), v_out [np][3], C_out [np][3][3],
+ *   F [np][3][3] in/out, A0, A_out [np][3][3]; u the grid field.
+ * FS_EINVAL on a NULL required array, np < 0 or non-finite dt, lo, hi. */
+int fs_g2p(fs_ctx *c, int np, float *x, float *v_out, float *C_out, float *F, const float *A0, float *A_out,
+           const fs_mac *u, double dt, int advance, double lo, double hi);
+
 /* Recurrent convolutional pressure solver (Sec. 3.4.1: the PeRCNN layer that
  * replaces the implicit pressure solve during the optimisation). The scheme's own
  * 7-point operator L_p with the cell-type boundary conditions is encoded; a fitted

@@ -543,6 +543,37 @@ int fs_pbd_project(fs_ctx *c, fs_mac *u, int hold_surface, int iters, double eps
     return launch_pbd_project(c, f3(u), hold_surface ? 1 : 0, iters, eps, div_norm);
 }
 
+int fs_p2g(fs_ctx *c, int np, const float *x, const float *v, const float *C, const float *m, fs_mac *u_out,
+           fs_mac *mass_out)
+{
+    if (!c) return set_error(FS_EINVAL, "NULL context");
+    g_err[0] = 0;
+    if (np < 0) return set_error(FS_EINVAL, "np must be >= 0");
+    if (np > 0 && (!x || !v || !C || !m)) return set_error(FS_EINVAL, "particle array is NULL");
+    int rc;
+    if ((rc = check_field(u_out, "u_out", false)) || (rc = check_field(mass_out, "mass_out", true))) return rc;
+    F3 mass{{nullptr, nullptr, nullptr}};
+    if (mass_out) mass = f3(mass_out);
+    if ((rc = launch_p2g(c, np, x, v, C, m, f3(u_out), mass))) return rc;
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    return FS_OK;
+}
+
+int fs_g2p(fs_ctx *c, int np, float *x, float *v_out, float *C_out, float *F, const float *A0, float *A_out,
+           const fs_mac *u, double dt, int advance, double lo, double hi)
+{
+    if (!c) return set_error(FS_EINVAL, "NULL context");
+    g_err[0] = 0;
+    if (np < 0) return set_error(FS_EINVAL, "np must be >= 0");
+    if (np > 0 && (!x || !v_out || !C_out)) return set_error(FS_EINVAL, "particle array is NULL");
+    if (!std::isfinite(dt) || !std::isfinite(lo) || !std::isfinite(hi)) return set_error(FS_EINVAL, "dt, lo, hi must be finite");
+    int rc;
+    if ((rc = check_field(u, "u", false))) return rc;
+    if ((rc = launch_g2p(c, np, x, v_out, C_out, F, A0, A_out, cf3(u), dt, advance, lo, hi))) return rc;
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    return FS_OK;
+}
+
 int fs_percnn_load(fs_ctx *c, const float *w27, int substeps)
 {
     if (!c) return set_error(FS_EINVAL, "NULL context");

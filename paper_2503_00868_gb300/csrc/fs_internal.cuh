@@ -286,6 +286,10 @@ int launch_to_face_space(fs_ctx *c, CF3 in);             // full field (fluid) -
 int launch_nu_grad(fs_ctx *c, CF3 uv, double *dot);      // <vx, L~ uv>
 int launch_loss(fs_ctx *c, CF3 u, CF3 t, int kind, double alpha, double beta, F3 g,
                 double *loss);
+// fs_apic.cu
+int launch_p2g(fs_ctx *c, int np, const float *x, const float *v, const float *C, const float *m, F3 u, F3 mass);
+int launch_g2p(fs_ctx *c, int np, float *x, float *v, float *C, float *F, const float *A0, float *A, CF3 u,
+               double dt, int advance, double lo, double hi);
 // fs_volume.cu
 int launch_wall_profile(fs_ctx *c, const double dir[3], const float *vinf, double delta, F3 u);
 int launch_pbd_project(fs_ctx *c, F3 u, int hold, int iters, double eps, double *norm);

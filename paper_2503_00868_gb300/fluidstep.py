@@ -88,6 +88,10 @@ _SIGS = {
     "fs_profile_read": ([C.c_void_p, C.POINTER(fs_kernel_time), C.c_int, C.POINTER(C.c_int)], C.c_int),
     "fs_precond_apply": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "fs_divergence": ([C.c_void_p, C.POINTER(fs_mac), C.c_void_p], C.c_int),
+    "fs_p2g": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(fs_mac),
+                C.POINTER(fs_mac)], C.c_int),
+    "fs_g2p": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                C.POINTER(fs_mac), C.c_double, C.c_int, C.c_double, C.c_double], C.c_int),
     "fs_percnn_load": ([C.c_void_p, C.POINTER(C.c_float), C.c_int], C.c_int),
     "fs_percnn_read": ([C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_int)], C.c_int),
     "fs_percnn_grad": ([C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_float)],
@@ -254,6 +258,31 @@ def _cell(t: torch.Tensor) -> C.c_void_p:
 
 def fs_divergence(ctx: int, u: Mac, b_out: torch.Tensor) -> None:
     _check(load().fs_divergence(C.c_void_p(ctx), _ref(_mac(u)), _cell(b_out)), (FS_OK,))
+
+
+def _parts(t: Optional[torch.Tensor], cols: int):
+    if t is None:
+        return None
+    if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or t.shape[-1] != cols:
+        raise ValueError(f"particle arrays must be contiguous float32 CUDA tensors with {cols} columns")
+    return C.c_void_p(t.data_ptr())
+
+
+def fs_p2g(ctx: int, x: torch.Tensor, v: torch.Tensor, Cp: torch.Tensor, m: torch.Tensor, u_out: Mac,
+           mass_out: Optional[Mac] = None) -> None:
+    """x, v: (np, 3); Cp: (np, 9) (row-major 3x3); m: (np, 1) or (np,) -- float32 CUDA."""
+    npart = x.shape[0]
+    _check(load().fs_p2g(C.c_void_p(ctx), int(npart), _parts(x, 3), _parts(v, 3), _parts(Cp, 9),
+                         _parts(m.reshape(-1, 1), 1), _ref(_mac(u_out)), _ref(_mac(mass_out))), (FS_OK,))
+
+
+def fs_g2p(ctx: int, x: torch.Tensor, v_out: torch.Tensor, C_out: torch.Tensor, u: Mac,
+           F: Optional[torch.Tensor] = None, A0: Optional[torch.Tensor] = None, A_out: Optional[torch.Tensor] = None,
+           dt: float = 0.0, advance: bool = False, lo: float = 0.0, hi: float = 1e30) -> None:
+    npart = x.shape[0]
+    _check(load().fs_g2p(C.c_void_p(ctx), int(npart), _parts(x, 3), _parts(v_out, 3), _parts(C_out, 9),
+                         _parts(F, 9), _parts(A0, 9), _parts(A_out, 9), _ref(_mac(u)), float(dt), int(bool(advance)),
+                         float(lo), float(hi)), (FS_OK,))
 
 
 def fs_percnn_load(ctx: int, w27, substeps: int) -> None:
