@@ -97,6 +97,7 @@ def lib():
                 "or_pbd_project": [G, _P3, C.c_int, C.c_int, C.c_double],
                 "or_percnn_solve": [G, _D, C.c_int, _D, _D, C.POINTER(Stats)],
                 "or_p2g": [G, C.c_int, _D, _D, _D, _D, _P3, C.c_void_p],
+                "or_splat_render": [C.c_int, _D, _D, _D, _D, C.c_void_p, _D, _D],
                 "or_g2p": [G, C.c_int, _D, _D, _D, _D, _D, _D, _P3, C.c_double, C.c_int, C.c_double, C.c_double],
                 "or_percnn_loss_grad": [G, _D, C.c_int, _D, _D, _D],
             }
@@ -405,3 +406,33 @@ def g2p(g: Grid, x, u, F=None, A0=None, dt=0.0, advance=False, lo=0.0, hi=1e30):
                  _ptr(_f64(A0)) if A0 is not None else _D(), _ptr(A) if A is not None else _D(), _p3(u),
                  float(dt), int(bool(advance)), float(lo), float(hi))
     return x, v, Cm, Fm, A
+
+
+class Camera(C.Structure):
+    """Pinhole camera of the splatting renderer: x_c = R x + t; pixels (fx, fy, cx, cy)."""
+    _fields_ = [("R", C.c_double * 9), ("t", C.c_double * 3), ("fx", C.c_double), ("fy", C.c_double),
+                ("cx", C.c_double), ("cy", C.c_double), ("width", C.c_int), ("height", C.c_int),
+                ("znear", C.c_double), ("bg", C.c_double * 3)]
+
+
+def make_camera(R, t, fx, fy, cx, cy, width, height, znear=0.01, bg=(0.0, 0.0, 0.0)):
+    cam = Camera()
+    for k in range(9):
+        cam.R[k] = float(np.asarray(R, float).ravel()[k])
+    for k in range(3):
+        cam.t[k] = float(t[k])
+        cam.bg[k] = float(bg[k])
+    cam.fx, cam.fy, cam.cx, cam.cy = float(fx), float(fy), float(cx), float(cy)
+    cam.width, cam.height, cam.znear = int(width), int(height), float(znear)
+    return cam
+
+
+def splat_render(x, opacity, A, color, cam):
+    """Front-to-back splatting (Sec. 3.2.1); returns rgb (h, w, 3) and transmittance (h, w)."""
+    x, o, A, c = _f64(x), _f64(opacity), _f64(A), _f64(color)
+    n = x.shape[0]
+    rgb = np.zeros((cam.height, cam.width, 3))
+    T = np.zeros((cam.height, cam.width))
+    lib().or_splat_render(n, _ptr(x), _ptr(o), _ptr(A), _ptr(c), C.cast(C.pointer(cam), C.c_void_p), _ptr(rgb),
+                          _ptr(T))
+    return rgb, T

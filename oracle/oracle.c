@@ -22,6 +22,7 @@
  *   - Sec. 3.2.2, Sec. 3.4.3: APIC transfers (Eq. eq::particle_map, the G2P and C
  *     update) per MAC face component, particle advection, and the deformation
  *     gradient and covariance update of the Gaussians.
+ *   - Sec. 3.2.1, Sec. 3.5: front-to-back splatting of the Gaussians into an image.
  *
  * Readings where the paper is silent (each is restated where it is used):
  *   R1 split order: advect -> body force -> implicit viscosity -> projection, so
@@ -1465,4 +1466,109 @@ void or_g2p(const or_grid *g, int np, double *x, double *v, double *C, double *F
             }
         }
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gaussian splatting forward rendering (Sec. 3.2.1, Sec. 3.5)               */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double R[9], t[3];          /* world -> camera: x_c = R x + t */
+    double fx, fy, cx, cy;      /* pinhole intrinsics (pixels) */
+    int width, height;
+    double znear;
+    double bg[3];
+} or_camera;
+
+/* Projection of one Gaussian: camera-space depth, pixel-space mean and the inverse
+ * of the 2D covariance J R A R^T J^T (J the Jacobian of the pinhole projection at
+ * the mean). Returns 0 when the Gaussian is culled (behind znear, degenerate). */
+static int splat_project(const or_camera *cam, const double x[3], const double A[9], double *depth,
+                         double mean[2], double conic[3])
+{
+    double xc[3];
+    for (int r = 0; r < 3; r++) xc[r] = cam->R[3 * r] * x[0] + cam->R[3 * r + 1] * x[1] + cam->R[3 * r + 2] * x[2] + cam->t[r];
+    if (!(xc[2] > cam->znear)) return 0;
+    double z = xc[2];
+    mean[0] = cam->fx * xc[0] / z + cam->cx;
+    mean[1] = cam->fy * xc[1] / z + cam->cy;
+    double J[6] = {cam->fx / z, 0.0, -cam->fx * xc[0] / (z * z), 0.0, cam->fy / z, -cam->fy * xc[1] / (z * z)};
+    double M[6]; /* J R */
+    for (int r = 0; r < 2; r++)
+        for (int c = 0; c < 3; c++)
+            M[3 * r + c] = J[3 * r] * cam->R[c] + J[3 * r + 1] * cam->R[3 + c] + J[3 * r + 2] * cam->R[6 + c];
+    double S[4] = {0, 0, 0, 0};
+    for (int r = 0; r < 2; r++)
+        for (int s = 0; s < 2; s++) {
+            double acc = 0.0;
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) acc += M[3 * r + a] * A[3 * a + b] * M[3 * s + b];
+            S[2 * r + s] = acc;
+        }
+    double det = S[0] * S[3] - S[1] * S[2];
+    if (!(det > 0.0)) return 0;
+    conic[0] = S[3] / det;
+    conic[1] = -S[1] / det;
+    conic[2] = S[0] / det;
+    *depth = z;
+    return 1;
+}
+
+typedef struct {
+    double depth;
+    int idx;
+} splat_key;
+
+static int splat_key_cmp(const void *a, const void *b)
+{
+    const splat_key *p = (const splat_key *)a, *q = (const splat_key *)b;
+    if (p->depth < q->depth) return -1;
+    if (p->depth > q->depth) return 1;
+    return p->idx - q->idx;
+}
+
+/* Front-to-back compositing of the splatting formula of Sec. 3.2.1 at every pixel
+ * centre (px + 1/2, py + 1/2):  C = sum_i alpha_i c_i prod_{j<i} (1 - alpha_j) + T bg,
+ * over the Gaussians in increasing depth (ties by index), with
+ * alpha_i = min(0.99, sigma_i exp(-d^T Sigma_i^-1 d / 2)), d the offset of the pixel
+ * centre from the projected mean, kept only inside the 3-sigma ellipse
+ * (d^T Sigma^-1 d <= 9) and when alpha >= 1/255; the walk stops once the
+ * transmittance T would fall below 1e-4. Colours are degree-0 spherical harmonics
+ * (RGB). x [n][3], opacity [n], A [n][3][3], color [n][3]; rgb [h][w][3], T [h][w]. */
+void or_splat_render(int n, const double *x, const double *opacity, const double *A, const double *color,
+                     const or_camera *cam, double *rgb, double *T_out)
+{
+    double *depth = (double *)malloc((size_t)n * sizeof(double));
+    double *mean = (double *)malloc((size_t)n * 2 * sizeof(double));
+    double *conic = (double *)malloc((size_t)n * 3 * sizeof(double));
+    int *ok = (int *)malloc((size_t)n * sizeof(int));
+    splat_key *keys = (splat_key *)malloc((size_t)(n > 0 ? n : 1) * sizeof(splat_key));
+    int m = 0;
+    for (int i = 0; i < n; i++) {
+        ok[i] = splat_project(cam, x + 3 * i, A + 9 * i, depth + i, mean + 2 * i, conic + 3 * i);
+        if (ok[i]) { keys[m].depth = depth[i]; keys[m].idx = i; m++; }
+    }
+    qsort(keys, (size_t)m, sizeof(splat_key), splat_key_cmp);
+    for (int py = 0; py < cam->height; py++)
+        for (int px = 0; px < cam->width; px++) {
+            double T = 1.0, c[3] = {0.0, 0.0, 0.0};
+            double pu = px + 0.5, pv = py + 0.5;
+            for (int q = 0; q < m; q++) {
+                int i = keys[q].idx;
+                double dx = pu - mean[2 * i], dy = pv - mean[2 * i + 1];
+                double md = conic[3 * i] * dx * dx + 2.0 * conic[3 * i + 1] * dx * dy + conic[3 * i + 2] * dy * dy;
+                if (md > 9.0) continue;
+                double alpha = opacity[i] * exp(-0.5 * md);
+                if (alpha > 0.99) alpha = 0.99;
+                if (alpha < 1.0 / 255.0) continue;
+                double Tn = T * (1.0 - alpha);
+                if (Tn < 1e-4) break;
+                for (int k = 0; k < 3; k++) c[k] += alpha * T * color[3 * i + k];
+                T = Tn;
+            }
+            long o = (long)py * cam->width + px;
+            for (int k = 0; k < 3; k++) rgb[3 * o + k] = c[k] + T * cam->bg[k];
+            if (T_out) T_out[o] = T;
+        }
+    free(depth); free(mean); free(conic); free(ok); free(keys);
 }
