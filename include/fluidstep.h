@@ -251,6 +251,34 @@ int fs_wall_profile(fs_ctx *c, const double dir[3], const float *vinf, double de
  * FS_EINVAL on bad arguments, FS_ENONFINITE if the divergence is not finite. */
 int fs_pbd_project(fs_ctx *c, fs_mac *u, int hold_surface, int iters, double eps, double *div_norm);
 
+/* Pinhole camera of the splatting renderer: x_c = R x + t (R row-major), pixel
+ * u = fx x_c / z_c + cx, v = fy y_c / z_c + cy; pixel (px, py) has its centre at
+ * (px + 1/2, py + 1/2). Gaussians with z_c <= znear are culled. */
+typedef struct {
+    double R[9], t[3];
+    double fx, fy, cx, cy;
+    int width, height;     /* pixels, each in [1, 16384] */
+    double znear;          /* > 0 */
+    double bg[3];          /* background colour */
+} fs_camera;
+
+/* Forward splatting of n Gaussians into an RGB image (Sec. 3.2.1 compositing
+ * formula, Sec. 3.5 rendering by splatting), into device buffers (headless):
+ *   C = sum_i alpha_i c_i prod_{j<i} (1 - alpha_j) + T bg over the Gaussians in
+ *   increasing depth (ties by index); alpha_i = min(0.99, sigma_i exp(-d^T S^-1 d / 2))
+ *   with S = J R A_i R^T J^T the projected covariance (J the pinhole Jacobian at the
+ *   mean) and d the pixel centre's offset from the projected mean, kept inside the
+ *   3-sigma ellipse and when alpha >= 1/255; the walk stops once the transmittance
+ *   would fall below 1e-4. Colours are degree-0 spherical harmonics (RGB).
+ *   x [n][3], opacity [n] in [0, 1], A [n][3][3] covariances, color [n][3]: DEVICE;
+ *   cam: HOST; rgb_out [height][width][3], T_out (nullable) [height][width]: DEVICE.
+ * A must be symmetric positive definite. Does not need a mask. Synchronises the
+ * stream once (the number of tile entries sizes a scratch buffer). FS_EINVAL on bad
+ * arguments or more than 2^32 (Gaussian, 16 x 16 tile) pairs, FS_ENOMEM when the
+ * scratch cannot grow. */
+int fs_splat_render(fs_ctx *c, int n, const float *x, const float *opacity, const float *A, const float *color,
+                    const fs_camera *cam, float *rgb_out, float *T_out);
+
 /* APIC particle -> grid transfer (Sec. 3.2.2, Eq. eq::particle_map), per MAC face
  * component c with quadratic B-spline weights w_ip over 3 x 3 x 3 nodes (the nodes
  * of component c sit at index * dx along axis c and (index + 1/2) * dx along the

@@ -157,6 +157,7 @@ static void free_ctx(fs_ctx *c)
     net_free(c);
     fcg_release(c);
     percnn_free(c);
+    splat_free(c);
     void *ptrs[] = {c->cflag, c->fflag, c->bc, c->dsum, c->pb, c->pr, c->pp[0], c->pp[1], c->pq, c->px, c->pz,
                     c->vx, c->vr, c->vp[0], c->vp[1], c->vq, c->fu[0], c->fu[1], c->fu[2], c->fg[0], c->fg[1],
                     c->fg[2], c->gc[0], c->gc[1], c->gc[2], c->mic_prec, c->scal, c->partials, c->err_word, c->pw[0], c->pw[1],
@@ -541,6 +542,25 @@ int fs_pbd_project(fs_ctx *c, fs_mac *u, int hold_surface, int iters, double eps
     if (iters < 0 || iters > 10000000) return set_error(FS_EINVAL, "iters must be in [0, 1e7]");
     if (!(eps >= 0.0) || !std::isfinite(eps)) return set_error(FS_EINVAL, "eps must be finite and >= 0");
     return launch_pbd_project(c, f3(u), hold_surface ? 1 : 0, iters, eps, div_norm);
+}
+
+int fs_splat_render(fs_ctx *c, int n, const float *x, const float *opacity, const float *A, const float *color,
+                    const fs_camera *cam, float *rgb_out, float *T_out)
+{
+    if (!c) return set_error(FS_EINVAL, "NULL context");
+    g_err[0] = 0;
+    if (n < 0) return set_error(FS_EINVAL, "n must be >= 0");
+    if (n > 0 && (!x || !opacity || !A || !color)) return set_error(FS_EINVAL, "Gaussian array is NULL");
+    if (!cam || !rgb_out) return set_error(FS_EINVAL, "cam / rgb_out is NULL");
+    if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384)
+        return set_error(FS_EINVAL, "image size must be in [1, 16384]");
+    const double *vals[] = {cam->R, cam->t, &cam->fx, &cam->fy, &cam->cx, &cam->cy, &cam->znear, cam->bg};
+    const int cnt[] = {9, 3, 1, 1, 1, 1, 1, 3};
+    for (int a = 0; a < 8; a++)
+        for (int k = 0; k < cnt[a]; k++)
+            if (!std::isfinite(vals[a][k])) return set_error(FS_EINVAL, "camera parameters must be finite");
+    if (!(cam->znear > 0.0)) return set_error(FS_EINVAL, "znear must be > 0");
+    return splat_render(c, n, x, opacity, A, color, cam, rgb_out, T_out);
 }
 
 int fs_p2g(fs_ctx *c, int np, const float *x, const float *v, const float *C, const float *m, fs_mac *u_out,

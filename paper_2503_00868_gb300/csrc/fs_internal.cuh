@@ -141,6 +141,7 @@ struct fs_ctx {
     void *net;
     void *fcg;
     void *percnn;         // recurrent convolutional pressure solver (fs_percnn.cu)
+    void *splat;          // splatting scratch (fs_splat.cu)
 
     // reductions
     fs::SolveScal *scal;        // device [4]: 0 pressure, 1 viscosity, 2 misc, 3 misc
@@ -286,6 +287,10 @@ int launch_to_face_space(fs_ctx *c, CF3 in);             // full field (fluid) -
 int launch_nu_grad(fs_ctx *c, CF3 uv, double *dot);      // <vx, L~ uv>
 int launch_loss(fs_ctx *c, CF3 u, CF3 t, int kind, double alpha, double beta, F3 g,
                 double *loss);
+// fs_splat.cu
+int splat_render(fs_ctx *c, int n, const float *x, const float *op, const float *A, const float *col,
+                 const fs_camera *cam, float *rgb, float *T);
+void splat_free(fs_ctx *c);
 // fs_apic.cu
 int launch_p2g(fs_ctx *c, int np, const float *x, const float *v, const float *C, const float *m, F3 u, F3 mass);
 int launch_g2p(fs_ctx *c, int np, float *x, float *v, float *C, float *F, const float *A0, float *A, CF3 u,

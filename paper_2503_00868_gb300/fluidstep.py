@@ -88,6 +88,8 @@ _SIGS = {
     "fs_profile_read": ([C.c_void_p, C.POINTER(fs_kernel_time), C.c_int, C.POINTER(C.c_int)], C.c_int),
     "fs_precond_apply": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "fs_divergence": ([C.c_void_p, C.POINTER(fs_mac), C.c_void_p], C.c_int),
+    "fs_splat_render": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                         C.c_void_p, C.c_void_p], C.c_int),
     "fs_p2g": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(fs_mac),
                 C.POINTER(fs_mac)], C.c_int),
     "fs_g2p": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -258,6 +260,43 @@ def _cell(t: torch.Tensor) -> C.c_void_p:
 
 def fs_divergence(ctx: int, u: Mac, b_out: torch.Tensor) -> None:
     _check(load().fs_divergence(C.c_void_p(ctx), _ref(_mac(u)), _cell(b_out)), (FS_OK,))
+
+
+class fs_camera(C.Structure):
+    _fields_ = [("R", C.c_double * 9), ("t", C.c_double * 3), ("fx", C.c_double), ("fy", C.c_double),
+                ("cx", C.c_double), ("cy", C.c_double), ("width", C.c_int), ("height", C.c_int),
+                ("znear", C.c_double), ("bg", C.c_double * 3)]
+
+
+def make_camera(R, t, fx, fy, cx, cy, width, height, znear=0.01, bg=(0.0, 0.0, 0.0)) -> fs_camera:
+    cam = fs_camera()
+    for k in range(9):
+        cam.R[k] = float(np.asarray(R, float).ravel()[k])
+    for k in range(3):
+        cam.t[k] = float(t[k])
+        cam.bg[k] = float(bg[k])
+    cam.fx, cam.fy, cam.cx, cam.cy = float(fx), float(fy), float(cx), float(cy)
+    cam.width, cam.height, cam.znear = int(width), int(height), float(znear)
+    return cam
+
+
+def fs_splat_render(ctx: int, x: torch.Tensor, opacity: torch.Tensor, A: torch.Tensor, color: torch.Tensor,
+                    cam: fs_camera, rgb_out: torch.Tensor, T_out: Optional[torch.Tensor] = None) -> None:
+    """x (n, 3), opacity (n,), A (n, 9), color (n, 3): float32 CUDA; rgb_out (h, w, 3), T_out (h, w)."""
+    n = x.shape[0]
+    for t, cols in ((x, 3), (A, 9), (color, 3), (opacity.reshape(-1, 1), 1)):
+        _parts(t, cols)
+        if t.shape[0] != n:
+            raise ValueError("x, opacity, A and color must have the same number of rows")
+    if T_out is not None and (T_out.shape != (cam.height, cam.width) or T_out.dtype != torch.float32
+                              or not T_out.is_cuda):
+        raise ValueError("T_out must be a float32 CUDA tensor of shape (height, width)")
+    if rgb_out.shape != (cam.height, cam.width, 3) or rgb_out.dtype != torch.float32 or not rgb_out.is_cuda:
+        raise ValueError("rgb_out must be a float32 CUDA tensor of shape (height, width, 3)")
+    _check(load().fs_splat_render(C.c_void_p(ctx), int(n), C.c_void_p(x.data_ptr()),
+                                  C.c_void_p(opacity.data_ptr()), C.c_void_p(A.data_ptr()),
+                                  C.c_void_p(color.data_ptr()), C.byref(cam), C.c_void_p(rgb_out.data_ptr()),
+                                  C.c_void_p(T_out.data_ptr()) if T_out is not None else None), (FS_OK,))
 
 
 def _parts(t: Optional[torch.Tensor], cols: int):

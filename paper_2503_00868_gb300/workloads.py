@@ -19,6 +19,13 @@ so these recipes stand in for them:
   and uniformly drawn centres, redrawn until the occupancy lies in [0.15, 0.50].
 * ``random_mac``: unblurred N(0, 1) per MAC component (a strongly divergent
   right-hand side for the projection).
+* ``gaussian_cloud``: Gaussians standing in for the generated and filled 3DGS
+  assets (Sec. 3.3.1 fills the liquid with Gaussians at grid centres), one per
+  liquid cell at a jittered position, covariance Q diag(s^2) Q^T with Q a random
+  rotation and s ~ U[0.3, 0.9] dx per axis, opacity ~ U[0.3, 0.95] and
+  degree-0 colour ~ U[0, 1]^3.
+* ``look_at``: a pinhole camera on a sphere around a target (world y up), as
+  (R, t, fx, fy, cx, cy) with x_c = R x + t and the vertical field of view given.
 
 Array conventions (dense, C order, x fastest):
     cell arrays            shape (nz, ny, nx)
@@ -148,3 +155,40 @@ def river_with_blob(nx: int, ny: int, nz: int, seed: int, depth: float = 0.25):
 def weighted_band_target(nx: int, ny: int, nz: int, seed: int, scale: float = 1.0):
     """Independent smooth target field (seed offset by 100 from the initial field)."""
     return blurred_noise_mac(nx, ny, nz, seed + 100, scale=scale)
+
+
+def gaussian_cloud(types: np.ndarray, dx: float, seed: int, jitter: float = 0.5):
+    """(x (n, 3), opacity (n,), A (n, 3, 3), color (n, 3)) in float64, one Gaussian
+    per liquid cell of `types` (nz, ny, nx)."""
+    rng = np.random.default_rng(seed)
+    k, j, i = np.nonzero(types == LIQUID)
+    n = k.size
+    x = (np.stack([i, j, k], axis=1) + 0.5 + jitter * (rng.random((n, 3)) - 0.5)) * dx
+    q = rng.standard_normal((n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    w, a, b, c = q.T
+    Q = np.stack([1 - 2 * (b * b + c * c), 2 * (a * b - w * c), 2 * (a * c + w * b),
+                  2 * (a * b + w * c), 1 - 2 * (a * a + c * c), 2 * (b * c - w * a),
+                  2 * (a * c - w * b), 2 * (b * c + w * a), 1 - 2 * (a * a + b * b)], axis=1).reshape(n, 3, 3)
+    sc = rng.uniform(0.3, 0.9, (n, 3)) * dx
+    A = np.einsum("nij,nj,nkj->nik", Q, sc * sc, Q)
+    opacity = rng.uniform(0.3, 0.95, n)
+    color = rng.random((n, 3))
+    return x, opacity, A, color
+
+
+def look_at(target, radius: float, azimuth: float, elevation: float, width: int, height: int,
+            fov_y: float = 0.8):
+    """(R, t, fx, fy, cx, cy) of a camera at `radius` from `target`, looking at it;
+    angles in radians, image y pointing down."""
+    target = np.asarray(target, float)
+    eye = target + radius * np.array([np.cos(elevation) * np.sin(azimuth), np.sin(elevation),
+                                      np.cos(elevation) * np.cos(azimuth)])
+    fwd = (target - eye) / np.linalg.norm(target - eye)
+    right = np.cross(fwd, [0.0, 1.0, 0.0])
+    right /= np.linalg.norm(right)
+    down = np.cross(fwd, right)
+    R = np.stack([right, down, fwd])
+    t = -R @ eye
+    f = 0.5 * height / np.tan(0.5 * fov_y)
+    return R, t, f, f, 0.5 * width, 0.5 * height
