@@ -279,6 +279,12 @@ typedef struct {
 int fs_splat_render(fs_ctx *c, int n, const float *x, const float *opacity, const float *A, const float *color,
                     const fs_camera *cam, float *rgb_out, float *T_out);
 
+/* Counters of the last fs_splat_render on this context, as host values (no GPU
+ * work): entries = the number of (Gaussian, tile) pairs binned, max_tile = the
+ * most Gaussians binned into one 16 x 16 tile. Both 0 before the first render.
+ * FS_EINVAL on a NULL argument. */
+int fs_splat_stats(const fs_ctx *c, unsigned long long *entries, unsigned long long *max_tile);
+
 /* APIC particle -> grid transfer (Sec. 3.2.2, Eq. eq::particle_map), per MAC face
  * component c with quadratic B-spline weights w_ip over 3 x 3 x 3 nodes (the nodes
  * of component c sit at index * dx along axis c and (index + 1/2) * dx along the

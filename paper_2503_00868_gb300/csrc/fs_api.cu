@@ -563,6 +563,13 @@ int fs_splat_render(fs_ctx *c, int n, const float *x, const float *opacity, cons
     return splat_render(c, n, x, opacity, A, color, cam, rgb_out, T_out);
 }
 
+int fs_splat_stats(const fs_ctx *c, unsigned long long *entries, unsigned long long *max_tile)
+{
+    if (!c || !entries || !max_tile) return set_error(FS_EINVAL, "NULL argument");
+    splat_stats(c, entries, max_tile);
+    return FS_OK;
+}
+
 int fs_p2g(fs_ctx *c, int np, const float *x, const float *v, const float *C, const float *m, fs_mac *u_out,
            fs_mac *mass_out)
 {

@@ -291,6 +291,7 @@ int launch_loss(fs_ctx *c, CF3 u, CF3 t, int kind, double alpha, double beta, F3
 int splat_render(fs_ctx *c, int n, const float *x, const float *op, const float *A, const float *col,
                  const fs_camera *cam, float *rgb, float *T);
 void splat_free(fs_ctx *c);
+void splat_stats(const fs_ctx *c, unsigned long long *entries, unsigned long long *max_tile);
 // fs_apic.cu
 int launch_p2g(fs_ctx *c, int np, const float *x, const float *v, const float *C, const float *m, F3 u, F3 mass);
 int launch_g2p(fs_ctx *c, int np, float *x, float *v, float *C, float *F, const float *A0, float *A, CF3 u,

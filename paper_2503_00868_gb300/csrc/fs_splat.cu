@@ -44,6 +44,7 @@ struct SplatState {
     int cap_t = 0;
     unsigned long long *keys = nullptr, *keys2 = nullptr;
     long long cap_k = 0, cap_k2 = 0;
+    unsigned long long last_entries = 0, last_max = 0;  // counters of the last render
 };
 
 namespace {
@@ -59,18 +60,54 @@ struct Cam {
     float bg[3];
 };
 
-__global__ void k_sp_project(int n, const float *__restrict__ x, const float *__restrict__ op,
-                             const float *__restrict__ A, const float *__restrict__ col, Cam cam,
-                             SplatRecord *rec, int4 *rect, float *depth, unsigned *tcount, int ntx, int nty)
+// Block-local table of tiles (open addressing, linear probing, no deletion): the
+// (Gaussian, tile) pairs of a block's 256 Gaussians, which are usually neighbours
+// in space and share tiles, are counted in shared memory and reach the global
+// per-tile counters with one atomic per distinct tile. A tile that finds no slot
+// within SP_PROBE probes goes to the global counter directly; since slots are
+// never freed, a later lookup of that tile fails the same way.
+constexpr int SP_HT = 1024;
+constexpr int SP_PROBE = 16;
+constexpr unsigned SP_EMPTY = 0xffffffffu;
+
+__device__ __forceinline__ int ht_slot(unsigned *hk, unsigned t, bool insert)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned h = (t * 2654435761u) >> 22;
+    for (int p = 0; p < SP_PROBE; p++) {
+        const unsigned sl = (h + p) & (SP_HT - 1);
+        unsigned cur = hk[sl];
+        if (cur == t) return (int)sl;
+        if (cur == SP_EMPTY) {
+            if (!insert) return -1;
+            cur = atomicCAS(hk + sl, SP_EMPTY, t);
+            if (cur == SP_EMPTY || cur == t) return (int)sl;
+        }
+    }
+    return -1;
+}
+
+__global__ void __launch_bounds__(256) k_sp_project(int n, const float *__restrict__ x,
+                                                    const float *__restrict__ op, const float *__restrict__ A,
+                                                    const float *__restrict__ col, Cam cam, SplatRecord *rec,
+                                                    int4 *rect, float *depth, unsigned *tcount, int ntx, int nty)
+{
+    __shared__ unsigned hk[SP_HT], hc[SP_HT];
+    for (int base = blockIdx.x * 256; base < n; base += gridDim.x * 256) {  // uniform over the block
+        for (int e = threadIdx.x; e < SP_HT; e += 256) {
+            hk[e] = SP_EMPTY;
+            hc[e] = 0;
+        }
+        __syncthreads();
+        const int i = base + threadIdx.x;
         int4 rc = make_int4(0, 0, 0, 0);
         float xc[3];
+        const int ii = min(i, n - 1);  // rows past n: read a valid row, record nothing
 #pragma unroll
         for (int r = 0; r < 3; r++)
-            xc[r] = cam.R[3 * r] * x[3 * i] + cam.R[3 * r + 1] * x[3 * i + 1] + cam.R[3 * r + 2] * x[3 * i + 2] + cam.t[r];
+            xc[r] = cam.R[3 * r] * x[3 * ii] + cam.R[3 * r + 1] * x[3 * ii + 1] + cam.R[3 * r + 2] * x[3 * ii + 2] +
+                    cam.t[r];
         const float z = xc[2];
-        if (z > cam.znear) {
+        if (i < n && z > cam.znear) {
             const float mx = cam.fx * xc[0] / z + cam.cx, my = cam.fy * xc[1] / z + cam.cy;
             const float J[6] = {cam.fx / z, 0.f, -cam.fx * xc[0] / (z * z), 0.f, cam.fy / z, -cam.fy * xc[1] / (z * z)};
             float M[6];
@@ -117,9 +154,20 @@ __global__ void k_sp_project(int n, const float *__restrict__ x, const float *__
                 }
             }
         }
-        rect[i] = rc;
+        if (i < n) rect[i] = rc;
         for (int ty = rc.z; ty < rc.w; ty++)
-            for (int tx = rc.x; tx < rc.y; tx++) atomicAdd(tcount + ty * ntx + tx, 1u);
+            for (int tx = rc.x; tx < rc.y; tx++) {
+                const unsigned t = (unsigned)(ty * ntx + tx);
+                const int sl = ht_slot(hk, t, true);
+                if (sl >= 0)
+                    atomicAdd(hc + sl, 1u);
+                else
+                    atomicAdd(tcount + t, 1u);
+            }
+        __syncthreads();
+        for (int e = threadIdx.x; e < SP_HT; e += 256)
+            if (hk[e] != SP_EMPTY) atomicAdd(tcount + hk[e], hc[e]);
+        __syncthreads();
     }
 }
 
@@ -160,28 +208,63 @@ __global__ void __launch_bounds__(1024) k_sp_scan(const unsigned *__restrict__ c
     if (threadIdx.x == 0) total[1] = pmax[0];
 }
 
-__global__ void k_sp_fill(int n, const int4 *__restrict__ rect, const float *__restrict__ depth,
-                          const unsigned *__restrict__ off, unsigned *fill, unsigned long long *keys, int ntx)
+// Writes each (Gaussian, tile) key into its tile's segment. Pass 1 counts a
+// block's pairs per tile in the shared table (pairs without a slot take a global
+// position at once); one global atomic per table slot then reserves a contiguous
+// range of the segment; pass 2 walks the pairs again and places them in the range.
+__global__ void __launch_bounds__(256) k_sp_fill(int n, const int4 *__restrict__ rect,
+                                                 const float *__restrict__ depth,
+                                                 const unsigned *__restrict__ off, unsigned *fill,
+                                                 unsigned long long *keys, int ntx)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int4 rc = rect[i];
-        if (rc.x >= rc.y) continue;
-        const unsigned long long key = ((unsigned long long)__float_as_uint(depth[i]) << 32) | (unsigned)i;
+    __shared__ unsigned hk[SP_HT], hc[SP_HT], hb[SP_HT];
+    for (int base = blockIdx.x * 256; base < n; base += gridDim.x * 256) {  // uniform over the block
+        for (int e = threadIdx.x; e < SP_HT; e += 256) {
+            hk[e] = SP_EMPTY;
+            hc[e] = 0;
+        }
+        __syncthreads();
+        const int i = base + threadIdx.x;
+        const int4 rc = i < n ? rect[i] : make_int4(0, 0, 0, 0);
+        const unsigned long long key =
+            i < n ? ((unsigned long long)__float_as_uint(depth[i]) << 32) | (unsigned)i : 0ull;
         for (int ty = rc.z; ty < rc.w; ty++)
             for (int tx = rc.x; tx < rc.y; tx++) {
-                const int t = ty * ntx + tx;
-                const unsigned pos = atomicAdd(fill + t, 1u);
-                keys[off[t] + pos] = key;
+                const unsigned t = (unsigned)(ty * ntx + tx);
+                const int sl = ht_slot(hk, t, true);
+                if (sl >= 0) {
+                    atomicAdd(hc + sl, 1u);
+                } else {
+                    const unsigned pos = atomicAdd(fill + t, 1u);
+                    keys[off[t] + pos] = key;
+                }
             }
+        __syncthreads();
+        for (int e = threadIdx.x; e < SP_HT; e += 256)
+            if (hk[e] != SP_EMPTY) {
+                hb[e] = off[hk[e]] + atomicAdd(fill + hk[e], hc[e]);
+                hc[e] = 0;
+            }
+        __syncthreads();
+        for (int ty = rc.z; ty < rc.w; ty++)
+            for (int tx = rc.x; tx < rc.y; tx++) {
+                const int sl = ht_slot(hk, (unsigned)(ty * ntx + tx), false);
+                if (sl >= 0) keys[hb[sl] + atomicAdd(hc + sl, 1u)] = key;
+            }
+        __syncthreads();
     }
 }
 
 // Stable LSD radix sort (8-bit digits) of each tile segment longer than SP_CAP,
 // one block of 256 threads per tile. Digits 0-3 are the Gaussian index (those
 // above the largest index are skipped), 4-7 the depth bits; a digit that all keys
-// share is skipped too. Per round of 256 keys, a key's rank among the warp's keys
-// with the same digit comes from __match_any_sync and the warps are ordered by a
+// share is skipped too. A round takes 2048 keys, warp w the 256 consecutive keys
+// [w * 256, w * 256 + 256) as BS_IT slots of 32; slot by slot, a key's rank among
+// the warp's keys with the same digit is the warp's running count of that digit
+// plus its rank within the slot (__match_any_sync), and the warps are ordered by a
 // per-digit prefix, so equal digits keep their order. The result ends in `keys`.
+constexpr int BS_IT = 8;
+
 __global__ void __launch_bounds__(256) k_sp_bigsort(unsigned long long *keys, unsigned long long *tmp,
                                                     const unsigned *__restrict__ off,
                                                     const unsigned *__restrict__ cnt, int idx_digits)
@@ -217,14 +300,24 @@ __global__ void __launch_bounds__(256) k_sp_bigsort(unsigned long long *keys, un
         for (int w = 0; w < warp; w++) wpre += wsum[w];
         hist[tid] = wpre + incl - v;
         __syncthreads();
-        for (unsigned r0 = 0; r0 < n; r0 += 256) {
-            const unsigned e = r0 + tid;
-            const bool valid = e < n;
-            const unsigned long long k = valid ? src[e] : 0ull;
-            const unsigned d = valid ? ((unsigned)(k >> shift) & 255u) : 256u;
-            const unsigned mask = __match_any_sync(0xffffffffu, d);
-            const unsigned rank = __popc(mask & ((1u << lane) - 1u));
-            if (valid && rank == 0) wcnt[warp][d] = __popc(mask);
+        for (unsigned r0 = 0; r0 < n; r0 += 256 * BS_IT) {
+            unsigned long long kv[BS_IT];
+            unsigned dg[BS_IT], rk[BS_IT];
+#pragma unroll
+            for (int q = 0; q < BS_IT; q++) {
+                const unsigned e = r0 + warp * 256 + q * 32 + lane;
+                kv[q] = e < n ? src[e] : 0ull;
+                dg[q] = e < n ? ((unsigned)(kv[q] >> shift) & 255u) : 256u;
+            }
+#pragma unroll
+            for (int q = 0; q < BS_IT; q++) {
+                const unsigned mask = __match_any_sync(0xffffffffu, dg[q]);
+                const unsigned before = dg[q] < 256u ? wcnt[warp][dg[q]] : 0u;
+                rk[q] = before + __popc(mask & ((1u << lane) - 1u));
+                __syncwarp();
+                if (dg[q] < 256u && lane == __ffs(mask) - 1) wcnt[warp][dg[q]] = before + __popc(mask);
+                __syncwarp();
+            }
             __syncthreads();
             unsigned run = hist[tid];  // thread tid owns digit tid
             for (int w = 0; w < 8; w++) {
@@ -234,7 +327,9 @@ __global__ void __launch_bounds__(256) k_sp_bigsort(unsigned long long *keys, un
             }
             hist[tid] = run;
             __syncthreads();
-            if (valid) dst[wpos[warp][d] + rank] = k;
+#pragma unroll
+            for (int q = 0; q < BS_IT; q++)
+                if (dg[q] < 256u) dst[wpos[warp][dg[q]] + rk[q]] = kv[q];
         }
         unsigned long long *t = src;
         src = dst;
@@ -397,6 +492,8 @@ int splat_render(fs_ctx *c, int n, const float *x, const float *op, const float 
     unsigned long long tot[2] = {0, 0};
     FS_CUDA(cudaMemcpyAsync(tot, total_d, sizeof(tot), cudaMemcpyDeviceToHost, c->stream));
     FS_CUDA(cudaStreamSynchronize(c->stream));
+    s->last_entries = tot[0];
+    s->last_max = tot[1];
     if (tot[0] > 0xffffffffull) return set_error(FS_EINVAL, "more than 2^32 tile entries");
     if ((rc = grow(&s->keys, s->cap_k, (long long)tot[0]))) return rc;
     if (n > 0) {
@@ -413,6 +510,13 @@ int splat_render(fs_ctx *c, int n, const float *x, const float *op, const float 
     c->n_launches += 1;
     FS_CUDA(cudaGetLastError());
     return FS_OK;
+}
+
+void splat_stats(const fs_ctx *c, unsigned long long *entries, unsigned long long *max_tile)
+{
+    const SplatState *s = static_cast<const SplatState *>(c->splat);
+    *entries = s ? s->last_entries : 0;
+    *max_tile = s ? s->last_max : 0;
 }
 
 }  // namespace fs

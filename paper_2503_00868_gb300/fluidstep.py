@@ -90,6 +90,7 @@ _SIGS = {
     "fs_divergence": ([C.c_void_p, C.POINTER(fs_mac), C.c_void_p], C.c_int),
     "fs_splat_render": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                          C.c_void_p, C.c_void_p], C.c_int),
+    "fs_splat_stats": ([C.c_void_p, C.POINTER(C.c_ulonglong), C.POINTER(C.c_ulonglong)], C.c_int),
     "fs_p2g": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(fs_mac),
                 C.POINTER(fs_mac)], C.c_int),
     "fs_g2p": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -297,6 +298,13 @@ def fs_splat_render(ctx: int, x: torch.Tensor, opacity: torch.Tensor, A: torch.T
                                   C.c_void_p(opacity.data_ptr()), C.c_void_p(A.data_ptr()),
                                   C.c_void_p(color.data_ptr()), C.byref(cam), C.c_void_p(rgb_out.data_ptr()),
                                   C.c_void_p(T_out.data_ptr()) if T_out is not None else None), (FS_OK,))
+
+
+def fs_splat_stats(ctx: int) -> dict:
+    """{"entries", "max_tile"} of the last fs_splat_render on this context."""
+    e, m = C.c_ulonglong(0), C.c_ulonglong(0)
+    _check(load().fs_splat_stats(C.c_void_p(ctx), C.byref(e), C.byref(m)), (FS_OK,))
+    return {"entries": int(e.value), "max_tile": int(m.value)}
 
 
 def _parts(t: Optional[torch.Tensor], cols: int):

@@ -61,6 +61,8 @@ def main():
                       "ms_per_frame_median": med, "ms_per_frame_min": float(min(ms)),
                       "frames_per_s": 1e3 / med, "gaussians_per_s": x.shape[0] / (med * 1e-3),
                       "covered_pixel_share": float((T < 1).float().mean()),
+                      "tile_entries": F.fs_splat_stats(grid.ctx)["entries"],
+                      "max_tile_entries": F.fs_splat_stats(grid.ctx)["max_tile"],
                       "finite": bool(torch.isfinite(rgb).all())}))
 
 

@@ -105,7 +105,9 @@ def test_tiles_beyond_shared_memory_with_depth_ties(ctx):
     col = rng.random((n, 3))
     x, op, A, col = f32(x), f32(op), f32(A), f32(col)
     cg, co = cams(np.eye(3), np.zeros(3), 300.0, 300.0, 48.0, 40.0, 96, 80)
-    compare(render_gpu(ctx, x, op, A, col, cg), O.splat_render(x, op, A, col, co))
+    g = render_gpu(ctx, x, op, A, col, cg)
+    assert F.fs_splat_stats(ctx.ctx)["max_tile"] > 4096  # the global-memory sort ran
+    compare(g, O.splat_render(x, op, A, col, co))
 
 
 def test_full_size_workload_windows(ctx):
