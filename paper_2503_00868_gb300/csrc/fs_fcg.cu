@@ -53,9 +53,10 @@ __global__ void __launch_bounds__(TH) k_fcg_dots(const float *__restrict__ z, co
             }
         }
     }
-    double v[FCG_M + 1], tot[FCG_M + 1];
+    KSum v[FCG_M + 1];
+    double tot[FCG_M + 1];
 #pragma unroll
-    for (int j = 0; j <= FCG_M; j++) v[j] = acc[j].value();
+    for (int j = 0; j <= FCG_M; j++) v[j] = acc[j];
     if (grid_reduce<FCG_M + 1>(v, partials, &s->ticket, tot) && threadIdx.x == 0) {
         bool ok = isfinite(tot[FCG_M]);
         for (int j = 0; j < FCG_M; j++) {
@@ -109,7 +110,8 @@ __global__ void __launch_bounds__(TH) k_fcg_apply(const float *__restrict__ p, f
         }
         q[t] = qv;
     }
-    double v[1] = {acc.value()}, tot[1];
+    KSum v[1] = {acc};
+    double tot[1];
     if (grid_reduce<1>(v, partials, &s->ticket, tot) && threadIdx.x == 0) {
         const double pq = tot[0];
         *pq_out = pq;
@@ -140,7 +142,8 @@ __global__ void __launch_bounds__(TH) k_fcg_update(float *__restrict__ x, float 
         r4[t] = rv;
         rr.add(rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w);
     }
-    double v[1] = {rr.value()}, tot[1];
+    KSum v[1] = {rr};
+    double tot[1];
     if (grid_reduce<1>(v, partials, &s->ticket, tot) && threadIdx.x == 0) {
         s->iter += 1;
         s->rr = tot[0];
@@ -163,7 +166,8 @@ __global__ void __launch_bounds__(TH) k_fcg_init(const float *__restrict__ b, fl
         reinterpret_cast<float4 *>(x)[t] = zero;
         bb.add(v.x * v.x + v.y * v.y + v.z * v.z + v.w * v.w);
     }
-    double v[1] = {bb.value()}, tot[1];
+    KSum v[1] = {bb};
+    double tot[1];
     if (grid_reduce<1>(v, partials, &s->ticket, tot) && threadIdx.x == 0) {
         s->bb = tot[0];
         s->rr = tot[0];

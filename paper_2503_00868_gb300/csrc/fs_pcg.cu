@@ -67,7 +67,8 @@ __global__ void __launch_bounds__(TH) k_spmv(const float *__restrict__ src, cons
         pnew[t] = pc;
         q[t] = qv;
     }
-    double v[1] = {acc.value()}, tot[1];
+    KSum v[1] = {acc};
+    double tot[1];
     if (grid_reduce<1>(v, partials, &s->ticket, tot) && threadIdx.x == 0) {
         double pq = tot[0];
         s->pq = pq;
@@ -115,7 +116,8 @@ __global__ void __launch_bounds__(TH) k_update(float *__restrict__ x, float *__r
         x4[t] = xv;
         r4[t] = rv;
     }
-    double v[2] = {rr.value(), rz.value()}, tot[2];
+    KSum v[2] = {rr, rz};
+    double tot[2];
     if (grid_reduce<2>(v, partials, &s->ticket, tot) && threadIdx.x == 0) {
         s->iter += 1;
         s->rr = tot[0];
@@ -141,7 +143,8 @@ __global__ void __launch_bounds__(TH) k_rz(const float *__restrict__ r, const fl
         const float4 a = __ldg(r4 + t), b = __ldg(z4 + t);
         acc.add(a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w);
     }
-    double v[1] = {acc.value()}, tot[1];
+    KSum v[1] = {acc};
+    double tot[1];
     if (grid_reduce<1>(v, partials, &s->ticket, tot) && threadIdx.x == 0) {
         if (!isfinite(tot[0])) { s->done = 1; s->status = FS_ENONFINITE; return; }
         s->beta = first ? 0.0 : tot[0] / s->rz;
@@ -196,7 +199,8 @@ __global__ void __launch_bounds__(TH) k_pois_init(const float *__restrict__ b, f
             reinterpret_cast<float4 *>(r)[t] = v;
         }
     }
-    double v[2] = {bb.value(), rz.value()}, tot[2];
+    KSum v[2] = {bb, rz};
+    double tot[2];
     if (grid_reduce<2>(v, partials, &s->ticket, tot) && threadIdx.x == 0)
         init_scalars(s, tot[0], tot[0], tot[1], tol2, maxit);
 }
@@ -227,7 +231,8 @@ __global__ void __launch_bounds__(TH) k_helm_init(const float *__restrict__ x, c
         p0[t] = 0.f;
         p1[t] = 0.f;
     }
-    double v[3] = {bb.value(), rr.value(), rz.value()}, tot[3];
+    KSum v[3] = {bb, rr, rz};
+    double tot[3];
     if (grid_reduce<3>(v, partials, &s->ticket, tot) && threadIdx.x == 0)
         init_scalars(s, tot[0], tot[1], tot[2], tol2, maxit);
 }
@@ -280,7 +285,8 @@ __global__ void __launch_bounds__(TH) k_pois_restart(const float *__restrict__ b
         p0[t] = 0.f;
         p1[t] = 0.f;
     }
-    double v[2] = {rr.value(), rz.value()}, tot[2];
+    KSum v[2] = {rr, rz};
+    double tot[2];
     if (grid_reduce<2>(v, partials, &s->ticket, tot) && threadIdx.x == 0) {
         s->rr = tot[0];
         s->rz = tot[1];
@@ -410,7 +416,8 @@ __global__ void __launch_bounds__(TH) k_nu_grad(const float *__restrict__ vx, CF
             acc.add(vx[o + idx] * lu);
         }
     }
-    double v[1] = {acc.value()}, tot[1];
+    KSum v[1] = {acc};
+    double tot[1];
     if (grid_reduce<1>(v, partials, &s->ticket, tot) && threadIdx.x == 0) s->aux[0] = tot[0];
 }
 

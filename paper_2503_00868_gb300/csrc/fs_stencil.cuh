@@ -93,7 +93,8 @@ __global__ void __launch_bounds__(256) k_update_q(float *x, float *r, const floa
         qm = qmn;
         idx = nidx;
     }
-    double vv[2] = {rr.value(), rz.value()}, tot[2];
+    KSum vv[2] = {rr, rz};
+    double tot[2];
     if (grid_reduce<2>(vv, partials, &s->ticket, tot) && threadIdx.x == 0 && threadIdx.y == 0) {
         s->iter += 1;
         s->rr = tot[0];

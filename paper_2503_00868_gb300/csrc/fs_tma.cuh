@@ -223,7 +223,8 @@ __global__ void __launch_bounds__(256) k_spmv_z(const __grid_constant__ CUtensor
         }
         __syncthreads();
     }
-    double vv[1] = {acc.value()}, tot[1];
+    KSum vv[1] = {acc};
+    double tot[1];
     if (grid_reduce<1>(vv, partials, &s->ticket, tot) && threadIdx.x == 0 && threadIdx.y == 0) {
         const double pq = tot[0];
         s->pq = pq;
