@@ -259,8 +259,11 @@ static std::vector<int4> zmarch_items(const std::vector<uint8_t> &act, const Til
                 if (active(e)) last = e;
                 e++;
             }
-            const int k1 = last + 1;  // run [k, k1)
-            for (int a = k; a < k1; a += zc) items.push_back(make_int4(col, a, std::min(a + zc, k1), 0));
+            const int k1 = last + 1;  // run [k, k1), cut into chunks of at most zc planes
+            const int len = k1 - k, nch = (len + zc - 1) / zc;
+            for (int c = 0; c < nch; c++)  // equal lengths (within one plane): no short tail chunk
+                items.push_back(make_int4(col, k + (int)((long long)len * c / nch),
+                                          k + (int)((long long)len * (c + 1) / nch), 0));
             k = k1;
         }
     }
