@@ -161,15 +161,18 @@ __global__ void __launch_bounds__(256) k_spmv_z(const __grid_constant__ CUtensor
             const int m = cons;
             const unsigned g = gbase + m;
             const int st = (int)(g % Z_NS);
-            const bool ok = mbar_wait_bounded(bar + st, (g / Z_NS) & 1u);
-            if (ok) {
+            // warp 0 waits for the plane's copies; the block barrier passes the
+            // completed phase (and the data it guards) on to the other warps
+            const bool ok = ty != 0 || mbar_wait_bounded(bar + st, (g / Z_NS) & 1u);
+            bad = __syncthreads_or(!ok);
+            if (bad) break;
+            {
                 const float4 *bz = reinterpret_cast<const float4 *>(base + st * 2 * ZB_PITCH);
                 const float4 *bo = reinterpret_cast<const float4 *>(base + st * 2 * ZB_PITCH + ZB_PITCH);
                 float4 *dst = reinterpret_cast<float4 *>(ring + (m % Z_RING) * ZB_ELEMS);
                 for (int e = tid; e < ZB_ELEMS / 4; e += 256) dst[e] = fma4(bz[e], beta, bo[e]);
             }
-            bad = __syncthreads_or(!ok);
-            if (bad) break;
+            __syncthreads();
             // stage st is free again: the plane Z_NS ahead goes into it
             if (m + Z_NS < L) {
                 if (tid == 0) {
