@@ -59,7 +59,7 @@ def args_parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--frames", type=int, default=FRAMES)
-    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "mic0"])
+    ap.add_argument("--precond", default="mg", choices=["jacobi", "mic0", "mg"])
     ap.add_argument("--cpu-sample-n", type=int, default=64)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -145,7 +145,8 @@ def make_scene(n, seed):
 def params_for(n, precond, warm_start=1):
     from paper_2503_00868_gb300 import fluidstep as F
     return dict(dx=1.0 / n, dt=1.0 / 30.0, nu=0.01, g=(0.0, 0.0, 0.0), tol_p=1e-6, tol_v=1e-6,
-                precond=F.FS_PRECOND_MIC0 if precond == "mic0" else F.FS_PRECOND_JACOBI, check_every=16,
+                precond={"mic0": F.FS_PRECOND_MIC0, "mg": F.FS_PRECOND_MG}.get(precond, F.FS_PRECOND_JACOBI),
+                check_every=16,
                 maxit_p=20000, maxit_v=4000, warm_start=warm_start)
 
 

@@ -79,7 +79,9 @@ enum { FS_AIR = 0, FS_LIQUID = 1, FS_SOLID = 2 };
 enum {
     FS_PRECOND_JACOBI = 0,  /* diagonal scaling */
     FS_PRECOND_MIC0 = 1,    /* modified incomplete Cholesky, level 0 */
-    FS_PRECOND_LEARNED = 2  /* the convolutional network, in flexible CG */
+    FS_PRECOND_LEARNED = 2, /* the convolutional network, in flexible CG */
+    FS_PRECOND_MG = 3       /* geometric multigrid V-cycle (not in the paper: damped-Jacobi
+                               smoothing, cell coarsening with air kept, trilinear transfers) */
 };
 
 enum {

@@ -41,7 +41,7 @@ static int check_params(const fs_params *p)
     if (!(p->rho > 0.0) || !std::isfinite(p->rho)) return set_error(FS_EINVAL, "rho must be > 0");
     for (int c = 0; c < 3; c++)
         if (!std::isfinite(p->g[c])) return set_error(FS_EINVAL, "g must be finite");
-    if (p->precond < FS_PRECOND_JACOBI || p->precond > FS_PRECOND_LEARNED)
+    if (p->precond < FS_PRECOND_JACOBI || p->precond > FS_PRECOND_MG)
         return set_error(FS_EINVAL, "unknown preconditioner %d", p->precond);
     if (p->maxit_p < 1 || p->maxit_v < 1) return set_error(FS_EINVAL, "iteration caps must be >= 1");
     if (!(p->tol_p > 0.0) || !(p->tol_v > 0.0)) return set_error(FS_EINVAL, "tolerances must be > 0");
@@ -158,6 +158,7 @@ static void free_ctx(fs_ctx *c)
     fcg_release(c);
     percnn_free(c);
     splat_free(c);
+    mg_free(c);
     void *ptrs[] = {c->cflag, c->fflag, c->bc, c->dsum, c->pb, c->pr, c->pp[0], c->pp[1], c->pq, c->px, c->pz,
                     c->vx, c->vr, c->vp[0], c->vp[1], c->vq, c->fu[0], c->fu[1], c->fu[2], c->fg[0], c->fg[1],
                     c->fg[2], c->gc[0], c->gc[1], c->gc[2], c->mic_prec, c->scal, c->partials, c->err_word, c->pw[0], c->pw[1],

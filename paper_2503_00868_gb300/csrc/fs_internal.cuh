@@ -142,6 +142,7 @@ struct fs_ctx {
     void *fcg;
     void *percnn;         // recurrent convolutional pressure solver (fs_percnn.cu)
     void *splat;          // splatting scratch (fs_splat.cu)
+    void *mg;             // multigrid hierarchy of the pressure preconditioner (fs_mg.cu)
 
     // reductions
     fs::SolveScal *scal;        // device [4]: 0 pressure, 1 viscosity, 2 misc, 3 misc
@@ -376,6 +377,10 @@ int launch_to_face_space(fs_ctx *c, CF3 in);             // full field (fluid) -
 int launch_nu_grad(fs_ctx *c, CF3 uv, double *dot);      // <vx, L~ uv>
 int launch_loss(fs_ctx *c, CF3 u, CF3 t, int kind, double alpha, double beta, F3 g,
                 double *loss);
+// fs_mg.cu
+int mg_apply(fs_ctx *c, const float *r, float *z);
+void mg_free(fs_ctx *c);
+int mg_levels(const fs_ctx *c);
 // fs_splat.cu
 int splat_render(fs_ctx *c, int n, const float *x, const float *op, const float *A, const float *col,
                  const fs_camera *cam, float *rgb, float *T);

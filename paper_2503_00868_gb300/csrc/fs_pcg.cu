@@ -662,8 +662,10 @@ static int pcg_iterate(fs_ctx *c, SolveScal &h, bool warm)
     const bool jac = c->prm.precond == FS_PRECOND_JACOBI;
     const int n4 = L.nC / 4;
     const double tol2 = c->prm.tol_p * c->prm.tol_p;
-    // z = M r for MIC(0), the stored-z preconditioner
-    auto apply_m = [&]() -> int { return mic0_apply(c, c->pr, c->pz); };
+    // z = M r for MIC(0) or the multigrid V-cycle (the stored-z preconditioners)
+    auto apply_m = [&]() -> int {
+        return c->prm.precond == FS_PRECOND_MG ? mg_apply(c, c->pr, c->pz) : mic0_apply(c, c->pr, c->pz);
+    };
     if (warm) {
         if (jac)
             k_pois_restart<true><<<grid_blocks(c, L.nC, TH), TH, 0, c->stream>>>(
@@ -951,6 +953,9 @@ int precond_apply_public(fs_ctx *c, const float *r, float *z)
     if (c->prm.precond == FS_PRECOND_JACOBI) {
         k_jacobi<<<grid_blocks(c, L.nC, TH), TH, 0, c->stream>>>(c->pr, c->pz, c->cflag, L.nC);
         c->n_launches += 1;
+    } else if (c->prm.precond == FS_PRECOND_MG) {
+        int rc = mg_apply(c, c->pr, c->pz);
+        if (rc) return rc;
     } else if (c->prm.precond == FS_PRECOND_MIC0) {
         FS_CUDA(cudaMemsetAsync(c->err_word, 0, sizeof(unsigned), c->stream));
         if (!c->mic_ready) {

@@ -25,7 +25,7 @@ FS_OK, FS_EINVAL, FS_ENOMEM, FS_ECUDA, FS_ENOCONV, FS_ENONFINITE, FS_ESTATE, FS_
 STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_ENOMEM", 3: "FS_ECUDA", 4: "FS_ENOCONV",
                 5: "FS_ENONFINITE", 6: "FS_ESTATE", 7: "FS_ETIMEOUT", 8: "FS_EBREAKDOWN"}
 FS_AIR, FS_LIQUID, FS_SOLID = 0, 1, 2
-FS_PRECOND_JACOBI, FS_PRECOND_MIC0, FS_PRECOND_LEARNED = 0, 1, 2
+FS_PRECOND_JACOBI, FS_PRECOND_MIC0, FS_PRECOND_LEARNED, FS_PRECOND_MG = 0, 1, 2, 3
 FS_MASK_SURFACE, FS_MASK_OCCUPIED = 0, 1
 FS_SOLVER_PCG, FS_SOLVER_PERCNN = 0, 1
 SOFT_STATUS = (FS_OK, FS_ENOCONV)
