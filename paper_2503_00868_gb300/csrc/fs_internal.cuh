@@ -119,7 +119,7 @@ struct fs_ctx {
     int pw_valid[2];
     int solve_kind;       // kind of the pressure solve being run
     // viscosity solve (face space)
-    float *vx, *vr, *vp[2], *vq;
+    float *vx, *vr, *vp[2], *vq, *vz;  // vz: preconditioned residual of a multigrid viscosity solve
     // full-layout scratch fields (3 * S each, public layout)
     float *fu[3];         // u_visc when the caller does not keep it
     float *fg[3];         // adjoint cotangent being projected
@@ -163,7 +163,7 @@ struct fs_ctx {
     int nitems_cell, nitems_face;
     // tensor maps of the vectors the operator apply reads (3-D: pitch x rows x
     // planes of the guarded space, 136 x 10 x 1 boxes)
-    CUtensorMap tmz_pr, tmz_pz, tmz_pp[2], tmz_vr, tmz_vp[2];
+    CUtensorMap tmz_pr, tmz_pz, tmz_pp[2], tmz_vr, tmz_vp[2], tmz_vz;
 
     // per-kernel timing (fs_profile)
     int prof_on;
@@ -378,7 +378,8 @@ int launch_nu_grad(fs_ctx *c, CF3 uv, double *dot);      // <vx, L~ uv>
 int launch_loss(fs_ctx *c, CF3 u, CF3 t, int kind, double alpha, double beta, F3 g,
                 double *loss);
 // fs_mg.cu
-int mg_apply(fs_ctx *c, const float *r, float *z);
+int mg_apply(fs_ctx *c, const float *r, float *z, const int *done);
+int mg_apply_faces(fs_ctx *c, const float *r, float *z, float cc, const int *done);
 void mg_free(fs_ctx *c);
 int mg_levels(const fs_ctx *c);
 // fs_splat.cu

@@ -231,7 +231,7 @@ int make_tensor_maps(fs_ctx *c)
         {&c->tmz_pr, c->pr, L.nC, zx, zy},         {&c->tmz_pz, c->pz, L.nC, zx, zy},
         {&c->tmz_pp[0], c->pp[0], L.nC, zx, zy},   {&c->tmz_pp[1], c->pp[1], L.nC, zx, zy},
         {&c->tmz_vr, c->vr, L.nF, zx, zy},         {&c->tmz_vp[0], c->vp[0], L.nF, zx, zy},
-        {&c->tmz_vp[1], c->vp[1], L.nF, zx, zy}};
+        {&c->tmz_vp[1], c->vp[1], L.nF, zx, zy},   {&c->tmz_vz, c->vz, L.nF, zx, zy}};
     for (auto &e : maps) {
         int rc = encode_map(e.m, e.p, L, e.len, e.bx, e.by);
         if (rc) return rc;

@@ -23,6 +23,13 @@
 //
 // Every kernel runs densely over a level's whole array and writes zero on cells
 // that are not liquid, so a stencil at the edge of the liquid reads zeros.
+//
+// The same V-cycle preconditions the implicit viscosity solve, one velocity
+// component at a time: each face volume is a box of unknown faces (FF_FLUID),
+// prescribed faces (FF_FIXED, Dirichlet) and mirror faces (Neumann), whose flag
+// bits coincide with the cell bits used here (FF_FLUID = CF_LIQ, FF_FIXED =
+// CF_AIR, FF_N = CF_D), and the operator gains the mass term: A_l = m I +
+// 4^-l cc L_l with m = 1 (m = 0 for the pressure).
 #include <cmath>
 #include <new>
 
@@ -53,7 +60,8 @@ struct MgGrid {
 
 struct MgLevel {
     MgGrid g;
-    float scale = 1.f;  // 4^-l
+    float scale = 1.f;  // 4^-l times the operator's coefficient
+    float mass = 0.f;   // identity term (1 for the Helmholtz operator)
     uint8_t *fl = nullptr;
     float *r = nullptr, *a = nullptr, *b = nullptr, *c = nullptr;  // right-hand side and three work arrays
 };
@@ -62,6 +70,16 @@ struct MgState {
     int nlev = 0;
     MgLevel lev[MG_MAX_LEVELS];
     long long epoch = -1;  // mask epoch the hierarchy was built for
+    float coef = 0.f;      // operator coefficient it was built for
+    bool own0 = true;      // level 0 work arrays belong to this hierarchy
+    const int *done = nullptr;  // the calling solve's convergence flag (nullable)
+};
+
+// the pressure hierarchy and one per face volume (viscosity); the face volumes
+// share two level-0 work arrays of face-space length
+struct MgAll {
+    MgState cell, face[3];
+    float *fb = nullptr, *fc = nullptr;
 };
 
 namespace {
@@ -77,21 +95,25 @@ __device__ __forceinline__ float lap(const float *__restrict__ e, int t, uint8_t
     return (float)(f & CF_D) * e[t] - ((e[t - 1] + e[t + 1]) + (e[t - g.sy] + e[t + g.sy]) + (e[t - g.sz] + e[t + g.sz]));
 }
 
-// omega / (scale d) for d = 0..6 (zero for d = 0)
-__device__ __forceinline__ void fill_wtab(float *wt, float scale)
+// omega / (m + scale d) for d = 0..7 (zero where the diagonal vanishes)
+__device__ __forceinline__ void fill_wtab(float *wt, float scale, float m)
 {
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    if (tid < 8) wt[tid] = tid > 0 && tid < 7 ? MG_OMEGA / (scale * (float)tid) : 0.f;
+    if (tid < 8) {
+        const float dg = m + scale * (float)tid;
+        wt[tid] = dg > 0.f ? MG_OMEGA / dg : 0.f;
+    }
     __syncthreads();
 }
 
 // the first two sweeps from e = 0 in one pass: e1 = omega D^-1 r is formed on
 // the fly at the cell and its six neighbours, then e2 = e1 + omega D^-1 (r - A e1)
 __global__ void __launch_bounds__(256) k_mg_smooth2(MgGrid g, const uint8_t *__restrict__ fl,
-                                                    const float *__restrict__ r, float *eo, float scale)
+                                                    const float *__restrict__ r, float *eo, float scale, float m, const int *done)
 {
+    if (done && *(volatile const int *)done) return;  // the solve has converged
     __shared__ float wt[8];
-    fill_wtab(wt, scale);
+    fill_wtab(wt, scale, m);
     MG_FOR_ROWS(g)
     {
         const int t = row * g.sy + e;
@@ -105,7 +127,7 @@ __global__ void __launch_bounds__(256) k_mg_smooth2(MgGrid g, const uint8_t *__r
             };
             const float c1 = e1(t);
             const float nb = (e1(t - 1) + e1(t + 1)) + (e1(t - g.sy) + e1(t + g.sy)) + (e1(t - g.sz) + e1(t + g.sz));
-            v = c1 + wt[d] * (r[t] - scale * ((float)d * c1 - nb));
+            v = c1 + wt[d] * (r[t] - m * c1 - scale * ((float)d * c1 - nb));
         }
         eo[t] = v;
     }
@@ -114,36 +136,39 @@ __global__ void __launch_bounds__(256) k_mg_smooth2(MgGrid g, const uint8_t *__r
 // e_out = e_in + omega D^-1 (r - A e_in)
 __global__ void __launch_bounds__(256) k_mg_smooth(MgGrid g, const uint8_t *__restrict__ fl,
                                                    const float *__restrict__ r, const float *__restrict__ ein,
-                                                   float *eout, float scale)
+                                                   float *eout, float scale, float m, const int *done)
 {
+    if (done && *(volatile const int *)done) return;  // the solve has converged
     __shared__ float wt[8];
-    fill_wtab(wt, scale);
+    fill_wtab(wt, scale, m);
     MG_FOR_ROWS(g)
     {
         const int t = row * g.sy + e;
         const uint8_t f = fl[t];
-        eout[t] = liq(f) ? ein[t] + wt[f & CF_D] * (r[t] - scale * lap(ein, t, f, g)) : 0.f;
+        eout[t] = liq(f) ? ein[t] + wt[f & CF_D] * (r[t] - m * ein[t] - scale * lap(ein, t, f, g)) : 0.f;
     }
 }
 
 // res = r - A e
 __global__ void __launch_bounds__(256) k_mg_residual(MgGrid g, const uint8_t *__restrict__ fl,
                                                      const float *__restrict__ r, const float *__restrict__ ev,
-                                                     float *res, float scale)
+                                                     float *res, float scale, float m, const int *done)
 {
+    if (done && *(volatile const int *)done) return;  // the solve has converged
     MG_FOR_ROWS(g)
     {
         const int t = row * g.sy + e;
         const uint8_t f = fl[t];
-        res[t] = liq(f) ? r[t] - scale * lap(ev, t, f, g) : 0.f;
+        res[t] = liq(f) ? r[t] - m * ev[t] - scale * lap(ev, t, f, g) : 0.f;
     }
 }
 
 // coarse r = (1/8) sum over the 4 x 4 x 4 fine window of w_a w_b w_c res_fine,
 // w = (1/4, 3/4, 3/4, 1/4) at fine indices 2I - 1 .. 2I + 2
 __global__ void __launch_bounds__(256) k_mg_restrict(MgGrid gf, const float *__restrict__ res, MgGrid gc,
-                                                     const uint8_t *__restrict__ flc, float *rc)
+                                                     const uint8_t *__restrict__ flc, float *rc, const int *done)
 {
+    if (done && *(volatile const int *)done) return;  // the solve has converged
     const float w[4] = {0.25f, 0.75f, 0.75f, 0.25f};
     MG_FOR_ROWS(gc)
     {
@@ -175,8 +200,9 @@ __global__ void __launch_bounds__(256) k_mg_restrict(MgGrid gf, const float *__r
 
 // e_fine += P e_coarse on liquid fine cells (in place)
 __global__ void __launch_bounds__(256) k_mg_prolong(MgGrid gf, const uint8_t *__restrict__ fl, float *ef,
-                                                    MgGrid gc, const float *__restrict__ ec)
+                                                    MgGrid gc, const float *__restrict__ ec, const int *done)
 {
+    if (done && *(volatile const int *)done) return;  // the solve has converged
     MG_FOR_ROWS(gf)
     {
         const int t = row * gf.sy + e;
@@ -237,16 +263,23 @@ __global__ void k_mg_count(MgGrid g, uint8_t *fl)
 
 // coarsest level: MG_COARSE_SWEEPS damped Jacobi sweeps from zero, in shared memory
 __global__ void __launch_bounds__(TH) k_mg_coarse(MgGrid g, const uint8_t *__restrict__ fl,
-                                                  const float *__restrict__ r, float *e, float scale)
+                                                  const float *__restrict__ r, float *e, float scale, float m, const int *done)
 {
+    if (done && *(volatile const int *)done) return;  // the solve has converged
     extern __shared__ float sm[];
+    __shared__ float wt[8];
     float *e0 = sm, *e1 = sm + g.n, *rs = sm + 2 * g.n;
     uint8_t *fs = reinterpret_cast<uint8_t *>(sm + 3 * g.n);
+    if (threadIdx.x < 8) {
+        const float dg = m + scale * (float)threadIdx.x;
+        wt[threadIdx.x] = dg > 0.f ? MG_OMEGA / dg : 0.f;
+    }
+    __syncthreads();
     for (int t = threadIdx.x; t < g.n; t += TH) {
-        fs[t] = fl[t];
-        rs[t] = r[t];
-        const int d = fl[t] & CF_D;
-        e0[t] = (liq(fl[t]) && d > 0) ? MG_OMEGA * r[t] / (scale * (float)d) : 0.f;
+        const uint8_t f = fl[t];
+        fs[t] = f;
+        rs[t] = liq(f) ? r[t] : 0.f;
+        e0[t] = liq(f) ? wt[f & CF_D] * r[t] : 0.f;
         e1[t] = 0.f;
     }
     __syncthreads();
@@ -255,10 +288,7 @@ __global__ void __launch_bounds__(TH) k_mg_coarse(MgGrid g, const uint8_t *__res
         float *eout = (s & 1) ? e1 : e0;
         for (int t = threadIdx.x; t < g.n; t += TH) {
             const uint8_t f = fs[t];
-            const int d = f & CF_D;
-            float v = 0.f;
-            if (liq(f) && d > 0) v = ein[t] + MG_OMEGA * (rs[t] - scale * lap(ein, t, f, g)) / (scale * (float)d);
-            eout[t] = v;
+            eout[t] = liq(f) ? ein[t] + wt[f & CF_D] * (rs[t] - m * ein[t] - scale * lap(ein, t, f, g)) : 0.f;
         }
         __syncthreads();
     }
@@ -268,20 +298,22 @@ __global__ void __launch_bounds__(TH) k_mg_coarse(MgGrid g, const uint8_t *__res
 
 size_t coarse_smem(const MgGrid &g) { return (size_t)g.n * 13 + 16; }
 
-int launch_blocks(fs_ctx *c, long long n) { return grid_blocks(c, n, TH); }
 int row_blocks(fs_ctx *c, const MgGrid &g) { return grid_blocks(c, g.rows, 8); }
 
-MgGrid level0_grid(const Layout &L)
+// a box of nx x ny x nz cells in the guarded layout of the context (pitch P, R
+// rows per plane, a guard plane before and after): the cell space, or one face
+// volume counted from its leading guard plane
+MgGrid level0_grid(const Layout &L, int nx, int ny, int nz)
 {
     MgGrid g;
-    g.nx = L.nx;
-    g.ny = L.ny;
-    g.nz = L.nz;
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
     g.sy = L.P;
     g.sz = L.PL;
     g.origin = L.PL;
-    g.n = L.nC;
-    g.rows = L.nC / L.P;
+    g.n = L.S + 2 * L.PL;
+    g.rows = g.n / L.P;
     g.rpp = L.R;
     g.ioff = 0;
     g.joff = 0;
@@ -318,74 +350,72 @@ void free_levels(MgState *s)
         cudaFree(v.c);
         v = MgLevel();
     }
-    cudaFree(s->lev[0].b);
-    cudaFree(s->lev[0].c);
+    if (s->own0) {
+        cudaFree(s->lev[0].b);
+        cudaFree(s->lev[0].c);
+    }
     s->lev[0] = MgLevel();
     s->nlev = 0;
     s->epoch = -1;
 }
 
-// The V-cycle on level l: r in lev[l].r (level 0: the given r), result in lev[l].a
-// (level 0: the given z).
+// The V-cycle on level l: r in lev[l].r, result in lev[l].a.
 int vcycle(fs_ctx *c, MgState *s, int l)
 {
     MgLevel &v = s->lev[l];
     const MgGrid &g = v.g;
     if (l == s->nlev - 1) {
-        k_mg_coarse<<<1, TH, coarse_smem(g), c->stream>>>(g, v.fl, v.r, v.a, v.scale);
+        k_mg_coarse<<<1, TH, coarse_smem(g), c->stream>>>(g, v.fl, v.r, v.a, v.scale, v.mass, s->done);
         c->n_launches += 1;
         return FS_OK;
     }
     const int nb = row_blocks(c, g);
-    k_mg_smooth2<<<nb, RT, 0, c->stream>>>(g, v.fl, v.r, v.b, v.scale);
-    k_mg_residual<<<nb, RT, 0, c->stream>>>(g, v.fl, v.r, v.b, v.c, v.scale);
+    k_mg_smooth2<<<nb, RT, 0, c->stream>>>(g, v.fl, v.r, v.b, v.scale, v.mass, s->done);
+    k_mg_residual<<<nb, RT, 0, c->stream>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, s->done);
     MgLevel &w = s->lev[l + 1];
-    k_mg_restrict<<<row_blocks(c, w.g), RT, 0, c->stream>>>(g, v.c, w.g, w.fl, w.r);
+    k_mg_restrict<<<row_blocks(c, w.g), RT, 0, c->stream>>>(g, v.c, w.g, w.fl, w.r, s->done);
     c->n_launches += 3;
     if (int rc = vcycle(c, s, l + 1)) return rc;
-    k_mg_prolong<<<nb, RT, 0, c->stream>>>(g, v.fl, v.b, w.g, w.a);
-    k_mg_smooth<<<nb, RT, 0, c->stream>>>(g, v.fl, v.r, v.b, v.c, v.scale);
-    k_mg_smooth<<<nb, RT, 0, c->stream>>>(g, v.fl, v.r, v.c, v.a, v.scale);
+    k_mg_prolong<<<nb, RT, 0, c->stream>>>(g, v.fl, v.b, w.g, w.a, s->done);
+    k_mg_smooth<<<nb, RT, 0, c->stream>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, s->done);
+    k_mg_smooth<<<nb, RT, 0, c->stream>>>(g, v.fl, v.r, v.c, v.a, v.scale, v.mass, s->done);
     c->n_launches += 3;
     FS_CUDA(cudaGetLastError());
     return FS_OK;
 }
 
-}  // namespace
-
-void mg_free(fs_ctx *c)
-{
-    MgState *s = static_cast<MgState *>(c->mg);
-    if (!s) return;
-    free_levels(s);
-    delete s;
-    c->mg = nullptr;
-}
-
-// Builds the hierarchy for the current mask (once per mask).
-static int mg_build(fs_ctx *c, MgState *s)
+// Builds a hierarchy under level 0 (grid g0, flags fl0, work arrays b0 and c0 of
+// the level-0 length, or allocated here when null).
+int mg_build(fs_ctx *c, MgState *s, const MgGrid &g0, uint8_t *fl0, float *b0, float *c0, float coef, float mass)
 {
     free_levels(s);
-    const Layout &L = c->L;
     MgLevel &l0 = s->lev[0];
-    l0.g = level0_grid(L);
-    l0.scale = 1.f;
-    l0.fl = c->cflag;
+    l0.g = g0;
+    l0.scale = coef;
+    l0.mass = mass;
+    l0.fl = fl0;
     s->nlev = 1;
+    s->own0 = b0 == nullptr;
     auto fail = [&](const char *what) {
         cudaGetLastError();
         free_levels(s);
         return set_error(FS_ENOMEM, "multigrid %s", what);
     };
-    if (cudaMalloc(&l0.b, (size_t)L.nC * 4) != cudaSuccess || cudaMalloc(&l0.c, (size_t)L.nC * 4) != cudaSuccess)
-        return fail("level-0 work arrays");
-    FS_CUDA(cudaMemsetAsync(l0.b, 0, (size_t)L.nC * 4, c->stream));
-    FS_CUDA(cudaMemsetAsync(l0.c, 0, (size_t)L.nC * 4, c->stream));
+    if (s->own0) {
+        if (cudaMalloc(&l0.b, (size_t)g0.n * 4) != cudaSuccess || cudaMalloc(&l0.c, (size_t)g0.n * 4) != cudaSuccess)
+            return fail("level-0 work arrays");
+        FS_CUDA(cudaMemsetAsync(l0.b, 0, (size_t)g0.n * 4, c->stream));
+        FS_CUDA(cudaMemsetAsync(l0.c, 0, (size_t)g0.n * 4, c->stream));
+    } else {
+        l0.b = b0;
+        l0.c = c0;
+    }
     while (s->lev[s->nlev - 1].g.n > MG_COARSE_CELLS && s->nlev < MG_MAX_LEVELS) {
         const MgGrid &gf = s->lev[s->nlev - 1].g;
         MgLevel &v = s->lev[s->nlev];
         v.g = coarse_grid((gf.nx + 1) / 2, (gf.ny + 1) / 2, (gf.nz + 1) / 2);
         v.scale = s->lev[s->nlev - 1].scale * 0.25f;
+        v.mass = mass;
         const size_t nb = (size_t)v.g.n;
         if (cudaMalloc(&v.fl, nb) != cudaSuccess || cudaMalloc(&v.r, nb * 4) != cudaSuccess ||
             cudaMalloc(&v.a, nb * 4) != cudaSuccess || cudaMalloc(&v.b, nb * 4) != cudaSuccess ||
@@ -405,20 +435,13 @@ static int mg_build(fs_ctx *c, MgState *s)
     if (s->lev[s->nlev - 1].g.n > MG_COARSE_CELLS)
         return set_error(FS_EINVAL, "multigrid: the coarsest level does not fit in shared memory");
     s->epoch = c->mask_epoch;
+    s->coef = coef;
     return FS_OK;
 }
 
-// z = M r on the cell space (r and z of length nC, zero off the liquid).
-int mg_apply(fs_ctx *c, const float *r, float *z)
+int apply_on(fs_ctx *c, MgState *s, const float *r, float *z, const int *done)
 {
-    MgState *s = static_cast<MgState *>(c->mg);
-    if (!s) {
-        s = new (std::nothrow) MgState();
-        if (!s) return set_error(FS_ENOMEM, "host allocation failed");
-        c->mg = s;
-    }
-    if (s->epoch != c->mask_epoch)
-        if (int rc = mg_build(c, s)) return rc;
+    s->done = done;
     MgLevel &l0 = s->lev[0];
     l0.r = const_cast<float *>(r);
     l0.a = z;
@@ -428,10 +451,80 @@ int mg_apply(fs_ctx *c, const float *r, float *z)
     return rc;
 }
 
+MgAll *state(fs_ctx *c)
+{
+    MgAll *m = static_cast<MgAll *>(c->mg);
+    if (!m) {
+        m = new (std::nothrow) MgAll();
+        c->mg = m;
+    }
+    return m;
+}
+
+}  // namespace
+
+void mg_free(fs_ctx *c)
+{
+    MgAll *m = static_cast<MgAll *>(c->mg);
+    if (!m) return;
+    free_levels(&m->cell);
+    for (MgState &f : m->face) free_levels(&f);
+    cudaFree(m->fb);
+    cudaFree(m->fc);
+    delete m;
+    c->mg = nullptr;
+}
+
+// z = M r on the cell space (r and z of length nC, zero off the liquid).
+int mg_apply(fs_ctx *c, const float *r, float *z, const int *done)
+{
+    MgAll *m = state(c);
+    if (!m) return set_error(FS_ENOMEM, "host allocation failed");
+    const Layout &L = c->L;
+    if (m->cell.epoch != c->mask_epoch)
+        if (int rc = mg_build(c, &m->cell, level0_grid(L, L.nx, L.ny, L.nz), c->cflag, nullptr, nullptr, 1.f, 0.f))
+            return rc;
+    return apply_on(c, &m->cell, r, z, done);
+}
+
+// z = M r on the face space for the Helmholtz operator I + cc L of the viscosity
+// solve, one V-cycle per velocity component (r and z of length nF, zero off the
+// unknown faces). With `done` set, every kernel returns at once once *done != 0.
+int mg_apply_faces(fs_ctx *c, const float *r, float *z, float cc, const int *done)
+{
+    MgAll *m = state(c);
+    if (!m) return set_error(FS_ENOMEM, "host allocation failed");
+    const Layout &L = c->L;
+    if (!m->fb) {
+        if (cudaMalloc(&m->fb, (size_t)L.nF * 4) != cudaSuccess || cudaMalloc(&m->fc, (size_t)L.nF * 4) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(m->fb);
+            m->fb = nullptr;
+            return set_error(FS_ENOMEM, "multigrid face work arrays");
+        }
+        FS_CUDA(cudaMemsetAsync(m->fb, 0, (size_t)L.nF * 4, c->stream));
+        FS_CUDA(cudaMemsetAsync(m->fc, 0, (size_t)L.nF * 4, c->stream));
+    }
+    for (int k = 0; k < 3; k++) {
+        MgState &s = m->face[k];
+        const size_t base = (size_t)L.face_origin(k) - L.PL;  // the volume's leading guard plane
+        if (s.epoch != c->mask_epoch) {
+            const MgGrid g0 = level0_grid(L, L.nx + (k == 0), L.ny + (k == 1), L.nz + (k == 2));
+            if (int rc = mg_build(c, &s, g0, c->fflag + base, m->fb + base, m->fc + base, cc, 1.f)) return rc;
+        } else if (s.coef != cc) {  // a new viscosity or time step: rescale the levels only
+            float sc = cc;
+            for (int l = 0; l < s.nlev; l++, sc *= 0.25f) s.lev[l].scale = sc;
+            s.coef = cc;
+        }
+        if (int rc = apply_on(c, &s, r + base, z + base, done)) return rc;
+    }
+    return FS_OK;
+}
+
 int mg_levels(const fs_ctx *c)
 {
-    const MgState *s = static_cast<const MgState *>(c->mg);
-    return s ? s->nlev : 0;
+    const MgAll *m = static_cast<const MgAll *>(c->mg);
+    return m ? m->cell.nlev : 0;
 }
 
 }  // namespace fs

@@ -206,7 +206,10 @@ __global__ void __launch_bounds__(TH) k_pois_init(const float *__restrict__ b, f
 }
 
 // Viscosity start from the guess x (fluid faces): rhs = x + cc * dsum (forward,
-// Dirichlet values) or rhs = x (adjoint); r = rhs - A x.
+// Dirichlet values) or rhs = x (adjoint); r = rhs - A x. Jacobi (JAC) keeps the
+// scaled residual D^-1 r and forms r.z here; otherwise r itself is stored and r.z
+// comes after the preconditioner.
+template <bool JAC>
 __global__ void __launch_bounds__(TH) k_helm_init(const float *__restrict__ x, const float *__restrict__ dsum,
                                                   float *__restrict__ r, float *__restrict__ p0,
                                                   float *__restrict__ p1, const uint8_t *__restrict__ fl,
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(TH) k_helm_init(const float *__restrict__ x, c
             rr.add(rv * rv);
             rz.add(rv * rv * inv_diag<HelmOp>(f, cc));
         }
-        r[t] = rv * inv_diag<HelmOp>(f, cc);  // Jacobi keeps the scaled residual z = D^-1 r
+        r[t] = JAC ? rv * inv_diag<HelmOp>(f, cc) : rv;
         p0[t] = 0.f;
         p1[t] = 0.f;
     }
@@ -664,7 +667,7 @@ static int pcg_iterate(fs_ctx *c, SolveScal &h, bool warm)
     const double tol2 = c->prm.tol_p * c->prm.tol_p;
     // z = M r for MIC(0) or the multigrid V-cycle (the stored-z preconditioners)
     auto apply_m = [&]() -> int {
-        return c->prm.precond == FS_PRECOND_MG ? mg_apply(c, c->pr, c->pz) : mic0_apply(c, c->pr, c->pz);
+        return c->prm.precond == FS_PRECOND_MG ? mg_apply(c, c->pr, c->pz, &s->done) : mic0_apply(c, c->pr, c->pz);
     };
     if (warm) {
         if (jac)
@@ -701,8 +704,10 @@ static int pcg_iterate(fs_ctx *c, SolveScal &h, bool warm)
     const TileMap &tm = c->tm_cell;
     const dim3 tdim(TILE_X / 4, TILE_Y);
     const TmaGrids<PoisOp> tg(c, c->nitems_cell, c->nact_cell);
+    // a multigrid iteration costs several operator applies: check convergence more often
+    const int check = c->prm.precond == FS_PRECOND_MG ? std::min(c->prm.check_every, 4) : c->prm.check_every;
     for (;;) {
-        for (int b = 0; b < c->prm.check_every; b++) {
+        for (int b = 0; b < check; b++) {
             const bool samp = c->prof_on && (b % c->prof_period) == 0;
             cudaEvent_t e0 = samp ? prof_mark(c) : nullptr;
             const float *zsrc = jac ? c->pr : c->pz;
@@ -742,7 +747,7 @@ static int pcg_iterate(fs_ctx *c, SolveScal &h, bool warm)
             }
             cur ^= 1;
         }
-        launched += c->prm.check_every;
+        launched += check;
         FS_CUDA(cudaGetLastError());
         int rc = read_scal(c, 0, &h);
         if (rc) return rc;
@@ -853,11 +858,29 @@ int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st)
     const int bs = grid_blocks(c, L.nF, TH);
     const int b4 = grid_blocks(c, n4, TH);
     FS_CUDA(cudaMemsetAsync(c->err_word, 0, sizeof(unsigned), c->stream));
-    k_helm_init<<<bs, TH, 0, c->stream>>>(c->vx, (dirichlet && c->has_bc) ? c->dsum : nullptr, c->vr, c->vp[0],
-                                         c->vp[1], c->fflag, L.nF, L.P, L.PL, cc, tol2, c->prm.maxit_v, s,
-                                         c->partials);
+    // the multigrid preconditioner serves both solves; otherwise Jacobi
+    const bool mg = c->prm.precond == FS_PRECOND_MG;
+    const float *dsum = (dirichlet && c->has_bc) ? c->dsum : nullptr;
+    if (mg)
+        k_helm_init<false><<<bs, TH, 0, c->stream>>>(c->vx, dsum, c->vr, c->vp[0], c->vp[1], c->fflag, L.nF, L.P, L.PL,
+                                                     cc, tol2, c->prm.maxit_v, s, c->partials);
+    else
+        k_helm_init<true><<<bs, TH, 0, c->stream>>>(c->vx, dsum, c->vr, c->vp[0], c->vp[1], c->fflag, L.nF, L.P, L.PL,
+                                                    cc, tol2, c->prm.maxit_v, s, c->partials);
     c->n_launches += 1;
     FS_CUDA(cudaGetLastError());
+    // z = M r and r.z (first: beta = 0)
+    auto precondition = [&](int first) -> int {
+        if (int rc = mg_apply_faces(c, c->vr, c->vz, cc, &s->done)) return rc;
+        k_rz<<<b4, TH, 0, c->stream>>>(c->vr, c->vz, n4, first, s, c->partials);
+        c->n_launches += 1;
+        FS_CUDA(cudaGetLastError());
+        return FS_OK;
+    };
+    if (mg)
+        if (int rc = precondition(1)) return rc;
+    // a multigrid iteration costs several operator applies: check convergence more often
+    const int check = mg ? std::min(c->prm.check_every, 4) : c->prm.check_every;
     int cur = 0;
     long long launched = 0;
     SolveScal h;
@@ -868,31 +891,42 @@ int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st)
     const dim3 tdim(TILE_X / 4, TILE_Y);
     const TmaGrids<HelmOp> tg(c, c->nitems_face, c->nact_face);
     for (;;) {
-        for (int b = 0; b < c->prm.check_every; b++) {
+        for (int b = 0; b < check; b++) {
             const bool samp = c->prof_on && (b % c->prof_period) == 0;
             cudaEvent_t e0 = samp ? prof_mark(c) : nullptr;
             if (tiled)
                 k_spmv_z<HelmOp><<<tg.spmv, tdim, zmarch_smem(), c->stream>>>(
-                    c->tmz_vr, c->tmz_vp[cur], c->vp[cur ^ 1], c->vq, c->fflag, c->items_face, c->nitems_face, tm,
-                    cc, s, c->partials, c->err_word);
+                    mg ? c->tmz_vz : c->tmz_vr, c->tmz_vp[cur], c->vp[cur ^ 1], c->vq, c->fflag, c->items_face,
+                    c->nitems_face, tm, cc, s, c->partials, c->err_word);
             else
-                k_spmv<HelmOp><<<bs, TH, 0, c->stream>>>(c->vr, c->vp[cur], c->vp[cur ^ 1], c->vq, c->fflag, L.nF,
-                                                         L.P, L.PL, cc, s, c->partials);
+                k_spmv<HelmOp><<<bs, TH, 0, c->stream>>>(mg ? c->vz : c->vr, c->vp[cur], c->vp[cur ^ 1], c->vq,
+                                                         c->fflag, L.nF, L.P, L.PL, cc, s, c->partials);
             cudaEvent_t e1 = samp ? prof_mark(c) : nullptr, e2 = samp ? prof_mark(c) : nullptr;
-            if (tiled)
-                k_update_q<HelmOp, true><<<tg.upd, tdim, 0, c->stream>>>(
-                    c->vx, c->vr, c->vp[cur ^ 1], c->vq, c->fflag, c->list_face, c->qmask_face, c->nact_face, tm, cc,
-                    s, c->partials);
-            else
+            if (tiled) {
+                if (mg)
+                    k_update_q<HelmOp, false><<<tg.upd, tdim, 0, c->stream>>>(
+                        c->vx, c->vr, c->vp[cur ^ 1], c->vq, c->fflag, c->list_face, c->qmask_face, c->nact_face, tm,
+                        cc, s, c->partials);
+                else
+                    k_update_q<HelmOp, true><<<tg.upd, tdim, 0, c->stream>>>(
+                        c->vx, c->vr, c->vp[cur ^ 1], c->vq, c->fflag, c->list_face, c->qmask_face, c->nact_face, tm,
+                        cc, s, c->partials);
+            } else if (mg) {
+                k_update<HelmOp, false><<<b4, TH, 0, c->stream>>>(c->vx, c->vr, c->vp[cur ^ 1], c->vq, c->fflag, n4,
+                                                                  cc, s, c->partials);
+            } else {
                 k_update<HelmOp, true><<<b4, TH, 0, c->stream>>>(c->vx, c->vr, c->vp[cur ^ 1], c->vq, c->fflag, n4,
                                                                  cc, s, c->partials);
+            }
             cudaEvent_t e3 = samp ? prof_mark(c) : nullptr;
             prof_add(c, K_V_SPMV, e0, e1, by_spmv);
             prof_add(c, K_V_UPDATE, e2, e3, by_upd);
             c->n_launches += 2;
+            if (mg)
+                if (int rc = precondition(0)) return rc;
             cur ^= 1;
         }
-        launched += c->prm.check_every;
+        launched += check;
         FS_CUDA(cudaGetLastError());
         int rc = read_scal(c, 1, &h);
         if (rc) return rc;
@@ -954,7 +988,7 @@ int precond_apply_public(fs_ctx *c, const float *r, float *z)
         k_jacobi<<<grid_blocks(c, L.nC, TH), TH, 0, c->stream>>>(c->pr, c->pz, c->cflag, L.nC);
         c->n_launches += 1;
     } else if (c->prm.precond == FS_PRECOND_MG) {
-        int rc = mg_apply(c, c->pr, c->pz);
+        int rc = mg_apply(c, c->pr, c->pz, nullptr);
         if (rc) return rc;
     } else if (c->prm.precond == FS_PRECOND_MIC0) {
         FS_CUDA(cudaMemsetAsync(c->err_word, 0, sizeof(unsigned), c->stream));
