@@ -368,7 +368,11 @@ def main():
     # ---- roofline of the dominant kernel -----------------------------------
     peaks = measured_peaks()
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
-    top = max((k for k in prof.items() if k[1][2] > 0), key=lambda kv: kv[1][1], default=None)
+    # the kernel with the largest estimated share of the step, among those with algorithmic bytes
+    sampled = ("pressure_spmv", "pressure_update", "visc_spmv", "visc_update", "fcg_vectors", "mg_smooth0",
+               "mg_vcycle_p", "mg_vcycle_v")
+    top = max((k for k in prof.items() if k[1][2] > 0 and k[1][0] > 0),
+              key=lambda kv: kv[1][1] * (PROFILE_PERIOD if kv[0] in sampled else 1), default=None)
     roofline = None
     if top:
         name, (launches, ms, by) = top
@@ -381,8 +385,7 @@ def main():
                     "algorithmic_bytes_per_launch": by / launches, "launches": launches,
                     "avg_launch_us": 1e3 * ms / launches,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback"}
-    # CG kernels are timed every PROFILE_PERIOD-th iteration, the others at every launch
-    sampled = ("pressure_spmv", "pressure_update", "visc_spmv", "visc_update", "fcg_vectors")
+    # CG kernels and V-cycles are timed every PROFILE_PERIOD-th iteration, the others at every launch
     kernels = {}
     for k, v in prof.items():
         if k == "all_kernels" or not v[0]:

@@ -88,7 +88,8 @@ static int alloc_zero(void **p, size_t bytes)
 
 // ---- per-kernel timing ---------------------------------------------------------
 static const char *kKernelNames[K_COUNT] = {"pressure_spmv", "pressure_update", "visc_spmv", "visc_update",
-                                            "advect", "advect_adjoint", "mic0_apply", "net_apply", "fcg_vectors"};
+                                            "advect", "advect_adjoint", "mic0_apply", "net_apply", "fcg_vectors",
+                                            "mg_smooth0", "mg_vcycle_p", "mg_vcycle_v"};
 
 struct Prof {
     std::vector<cudaEvent_t> free_ev, all_ev;

@@ -444,6 +444,9 @@ enum KernelId : int {
     K_MIC_APPLY,
     K_NET_APPLY,
     K_FCG_VEC,
+    K_MG_SMOOTH,    // the last damped-Jacobi sweep on level 0 of a pressure V-cycle
+    K_MG_VCYCLE_P,  // one pressure V-cycle (time only)
+    K_MG_VCYCLE_V,  // one viscosity V-cycle over the three face volumes (time only)
     K_COUNT
 };
 cudaEvent_t prof_mark(fs_ctx *c);   // records an event on the stream (nullptr when off)

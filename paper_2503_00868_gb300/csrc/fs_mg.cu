@@ -21,8 +21,10 @@
 // in one block. Every step is linear in r with symmetric smoothing and restriction
 // proportional to the transposed prolongation, so M is symmetric, as CG needs.
 //
-// Every kernel runs densely over a level's whole array and writes zero on cells
-// that are not liquid, so a stencil at the edge of the liquid reads zeros.
+// Every kernel walks a level's whole array. The work arrays are zeroed when the
+// hierarchy is built and only ever written on liquid cells, so a stencil at the
+// edge of the liquid reads zeros; the level-0 output (the solver's z) is written
+// densely, zeros included.
 //
 // The same V-cycle preconditions the implicit viscosity solve, one velocity
 // component at a time: each face volume is a box of unknown faces (FF_FLUID),
@@ -30,6 +32,7 @@
 // bits coincide with the cell bits used here (FF_FLUID = CF_LIQ, FF_FIXED =
 // CF_AIR, FF_N = CF_D), and the operator gains the mass term: A_l = m I +
 // 4^-l cc L_l with m = 1 (m = 0 for the pressure).
+#include <algorithm>
 #include <cmath>
 #include <new>
 
@@ -73,13 +76,19 @@ struct MgState {
     float coef = 0.f;      // operator coefficient it was built for
     bool own0 = true;      // level 0 work arrays belong to this hierarchy
     const int *done = nullptr;  // the calling solve's convergence flag (nullable)
+    long long calls = 0;        // applies so far (profiling samples every prof_period-th)
+    double smooth_bytes = 0.0;  // algorithmic bytes of one level-0 sweep (profiled when > 0)
 };
 
 // the pressure hierarchy and one per face volume (viscosity); the face volumes
 // share two level-0 work arrays of face-space length
+// the face volumes' V-cycles are independent: volumes 1 and 2 run on two side
+// streams, forked from and joined back to the context's stream
 struct MgAll {
     MgState cell, face[3];
     float *fb = nullptr, *fc = nullptr;
+    cudaStream_t side[2] = {nullptr, nullptr};
+    cudaEvent_t fork = nullptr, join[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -118,8 +127,8 @@ __global__ void __launch_bounds__(256) k_mg_smooth2(MgGrid g, const uint8_t *__r
     {
         const int t = row * g.sy + e;
         const uint8_t f = fl[t];
-        float v = 0.f;
         if (liq(f)) {
+            float v;
             const int d = f & CF_D;
             auto e1 = [&](int u) {
                 const uint8_t fu = fl[u];
@@ -128,15 +137,15 @@ __global__ void __launch_bounds__(256) k_mg_smooth2(MgGrid g, const uint8_t *__r
             const float c1 = e1(t);
             const float nb = (e1(t - 1) + e1(t + 1)) + (e1(t - g.sy) + e1(t + g.sy)) + (e1(t - g.sz) + e1(t + g.sz));
             v = c1 + wt[d] * (r[t] - m * c1 - scale * ((float)d * c1 - nb));
+            eo[t] = v;
         }
-        eo[t] = v;
     }
 }
 
 // e_out = e_in + omega D^-1 (r - A e_in)
 __global__ void __launch_bounds__(256) k_mg_smooth(MgGrid g, const uint8_t *__restrict__ fl,
                                                    const float *__restrict__ r, const float *__restrict__ ein,
-                                                   float *eout, float scale, float m, const int *done)
+                                                   float *eout, float scale, float m, int dense, const int *done)
 {
     if (done && *(volatile const int *)done) return;  // the solve has converged
     __shared__ float wt[8];
@@ -145,7 +154,10 @@ __global__ void __launch_bounds__(256) k_mg_smooth(MgGrid g, const uint8_t *__re
     {
         const int t = row * g.sy + e;
         const uint8_t f = fl[t];
-        eout[t] = liq(f) ? ein[t] + wt[f & CF_D] * (r[t] - m * ein[t] - scale * lap(ein, t, f, g)) : 0.f;
+        if (liq(f))
+            eout[t] = ein[t] + wt[f & CF_D] * (r[t] - m * ein[t] - scale * lap(ein, t, f, g));
+        else if (dense)
+            eout[t] = 0.f;
     }
 }
 
@@ -159,7 +171,7 @@ __global__ void __launch_bounds__(256) k_mg_residual(MgGrid g, const uint8_t *__
     {
         const int t = row * g.sy + e;
         const uint8_t f = fl[t];
-        res[t] = liq(f) ? r[t] - m * ev[t] - scale * lap(ev, t, f, g) : 0.f;
+        if (liq(f)) res[t] = r[t] - m * ev[t] - scale * lap(ev, t, f, g);
     }
 }
 
@@ -173,8 +185,8 @@ __global__ void __launch_bounds__(256) k_mg_restrict(MgGrid gf, const float *__r
     MG_FOR_ROWS(gc)
     {
         const int t = row * gc.sy + e;
-        float acc = 0.f;
         if (liq(flc[t])) {
+            float acc = 0.f;
             const int I = e - gc.ioff, J = row % gc.rpp - gc.joff, K = row / gc.rpp - gc.koff;
             for (int c = 0; c < 4; c++) {
                 const int k = 2 * K - 1 + c;
@@ -192,9 +204,8 @@ __global__ void __launch_bounds__(256) k_mg_restrict(MgGrid gf, const float *__r
                     acc += w[c] * w[b] * sr;
                 }
             }
-            acc *= 0.125f;
+            rc[t] = 0.125f * acc;
         }
-        rc[t] = acc;
     }
 }
 
@@ -296,6 +307,15 @@ __global__ void __launch_bounds__(TH) k_mg_coarse(MgGrid g, const uint8_t *__res
     for (int t = threadIdx.x; t < g.n; t += TH) e[t] = res[t];
 }
 
+// number of unknown cells of a level (once per mask, for the profiled byte count)
+__global__ void k_mg_count_liq(MgGrid g, const uint8_t *__restrict__ fl, unsigned long long *out)
+{
+    unsigned long long k = 0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < g.n; t += gridDim.x * blockDim.x) k += liq(fl[t]) ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+    if ((threadIdx.x & 31) == 0 && k) atomicAdd(out, k);
+}
+
 size_t coarse_smem(const MgGrid &g) { return (size_t)g.n * 13 + 16; }
 
 int row_blocks(fs_ctx *c, const MgGrid &g) { return grid_blocks(c, g.rows, 8); }
@@ -359,26 +379,32 @@ void free_levels(MgState *s)
     s->epoch = -1;
 }
 
-// The V-cycle on level l: r in lev[l].r, result in lev[l].a.
-int vcycle(fs_ctx *c, MgState *s, int l)
+// The V-cycle on level l: r in lev[l].r, result in lev[l].a. With `sample`, the
+// last level-0 sweep is timed.
+int vcycle(fs_ctx *c, MgState *s, int l, bool sample, cudaStream_t st)
 {
     MgLevel &v = s->lev[l];
     const MgGrid &g = v.g;
     if (l == s->nlev - 1) {
-        k_mg_coarse<<<1, TH, coarse_smem(g), c->stream>>>(g, v.fl, v.r, v.a, v.scale, v.mass, s->done);
+        k_mg_coarse<<<1, TH, coarse_smem(g), st>>>(g, v.fl, v.r, v.a, v.scale, v.mass, s->done);
         c->n_launches += 1;
         return FS_OK;
     }
     const int nb = row_blocks(c, g);
-    k_mg_smooth2<<<nb, RT, 0, c->stream>>>(g, v.fl, v.r, v.b, v.scale, v.mass, s->done);
-    k_mg_residual<<<nb, RT, 0, c->stream>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, s->done);
+    k_mg_smooth2<<<nb, RT, 0, st>>>(g, v.fl, v.r, v.b, v.scale, v.mass, s->done);
+    k_mg_residual<<<nb, RT, 0, st>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, s->done);
     MgLevel &w = s->lev[l + 1];
-    k_mg_restrict<<<row_blocks(c, w.g), RT, 0, c->stream>>>(g, v.c, w.g, w.fl, w.r, s->done);
+    k_mg_restrict<<<row_blocks(c, w.g), RT, 0, st>>>(g, v.c, w.g, w.fl, w.r, s->done);
     c->n_launches += 3;
-    if (int rc = vcycle(c, s, l + 1)) return rc;
-    k_mg_prolong<<<nb, RT, 0, c->stream>>>(g, v.fl, v.b, w.g, w.a, s->done);
-    k_mg_smooth<<<nb, RT, 0, c->stream>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, s->done);
-    k_mg_smooth<<<nb, RT, 0, c->stream>>>(g, v.fl, v.r, v.c, v.a, v.scale, v.mass, s->done);
+    if (int rc = vcycle(c, s, l + 1, false, st)) return rc;
+    k_mg_prolong<<<nb, RT, 0, st>>>(g, v.fl, v.b, w.g, w.a, s->done);
+    k_mg_smooth<<<nb, RT, 0, st>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, 0, s->done);
+    // a timed sweep always runs in full (an early exit would record work not done)
+    const bool timed = sample && l == 0 && s->smooth_bytes > 0.0;
+    cudaEvent_t e0 = timed ? prof_mark(c) : nullptr;
+    k_mg_smooth<<<nb, RT, 0, st>>>(g, v.fl, v.r, v.c, v.a, v.scale, v.mass, l == 0 ? 1 : 0,
+                                          timed ? nullptr : s->done);
+    if (timed) prof_add(c, K_MG_SMOOTH, e0, prof_mark(c), s->smooth_bytes);
     c->n_launches += 3;
     FS_CUDA(cudaGetLastError());
     return FS_OK;
@@ -434,18 +460,26 @@ int mg_build(fs_ctx *c, MgState *s, const MgGrid &g0, uint8_t *fl0, float *b0, f
     }
     if (s->lev[s->nlev - 1].g.n > MG_COARSE_CELLS)
         return set_error(FS_EINVAL, "multigrid: the coarsest level does not fit in shared memory");
+    // the least a level-0 sweep must move: the flag of every element, and r and e
+    // read and e written on the unknowns (the zeros it writes elsewhere are excess)
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(c->partials), nliq = 0;
+    FS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(nliq), c->stream));
+    k_mg_count_liq<<<grid_blocks(c, g0.n, TH), TH, 0, c->stream>>>(g0, fl0, cnt);
+    FS_CUDA(cudaMemcpyAsync(&nliq, cnt, sizeof(nliq), cudaMemcpyDeviceToHost, c->stream));
+    FS_CUDA(cudaStreamSynchronize(c->stream));
+    s->smooth_bytes = 1.0 * (double)g0.n + 12.0 * (double)nliq;
     s->epoch = c->mask_epoch;
     s->coef = coef;
     return FS_OK;
 }
 
-int apply_on(fs_ctx *c, MgState *s, const float *r, float *z, const int *done)
+int apply_on(fs_ctx *c, MgState *s, const float *r, float *z, const int *done, bool sample, cudaStream_t st)
 {
     s->done = done;
     MgLevel &l0 = s->lev[0];
     l0.r = const_cast<float *>(r);
     l0.a = z;
-    const int rc = vcycle(c, s, 0);
+    const int rc = vcycle(c, s, 0, sample, st);
     l0.r = nullptr;
     l0.a = nullptr;
     return rc;
@@ -471,6 +505,11 @@ void mg_free(fs_ctx *c)
     for (MgState &f : m->face) free_levels(&f);
     cudaFree(m->fb);
     cudaFree(m->fc);
+    for (int k = 0; k < 2; k++) {
+        if (m->side[k]) cudaStreamDestroy(m->side[k]);
+        if (m->join[k]) cudaEventDestroy(m->join[k]);
+    }
+    if (m->fork) cudaEventDestroy(m->fork);
     delete m;
     c->mg = nullptr;
 }
@@ -484,7 +523,11 @@ int mg_apply(fs_ctx *c, const float *r, float *z, const int *done)
     if (m->cell.epoch != c->mask_epoch)
         if (int rc = mg_build(c, &m->cell, level0_grid(L, L.nx, L.ny, L.nz), c->cflag, nullptr, nullptr, 1.f, 0.f))
             return rc;
-    return apply_on(c, &m->cell, r, z, done);
+    const bool sample = c->prof_on && (m->cell.calls++ % std::max(1, c->prof_period)) == 0;
+    cudaEvent_t e0 = sample ? prof_mark(c) : nullptr;
+    const int rc = apply_on(c, &m->cell, r, z, done, sample, c->stream);
+    if (sample) prof_add(c, K_MG_VCYCLE_P, e0, prof_mark(c), 0.0);
+    return rc;
 }
 
 // z = M r on the face space for the Helmholtz operator I + cc L of the viscosity
@@ -504,7 +547,18 @@ int mg_apply_faces(fs_ctx *c, const float *r, float *z, float cc, const int *don
         }
         FS_CUDA(cudaMemsetAsync(m->fb, 0, (size_t)L.nF * 4, c->stream));
         FS_CUDA(cudaMemsetAsync(m->fc, 0, (size_t)L.nF * 4, c->stream));
+        for (int k = 0; k < 2; k++) {
+            FS_CUDA(cudaStreamCreateWithFlags(&m->side[k], cudaStreamNonBlocking));
+            FS_CUDA(cudaEventCreateWithFlags(&m->join[k], cudaEventDisableTiming));
+        }
+        FS_CUDA(cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming));
     }
+    if (m->face[0].epoch != c->mask_epoch) {  // new mask: the shared work arrays start from zero again
+        FS_CUDA(cudaMemsetAsync(m->fb, 0, (size_t)L.nF * 4, c->stream));
+        FS_CUDA(cudaMemsetAsync(m->fc, 0, (size_t)L.nF * 4, c->stream));
+    }
+    const bool sample = c->prof_on && (m->face[0].calls++ % std::max(1, c->prof_period)) == 0;
+    cudaEvent_t e0 = sample ? prof_mark(c) : nullptr;
     for (int k = 0; k < 3; k++) {
         MgState &s = m->face[k];
         const size_t base = (size_t)L.face_origin(k) - L.PL;  // the volume's leading guard plane
@@ -516,8 +570,21 @@ int mg_apply_faces(fs_ctx *c, const float *r, float *z, float cc, const int *don
             for (int l = 0; l < s.nlev; l++, sc *= 0.25f) s.lev[l].scale = sc;
             s.coef = cc;
         }
-        if (int rc = apply_on(c, &s, r + base, z + base, done)) return rc;
     }
+    // volume 0 on the context's stream, 1 and 2 beside it (their sweeps share the
+    // GPU, so none is timed alone: the profiled sweep is the pressure V-cycle's)
+    FS_CUDA(cudaEventRecord(m->fork, c->stream));
+    for (int k = 0; k < 2; k++) FS_CUDA(cudaStreamWaitEvent(m->side[k], m->fork, 0));
+    for (int k = 2; k >= 0; k--) {
+        const size_t base = (size_t)L.face_origin(k) - L.PL;
+        cudaStream_t st = k == 0 ? c->stream : m->side[k - 1];
+        if (int rc = apply_on(c, &m->face[k], r + base, z + base, done, false, st)) return rc;
+    }
+    for (int k = 0; k < 2; k++) {
+        FS_CUDA(cudaEventRecord(m->join[k], m->side[k]));
+        FS_CUDA(cudaStreamWaitEvent(c->stream, m->join[k], 0));
+    }
+    if (sample) prof_add(c, K_MG_VCYCLE_V, e0, prof_mark(c), 0.0);
     return FS_OK;
 }
 
