@@ -43,10 +43,11 @@ UNIT = "cell-steps/s"
 # the files that define the kernel and the data layout it reads, and is reported
 # only while those files are unchanged (capture commands in profiles/).
 NCU_TRAFFIC = {
-    # ncu --set full on the benchmark's 256^3 blob (profiles/cg_kernels_256_ncu.md); DRAM writes
-    # still held dirty in L2 when the kernel ends are not counted
-    "pressure_spmv": {"bytes_per_launch": 122095872 + 24217344, "source": "c05aabbc521428b2"},
-    "pressure_update": {"bytes_per_launch": 139048448 + 19815168, "source": "c05aabbc521428b2"},
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on the benchmark's 256^3 blob with the
+    # multigrid preconditioner (profiles/fwd_adjoint_256.md); DRAM writes still held dirty in L2
+    # when the kernel ends are not counted
+    "visc_spmv": {"bytes_per_launch": 342685440 + 134320896, "source": "5e31bb1c3ef8787b"},
+    "visc_update": {"bytes_per_launch": 387683584 + 125340416, "source": "5e31bb1c3ef8787b"},
 }
 KERNEL_FILES = ("fs_stencil.cuh", "fs_tma.cuh", "fs_mask.cu")
 
@@ -209,8 +210,9 @@ def workload_config(a):
 
 def precond_compare(n, seeds=(0,)):
     """Projection of an unblurred N(0,1) MAC field (the stress right-hand side) on
-    a union of 8 spheres at n^3, to relative residual 1e-6, with Jacobi, MIC(0)
-    and the shipped learned network (flexible CG): device wall time of fs_project
+    a union of 8 spheres at n^3, to relative residual 1e-6, with Jacobi, MIC(0),
+    the multigrid V-cycle and the shipped learned network (flexible CG): device
+    wall time of fs_project
     (CUDA events, after one warm-up solve), iterations, true residual."""
     import torch
     from paper_2503_00868_gb300 import fluidstep as F
@@ -218,7 +220,8 @@ def precond_compare(n, seeds=(0,)):
     from paper_2503_00868_gb300 import workloads as W
     out = {"workload": f"projection of a divergent N(0,1) MAC field on a union of 8 spheres at {n}^3, "
                        "tol 1e-6, maxit 20000", "rows": []}
-    pcs = (("jacobi", F.FS_PRECOND_JACOBI), ("mic0", F.FS_PRECOND_MIC0), ("learned", F.FS_PRECOND_LEARNED))
+    pcs = (("jacobi", F.FS_PRECOND_JACOBI), ("mic0", F.FS_PRECOND_MIC0), ("mg", F.FS_PRECOND_MG),
+           ("learned", F.FS_PRECOND_LEARNED))
     for seed in seeds:
         types, info = W.sphere_union(n, n, n, seed)
         row = {"seed": seed, "occupancy": info["occupancy"]}
