@@ -230,6 +230,162 @@ __global__ void __launch_bounds__(256) k_mg_prolong(MgGrid gf, const uint8_t *__
     }
 }
 
+// ---- level 0: four elements per thread ---------------------------------------
+// Level 0 (the cell space or a face volume) has a row pitch and origin that are
+// multiples of 4, so a quad of 4 consecutive elements never crosses a row and its
+// float4 / uchar4 loads are aligned. A quad without an unknown is skipped; a quad
+// with one is read whole (its row is interior, so every neighbour load is inside
+// the array) and written whole, with zeros on the elements that are not unknowns.
+
+__device__ __forceinline__ float4 ld4g(const float *__restrict__ p, int t)
+{
+    return __ldg(reinterpret_cast<const float4 *>(p + t));
+}
+__device__ __forceinline__ uchar4 ldf4(const uint8_t *__restrict__ p, int t)
+{
+    return __ldg(reinterpret_cast<const uchar4 *>(p + t));
+}
+__device__ __forceinline__ bool any_liq(uchar4 f) { return ((f.x | f.y | f.z | f.w) & CF_LIQ) != 0; }
+
+// e_out on one element from e_in: c (centre), the sum of its six neighbours nb
+__device__ __forceinline__ float sweep1(uint8_t f, float c, float nb, float rv, const float *wt, float scale, float m)
+{
+    return liq(f) ? c + wt[f & CF_D] * (rv - m * c - scale * ((float)(f & CF_D) * c - nb)) : 0.f;
+}
+
+__global__ void __launch_bounds__(256) k_mg0_smooth(MgGrid g, const uint8_t *__restrict__ fl,
+                                                    const float *__restrict__ r, const float *__restrict__ ein,
+                                                    float *eout, float scale, float m, int dense, const int *done)
+{
+    if (done && *(volatile const int *)done) return;  // the solve has converged
+    __shared__ float wt[8];
+    fill_wtab(wt, scale, m);
+    const int nq = g.n >> 2;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+        const int t = q << 2;
+        const uchar4 f = ldf4(fl, t);
+        if (!any_liq(f)) {
+            if (dense) *reinterpret_cast<float4 *>(eout + t) = make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
+        const float4 c = ld4g(ein, t), rv = ld4g(r, t);
+        const float4 dn = ld4g(ein, t - g.sy), up = ld4g(ein, t + g.sy);
+        const float4 bk = ld4g(ein, t - g.sz), fw = ld4g(ein, t + g.sz);
+        const float lf = __ldg(ein + t - 1), rt = __ldg(ein + t + 4);
+        float4 v;
+        v.x = sweep1(f.x, c.x, (lf + c.y) + (dn.x + up.x) + (bk.x + fw.x), rv.x, wt, scale, m);
+        v.y = sweep1(f.y, c.y, (c.x + c.z) + (dn.y + up.y) + (bk.y + fw.y), rv.y, wt, scale, m);
+        v.z = sweep1(f.z, c.z, (c.y + c.w) + (dn.z + up.z) + (bk.z + fw.z), rv.z, wt, scale, m);
+        v.w = sweep1(f.w, c.w, (c.z + rt) + (dn.w + up.w) + (bk.w + fw.w), rv.w, wt, scale, m);
+        *reinterpret_cast<float4 *>(eout + t) = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_mg0_residual(MgGrid g, const uint8_t *__restrict__ fl,
+                                                      const float *__restrict__ r, const float *__restrict__ ev,
+                                                      float *res, float scale, float m, const int *done)
+{
+    if (done && *(volatile const int *)done) return;  // the solve has converged
+    const int nq = g.n >> 2;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+        const int t = q << 2;
+        const uchar4 f = ldf4(fl, t);
+        if (!any_liq(f)) continue;
+        const float4 c = ld4g(ev, t), rv = ld4g(r, t);
+        const float4 dn = ld4g(ev, t - g.sy), up = ld4g(ev, t + g.sy);
+        const float4 bk = ld4g(ev, t - g.sz), fw = ld4g(ev, t + g.sz);
+        const float lf = __ldg(ev + t - 1), rt = __ldg(ev + t + 4);
+        auto one = [&](uint8_t fe, float ce, float nb, float re) {
+            return liq(fe) ? re - m * ce - scale * ((float)(fe & CF_D) * ce - nb) : 0.f;
+        };
+        float4 v;
+        v.x = one(f.x, c.x, (lf + c.y) + (dn.x + up.x) + (bk.x + fw.x), rv.x);
+        v.y = one(f.y, c.y, (c.x + c.z) + (dn.y + up.y) + (bk.y + fw.y), rv.y);
+        v.z = one(f.z, c.z, (c.y + c.w) + (dn.z + up.z) + (bk.z + fw.z), rv.z);
+        v.w = one(f.w, c.w, (c.z + rt) + (dn.w + up.w) + (bk.w + fw.w), rv.w);
+        *reinterpret_cast<float4 *>(res + t) = v;
+    }
+}
+
+// the first two sweeps from e = 0: e1 = omega D^-1 r on the fly, then one sweep
+__global__ void __launch_bounds__(256) k_mg0_smooth2(MgGrid g, const uint8_t *__restrict__ fl,
+                                                     const float *__restrict__ r, float *eo, float scale, float m,
+                                                     const int *done)
+{
+    if (done && *(volatile const int *)done) return;  // the solve has converged
+    __shared__ float wt[8];
+    fill_wtab(wt, scale, m);
+    const int nq = g.n >> 2;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+        const int t = q << 2;
+        const uchar4 f = ldf4(fl, t);
+        if (!any_liq(f)) continue;
+        auto e1q = [&](int u) {  // e1 on the quad at u
+            const uchar4 fu = ldf4(fl, u);
+            const float4 ru = ld4g(r, u);
+            return make_float4(liq(fu.x) ? wt[fu.x & CF_D] * ru.x : 0.f, liq(fu.y) ? wt[fu.y & CF_D] * ru.y : 0.f,
+                               liq(fu.z) ? wt[fu.z & CF_D] * ru.z : 0.f, liq(fu.w) ? wt[fu.w & CF_D] * ru.w : 0.f);
+        };
+        auto e1s = [&](int u) {
+            const uint8_t fu = fl[u];
+            return liq(fu) ? wt[fu & CF_D] * __ldg(r + u) : 0.f;
+        };
+        const float4 c = e1q(t), rv = ld4g(r, t);
+        const float4 dn = e1q(t - g.sy), up = e1q(t + g.sy), bk = e1q(t - g.sz), fw = e1q(t + g.sz);
+        const float lf = e1s(t - 1), rt = e1s(t + 4);
+        float4 v;
+        v.x = sweep1(f.x, c.x, (lf + c.y) + (dn.x + up.x) + (bk.x + fw.x), rv.x, wt, scale, m);
+        v.y = sweep1(f.y, c.y, (c.x + c.z) + (dn.y + up.y) + (bk.y + fw.y), rv.y, wt, scale, m);
+        v.z = sweep1(f.z, c.z, (c.y + c.w) + (dn.z + up.z) + (bk.z + fw.z), rv.z, wt, scale, m);
+        v.w = sweep1(f.w, c.w, (c.z + rt) + (dn.w + up.w) + (bk.w + fw.w), rv.w, wt, scale, m);
+        *reinterpret_cast<float4 *>(eo + t) = v;
+    }
+}
+
+// e_fine += P e_coarse on the unknowns of a quad (in place). The quad's elements
+// i .. i + 3 (i a multiple of 4) take their x samples from coarse I0 - 1 .. I0 + 2
+// (I0 = i / 2); indices past the coarse halo are clamped to it (a sample that
+// only padding elements use).
+__global__ void __launch_bounds__(256) k_mg0_prolong(MgGrid gf, const uint8_t *__restrict__ fl, float *ef,
+                                                     MgGrid gc, const float *__restrict__ ec, const int *done)
+{
+    if (done && *(volatile const int *)done) return;  // the solve has converged
+    const int nq = gf.n >> 2;
+    const int qrow = gf.sy >> 2;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+        const int t = q << 2;
+        const uchar4 f = ldf4(fl, t);
+        if (!any_liq(f)) continue;
+        const int row = q / qrow, e = (q - row * qrow) << 2;
+        const int i = e - gf.ioff, j = row % gf.rpp - gf.joff, k = row / gf.rpp - gf.koff;
+        const int I0 = i >> 1, J = j >> 1, K = k >> 1;
+        const int J2 = (j & 1) ? J + 1 : J - 1, K2 = (k & 1) ? K + 1 : K - 1;
+        const int xs[4] = {max(I0 - 1, -1), I0, min(I0 + 1, gc.nx), min(I0 + 2, gc.nx)};
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        const int jj[2] = {J, J2}, kk[2] = {K, K2};
+        const float wy[2] = {0.75f, 0.25f};
+#pragma unroll
+        for (int b = 0; b < 2; b++)
+#pragma unroll
+            for (int a = 0; a < 2; a++) {
+                const int base = gc.idx(0, jj[a], kk[b]);
+                const float w = wy[a] * wy[b];
+                const float cm = __ldg(ec + base + xs[0]), c0 = __ldg(ec + base + xs[1]);
+                const float c1 = __ldg(ec + base + xs[2]), c2 = __ldg(ec + base + xs[3]);
+                s0 += w * (0.75f * c0 + 0.25f * cm);
+                s1 += w * (0.75f * c0 + 0.25f * c1);
+                s2 += w * (0.75f * c1 + 0.25f * c0);
+                s3 += w * (0.75f * c1 + 0.25f * c2);
+            }
+        float4 v = *reinterpret_cast<const float4 *>(ef + t);
+        if (liq(f.x)) v.x += s0;
+        if (liq(f.y)) v.y += s1;
+        if (liq(f.z)) v.z += s2;
+        if (liq(f.w)) v.w += s3;
+        *reinterpret_cast<float4 *>(ef + t) = v;
+    }
+}
+
 // coarse flags from the level above: air if any child is air, else liquid if any
 // child is liquid; the halo stays solid (zero)
 __global__ void k_mg_coarsen(MgGrid gf, const uint8_t *__restrict__ flf, MgGrid gc, uint8_t *flc)
@@ -391,19 +547,33 @@ int vcycle(fs_ctx *c, MgState *s, int l, bool sample, cudaStream_t st)
         return FS_OK;
     }
     const int nb = row_blocks(c, g);
-    k_mg_smooth2<<<nb, RT, 0, st>>>(g, v.fl, v.r, v.b, v.scale, v.mass, s->done);
-    k_mg_residual<<<nb, RT, 0, st>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, s->done);
+    const bool quad = l == 0;  // level 0: four elements per thread
+    const int nq = grid_blocks(c, g.n / 4, TH);
+    if (quad) {
+        k_mg0_smooth2<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.b, v.scale, v.mass, s->done);
+        k_mg0_residual<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, s->done);
+    } else {
+        k_mg_smooth2<<<nb, RT, 0, st>>>(g, v.fl, v.r, v.b, v.scale, v.mass, s->done);
+        k_mg_residual<<<nb, RT, 0, st>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, s->done);
+    }
     MgLevel &w = s->lev[l + 1];
     k_mg_restrict<<<row_blocks(c, w.g), RT, 0, st>>>(g, v.c, w.g, w.fl, w.r, s->done);
     c->n_launches += 3;
     if (int rc = vcycle(c, s, l + 1, false, st)) return rc;
-    k_mg_prolong<<<nb, RT, 0, st>>>(g, v.fl, v.b, w.g, w.a, s->done);
-    k_mg_smooth<<<nb, RT, 0, st>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, 0, s->done);
+    if (quad) {
+        k_mg0_prolong<<<nq, TH, 0, st>>>(g, v.fl, v.b, w.g, w.a, s->done);
+        k_mg0_smooth<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, 0, s->done);
+    } else {
+        k_mg_prolong<<<nb, RT, 0, st>>>(g, v.fl, v.b, w.g, w.a, s->done);
+        k_mg_smooth<<<nb, RT, 0, st>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, 0, s->done);
+    }
     // a timed sweep always runs in full (an early exit would record work not done)
     const bool timed = sample && l == 0 && s->smooth_bytes > 0.0;
     cudaEvent_t e0 = timed ? prof_mark(c) : nullptr;
-    k_mg_smooth<<<nb, RT, 0, st>>>(g, v.fl, v.r, v.c, v.a, v.scale, v.mass, l == 0 ? 1 : 0,
-                                          timed ? nullptr : s->done);
+    if (quad)
+        k_mg0_smooth<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.c, v.a, v.scale, v.mass, 1, timed ? nullptr : s->done);
+    else
+        k_mg_smooth<<<nb, RT, 0, st>>>(g, v.fl, v.r, v.c, v.a, v.scale, v.mass, 0, timed ? nullptr : s->done);
     if (timed) prof_add(c, K_MG_SMOOTH, e0, prof_mark(c), s->smooth_bytes);
     c->n_launches += 3;
     FS_CUDA(cudaGetLastError());
