@@ -386,6 +386,47 @@ __global__ void __launch_bounds__(256) k_mg0_prolong(MgGrid gf, const uint8_t *_
     }
 }
 
+// Restriction from level 0: one thread per pair of coarse cells (2m, 2m + 1) of
+// an interior coarse row. Per fine row of the 4 x 4 window it reads the aligned
+// quad 4m .. 4m + 3 and the scalars at 4m - 1 and 4m + 4 (excluded at or past nx,
+// where the next row begins), and forms both cells' x weights from them.
+__global__ void __launch_bounds__(256) k_mg0_restrict(MgGrid gf, const float *__restrict__ res, MgGrid gc,
+                                                      const uint8_t *__restrict__ flc, float *rc, const int *done)
+{
+    if (done && *(volatile const int *)done) return;  // the solve has converged
+    const int npair = (gc.nx + 1) >> 1;
+    const long long items = (long long)npair * gc.ny * gc.nz;
+    const float w[4] = {0.25f, 0.75f, 0.75f, 0.25f};
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
+         it += (long long)gridDim.x * blockDim.x) {
+        const int m = (int)(it % npair);
+        const long long jk = it / npair;
+        const int J = (int)(jk % gc.ny), K = (int)(jk / gc.ny);
+        const int I0 = 2 * m, t0 = gc.idx(I0, J, K);
+        const bool l0 = liq(flc[t0]), l1 = I0 + 1 < gc.nx && liq(flc[t0 + 1]);
+        if (!l0 && !l1) continue;
+        float a0 = 0.f, a1 = 0.f;
+        for (int c = 0; c < 4; c++) {
+            const int k = 2 * K - 1 + c;
+            if (k < 0 || k >= gf.nz) continue;
+            for (int b = 0; b < 4; b++) {
+                const int j = 2 * J - 1 + b;
+                if (j < 0 || j >= gf.ny) continue;
+                const int row = gf.idx(0, j, k) + 4 * m;  // a multiple of 4
+                const float4 qd = ld4g(res, row);
+                const float lf = m > 0 ? __ldg(res + row - 1) : 0.f;
+                const float rt = 4 * m + 4 < gf.nx ? __ldg(res + row + 4) : 0.f;
+                const float wyz = w[c] * w[b];
+                // coarse 2m: fine 4m - 1 .. 4m + 2; coarse 2m + 1: fine 4m + 1 .. 4m + 4
+                a0 += wyz * (0.25f * lf + 0.75f * qd.x + 0.75f * qd.y + 0.25f * qd.z);
+                a1 += wyz * (0.25f * qd.y + 0.75f * qd.z + 0.75f * qd.w + 0.25f * rt);
+            }
+        }
+        if (l0) rc[t0] = 0.125f * a0;
+        if (l1) rc[t0 + 1] = 0.125f * a1;
+    }
+}
+
 // coarse flags from the level above: air if any child is air, else liquid if any
 // child is liquid; the halo stays solid (zero)
 __global__ void k_mg_coarsen(MgGrid gf, const uint8_t *__restrict__ flf, MgGrid gc, uint8_t *flc)
@@ -557,7 +598,11 @@ int vcycle(fs_ctx *c, MgState *s, int l, bool sample, cudaStream_t st)
         k_mg_residual<<<nb, RT, 0, st>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, s->done);
     }
     MgLevel &w = s->lev[l + 1];
-    k_mg_restrict<<<row_blocks(c, w.g), RT, 0, st>>>(g, v.c, w.g, w.fl, w.r, s->done);
+    if (quad)
+        k_mg0_restrict<<<grid_blocks(c, (long long)((w.g.nx + 1) / 2) * w.g.ny * w.g.nz, TH), TH, 0, st>>>(
+            g, v.c, w.g, w.fl, w.r, s->done);
+    else
+        k_mg_restrict<<<row_blocks(c, w.g), RT, 0, st>>>(g, v.c, w.g, w.fl, w.r, s->done);
     c->n_launches += 3;
     if (int rc = vcycle(c, s, l + 1, false, st)) return rc;
     if (quad) {
