@@ -538,19 +538,22 @@ MgGrid level0_grid(const Layout &L, int nx, int ny, int nz)
     return g;
 }
 
+// a coarse level: a solid halo of one plane and one row on each side, and of 4
+// elements before each row (at least 1 after it), with the row pitch a multiple
+// of 4, so that its quads are aligned like level 0's
 MgGrid coarse_grid(int nx, int ny, int nz)
 {
     MgGrid g;
     g.nx = nx;
     g.ny = ny;
     g.nz = nz;
-    g.sy = nx + 2;
-    g.sz = (nx + 2) * (ny + 2);
-    g.origin = g.sz + g.sy + 1;
+    g.sy = (nx + 5 + 3) / 4 * 4;
+    g.sz = g.sy * (ny + 2);
+    g.origin = g.sz + g.sy + 4;
     g.n = g.sz * (nz + 2);
     g.rows = (ny + 2) * (nz + 2);
     g.rpp = ny + 2;
-    g.ioff = 1;
+    g.ioff = 4;
     g.joff = 1;
     g.koff = 1;
     return g;
@@ -588,7 +591,9 @@ int vcycle(fs_ctx *c, MgState *s, int l, bool sample, cudaStream_t st)
         return FS_OK;
     }
     const int nb = row_blocks(c, g);
-    const bool quad = l == 0;  // level 0: four elements per thread
+    // four elements per thread where the rows are quad-aligned (level 0 and, with
+    // their 4-element x halo, the coarse levels)
+    const bool quad = g.sy % 4 == 0 && g.origin % 4 == 0 && g.n % 4 == 0;
     const int nq = grid_blocks(c, g.n / 4, TH);
     if (quad) {
         k_mg0_smooth2<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.b, v.scale, v.mass, s->done);
