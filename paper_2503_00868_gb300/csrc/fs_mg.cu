@@ -115,124 +115,10 @@ __device__ __forceinline__ void fill_wtab(float *wt, float scale, float m)
     __syncthreads();
 }
 
-// the first two sweeps from e = 0 in one pass: e1 = omega D^-1 r is formed on
-// the fly at the cell and its six neighbours, then e2 = e1 + omega D^-1 (r - A e1)
-__global__ void __launch_bounds__(256) k_mg_smooth2(MgGrid g, const uint8_t *__restrict__ fl,
-                                                    const float *__restrict__ r, float *eo, float scale, float m, const int *done)
-{
-    if (done && *(volatile const int *)done) return;  // the solve has converged
-    __shared__ float wt[8];
-    fill_wtab(wt, scale, m);
-    MG_FOR_ROWS(g)
-    {
-        const int t = row * g.sy + e;
-        const uint8_t f = fl[t];
-        if (liq(f)) {
-            float v;
-            const int d = f & CF_D;
-            auto e1 = [&](int u) {
-                const uint8_t fu = fl[u];
-                return liq(fu) ? wt[fu & CF_D] * r[u] : 0.f;
-            };
-            const float c1 = e1(t);
-            const float nb = (e1(t - 1) + e1(t + 1)) + (e1(t - g.sy) + e1(t + g.sy)) + (e1(t - g.sz) + e1(t + g.sz));
-            v = c1 + wt[d] * (r[t] - m * c1 - scale * ((float)d * c1 - nb));
-            eo[t] = v;
-        }
-    }
-}
-
-// e_out = e_in + omega D^-1 (r - A e_in)
-__global__ void __launch_bounds__(256) k_mg_smooth(MgGrid g, const uint8_t *__restrict__ fl,
-                                                   const float *__restrict__ r, const float *__restrict__ ein,
-                                                   float *eout, float scale, float m, int dense, const int *done)
-{
-    if (done && *(volatile const int *)done) return;  // the solve has converged
-    __shared__ float wt[8];
-    fill_wtab(wt, scale, m);
-    MG_FOR_ROWS(g)
-    {
-        const int t = row * g.sy + e;
-        const uint8_t f = fl[t];
-        if (liq(f))
-            eout[t] = ein[t] + wt[f & CF_D] * (r[t] - m * ein[t] - scale * lap(ein, t, f, g));
-        else if (dense)
-            eout[t] = 0.f;
-    }
-}
-
-// res = r - A e
-__global__ void __launch_bounds__(256) k_mg_residual(MgGrid g, const uint8_t *__restrict__ fl,
-                                                     const float *__restrict__ r, const float *__restrict__ ev,
-                                                     float *res, float scale, float m, const int *done)
-{
-    if (done && *(volatile const int *)done) return;  // the solve has converged
-    MG_FOR_ROWS(g)
-    {
-        const int t = row * g.sy + e;
-        const uint8_t f = fl[t];
-        if (liq(f)) res[t] = r[t] - m * ev[t] - scale * lap(ev, t, f, g);
-    }
-}
-
-// coarse r = (1/8) sum over the 4 x 4 x 4 fine window of w_a w_b w_c res_fine,
-// w = (1/4, 3/4, 3/4, 1/4) at fine indices 2I - 1 .. 2I + 2
-__global__ void __launch_bounds__(256) k_mg_restrict(MgGrid gf, const float *__restrict__ res, MgGrid gc,
-                                                     const uint8_t *__restrict__ flc, float *rc, const int *done)
-{
-    if (done && *(volatile const int *)done) return;  // the solve has converged
-    const float w[4] = {0.25f, 0.75f, 0.75f, 0.25f};
-    MG_FOR_ROWS(gc)
-    {
-        const int t = row * gc.sy + e;
-        if (liq(flc[t])) {
-            float acc = 0.f;
-            const int I = e - gc.ioff, J = row % gc.rpp - gc.joff, K = row / gc.rpp - gc.koff;
-            for (int c = 0; c < 4; c++) {
-                const int k = 2 * K - 1 + c;
-                if (k < 0 || k >= gf.nz) continue;
-                for (int b = 0; b < 4; b++) {
-                    const int j = 2 * J - 1 + b;
-                    if (j < 0 || j >= gf.ny) continue;
-                    const int frow = gf.idx(0, j, k);
-                    float sr = 0.f;
-#pragma unroll
-                    for (int a = 0; a < 4; a++) {
-                        const int i = 2 * I - 1 + a;
-                        if (i >= 0 && i < gf.nx) sr += w[a] * res[frow + i];
-                    }
-                    acc += w[c] * w[b] * sr;
-                }
-            }
-            rc[t] = 0.125f * acc;
-        }
-    }
-}
-
-// e_fine += P e_coarse on liquid fine cells (in place)
-__global__ void __launch_bounds__(256) k_mg_prolong(MgGrid gf, const uint8_t *__restrict__ fl, float *ef,
-                                                    MgGrid gc, const float *__restrict__ ec, const int *done)
-{
-    if (done && *(volatile const int *)done) return;  // the solve has converged
-    MG_FOR_ROWS(gf)
-    {
-        const int t = row * gf.sy + e;
-        if (!liq(fl[t])) continue;
-        const int i = e - gf.ioff, j = row % gf.rpp - gf.joff, k = row / gf.rpp - gf.koff;
-        const int I = i >> 1, J = j >> 1, K = k >> 1;
-        const int I2 = (i & 1) ? I + 1 : I - 1, J2 = (j & 1) ? J + 1 : J - 1, K2 = (k & 1) ? K + 1 : K - 1;
-        // coarse indices -1 and n land in the coarse halo, which holds zeros
-        const float v = 0.421875f * ec[gc.idx(I, J, K)] +
-                        0.140625f * (ec[gc.idx(I2, J, K)] + ec[gc.idx(I, J2, K)] + ec[gc.idx(I, J, K2)]) +
-                        0.046875f * (ec[gc.idx(I2, J2, K)] + ec[gc.idx(I2, J, K2)] + ec[gc.idx(I, J2, K2)]) +
-                        0.015625f * ec[gc.idx(I2, J2, K2)];
-        ef[t] += v;
-    }
-}
-
-// ---- level 0: four elements per thread ---------------------------------------
-// Level 0 (the cell space or a face volume) has a row pitch and origin that are
-// multiples of 4, so a quad of 4 consecutive elements never crosses a row and its
+// ---- four elements per thread -------------------------------------------------
+// Every level but the coarsest has a row pitch, plane stride and origin that are
+// multiples of 4 (level 0 by the context's layout, a coarse level by its 4-element
+// x halo), so a quad of 4 consecutive elements never crosses a row and its
 // float4 / uchar4 loads are aligned. A quad without an unknown is skipped; a quad
 // with one is read whole (its row is interior, so every neighbour load is inside
 // the array) and written whole, with zeros on the elements that are not unknowns.
@@ -590,40 +476,22 @@ int vcycle(fs_ctx *c, MgState *s, int l, bool sample, cudaStream_t st)
         c->n_launches += 1;
         return FS_OK;
     }
-    const int nb = row_blocks(c, g);
-    // four elements per thread where the rows are quad-aligned (level 0 and, with
-    // their 4-element x halo, the coarse levels)
-    const bool quad = g.sy % 4 == 0 && g.origin % 4 == 0 && g.n % 4 == 0;
+    // four elements per thread: every level but the coarsest has quad-aligned rows
     const int nq = grid_blocks(c, g.n / 4, TH);
-    if (quad) {
-        k_mg0_smooth2<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.b, v.scale, v.mass, s->done);
-        k_mg0_residual<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, s->done);
-    } else {
-        k_mg_smooth2<<<nb, RT, 0, st>>>(g, v.fl, v.r, v.b, v.scale, v.mass, s->done);
-        k_mg_residual<<<nb, RT, 0, st>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, s->done);
-    }
+    k_mg0_smooth2<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.b, v.scale, v.mass, s->done);
+    k_mg0_residual<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, s->done);
     MgLevel &w = s->lev[l + 1];
-    if (quad)
-        k_mg0_restrict<<<grid_blocks(c, (long long)((w.g.nx + 1) / 2) * w.g.ny * w.g.nz, TH), TH, 0, st>>>(
-            g, v.c, w.g, w.fl, w.r, s->done);
-    else
-        k_mg_restrict<<<row_blocks(c, w.g), RT, 0, st>>>(g, v.c, w.g, w.fl, w.r, s->done);
+    k_mg0_restrict<<<grid_blocks(c, (long long)((w.g.nx + 1) / 2) * w.g.ny * w.g.nz, TH), TH, 0, st>>>(
+        g, v.c, w.g, w.fl, w.r, s->done);
     c->n_launches += 3;
     if (int rc = vcycle(c, s, l + 1, false, st)) return rc;
-    if (quad) {
-        k_mg0_prolong<<<nq, TH, 0, st>>>(g, v.fl, v.b, w.g, w.a, s->done);
-        k_mg0_smooth<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, 0, s->done);
-    } else {
-        k_mg_prolong<<<nb, RT, 0, st>>>(g, v.fl, v.b, w.g, w.a, s->done);
-        k_mg_smooth<<<nb, RT, 0, st>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, 0, s->done);
-    }
+    k_mg0_prolong<<<nq, TH, 0, st>>>(g, v.fl, v.b, w.g, w.a, s->done);
+    k_mg0_smooth<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, 0, s->done);
     // a timed sweep always runs in full (an early exit would record work not done)
     const bool timed = sample && l == 0 && s->smooth_bytes > 0.0;
     cudaEvent_t e0 = timed ? prof_mark(c) : nullptr;
-    if (quad)
-        k_mg0_smooth<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.c, v.a, v.scale, v.mass, 1, timed ? nullptr : s->done);
-    else
-        k_mg_smooth<<<nb, RT, 0, st>>>(g, v.fl, v.r, v.c, v.a, v.scale, v.mass, 0, timed ? nullptr : s->done);
+    k_mg0_smooth<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.c, v.a, v.scale, v.mass, l == 0 ? 1 : 0,
+                                    timed ? nullptr : s->done);
     if (timed) prof_add(c, K_MG_SMOOTH, e0, prof_mark(c), s->smooth_bytes);
     c->n_launches += 3;
     FS_CUDA(cudaGetLastError());
@@ -680,6 +548,11 @@ int mg_build(fs_ctx *c, MgState *s, const MgGrid &g0, uint8_t *fl0, float *b0, f
     }
     if (s->lev[s->nlev - 1].g.n > MG_COARSE_CELLS)
         return set_error(FS_EINVAL, "multigrid: the coarsest level does not fit in shared memory");
+    for (int l = 0; l + 1 < s->nlev; l++) {  // the quad kernels' alignment (true by construction)
+        const MgGrid &g = s->lev[l].g;
+        if (g.sy % 4 || g.sz % 4 || g.origin % 4 || g.n % 4)
+            return set_error(FS_EINVAL, "multigrid: level %d rows are not quad-aligned", l);
+    }
     // the least a level-0 sweep must move: the flag of every element, and r and e
     // read and e written on the unknowns (the zeros it writes elsewhere are excess)
     unsigned long long *cnt = reinterpret_cast<unsigned long long *>(c->partials), nliq = 0;
