@@ -18,7 +18,8 @@
  *   3. implicit viscosity: (I + nu dt L_f) u_v = u_b on the fluid faces, per
  *      component, L_f the 7-point face Laplacian (fluid neighbours coupled, fixed
  *      neighbours Dirichlet, air neighbours and box-wall tangential neighbours
- *      zero-flux), solved by Jacobi-preconditioned CG;
+ *      zero-flux), solved by CG preconditioned with Jacobi, or with the multigrid
+ *      V-cycle when precond = FS_PRECOND_MG;
  *   4. projection: b = -dx * div(u_v) on liquid cells, L_p q = b (7-point, p = 0
  *      in air, solid walls zero-flux) by PCG, then u -= grad q / dx on fluid faces.
  *      The pressure is p = rho * q / dt.
@@ -107,7 +108,8 @@ typedef struct {
     double nu;         /* kinematic viscosity, >= 0 */
     double rho;        /* density, > 0; only scales the reported pressure */
     double g[3];       /* body acceleration per component */
-    int precond;       /* FS_PRECOND_* for the pressure solve */
+    int precond;       /* FS_PRECOND_* for the pressure solve; FS_PRECOND_MG also
+                          preconditions the viscosity solve (Jacobi otherwise) */
     int maxit_p;       /* pressure iteration cap, >= 1 */
     int maxit_v;       /* viscosity iteration cap, >= 1 */
     double tol_p;      /* pressure relative residual target |r|/|b|, > 0 */
@@ -342,7 +344,10 @@ int fs_percnn_grad(fs_ctx *c, const float *b, const float *q, double *loss, floa
  * z = M^-1 r on the liquid cells (zero elsewhere). Jacobi: M = diag(L_p);
  * MIC(0): M = L L^T with the modified incomplete Cholesky factor of L_p (Bridson,
  * cited by the paper for its pressure projection, Sec. 3.2.2), factored on first
- * use after fs_set_mask, computed in lexicographic order (x fastest).
+ * use after fs_set_mask, computed in lexicographic order (x fastest). Multigrid:
+ * one V-cycle of damped-Jacobi smoothing on a cell hierarchy (a symmetric linear
+ * operator; the paper has no counterpart), built on first use after fs_set_mask,
+ * which synchronises the stream once. Learned: the network (needs fs_net_load).
  * r, z: DEVICE cell arrays in the library layout, must not alias.
  * Returns FS_ETIMEOUT if a bounded device wait of the MIC(0) wavefront ran out. */
 int fs_precond_apply(fs_ctx *c, const float *r, float *z);
