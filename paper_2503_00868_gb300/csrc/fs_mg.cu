@@ -640,9 +640,11 @@ int mg_apply_faces(fs_ctx *c, const float *r, float *z, float cc, const int *don
         }
         FS_CUDA(cudaMemsetAsync(m->fb, 0, (size_t)L.nF * 4, c->stream));
         FS_CUDA(cudaMemsetAsync(m->fc, 0, (size_t)L.nF * 4, c->stream));
+    }
+    if (!m->fork) {  // the side streams and their events, once (the fork event last)
         for (int k = 0; k < 2; k++) {
-            FS_CUDA(cudaStreamCreateWithFlags(&m->side[k], cudaStreamNonBlocking));
-            FS_CUDA(cudaEventCreateWithFlags(&m->join[k], cudaEventDisableTiming));
+            if (!m->side[k]) FS_CUDA(cudaStreamCreateWithFlags(&m->side[k], cudaStreamNonBlocking));
+            if (!m->join[k]) FS_CUDA(cudaEventCreateWithFlags(&m->join[k], cudaEventDisableTiming));
         }
         FS_CUDA(cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming));
     }
