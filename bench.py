@@ -266,6 +266,30 @@ def precond_compare(n, seeds=(0,)):
     return out
 
 
+def dist_env():
+    """(world size, rank, local rank) from the torchrun environment (1, 0, 0 alone)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest x over the ranks of the process group: a job's time is its
+    slowest rank's."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps: int, cells: int, frames: int, seconds: float) -> float:
+    """Cell-steps per second of the whole job: every rank runs its own scene
+    (weak scaling), and the job takes the slowest rank's time."""
+    return world * steps * cells * frames / seconds
+
+
 def main():
     a = args_parse()
     if a.impl == "reference":
@@ -274,9 +298,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = dist_env()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -330,12 +352,9 @@ def main():
     elapsed = ev0.elapsed_time(ev1) / 1e3
     prof = grid.profile_read()
     grid.profile(0)
-    if world > 1:
-        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed, world, "cuda")
     cells = n ** 3
-    value = world * a.steps * cells * frames / elapsed
+    value = job_throughput(world, a.steps, cells, frames, elapsed)
     ms_per_step = 1e3 * elapsed / a.steps
     iters_p = [s[2]["iters_p"] for s in stats if s[0] == "fwd"]
     iters_v = [s[2]["iters_v"] for s in stats if s[0] == "fwd"]
@@ -360,13 +379,9 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        t_e2e = e0.elapsed_time(e1) / 1e3
-        if world > 1:
-            t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        e2e = {"value": world * a.steps * cells * frames / t_e2e, "unit": UNIT, "h2d_bytes_per_step": hb,
-               "d2h_bytes_per_step": 16}
+        t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, "cuda")
+        e2e = {"value": job_throughput(world, a.steps, cells, frames, t_e2e), "unit": UNIT,
+               "h2d_bytes_per_step": hb, "d2h_bytes_per_step": 16}
 
     # ---- roofline of the dominant kernel -----------------------------------
     peaks = measured_peaks()
