@@ -10,8 +10,9 @@
 // (cells beyond an odd edge count as solid): it is air (a Dirichlet cell, p = 0)
 // when any child is air, else liquid when any child is liquid, else solid. Each
 // coarse level stores the same flag bits, with its own neighbour counts, in a
-// dense array with a one-cell solid halo. The operator on level l is the same
-// 7-point stencil rediscretised on cells of size 2^l dx, i.e. scaled by 4^-l.
+// dense array with a solid halo (a plane and a row on each side, 4 elements
+// before each row, the row pitch a multiple of 4). The operator on level l is the
+// same 7-point stencil rediscretised on cells of size 2^l dx, i.e. scaled by 4^-l.
 //
 // V-cycle on level l for A_l e = r: two damped Jacobi sweeps from e = 0
 // (omega = 0.8), the residual, restriction (the transpose of cell-centred
@@ -21,10 +22,11 @@
 // in one block. Every step is linear in r with symmetric smoothing and restriction
 // proportional to the transposed prolongation, so M is symmetric, as CG needs.
 //
-// Every kernel walks a level's whole array. The work arrays are zeroed when the
-// hierarchy is built and only ever written on liquid cells, so a stencil at the
-// edge of the liquid reads zeros; the level-0 output (the solver's z) is written
-// densely, zeros included.
+// The sweeps, the residual and the transfers take four elements per thread over a
+// level's whole array and skip the quads without an unknown. The work arrays are
+// zeroed when the hierarchy is built and written only on quads that hold an
+// unknown (with zeros on their other elements), so a stencil at the edge of the
+// liquid reads zeros; the level-0 output (the solver's z) is written densely.
 //
 // The same V-cycle preconditions the implicit viscosity solve, one velocity
 // component at a time: each face volume is a box of unknown faces (FF_FLUID),
@@ -46,8 +48,8 @@ constexpr int MG_COARSE_SWEEPS = 30;
 constexpr float MG_OMEGA = 0.8f;
 
 // A level's array is `rows` rows of `sy` elements, `rpp` rows per plane; element
-// e of row w is cell (e - ioff, w % rpp - joff, w / rpp - koff). Kernels walk
-// rows (a warp along a row), so no element index is divided.
+// e of row w is cell (e - ioff, w % rpp - joff, w / rpp - koff). The set-up
+// kernels walk rows (a warp along a row), so they divide no element index.
 struct MgGrid {
     int nx, ny, nz;    // cells of the level
     int sy, sz;        // element strides of a row and a plane
@@ -80,10 +82,10 @@ struct MgState {
     double smooth_bytes = 0.0;  // algorithmic bytes of one level-0 sweep (profiled when > 0)
 };
 
-// the pressure hierarchy and one per face volume (viscosity); the face volumes
-// share two level-0 work arrays of face-space length
-// the face volumes' V-cycles are independent: volumes 1 and 2 run on two side
-// streams, forked from and joined back to the context's stream
+// The pressure hierarchy and one per face volume (viscosity). The face volumes
+// share two level-0 work arrays of face-space length, and their V-cycles are
+// independent: volumes 1 and 2 run on two side streams, forked from and joined
+// back to the context's stream.
 struct MgAll {
     MgState cell, face[3];
     float *fb = nullptr, *fc = nullptr;
@@ -272,8 +274,8 @@ __global__ void __launch_bounds__(256) k_mg0_prolong(MgGrid gf, const uint8_t *_
     }
 }
 
-// Restriction from level 0: one thread per pair of coarse cells (2m, 2m + 1) of
-// an interior coarse row. Per fine row of the 4 x 4 window it reads the aligned
+// Restriction from a quad-aligned level: one thread per pair of coarse cells
+// (2m, 2m + 1) of an interior coarse row. Per fine row of the 4 x 4 window it reads the aligned
 // quad 4m .. 4m + 3 and the scalars at 4m - 1 and 4m + 4 (excluded at or past nx,
 // where the next row begins), and forms both cells' x weights from them.
 __global__ void __launch_bounds__(256) k_mg0_restrict(MgGrid gf, const float *__restrict__ res, MgGrid gc,
