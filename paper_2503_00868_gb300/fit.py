@@ -32,7 +32,8 @@ from . import fluidstep as F
 from . import workloads as W
 from .rollout import forward_states, rollout_loss
 
-PRECONDS = {"jacobi": F.FS_PRECOND_JACOBI, "mic0": F.FS_PRECOND_MIC0, "learned": F.FS_PRECOND_LEARNED}
+PRECONDS = {"jacobi": F.FS_PRECOND_JACOBI, "mic0": F.FS_PRECOND_MIC0, "learned": F.FS_PRECOND_LEARNED,
+            "mg": F.FS_PRECOND_MG}
 
 
 def river_scene(nx: int, ny: int, nz: int, seed: int, inflow_speed: float = 0.5, depth: float = 0.25):
