@@ -56,3 +56,45 @@ def test_init_rejects_bad_sizes_before_touching_the_device(lib):
     with pytest.raises(F.FluidStepError) as e:
         F.fs_init_grid(8, 8, 8, p)
     assert e.value.status == F.FS_EINVAL
+
+
+def test_enum_values_match_the_header():
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    consts = dict((k, int(v)) for k, v in re.findall(r"\b(FS_[A-Z0-9_]+)\s*=\s*(-?\d+)", text))
+    assert {"FS_PRECOND_MG", "FS_SOLVER_PERCNN", "FS_OK", "FS_EINVAL"} <= set(consts)
+    for name in ("FS_PRECOND_JACOBI", "FS_PRECOND_MIC0", "FS_PRECOND_LEARNED", "FS_PRECOND_MG",
+                 "FS_SOLVER_PCG", "FS_SOLVER_PERCNN"):
+        assert getattr(F, name) == consts[name], name
+    mirrored = [k for k in consts if hasattr(F, k)]
+    assert len(mirrored) >= 10
+    for name in mirrored:
+        assert getattr(F, name) == consts[name], name
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """sizeof and every field's offset of the structs the binding mirrors, as the C
+    compiler lays them out from the header."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [F.fs_params, F.fs_stats, F.fs_layout_t, F.fs_kernel_time, F.fs_mac, F.fs_camera]
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "fluidstep.h"', "int main(void) {"]
+    for st in structs:
+        n = st.__name__
+        lines.append(f'printf("{n} %zu\\n", sizeof({n}));')
+        for fname, _ in st._fields_:
+            lines.append(f'printf("{n}.{fname} %zu\\n", offsetof({n}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                       text=True).stdout.splitlines())
+    for st in structs:
+        n = st.__name__
+        assert int(out[n]) == ctypes.sizeof(st), n
+        for fname, _ in st._fields_:
+            assert int(out[f"{n}.{fname}"]) == getattr(st, fname).offset, f"{n}.{fname}"
