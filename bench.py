@@ -80,6 +80,36 @@ def source_hash(files=KERNEL_FILES):
     return h.hexdigest()[:16]
 
 
+# profile entries timed every PROFILE_PERIOD-th CG iteration or V-cycle (the
+# others are timed at every launch)
+SAMPLED = ("pressure_spmv", "pressure_update", "visc_spmv", "visc_update", "fcg_vectors", "mg_smooth0",
+           "mg_vcycle_p", "mg_vcycle_v")
+
+
+def roofline_of(prof, peaks, src_hash, traffic_table=None):
+    """The roofline object of the profile entry with the largest estimated share
+    of the step among those that carry algorithmic bytes. prof maps a name to
+    (timed launches, total ms, total algorithmic bytes). achieved = bytes per
+    launch / mean launch time; the peak is the measured HBM copy bandwidth (the
+    6800 GB/s fallback without a measurement); the ncu traffic is reported only
+    while the hash of the files that define the kernels matches its capture's."""
+    traffic_table = NCU_TRAFFIC if traffic_table is None else traffic_table
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    top = max((k for k in prof.items() if k[0] != "all_kernels" and k[1][2] > 0 and k[1][0] > 0),
+              key=lambda kv: kv[1][1] * (PROFILE_PERIOD if kv[0] in SAMPLED else 1), default=None)
+    if top is None:
+        return None
+    name, (launches, ms, by) = top
+    achieved = (by / launches) / (ms / launches * 1e-3) / 1e9
+    tr = traffic_table.get(name)
+    traffic = tr["bytes_per_launch"] if tr and tr.get("source") == src_hash else None
+    return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": traffic,
+            "algorithmic_bytes_per_launch": by / launches, "launches": launches,
+            "avg_launch_us": 1e3 * ms / launches,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback"}
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -384,31 +414,13 @@ def main():
                "h2d_bytes_per_step": hb, "d2h_bytes_per_step": 16}
 
     # ---- roofline of the dominant kernel -----------------------------------
-    peaks = measured_peaks()
-    hbm = peaks["hbm_gbs"] if peaks else 6800.0
-    # the kernel with the largest estimated share of the step, among those with algorithmic bytes
-    sampled = ("pressure_spmv", "pressure_update", "visc_spmv", "visc_update", "fcg_vectors", "mg_smooth0",
-               "mg_vcycle_p", "mg_vcycle_v")
-    top = max((k for k in prof.items() if k[1][2] > 0 and k[1][0] > 0),
-              key=lambda kv: kv[1][1] * (PROFILE_PERIOD if kv[0] in sampled else 1), default=None)
-    roofline = None
-    if top:
-        name, (launches, ms, by) = top
-        achieved = (by / launches) / (ms / launches * 1e-3) / 1e9
-        src = source_hash()
-        tr = NCU_TRAFFIC.get(name)
-        traffic = tr["bytes_per_launch"] if tr and tr.get("source") == src else None
-        roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved / hbm, "traffic": traffic,
-                    "algorithmic_bytes_per_launch": by / launches, "launches": launches,
-                    "avg_launch_us": 1e3 * ms / launches,
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback"}
+    roofline = roofline_of(prof, measured_peaks(), source_hash())
     # CG kernels and V-cycles are timed every PROFILE_PERIOD-th iteration, the others at every launch
     kernels = {}
     for k, v in prof.items():
         if k == "all_kernels" or not v[0]:
             continue
-        scale = PROFILE_PERIOD if k in sampled else 1
+        scale = PROFILE_PERIOD if k in SAMPLED else 1
         kernels[k] = {"timed_launches": v[0], "mean_us": round(1e3 * v[1] / v[0], 2),
                       "est_share_of_step": round(scale * v[1] / (1e3 * elapsed), 4)}
     gpu_launches = None
