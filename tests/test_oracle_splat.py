@@ -114,3 +114,35 @@ def test_joint_rotation_of_scene_and_camera_changes_nothing():
     c2 = cam(40, 30, 45.0, R=Q.T)           # x_c = Q^T (Q x) = x
     rgb2, T2 = O.splat_render(x @ Q.T, op, Q @ A @ Q.T, col, c2)
     assert np.allclose(rgb, rgb2, atol=1e-9) and np.allclose(T, T2, atol=1e-9)
+
+
+def test_walk_stops_before_the_gaussian_that_would_cross_the_floor():
+    """One pixel on the axis, three Gaussians behind it with alphas 0.98, 0.99 and
+    0.99 (opacities 0.98, 0.99 and 1.0, the last capped): after two, T = 0.02 *
+    0.01 = 2e-4 is still above the 1e-4 floor, so both are composited; the third
+    would take T to 2e-6, so the walk stops before it and it adds nothing."""
+    c = cam(1, 1, 40.0, bg=(0.0, 0.0, 0.0))       # pixel centre (0.5, 0.5) = the axis
+    x = np.array([[0.0, 0.0, 2.0], [0.0, 0.0, 3.0], [0.0, 0.0, 4.0]])
+    A = np.stack([0.2 ** 2 * np.eye(3)] * 3)
+    cols = np.eye(3)
+    rgb, T = O.splat_render(x, [0.98, 0.99, 1.0], A, cols, c)
+    assert T[0, 0] == pytest.approx(0.02 * 0.01, rel=1e-12)
+    assert rgb[0, 0, 0] == pytest.approx(0.98, rel=1e-12)
+    assert rgb[0, 0, 1] == pytest.approx(0.02 * 0.99, rel=1e-12)
+    assert rgb[0, 0, 2] == 0.0
+    # without the third Gaussian in front of the floor, the first two are unchanged
+    rgb2, T2 = O.splat_render(x[:2], [0.98, 0.99], A[:2], cols[:2], c)
+    assert np.allclose(rgb2, rgb) and np.allclose(T2, T)
+
+
+def test_alpha_threshold_of_one_over_255():
+    """A Gaussian whose alpha at the pixel centre sits just below 1/255 leaves the
+    pixel untouched; just above, it is composited."""
+    c = cam(1, 1, 40.0, bg=(0.0, 0.0, 0.0))       # one pixel, centre on the axis
+    A = (0.2 ** 2 * np.eye(3))[None]
+    x = np.array([[0.0, 0.0, 2.0]])
+    lo, hi = (1.0 / 255.0) * (1 - 1e-6), (1.0 / 255.0) * (1 + 1e-6)
+    _, T_lo = O.splat_render(x, [lo], A, np.ones((1, 3)), c)
+    rgb_hi, T_hi = O.splat_render(x, [hi], A, np.ones((1, 3)), c)
+    assert T_lo[0, 0] == 1.0
+    assert T_hi[0, 0] == pytest.approx(1.0 - hi, abs=1e-15) and rgb_hi[0, 0, 0] == pytest.approx(hi, abs=1e-15)
