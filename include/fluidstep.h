@@ -442,9 +442,10 @@ int fs_profile_read(fs_ctx *c, fs_kernel_time *out, int max, int *count);
  * with FS_EINVAL (and a message giving the bytes it needs) before any work.
  * The call never calls cudaMalloc, cudaFree or any other allocating routine.
  *
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture. Every call shares the one array, and each clears the parts
+ * Every call looks up the array's device address (cudaGetSymbolAddress) with
+ * the caller's current device, so the array of that device is used; the first
+ * call on a device may load the library's device code there, so make that first
+ * call before any stream capture. Every call shares the one array, and each clears the parts
  * that must start at zero: calls that overlap on the GPU (on different streams or
  * host threads, for the same device) race and corrupt each other's results.
  * The call synchronises `cuda_stream` before it returns. */

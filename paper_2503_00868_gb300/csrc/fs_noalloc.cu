@@ -11,11 +11,11 @@
 //
 // The array is a module-scope __device__ variable: every GPU that loads this
 // library holds it until the process exits. In host code the array's name is
-// only a host-side stand-in, so its device address is looked up once per device
-// with cudaGetSymbolAddress (on the first call on that device, with that device
-// current) and passed to the kernels.
+// only a host-side stand-in, so every call looks up its device address with
+// cudaGetSymbolAddress, with the caller's device current, and passes that to the
+// kernels. The lookup is cheap and is not cached: an address kept from before a
+// reset of the device's primary context would be stale.
 #include <cstring>
-#include <mutex>
 
 #include "fs_internal.cuh"
 
@@ -23,27 +23,18 @@ namespace fs {
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = 16u << 20;  // 16 MiB: every grid up to 64^3 fits
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-std::mutex g_addr_mutex;
-void *g_addr[kMaxDevices] = {};
-
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-// Device address of the scratch array on the current device (looked up once).
-int scratch_address(int device, void **out)
+// Device address of the scratch array in the current device's context.
+int scratch_address(void **out)
 {
-    if (device < 0 || device >= kMaxDevices) return set_error(FS_EINVAL, "device ordinal %d out of range", device);
-    std::lock_guard<std::mutex> lock(g_addr_mutex);
-    if (!g_addr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return check_cuda(e, "cudaGetSymbolAddress(noalloc scratch)");
-        g_addr[device] = p;
-    }
-    *out = g_addr[device];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return check_cuda(e, "cudaGetSymbolAddress(noalloc scratch)");
+    *out = p;
     return FS_OK;
 }
 
@@ -99,7 +90,7 @@ extern "C" int fs_project_noalloc(int nx, int ny, int nz, const uint8_t *cell_ty
                          "%zu bytes (every grid up to 64x64x64 fits)",
                          nx, ny, nz, need, kNoAllocScratchBytes);
     void *base = nullptr;
-    if ((rc = scratch_address(c.device, &base))) return rc;
+    if ((rc = scratch_address(&base))) return rc;
     unsigned char *p = static_cast<unsigned char *>(base);
     auto take = [&](size_t bytes) {
         unsigned char *q = p;

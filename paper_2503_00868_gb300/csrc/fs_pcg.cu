@@ -240,28 +240,36 @@ __global__ void __launch_bounds__(TH) k_helm_init(const float *__restrict__ x, c
         init_scalars(s, tot[0], tot[1], tot[2], tol2, maxit);
 }
 
-// |b - A x|^2 of the pressure system -> s->aux[0].
-// |b - A x|^2 over the liquid -> s->aux[0]. For a singular operator (liquid
-// touching no air) the component along the null vector (the constant), which
-// no iterate can change, is left out: sum e^2 - (sum e)^2 / N.
+// |b - A x|^2 over the liquid -> s->aux[0] and |b|^2 -> s->aux[1], the final
+// convergence check. It is evaluated in FP64 throughout: A x of the FP32
+// iterate (integer stencil weights) and b - A x are then exact unless the
+// entries span more than about 2^29 in magnitude, and only the sums of squares
+// round. For a singular operator (liquid touching no air) the component along
+// the null vector (the constant), which no iterate can change, is left out:
+// sum e^2 - (sum e)^2 / N.
 __global__ void __launch_bounds__(TH) k_pois_true_res(const float *__restrict__ b, const float *__restrict__ x,
                                                       const uint8_t *__restrict__ fl, int n, int P, int PL,
                                                       int singular, SolveScal *s, double *partials)
 {
-    double acc = 0.0, sum = 0.0, cnt = 0.0;
+    double acc = 0.0, sum = 0.0, cnt = 0.0, bsq = 0.0;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
         const uint8_t f = fl[t];
         if (!(f & CF_LIQ)) continue;
-        const float nb = (x[t - 1] + x[t + 1]) + (x[t - P] + x[t + P]) + (x[t - PL] + x[t + PL]);
-        const float ax = PoisOp::diag(f, 0.f) * x[t] - nb;
-        const double e = (double)b[t] - (double)ax;
+        const double nb = ((double)x[t - 1] + (double)x[t + 1]) + ((double)x[t - P] + (double)x[t + P]) +
+                          ((double)x[t - PL] + (double)x[t + PL]);
+        const double ax = (double)PoisOp::diag(f, 0.f) * (double)x[t] - nb;
+        const double bv = (double)b[t];
+        const double e = bv - ax;
         acc += e * e;
         sum += e;
         cnt += 1.0;
+        bsq += bv * bv;
     }
-    double v[3] = {acc, sum, cnt}, tot[3];
-    if (grid_reduce<3>(v, partials, &s->ticket, tot) && threadIdx.x == 0)
+    double v[4] = {acc, sum, cnt, bsq}, tot[4];
+    if (grid_reduce<4>(v, partials, &s->ticket, tot) && threadIdx.x == 0) {
         s->aux[0] = (singular && tot[2] > 0.0) ? fmax(0.0, tot[0] - tot[1] * tot[1] / tot[2]) : tot[0];
+        s->aux[1] = tot[3];
+    }
 }
 
 // Residual replacement: restart CG from the current x with the true residual
@@ -614,7 +622,7 @@ static int try_warm_start(fs_ctx *c, bool jac)
     SolveScal m, h0;
     int rc;
     if ((rc = read_scal(c, 2, &m)) || (rc = read_scal(c, 0, &h0))) return rc;
-    if (h0.done || !(m.aux[0] < 0.5 * h0.bb)) return FS_OK;
+    if (h0.done || !(m.aux[0] < 0.5 * m.aux[1])) return FS_OK;
     FS_CUDA(cudaMemcpyAsync(c->px, c->pw[k], (size_t)L.nC * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
     if (jac)
         k_pois_restart<true><<<bs, TH, 0, c->stream>>>(c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, L.nC,
@@ -793,7 +801,7 @@ static int solve_pressure_once(fs_ctx *c, fs_stats *st)
         FS_CUDA(cudaGetLastError());
         SolveScal m;
         if ((rc = read_scal(c, 2, &m))) return rc;
-        if (m.aux[0] <= 4.0 * h.tol2 * h.bb) break;
+        if (m.aux[0] <= 4.0 * h.tol2 * m.aux[1]) break;
         if (st) st->restarts_p += 1;
     }
     int rc = pressure_tail(c, h, st);
@@ -823,7 +831,7 @@ static int pressure_tail(fs_ctx *c, const SolveScal &h, fs_stats *st)
     if (st) {
         st->iters_p += h.iter;
         st->relres_p = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
-        st->true_relres_p = h.bb > 0 ? std::sqrt(m.aux[0] / h.bb) : 0.0;
+        st->true_relres_p = m.aux[1] > 0 ? std::sqrt(m.aux[0] / m.aux[1]) : 0.0;
         if (h.status != FS_OK && st->status == FS_OK) st->status = h.status;
     }
     return finish_status(h.status);

@@ -422,14 +422,56 @@ def fs_net_train_step(ctx: int, b_batch: torch.Tensor, q_batch: torch.Tensor, lr
     return loss.value
 
 
+def noalloc_layout(nx: int, ny: int, nz: int):
+    """(planes, rows, pitch) of a field of an nx x ny x nz grid: the layout
+    fs_init_grid uses, which fs_project_noalloc assumes without a context."""
+    return nz + 1, ny + 1, (nx + 1 + 3) // 4 * 4
+
+
+def check_noalloc_args(nx, ny, nz, cell_type_dense, u, q_out=None, device=None):
+    """Raises ValueError unless the arguments of fs_project_noalloc match the
+    grid: cell types uint8 with nx*ny*nz elements, the three components of u and
+    q_out (if given) contiguous float32 of shape noalloc_layout(nx, ny, nz), and
+    every tensor on `device` (default: the current CUDA device)."""
+    if min(int(nx), int(ny), int(nz)) < 2:
+        raise ValueError(f"grid sizes must be >= 2 (got {nx} {ny} {nz})")
+    if device is None:
+        device = torch.device("cuda", torch.cuda.current_device())
+    shape = noalloc_layout(nx, ny, nz)
+
+    def on_device(t, what):
+        if t.device != torch.device(device):
+            raise ValueError(f"{what} is on {t.device}, not on the current device {device}")
+
+    if not isinstance(cell_type_dense, torch.Tensor) or cell_type_dense.dtype != torch.uint8 \
+            or not cell_type_dense.is_contiguous() or cell_type_dense.numel() != nx * ny * nz:
+        raise ValueError(f"cell types must be a contiguous uint8 tensor of {nx}*{ny}*{nz} elements")
+    on_device(cell_type_dense, "the cell-type tensor")
+    if u is None or len(u) != 3:
+        raise ValueError("u must be a Mac of three components")
+    for name, t in zip("uvw", u):
+        if t.dtype != torch.float32 or not t.is_contiguous() or tuple(t.shape) != shape:
+            raise ValueError(f"u.{name} must be a contiguous float32 tensor of shape {shape}, "
+                             f"got {tuple(t.shape)} {t.dtype}")
+        on_device(t, f"u.{name}")
+    if q_out is not None:
+        if q_out.dtype != torch.float32 or not q_out.is_contiguous() or tuple(q_out.shape) != shape:
+            raise ValueError(f"q_out must be a contiguous float32 tensor of shape {shape}, "
+                             f"got {tuple(q_out.shape)} {q_out.dtype}")
+        on_device(q_out, "q_out")
+
+
 def fs_project_noalloc(nx: int, ny: int, nz: int, cell_type_dense: torch.Tensor, u: Mac,
                        q_out: Optional[torch.Tensor] = None, dx: float = 1.0, tol: float = 1e-6,
                        maxit: int = 20000, stream: Optional[int] = None):
     """Projection for callers that cannot allocate device memory: the library
     uses a fixed static scratch array (grids up to 64^3) instead of a context.
-    The tensors passed in are the caller's; this wrapper allocates nothing."""
-    if cell_type_dense.dtype != torch.uint8 or not cell_type_dense.is_cuda or not cell_type_dense.is_contiguous():
-        raise ValueError("cell types must be a contiguous uint8 CUDA tensor")
+    The tensors passed in are the caller's; this wrapper allocates nothing.
+
+    There is no context to hold the layout, so the library trusts the pointers:
+    every tensor is checked here first (shape, dtype, contiguity, and that it
+    sits on the current CUDA device) and ValueError is raised before any call."""
+    check_noalloc_args(nx, ny, nz, cell_type_dense, u, q_out)
     st = fs_stats()
     s = torch.cuda.current_stream().cuda_stream if stream is None else stream
     q = C.c_void_p(q_out.data_ptr()) if q_out is not None else None

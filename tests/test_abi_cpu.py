@@ -98,3 +98,56 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(out[n]) == ctypes.sizeof(st), n
         for fname, _ in st._fields_:
             assert int(out[f"{n}.{fname}"]) == getattr(st, fname).offset, f"{n}.{fname}"
+
+
+def _noalloc_args(nx, ny, nz):
+    import torch
+    shape = F.noalloc_layout(nx, ny, nz)
+    types = torch.ones(nx * ny * nz, dtype=torch.uint8).reshape(nz, ny, nx)
+    u = F.Mac(*(torch.zeros(shape, dtype=torch.float32) for _ in range(3)))
+    q = torch.zeros(shape, dtype=torch.float32)
+    return types, u, q
+
+
+def test_noalloc_arguments_checked_against_the_grid():
+    """fs_project_noalloc has no context to hold the layout, so the binding checks
+    every tensor against the grid before the library sees a pointer."""
+    import torch
+    nx, ny, nz = 10, 7, 9
+    assert F.noalloc_layout(nx, ny, nz) == (10, 8, 12)
+    types, u, q = _noalloc_args(nx, ny, nz)
+    F.check_noalloc_args(nx, ny, nz, types, u, q, device="cpu")       # consistent: accepted
+    F.check_noalloc_args(nx, ny, nz, types, u, None, device="cpu")
+    bad = [
+        dict(types=types[:, :, :-1].contiguous()),                           # too few cell types
+        dict(types=types.to(torch.int32)),                                   # wrong dtype
+        dict(u=F.Mac(u.u[:, :, :-4].contiguous(), u.v, u.w)),                # pitch too small
+        dict(u=F.Mac(u.u, u.v[:-1].contiguous(), u.w)),                      # a plane short
+        dict(u=F.Mac(u.u, u.v, u.w.to(torch.float64))),                     # wrong dtype
+        dict(u=F.Mac(u.u, u.v, u.w.transpose(1, 2).contiguous().transpose(1, 2))),  # not contiguous
+        dict(q=q[:, :-1].contiguous()),                                      # q_out a row short
+        dict(q=q.to(torch.float16)),
+    ]
+    for b in bad:
+        with pytest.raises(ValueError):
+            F.check_noalloc_args(nx, ny, nz, b.get("types", types), b.get("u", u), b.get("q", q), device="cpu")
+    with pytest.raises(ValueError):      # a tensor on another device than the current one
+        F.check_noalloc_args(nx, ny, nz, types, u, q, device="cuda:0")
+    with pytest.raises(ValueError):
+        F.check_noalloc_args(1, ny, nz, types, u, q, device="cpu")
+
+
+def test_noalloc_wrong_shape_rejected_before_the_library_is_called(monkeypatch):
+    import torch
+
+    def no_library(*a, **k):
+        raise AssertionError("the library must not be reached")
+
+    monkeypatch.setattr(F, "load", no_library)
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+    nx, ny, nz = 10, 7, 9
+    types, u, q = _noalloc_args(nx, ny, nz)
+    with pytest.raises(ValueError):
+        F.fs_project_noalloc(nx, ny, nz, types, F.Mac(u.u[:, :, :4].contiguous(), u.v, u.w), q)
+    with pytest.raises(ValueError):   # right shapes, but host tensors, not on the current CUDA device
+        F.fs_project_noalloc(nx, ny, nz, types, u, q)

@@ -352,3 +352,32 @@ def test_viscosity_solve_is_symmetric_and_dirichlet_enters(oracle_mod):
     # nonzero near walls and vanish when bc = 0
     diff = sum(np.abs(out[c] - ax[c]).max() for c in range(3))
     assert diff > 1e-6
+
+
+def test_mic0_safety_branch_by_hand(oracle_mod):
+    """The safety branch of MIC(0) (a pivot e below sigma * diag is replaced by
+    diag, Bridson's recipe cited for the projection), on the closed 2 x 2 x 2 box
+    of liquid, where every cell has diag 3 and the pivots follow by hand in
+    lexicographic order (x fastest), with A's off-diagonals -1:
+      e0 = 3;  e1 = e2 = e4 = 3 - 1/3 - tau * 2/3 = 2.02 (tau = 0.97);
+      e3 = e5 = e6 = 3 - 2 (1 + tau) / 2.02 = 3 - 3.94/2.02 (two lower neighbours,
+           each with one further coupling);
+      e7 = 3 - 3 / e3 (three lower neighbours, no further couplings) = 0.14150...
+    With sigma = 0.25, e7 < 0.75 is replaced by diag = 3. With sigma = 0.36,
+    e3, e5, e6 (1.0495 < 1.08) are replaced by 3 first, which makes
+    e7 = 3 - 3/3 = 2 >= 1.08, kept."""
+    O = oracle_mod
+    g = O.Grid(np.full((2, 2, 2), LIQ, dtype=np.uint8), 1.0, 0.1, 0.0)
+    tau = 0.97
+    e12 = 3.0 - 1.0 / 3.0 - tau * 2.0 / 3.0
+    e3 = 3.0 - 2.0 * (1.0 + tau) / e12
+    # order of prec.ravel(): (k, j, i) C order = lexicographic with x fastest
+    expect = {
+        0.0: [3.0, e12, e12, e3, e12, e3, e3, 3.0 - 3.0 / e3],
+        0.25: [3.0, e12, e12, e3, e12, e3, e3, 3.0],
+        0.36: [3.0, e12, e12, 3.0, e12, 3.0, 3.0, 2.0],
+    }
+    assert abs(e12 - 2.02) < 1e-15 and abs(3.0 - 3.0 / e3 - 0.14150943396) < 1e-10
+    for sigma, e in expect.items():
+        prec = O.mic0_factor(g, tau=tau, sigma=sigma).ravel()
+        np.testing.assert_allclose(prec, 1.0 / np.sqrt(e), rtol=1e-14, atol=0)

@@ -36,12 +36,16 @@ def rel(a, b):
 
 
 def test_noalloc_projection_matches_fs_project_on_consecutive_calls():
-    cases = [((44, 37, 41), "spheres", 1), ((23, 19, 26), "blob", 2)]
+    # the closed box full of liquid is the singular case: the liquid mean of the
+    # right-hand side is removed and q is reported mean-free
+    cases = [((44, 37, 41), "spheres", 1), ((23, 19, 26), "blob", 2), ((21, 18, 19), "closed_box", 3)]
     for (nx, ny, nz), kind, seed in cases:
         if kind == "spheres":
             types, _ = W.sphere_union(nx, ny, nz, seed)
-        else:
+        elif kind == "blob":
             types, _ = W.ellipsoid_blob(nx, ny, nz, seed)
+        else:
+            types = W.all_liquid(nx, ny, nz)
         u0 = W.random_mac(nx, ny, nz, seed + 10)
         dx = 1.0 / ny
         ref = F.Grid(nx, ny, nz, dx=dx, tol_p=1e-7)
@@ -58,6 +62,12 @@ def test_noalloc_projection_matches_fs_project_on_consecutive_calls():
         assert st["true_relres_p"] < 1e-6
         assert rel(u_new, u_ref) < TOL_U
         assert rel([q_new], [q_ref]) < TOL_Q
+
+        # without q_out: the same velocity
+        u_noq = ref.pack(u0)
+        rc, st = F.fs_project_noalloc(nx, ny, nz, t, u_noq, None, dx=dx, tol=1e-7, maxit=20000)
+        assert rc == F.FS_OK, st
+        assert rel(u_noq, u_ref) < TOL_U
         ref.close()
 
 
