@@ -137,11 +137,15 @@ typedef struct {
     int iters_v;           /* viscosity iterations, summed over the call's solves */
     double relres_p;       /* last pressure solve: recursive |r|/|b| at exit */
     double relres_v;       /* last viscosity solve: recursive |r|/|b| at exit */
-    double true_relres_p;  /* last pressure solve: |b - A q|/|b| recomputed at exit */
+    double true_relres_p;  /* last pressure solve: |b - A q|/|b| recomputed at exit in FP64
+                              (A q of the FP32 pressure, b - A q and both norms in FP64) */
     int fallbacks;         /* pressure solves redone with MIC(0) after the learned one failed */
-    int restarts_p;        /* pressure CG restarts from the current iterate with the true
-                              residual (taken when the recursive residual meets tol_p but
-                              |b - A q| > 2 tol_p |b|; at most two per solve) */
+    int restarts_p;        /* refinement steps of the pressure solves (summed over the call):
+                              when the recursive residual meets tol_p but the FP64 residual
+                              |b - A q| is above tol_p |b|, CG runs again on the correction
+                              system A d = b - A q (right-hand side rounded once from FP64)
+                              to tol_p |b| / 2, and the pressure is kept as the pair q + d;
+                              at most two per solve */
 } fs_stats;
 
 typedef struct {

@@ -76,6 +76,7 @@ def lib():
                 "or_face_class": [G, C.c_int, C.POINTER(C.c_uint8)],
                 "or_advect": [G, _P3, _P3],
                 "or_advect_adjoint": [G, _P3, _P3, _P3],
+                "or_advect_samples": [G, C.c_int, _P3, _D],
                 "or_visc_apply": [G, _P3, _P3],
                 "or_visc_solve": [G, _P3, _P3, C.POINTER(Stats)],
                 "or_divergence": [G, _P3, _D],
@@ -194,6 +195,33 @@ def advect(g: Grid, u):
     out = g.zeros()
     lib().or_advect(g.cstruct(), _p3(u), _p3(out))
     return out
+
+
+def advect_samples(g: Grid, u, c: int):
+    """Back-traced sample points (index space, before clamping) of the fluid
+    faces of component c, shape face_shapes[c] + (3,) in (x, y, z) order; NaN on
+    faces that are not advected."""
+    u = _field(g, u)
+    out = np.zeros(g.shapes()[c] + (3,))
+    lib().or_advect_samples(g.cstruct(), int(c), _p3(u), _ptr(out))
+    return out
+
+
+def kink_faces(g: Grid, u, eps: float = 3e-5, halo: int = 2):
+    """Per component, the faces whose reverse-mode value is not unique under a
+    perturbation of the sample point by eps: those within `halo` cells of a
+    fluid face whose back-traced sample has a coordinate within eps of an
+    integer (a kink of the trilinear interpolation). Boolean arrays of the face
+    shapes. Used by tests that bound errors face by face."""
+    from scipy.ndimage import binary_dilation
+    cell = np.zeros((g.nz + 1, g.ny + 1, g.nx + 1), dtype=bool)
+    for c in range(3):
+        s = advect_samples(g, u, c)
+        near = np.any(np.abs(s - np.round(s)) < eps, axis=-1)   # NaN compares False
+        k, j, i = np.nonzero(near)
+        cell[k, j, i] = True
+    cell = binary_dilation(cell, iterations=halo)
+    return tuple(cell[:sh[0], :sh[1], :sh[2]] for sh in g.shapes())
 
 
 def advect_adjoint(g: Grid, u, ga):

@@ -248,6 +248,31 @@ void or_advect(const or_grid *g, const double *const u[3], double *const ua[3])
     }
 }
 
+/* The back-traced sample point of every face of component c, as used by
+ * or_advect: s_out[3 f + e] = idx_e - (dt/dx) vel_e before clamping, for the
+ * fluid faces f (NaN on fixed and air faces, which are not advected). A test
+ * helper: trilinear interpolation is not differentiable where a coordinate of
+ * s is an integer, so the reverse pass is not unique there. */
+void or_advect_samples(const or_grid *g, int c, const double *const u[3], double *s_out)
+{
+    int d[3];
+    face_dims(g, c, d);
+    const double h = g->dt / g->dx;
+    for (int k = 0; k < d[2]; k++)
+        for (int j = 0; j < d[1]; j++)
+            for (int i = 0; i < d[0]; i++) {
+                long f = fidx(d, i, j, k);
+                int idx[3] = {i, j, k};
+                if (face_class(g, c, i, j, k) != FC_FLUID) {
+                    for (int e = 0; e < 3; e++) s_out[3 * f + e] = NAN;
+                    continue;
+                }
+                double vel[3];
+                face_velocity(g, c, i, j, k, u, vel);
+                for (int e = 0; e < 3; e++) s_out[3 * f + e] = (double)idx[e] - h * vel[e];
+            }
+}
+
 /* Exact discrete adjoint of or_advect w.r.t. the input field: given the
  * cotangent ga of the advected field, ACCUMULATE d<ga, advect(u)>/du into gu.
  * Fixed and air faces of the output are constants and contribute nothing. */

@@ -161,7 +161,7 @@ static void free_ctx(fs_ctx *c)
     splat_free(c);
     mg_free(c);
     void *ptrs[] = {c->cflag, c->fflag, c->bc, c->dsum, c->pb, c->pr, c->pp[0], c->pp[1], c->pq, c->px, c->pz,
-                    c->vx, c->vr, c->vp[0], c->vp[1], c->vq, c->vz, c->fu[0], c->fu[1], c->fu[2], c->fg[0], c->fg[1],
+                    c->pxh, c->pxt, c->pbr, c->vx, c->vr, c->vp[0], c->vp[1], c->vq, c->vz, c->fu[0], c->fu[1], c->fu[2], c->fg[0], c->fg[1],
                     c->fg[2], c->gc[0], c->gc[1], c->gc[2], c->mic_prec, c->scal, c->partials, c->err_word, c->pw[0], c->pw[1],
                     c->act_cell, c->act_face, c->list_cell, c->list_face, c->items_cell, c->items_face, c->qmask_cell, c->qmask_face,
                     c->py, c->mic_order,
@@ -307,6 +307,9 @@ int fs_init_grid(fs_ctx **out, int nx, int ny, int nz, const fs_params *p, void 
     ALLOC(c->pp[1], cb);
     ALLOC(c->pq, cb);
     ALLOC(c->px, cb);
+    ALLOC(c->pxh, cb);
+    ALLOC(c->pxt, cb);
+    ALLOC(c->pbr, cb);
     ALLOC(c->pz, cb);
     ALLOC(c->vx, fb);
     ALLOC(c->vr, fb);

@@ -247,7 +247,7 @@ int solve_pressure_fcg(fs_ctx *c, SolveScal *h, bool warm)
     SolveScal *s = c->scal + 0;
     const int n4 = L.nC / 4;
     const int b4 = grid_blocks(c, n4, TH), bs = grid_blocks(c, L.nC, TH);
-    const double tol2 = c->prm.tol_p * c->prm.tol_p;
+    const double tol2 = c->prm.tol_p * c->prm.tol_p * (c->tol2_scale > 0.0 ? c->tol2_scale : 1.0);
     const double by_vec = (double)L.nC * 4.0;
     if (warm) {
         if ((rc = pressure_restart(c))) return rc;  // r = b - A x, iteration count kept

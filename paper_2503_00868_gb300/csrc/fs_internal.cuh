@@ -113,6 +113,13 @@ struct fs_ctx {
 
     // pressure solve (cell space)
     float *pb, *pr, *pp[2], *pq, *px, *pz;
+    // iterative refinement of the pressure solve: the first solution (head), the
+    // sum of earlier corrections (tail) and the right-hand side of the correction
+    // being solved. After a refined solve the pressure is the pair q_head + px.
+    float *pxh, *pxt, *pbr;
+    const float *q_head;  // null unless the last pressure solve was refined
+    int refining;         // a correction is being solved: no warm start
+    double tol2_scale;    // the stopping test is r.r <= tol_p^2 * tol2_scale * b.b (0 reads as 1)
     // warm start: last converged pressure of a forward (0) / adjoint (1) projection,
     // allocated on first use, invalidated by set_mask
     float *pw[2];

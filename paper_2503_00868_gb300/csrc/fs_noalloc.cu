@@ -82,7 +82,7 @@ extern "C" int fs_project_noalloc(int nx, int ny, int nz, const uint8_t *cell_ty
 
     // carve the scratch: flags, the Jacobi-PCG vectors, scalars, partials
     const size_t cb = round256((size_t)nC * sizeof(float));
-    const size_t need = round256((size_t)nC) + round256((size_t)nF) + round256((size_t)nF * sizeof(float)) + 6 * cb +
+    const size_t need = round256((size_t)nC) + round256((size_t)nF) + round256((size_t)nF * sizeof(float)) + 9 * cb +
                         round256(4 * sizeof(SolveScal)) + round256((size_t)c.max_blocks * 8 * sizeof(double)) + 256;
     if (need > kNoAllocScratchBytes)
         return set_error(FS_EINVAL,
@@ -106,6 +106,9 @@ extern "C" int fs_project_noalloc(int nx, int ny, int nz, const uint8_t *cell_ty
     c.pp[1] = reinterpret_cast<float *>(take(cb));
     c.pq = reinterpret_cast<float *>(take(cb));
     c.px = reinterpret_cast<float *>(take(cb));
+    c.pxh = reinterpret_cast<float *>(take(cb));
+    c.pxt = reinterpret_cast<float *>(take(cb));
+    c.pbr = reinterpret_cast<float *>(take(cb));
     c.scal = reinterpret_cast<SolveScal *>(take(4 * sizeof(SolveScal)));
     c.partials = reinterpret_cast<double *>(take((size_t)c.max_blocks * 8 * sizeof(double)));
     c.err_word = reinterpret_cast<unsigned *>(take(16));

@@ -272,6 +272,49 @@ __global__ void __launch_bounds__(TH) k_pois_true_res(const float *__restrict__ 
     }
 }
 
+// The right-hand side of a refinement step: r = b - A x evaluated in FP64 and
+// rounded once to FP32, on the liquid (zero elsewhere, guard planes included).
+// r may alias b: every thread reads b only at the element it writes.
+__global__ void __launch_bounds__(TH) k_pois_refine_rhs(const float *b, const float *__restrict__ x,
+                                                        const uint8_t *__restrict__ fl, int n, int P, int PL,
+                                                        float *r)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        float v = 0.f;
+        if (fl[t] & CF_LIQ) {
+            const double nb = ((double)x[t - 1] + (double)x[t + 1]) + ((double)x[t - P] + (double)x[t + P]) +
+                              ((double)x[t - PL] + (double)x[t + PL]);
+            v = (float)((double)b[t] - ((double)PoisOp::diag(fl[t], 0.f) * (double)x[t] - nb));
+        }
+        r[t] = v;
+    }
+}
+
+// a += b over n elements (n a multiple of 4)
+__global__ void __launch_bounds__(TH) k_add4(float *a, const float *__restrict__ b, int n4)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += gridDim.x * blockDim.x) {
+        float4 u = reinterpret_cast<float4 *>(a)[t];
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(b) + t);
+        u.x += v.x;
+        u.y += v.y;
+        u.z += v.z;
+        u.w += v.w;
+        reinterpret_cast<float4 *>(a)[t] = u;
+    }
+}
+
+// out = a + b over n elements (n a multiple of 4)
+__global__ void __launch_bounds__(TH) k_sum4(float *out, const float *__restrict__ a, const float *__restrict__ b,
+                                             int n4)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += gridDim.x * blockDim.x) {
+        const float4 u = __ldg(reinterpret_cast<const float4 *>(a) + t);
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(b) + t);
+        reinterpret_cast<float4 *>(out)[t] = make_float4(u.x + v.x, u.y + v.y, u.z + v.z, u.w + v.w);
+    }
+}
+
 // Residual replacement: restart CG from the current x with the true residual
 // r = b - A x (Jacobi: stored as z = D^-1 r), both p buffers zero; r.r (and
 // for Jacobi r.z) recomputed, the iteration count kept.
@@ -350,16 +393,18 @@ __global__ void __launch_bounds__(TH) k_divergence(CF3 u, float *__restrict__ b,
 }
 
 // out = in - grad q / dx on fluid faces, in elsewhere, 0 in padding; the
-// y = 3 slice copies q to q_out (public layout).
+// y = 3 slice copies q to q_out (public layout). After a refined solve the
+// pressure is the pair q + q2 (q2 nullable), whose differences are taken term
+// by term, so it is never rounded to one FP32 value on the way to the velocity.
 __global__ void __launch_bounds__(TH) k_grad_subtract(CF3 in, F3 out, const float *__restrict__ q,
-                                                      float *q_out, const uint8_t *__restrict__ ff, Layout L,
-                                                      float inv_dx)
+                                                      const float *__restrict__ q2, float *q_out,
+                                                      const uint8_t *__restrict__ ff, Layout L, float inv_dx)
 {
     const int c = blockIdx.y;
     if (c == 3) {
         if (!q_out) return;
         for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < L.S; idx += gridDim.x * blockDim.x)
-            q_out[idx] = q[L.PL + idx];
+            q_out[idx] = q2 ? q[L.PL + idx] + q2[L.PL + idx] : q[L.PL + idx];
         return;
     }
     const int off = c == 0 ? 1 : (c == 1 ? L.P : L.PL);
@@ -369,7 +414,11 @@ __global__ void __launch_bounds__(TH) k_grad_subtract(CF3 in, F3 out, const floa
         float v = 0.f;
         if (f) {
             v = in.c[c][idx];
-            if (f & FF_FLUID) v -= (q[L.PL + idx] - q[L.PL + idx - off]) * inv_dx;
+            if (f & FF_FLUID) {
+                float dq = q[L.PL + idx] - q[L.PL + idx - off];
+                if (q2) dq += q2[L.PL + idx] - q2[L.PL + idx - off];
+                v -= dq * inv_dx;
+            }
         }
         out.c[c][idx] = v;
     }
@@ -604,7 +653,7 @@ int remove_null_mode(fs_ctx *c, float *z)
     return FS_OK;
 }
 
-static int pressure_tail(fs_ctx *c, const SolveScal &h, fs_stats *st);
+static int pressure_tail(fs_ctx *c, const SolveScal &h, long long iters, double bb0, fs_stats *st);
 
 // Warm start (fs_params.warm_start): after the x = 0 initialisation, start
 // instead from the last converged pressure of the same kind of projection when
@@ -648,7 +697,14 @@ static int save_warm_start(fs_ctx *c)
             return FS_OK;  // no warm start then; not an error of the solve
         }
     }
-    FS_CUDA(cudaMemcpyAsync(c->pw[k], c->px, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    if (c->q_head) {
+        const int n4 = c->L.nC / 4;
+        k_sum4<<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(c->pw[k], c->q_head, c->px, n4);
+        c->n_launches += 1;
+        FS_CUDA(cudaGetLastError());
+    } else {
+        FS_CUDA(cudaMemcpyAsync(c->pw[k], c->px, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    }
     c->pw_valid[k] = 1;
     return FS_OK;
 }
@@ -664,35 +720,27 @@ int pressure_restart(fs_ctx *c)
     return FS_OK;
 }
 
-// Jacobi- or MIC(0)-PCG on pb -> px: from x = 0, or (warm) from the current x
-// with the true residual (residual replacement). Final scalars in h.
-static int pcg_iterate(fs_ctx *c, SolveScal &h, bool warm)
+// Jacobi-, MIC(0)- or multigrid-PCG on pb -> px from x = 0 (or from the last
+// converged pressure, with fs_params.warm_start). Final scalars in h.
+static int pcg_iterate(fs_ctx *c, SolveScal &h)
 {
     const Layout &L = c->L;
     SolveScal *s = c->scal + 0;
     const bool jac = c->prm.precond == FS_PRECOND_JACOBI;
     const int n4 = L.nC / 4;
-    const double tol2 = c->prm.tol_p * c->prm.tol_p;
+    const double tol2 = c->prm.tol_p * c->prm.tol_p * (c->tol2_scale > 0.0 ? c->tol2_scale : 1.0);
     // z = M r for MIC(0) or the multigrid V-cycle (the stored-z preconditioners)
     auto apply_m = [&]() -> int {
         return c->prm.precond == FS_PRECOND_MG ? mg_apply(c, c->pr, c->pz, &s->done) : mic0_apply(c, c->pr, c->pz);
     };
-    if (warm) {
-        if (jac)
-            k_pois_restart<true><<<grid_blocks(c, L.nC, TH), TH, 0, c->stream>>>(
-                c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, L.nC, L.P, L.PL, s, c->partials);
-        else
-            k_pois_restart<false><<<grid_blocks(c, L.nC, TH), TH, 0, c->stream>>>(
-                c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, L.nC, L.P, L.PL, s, c->partials);
-    } else {
-        if (jac)
-            k_pois_init<true><<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(
-                c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, n4, tol2, c->prm.maxit_p, s, c->partials);
-        else
-            k_pois_init<false><<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(
-                c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, n4, tol2, c->prm.maxit_p, s, c->partials);
+    if (jac)
+        k_pois_init<true><<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(
+            c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, n4, tol2, c->prm.maxit_p, s, c->partials);
+    else
+        k_pois_init<false><<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(
+            c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, n4, tol2, c->prm.maxit_p, s, c->partials);
+    if (!c->refining)
         if (int rc = try_warm_start(c, jac)) return rc;
-    }
     if (!jac) {
         int rc = apply_m();
         if (rc) return rc;
@@ -766,14 +814,19 @@ static int pcg_iterate(fs_ctx *c, SolveScal &h, bool warm)
     return check_wait_error(c, "pressure solve");
 }
 
+// At most this many refinement steps per solve (one suffices unless CG itself
+// stalled on the first pass).
+constexpr int kMaxRefine = 2;
+
 static int solve_pressure_once(fs_ctx *c, fs_stats *st)
 {
+    c->q_head = nullptr;
     if (c->prm.pressure_solver == FS_SOLVER_PERCNN) {
         // K recurrent sub-steps: no convergence test, the true residual is reported
         SolveScal h;
         int rc = solve_pressure_percnn(c, &h);
         if (rc) return rc;
-        return pressure_tail(c, h, st);
+        return pressure_tail(c, h, h.iter, 0.0, st);
     }
     const bool learned = c->prm.precond == FS_PRECOND_LEARNED;
     if (learned && !net_loaded(c))
@@ -785,33 +838,82 @@ static int solve_pressure_once(fs_ctx *c, fs_stats *st)
     }
     const Layout &L = c->L;
     const int bs = grid_blocks(c, L.nC, TH);
-    SolveScal h;
-    // The recursively updated FP32 residual drifts from b - A x over many
-    // iterations; when it meets the tolerance but the true residual is above
-    // twice the tolerance, CG restarts from x with the true residual (at most
-    // twice).
-    for (int restart = 0;; restart++) {
-        int rc = learned ? solve_pressure_fcg(c, &h, restart > 0) : pcg_iterate(c, h, restart > 0);
-        if (rc) return rc;
-        // (a singular system keeps its iterates in the operator's range: no restart)
-        if (h.status != FS_OK || restart == 2 || !(h.bb > 0.0) || c->singular) break;
+    // Mixed-precision iterative refinement. CG runs on FP32 vectors, so its
+    // recursively updated residual drifts from b - A x, and the rounding of the
+    // FP32 iterate alone leaves |b - A x| ~ 2e-7 |A x| |x| / |x|: with a smooth
+    // right-hand side (|x| >> |b|) that is above the tolerance (7.9e-6 |b| on a
+    // 256^3 blob). When the FP64-evaluated residual of x is above tol |b|, the
+    // solve runs again on the correction system A d = b - A x, whose right-hand
+    // side is that FP64 residual rounded once to FP32, to an absolute target of
+    // tol |b| / 2. The pressure is then kept as the FP32 pair (x, d): the gradient
+    // subtract and the warm start read both terms, so it is never rounded to a
+    // single FP32 vector on the solver's path.
+    float *const b0 = c->pb;
+    SolveScal h, m;
+    double bb0 = 0.0;
+    long long iters = 0;
+    int rc = FS_OK, nref = 0;
+    for (int pass = 0;; pass++) {
+        rc = learned ? solve_pressure_fcg(c, &h, false) : pcg_iterate(c, h);
+        if (rc) break;
+        iters += h.iter;
+        if (h.status != FS_OK) break;
         k_pois_true_res<<<bs, TH, 0, c->stream>>>(c->pb, c->px, c->cflag, L.nC, L.P, L.PL, c->singular,
                                                   c->scal + 2, c->partials);
         c->n_launches += 1;
-        FS_CUDA(cudaGetLastError());
-        SolveScal m;
-        if ((rc = read_scal(c, 2, &m))) return rc;
-        if (m.aux[0] <= 4.0 * h.tol2 * m.aux[1]) break;
+        if ((rc = check_cuda(cudaGetLastError(), "k_pois_true_res")) || (rc = read_scal(c, 2, &m))) break;
+        if (pass == 0) bb0 = m.aux[1];
+        const double tol2 = c->prm.tol_p * c->prm.tol_p;
+        if (pass == kMaxRefine || !(bb0 > 0.0) || !(m.aux[0] > tol2 * bb0)) break;
+        // the next correction: its right-hand side from the FP64 residual of the
+        // pressure so far, the terms solved so far kept in the head and the tail
+        if (pass == 0) {
+            if ((rc = check_cuda(cudaMemcpyAsync(c->pxh, c->px, (size_t)L.nC * sizeof(float),
+                                                 cudaMemcpyDeviceToDevice, c->stream),
+                                 "cudaMemcpyAsync")) ||
+                (rc = remove_null_mode(c, c->pxh)))
+                break;
+            c->q_head = c->pxh;
+            c->pb = c->pbr;
+            k_pois_refine_rhs<<<bs, TH, 0, c->stream>>>(b0, c->pxh, c->cflag, L.nC, L.P, L.PL, c->pbr);
+        } else {
+            k_pois_refine_rhs<<<bs, TH, 0, c->stream>>>(c->pbr, c->px, c->cflag, L.nC, L.P, L.PL, c->pbr);
+            if (pass == 1) {
+                if ((rc = check_cuda(cudaMemcpyAsync(c->pxt, c->px, (size_t)L.nC * sizeof(float),
+                                                     cudaMemcpyDeviceToDevice, c->stream),
+                                     "cudaMemcpyAsync")))
+                    break;
+            } else {
+                k_add4<<<grid_blocks(c, L.nC / 4, TH), TH, 0, c->stream>>>(c->pxt, c->px, L.nC / 4);
+            }
+        }
+        c->n_launches += 1;
+        if ((rc = check_cuda(cudaGetLastError(), "k_pois_refine_rhs")) || (rc = remove_null_mode(c, c->pbr))) break;
+        c->tol2_scale = 0.25 * bb0 / m.aux[0];
+        c->refining = 1;
+        nref += 1;
         if (st) st->restarts_p += 1;
     }
-    int rc = pressure_tail(c, h, st);
+    c->refining = 0;
+    c->tol2_scale = 1.0;
+    c->pb = b0;
+    if (rc) return rc;
+    if (nref >= 2) {  // fold the earlier corrections into the tail
+        k_add4<<<grid_blocks(c, L.nC / 4, TH), TH, 0, c->stream>>>(c->px, c->pxt, L.nC / 4);
+        c->n_launches += 1;
+    }
+    if (c->q_head) c->pb = c->pbr;  // the residual of the pair is that of the last correction
+    rc = pressure_tail(c, h, iters, bb0, st);
+    c->pb = b0;
     if (rc == FS_OK) rc = save_warm_start(c);
     return rc;
 }
 
-// After the iterations: the true residual b - A x, the mean-free representative
-// of a singular solve, and the statistics.
-static int pressure_tail(fs_ctx *c, const SolveScal &h, fs_stats *st)
+// After the iterations: the true residual (FP64) of the system in pb and px,
+// relative to |b0|^2 when bb0 > 0 (the original right-hand side of a refined
+// solve), else to |b|^2; the mean-free representative of a singular solve; the
+// statistics.
+static int pressure_tail(fs_ctx *c, const SolveScal &h, long long iters, double bb0, fs_stats *st)
 {
     const Layout &L = c->L;
     const int bs = grid_blocks(c, L.nC, TH);
@@ -828,10 +930,11 @@ static int pressure_tail(fs_ctx *c, const SolveScal &h, fs_stats *st)
     SolveScal m;
     int rc = read_scal(c, 2, &m);
     if (rc) return rc;
+    const double bb = bb0 > 0.0 ? bb0 : m.aux[1];
     if (st) {
-        st->iters_p += h.iter;
-        st->relres_p = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
-        st->true_relres_p = m.aux[1] > 0 ? std::sqrt(m.aux[0] / m.aux[1]) : 0.0;
+        st->iters_p += (int)iters;
+        st->relres_p = bb > 0 ? std::sqrt(h.rr / bb) : 0.0;
+        st->true_relres_p = bb > 0 ? std::sqrt(m.aux[0] / bb) : 0.0;
         if (h.status != FS_OK && st->status == FS_OK) st->status = h.status;
     }
     return finish_status(h.status);
@@ -1027,7 +1130,8 @@ int launch_grad_subtract(fs_ctx *c, CF3 in, F3 out, float *q_out)
 {
     const Layout &L = c->L;
     dim3 grid(grid_blocks(c, L.S, TH), 4);
-    k_grad_subtract<<<grid, TH, 0, c->stream>>>(in, out, c->px, q_out, c->fflag, L, (float)(1.0 / c->prm.dx));
+    k_grad_subtract<<<grid, TH, 0, c->stream>>>(in, out, c->px, c->q_head, q_out, c->fflag, L,
+                                                (float)(1.0 / c->prm.dx));
     c->n_launches += 1;
     FS_CUDA(cudaGetLastError());
     return FS_OK;

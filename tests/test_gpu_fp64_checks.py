@@ -8,7 +8,9 @@ span eight decades (a divergent field scaled face by face by 10^U(-4, 4)):
 
 * the reported true relative residual equals |b - A q|_2 / |b|_2 recomputed in
   FP64 from the solver's own b (fs_divergence) and q (q_out), with A the
-  oracle's FP64 operator, to 1e-10 relative;
+  oracle's FP64 operator, to 1e-10 relative (at tolerance 1e-5, where no
+  refinement step runs, so q_out is the solver's FP32 iterate itself; after a
+  refinement the pressure is an FP32 pair and q_out its rounding);
 * the first iteration's step length alpha = r.z / p.Ap (Jacobi: z = p =
   D^-1 b) read back from q = alpha p agrees with alpha recomputed in FP64 to
   the FP32 resolution of q (2e-6 relative)."""
@@ -43,7 +45,7 @@ def test_true_residual_matches_fp64_recomputation(precond, field):
     n = 48
     types, _ = W.sphere_union(n, n, n, 6)
     og = O.Grid(types, 1.0 / n, 1 / 30, 0.01)
-    gg = F.Grid(n, n, n, dx=1.0 / n, tol_p=1e-6, maxit_p=5000, precond=precond)
+    gg = F.Grid(n, n, n, dx=1.0 / n, tol_p=1e-5, maxit_p=5000, precond=precond)
     gg.set_mask(types)
     u0 = wide_range_field(n, n, n, 3) if field == "wide_range" else W.random_mac(n, n, n, 3)
     u = gg.pack(u0)
@@ -51,7 +53,7 @@ def test_true_residual_matches_fp64_recomputation(precond, field):
     F.fs_divergence(gg.ctx, u, b)
     q = gg.empty_cell()
     rc, st = gg.project(u, q)
-    assert rc in (F.FS_OK, F.FS_ENOCONV), st
+    assert rc == F.FS_OK and st["restarts_p"] == 0, st
     b64 = gg.unpack_cell(b)
     q64 = gg.unpack_cell(q)
     liq = types == 1

@@ -10,7 +10,13 @@ solver (Jacobi, MIC(0), the multigrid V-cycle) works across it.
 Every field is compared twice: a global relative L2 error (velocity 1e-5,
 gradients 1e-4, the tolerances of the fluid-step parity tests) and a per-face
 bound, max |gpu - oracle| <= TOL * max |oracle|, so that an error confined to a
-few hundred faces (a tile edge) cannot hide in the global norm.
+few hundred faces (a tile edge) cannot hide in the global norm. For gradients
+the per-face bound leaves out the neighbourhoods (2 cells) of faces whose
+back-traced sample point lies within 3e-5 of a grid line in some axis, a few
+FP32 roundings of the index-space coordinate: trilinear interpolation has a kink
+there, the discrete adjoint jumps, and either one-sided value is correct, so
+the GPU (FP32 sample) and the oracle (FP64 sample) may take different sides.
+The faces left out are fewer than one in ten.
 
 The rollout test runs the benchmark's configuration: multigrid in both solves,
 warm-started pressure solves, tolerance 1e-6, a checkpointed rollout and its
@@ -53,8 +59,15 @@ def maxrel(a, b):
     return num / max(den, 1e-300)
 
 
-def check(a, b, tol, tol_max, what):
-    e2, em = rel(a, b), maxrel(a, b)
+def check(a, b, tol, tol_max, what, skip=None):
+    """rel-L2 over all faces; the per-face max over the faces not in `skip`"""
+    e2 = rel(a, b)
+    if skip is None:
+        em = maxrel(a, b)
+    else:
+        assert sum(int(k.sum()) for k in skip) < 0.1 * sum(k.size for k in skip)
+        num = max(float(np.abs(np.asarray(x, np.float64) - y)[~k].max()) for x, y, k in zip(a, b, skip))
+        em = num / max(float(np.abs(y).max()) for y in b)
     assert e2 < tol and em < tol_max, f"{what}: rel-L2 {e2:.3e} (bound {tol}), max {em:.3e} (bound {tol_max})"
 
 
@@ -131,11 +144,12 @@ def test_wide_step_and_adjoint(precond):
     gin = gg.zeros()
     rc, gnu, st = gg.adjoint_step(u, gg.pack(gout), gin, uv)
     assert rc == F.FS_OK, st
-    check(gg.unpack(gin), ogin, TOL_G, MAX_G, "adjoint")
+    check(gg.unpack(gin), ogin, TOL_G, MAX_G, "adjoint", skip=O.kink_faces(og, u0))
     assert abs(gnu - ognu) <= TOL_G * abs(ognu), (gnu, ognu)
 
 
 def oracle_rollout(og, u0, targets, nsteps):
+    """(loss, dL/du0, dL/dnu, the states of the forward pass)"""
     states = [u0]
     for _ in range(nsteps):
         states.append(O.step(og, states[-1])[0])
@@ -147,7 +161,7 @@ def oracle_rollout(og, u0, targets, nsteps):
             g = tuple(a + b for a, b in zip(g, O.loss_grad(og, states[n], targets[n])[1]))
         g, dnu = O.adjoint_step(og, states[n - 1], g)
         gnu += dnu
-    return loss, g, gnu
+    return loss, g, gnu, states
 
 
 def test_wide_rollout_benchmark_configuration():
@@ -164,7 +178,9 @@ def test_wide_rollout_benchmark_configuration():
         fc = O.face_class(og, c)
         u0[c][fc == 2] = bc[c][fc == 2]
     tg = {1: W.blurred_noise_mac(nx, ny, nz, 101), 3: W.blurred_noise_mac(nx, ny, nz, 103)}
-    oloss, og_u0, ognu = oracle_rollout(og, u0, tg, 3)
+    oloss, og_u0, ognu, states = oracle_rollout(og, u0, tg, 3)
+    kinks = [O.kink_faces(og, st) for st in states[:3]]
+    skip = tuple(np.logical_or.reduce([k[c] for k in kinks]) for c in range(3))
 
     stats = []
     leaves = [t.requires_grad_(True) for t in gg.pack(u0)]
@@ -173,10 +189,10 @@ def test_wide_rollout_benchmark_configuration():
                         checkpoint_every=2, stats=stats)
     loss.backward()
     assert all(s[2]["status"] == F.FS_OK for s in stats), stats
-    assert abs(float(loss) - oloss) <= 1e-5 * abs(oloss), (float(loss), oloss)
+    assert abs(float(loss.detach()) - oloss) <= 1e-5 * abs(oloss), (float(loss.detach()), oloss)
     gu = gg.unpack(F.Mac(*(t.grad for t in leaves)))
     # fixed faces are inputs the step overwrites: their gradient is zero on both sides
-    check(gu, og_u0, TOL_G, MAX_G, "dL/du0")
+    check(gu, og_u0, TOL_G, MAX_G, "dL/du0", skip=skip)
     assert abs(float(nu_t.grad) - ognu) <= TOL_G * abs(ognu), (float(nu_t.grad), ognu)
 
 
@@ -211,9 +227,12 @@ def test_full_size_step_is_divergence_free_and_keeps_the_mask():
     div0 = torch_div(a, n, n, n)[liq].norm()
     for _ in range(2):
         rc, st = gg.step(a, b)
-        assert rc == F.FS_OK and st["true_relres_p"] <= 2e-6, st
+        # the FP64 residual of the pressure the velocity was corrected with
+        assert rc == F.FS_OK and st["true_relres_p"] <= 1e-6, st
+        # the divergence left in the FP32 output: the solve's residual plus the
+        # rounding of the output faces
         d = torch_div(b, n, n, n)[liq].norm()
-        assert float(d / div0) < 1e-5, float(d / div0)
+        assert float(d / div0) < 2e-6, float(d / div0)
         # no liquid cell next to a face: the face holds 0
         nb = torch.zeros((n, n, n + 1), dtype=torch.bool, device="cuda")
         nb[:, :, 1:] |= liq
