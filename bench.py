@@ -12,7 +12,16 @@ Scene (stand-in for the paper's video-derived liquid blob): an ellipsoid of
 liquid resting on the floor, 40 % occupancy, air elsewhere, box walls solid;
 initial velocity = seeded N(0,1) noise blurred by a sigma = 3 cell Gaussian;
 target = an independent blurred field (seed + 100); nu = 0.01, dt = 1/30,
-dx = 1/256, Jacobi-PCG to relative residual 1e-6 for both solves.
+dx = 1/256; both implicit solves by multigrid-preconditioned CG to relative
+residual 1e-6 (--precond jacobi / mic0 for the others), pressure solves warm
+started from the previous frame's pressure.
+
+Besides the headline line's keys it reports, per kernel, the live mean duration,
+the launches that did work and their estimated share of the step; a roofline for
+the single kernel with the largest share and one for the level-0 multigrid
+kernels together; the oracle on one host core and on all of them; the smaller
+configurations (32^3 plain forward with MIC(0), 128^3 forward + adjoint over four
+viscosities); and the projection comparison of the preconditioners at 256^3.
 
 Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 Multi-GPU runs are independent replicas (one scene per rank, no collective on
@@ -64,6 +73,8 @@ def args_parse():
     ap.add_argument("--cpu-sample-n", type=int, default=64)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 32^3 plain-forward and 128^3 four-viscosity configurations")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the Jacobi / MIC(0) / learned projection comparison")
     ap.add_argument("--compare-n", type=int, default=256)
@@ -80,34 +91,80 @@ def source_hash(files=KERNEL_FILES):
     return h.hexdigest()[:16]
 
 
-# profile entries timed every PROFILE_PERIOD-th CG iteration or V-cycle (the
-# others are timed at every launch)
-SAMPLED = ("pressure_spmv", "pressure_update", "visc_spmv", "visc_update", "fcg_vectors", "mg_smooth0",
-           "mg_vcycle_p", "mg_vcycle_v")
+# profile entries that aggregate several kernels (a whole V-cycle, the coarse
+# levels of one): reported, but not a kernel for the roofline
+AGGREGATES = ("all_kernels", "mg_vcycle_p", "mg_vcycle_v", "mg_coarse")
+# the level-0 multigrid kernels, reported together as one family
+MG_LEVEL0 = ("mg0_smooth2", "mg0_residual", "mg0_restrict", "mg0_prolong", "mg0_smooth", "mg0_smooth_z")
+
+
+def _entry(v):
+    """(timed launches, total ms, bytes, all launches) from a profile value (the
+    all-launch count defaults to the timed count)"""
+    return (v[0], v[1], v[2], v[3] if len(v) > 3 else v[0])
+
+
+def kernel_table(prof, step_ms, steps, hbm):
+    """Per profile entry: timed launches, launches that did work, live mean, the
+    estimated share of the step (mean x all launches / timed region) and, where
+    algorithmic bytes are known, the achieved GB/s and its fraction of `hbm`."""
+    out = {}
+    for k, v in prof.items():
+        launches, ms, by, alln = _entry(v)
+        if k == "all_kernels" or not launches:
+            continue
+        mean_ms = ms / launches
+        e = {"timed_launches": launches, "launches": alln, "mean_us": round(1e3 * mean_ms, 2),
+             "est_share_of_step": round(mean_ms * alln / (step_ms * steps), 4)}
+        if by > 0:
+            gbs = (by / launches) / (mean_ms * 1e-3) / 1e9
+            e["achieved_gbs"] = round(gbs, 1)
+            e["frac_of_hbm"] = round(gbs / hbm, 3)
+            e["algorithmic_bytes_per_launch"] = by / launches
+        out[k] = e
+    return out
 
 
 def roofline_of(prof, peaks, src_hash, traffic_table=None):
-    """The roofline object of the profile entry with the largest estimated share
-    of the step among those that carry algorithmic bytes. prof maps a name to
-    (timed launches, total ms, total algorithmic bytes). achieved = bytes per
-    launch / mean launch time; the peak is the measured HBM copy bandwidth (the
-    6800 GB/s fallback without a measurement); the ncu traffic is reported only
-    while the hash of the files that define the kernels matches its capture's."""
+    """The roofline object of the single kernel with the largest estimated share
+    of the step among those that carry algorithmic bytes (the share is its mean
+    duration times the launches that did work). prof maps a name to (timed
+    launches, total ms, total algorithmic bytes[, all launches]). achieved = bytes
+    per launch / mean launch time; the peak is the measured HBM copy bandwidth
+    (the 6800 GB/s fallback without a measurement); the ncu traffic is reported
+    only while the hash of the files that define the kernels matches its
+    capture's."""
     traffic_table = NCU_TRAFFIC if traffic_table is None else traffic_table
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
-    top = max((k for k in prof.items() if k[0] != "all_kernels" and k[1][2] > 0 and k[1][0] > 0),
-              key=lambda kv: kv[1][1] * (PROFILE_PERIOD if kv[0] in SAMPLED else 1), default=None)
+    cands = [(k, _entry(v)) for k, v in prof.items() if k not in AGGREGATES]
+    top = max((kv for kv in cands if kv[1][2] > 0 and kv[1][0] > 0),
+              key=lambda kv: kv[1][1] / kv[1][0] * kv[1][3], default=None)
     if top is None:
         return None
-    name, (launches, ms, by) = top
+    name, (launches, ms, by, alln) = top
     achieved = (by / launches) / (ms / launches * 1e-3) / 1e9
     tr = traffic_table.get(name)
     traffic = tr["bytes_per_launch"] if tr and tr.get("source") == src_hash else None
     return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": traffic,
-            "algorithmic_bytes_per_launch": by / launches, "launches": launches,
+            "algorithmic_bytes_per_launch": by / launches, "launches": launches, "launches_all": alln,
             "avg_launch_us": 1e3 * ms / launches,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback"}
+
+
+def family_roofline(prof, peaks, names=MG_LEVEL0):
+    """The level-0 multigrid kernels as one family: summed algorithmic bytes of
+    their timed launches over their summed durations."""
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    got = [_entry(prof[k]) for k in names if k in prof and prof[k][0] > 0]
+    if not got:
+        return None
+    by = sum(v[2] for v in got)
+    ms = sum(v[1] for v in got)
+    achieved = by / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernels": [k for k in names if k in prof], "achieved": achieved, "peak": hbm,
+            "unit": "GB/s", "frac": achieved / hbm,
+            "note": "level 0 of the pressure V-cycle, timed kernel by kernel on the library stream"}
 
 
 def measured_peaks():
@@ -181,14 +238,19 @@ def params_for(n, precond, warm_start=1):
                 maxit_p=20000, maxit_v=4000, warm_start=warm_start)
 
 
-def cpu_oracle_sample(n, frames=1):
+ORACLE_SAMPLE = ("FP64 oracle (plain C), fwd+adjoint of 1 frame of the same scene recipe at {n}^3: "
+                 "MIC(0)-PCG pressure and Jacobi-PCG viscosity to 1e-6, loss at that frame")
+
+
+def cpu_oracle_sample(n, frames=1, seed=0):
     """The FP64 oracle, as it stands, on a bounded sample of the workload: the
-    same scene recipe at n^3, one forward step + loss + one adjoint step."""
+    same scene recipe at n^3, one forward step + loss + one adjoint step, with
+    the oracle's fastest pressure preconditioner (MIC(0))."""
     import oracle as O
-    types, u0, tgt, _ = make_scene(n, 0)
+    types, u0, tgt, _ = make_scene(n, seed)
     kw = params_for(n, "jacobi")
     g = O.Grid(types, kw["dx"], kw["dt"], kw["nu"], g=kw["g"], tol_p=kw["tol_p"], tol_v=kw["tol_v"],
-               precond=O.PC_JACOBI)
+               precond=O.PC_MIC0)
     t0 = time.perf_counter()
     states = [u0]
     for _ in range(frames):
@@ -198,6 +260,37 @@ def cpu_oracle_sample(n, frames=1):
         gbar, _ = O.adjoint_step(g, states[k], gbar)
     dt = time.perf_counter() - t0
     return n ** 3 * frames / dt, dt
+
+
+def _oracle_worker(args):
+    n, seed = args
+    import oracle as O
+    O.build()
+    return cpu_oracle_sample(n, seed=seed)
+
+
+def cpu_oracle_all_cores(n, cores=None):
+    """The same oracle sample run as independent copies, one per host core (a
+    process pool started with spawn): the host's whole-machine throughput on the
+    sample, cell-steps/s summed over the copies."""
+    import multiprocessing as mp
+    cores = cores or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_worker, [(n, s) for s in range(cores)])
+    wall = time.perf_counter() - t0
+    return cores * n ** 3 / wall, cores, wall, res
+
+
+def reference_config(a):
+    """The configuration the reference arm actually runs: the oracle on a bounded
+    sample of the benchmark's scene recipe."""
+    n = a.cpu_sample_n
+    return {"workload": ORACLE_SAMPLE.format(n=n) + f"; stands in for the {a.n}^3, {a.frames}-frame benchmark, "
+                        "whose full size the oracle cannot finish in minutes",
+            "grid": [n, n, n], "frames": 1, "precond": "mic0 (pressure), jacobi (viscosity)", "tol": 1e-6,
+            "nu": 0.01, "dt": 1.0 / 30.0, "dtype": "f64", "cores": 1, "parallelism": "single"}
 
 
 def run_reference(a):
@@ -215,12 +308,12 @@ def run_reference(a):
         vals.append(v)
         total += dt
     value = a.steps * n ** 3 / total
-    sample = (f"oracle fwd+adjoint of 1 step of the same scene recipe at {n}^3 (iteration counts grow with n, "
-              f"so this overstates the oracle's throughput at 256^3)")
+    sample = (ORACLE_SAMPLE.format(n=n) + ", one host core (iteration counts grow with n, so this overstates "
+              "the oracle's throughput at 256^3)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total / a.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(a),
+            "data": "synthetic", "config": reference_config(a),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -294,6 +387,77 @@ def precond_compare(n, seeds=(0,)):
         g.close()
         out["rows"].append(row)
     return out
+
+
+def config_c1():
+    """The plain forward configuration: 32^3, all cells liquid in a closed box,
+    dx = 1/32, dt = 1/30, nu = 0.01, 10 steps from the blurred noise field,
+    MIC(0)-PCG to 1e-6 (Jacobi-PCG for the viscosity). Device time of the 10
+    steps after one untimed run."""
+    import torch
+    from paper_2503_00868_gb300 import fluidstep as F
+    from paper_2503_00868_gb300 import workloads as W
+    n, steps = 32, 10
+    g = F.Grid(n, n, n, dx=1.0 / n, dt=1.0 / 30.0, nu=0.01, precond=F.FS_PRECOND_MIC0, tol_p=1e-6, tol_v=1e-6,
+               maxit_p=20000, maxit_v=4000)
+    g.set_mask(W.all_liquid(n, n, n))
+    u0 = g.pack(W.blurred_noise_mac(n, n, n, 0))
+    a, b = g.zeros(), g.zeros()
+    sts = []
+    for rep in range(2):
+        for t, s0 in zip(a, u0):
+            t.copy_(s0)
+        sts.clear()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            rc, st = g.step(a, b)
+            sts.append(st)
+            a, b = b, a
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    g.close()
+    return {"workload": "plain forward, 32^3 closed box full of liquid, 10 steps, MIC(0)-PCG to 1e-6",
+            "value": n ** 3 * steps / (ms * 1e-3), "unit": "cell-steps/s", "ms": round(ms, 3),
+            "pressure_iters_mean": sum(x["iters_p"] for x in sts) / len(sts),
+            "true_relres_p_max": max(x["true_relres_p"] for x in sts)}
+
+
+def config_c2(nus=(1e-4, 1e-3, 1e-2, 1e-1), frames=24):
+    """Forward + adjoint at 128^3: the ellipsoid blob (40 % occupancy), 24 frames,
+    checkpoint every 4, the band loss at the last frame against an independent
+    blurred target, gradients w.r.t. nu and u0, one run per viscosity (after an
+    untimed one), with the benchmark's multigrid solves."""
+    import torch
+    from paper_2503_00868_gb300 import fluidstep as F
+    from paper_2503_00868_gb300.rollout import rollout_loss
+    n = 128
+    types, u0_np, tgt_np, info = make_scene(n, 0)
+    grid = F.Grid(n, n, n, **params_for(n, "mg", 1))
+    grid.set_mask(types)
+    u0, tgt = grid.pack(u0_np), grid.pack(tgt_np)
+    rows, total_ms = [], 0.0
+    for nu in nus:
+        for rep in range(2):
+            leaves = [t.detach().clone().requires_grad_(True) for t in u0]
+            nu_t = torch.tensor(nu, dtype=torch.float32, requires_grad=True)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            loss = rollout_loss(grid, F.Mac(*leaves), nu_t, frames, {frames: tgt}, CHECKPOINT)
+            loss.backward()
+            e1.record()
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        total_ms += ms
+        rows.append({"nu": nu, "ms": round(ms, 2), "cell_steps_per_s": n ** 3 * frames / (ms * 1e-3),
+                     "loss": float(loss.detach()), "dL_dnu": float(nu_t.grad)})
+    grid.close()
+    return {"workload": f"fwd+adjoint, 128^3 ellipsoid blob ({info['occupancy']:.2f} occupancy), {frames} frames, "
+                        "checkpoint 4, band loss at the last frame, multigrid PCG to 1e-6",
+            "value": len(nus) * n ** 3 * frames / (total_ms * 1e-3), "unit": "cell-steps/s", "rows": rows}
 
 
 def dist_env():
@@ -388,13 +552,16 @@ def main():
     ms_per_step = 1e3 * elapsed / a.steps
     iters_p = [s[2]["iters_p"] for s in stats if s[0] == "fwd"]
     iters_v = [s[2]["iters_v"] for s in stats if s[0] == "fwd"]
+    refines = [s[2]["restarts_p"] for s in stats]
 
     # ---- end to end through the public API with host buffers ---------------
     e2e = None
     if not a.no_e2e:
         host_u0 = [t.cpu().pin_memory() for t in u0]
         host_t = [t.cpu().pin_memory() for t in tgt]
+        host_g = [torch.empty_like(t, device="cpu").pin_memory() for t in u0]
         hb = sum(t.numel() * 4 for t in host_u0) + sum(t.numel() * 4 for t in host_t)
+        db = sum(t.numel() * 4 for t in host_g) + 16
         results = []
         barrier()
         torch.cuda.synchronize()
@@ -403,38 +570,44 @@ def main():
         for _ in range(a.steps):
             du = F.Mac(*(h.to("cuda", non_blocking=True) for h in host_u0))
             dtg = F.Mac(*(h.to("cuda", non_blocking=True) for h in host_t))
-            loss, gnu, _ = one_step(du, dtg)
-            # the step's result read back on the host: loss and dL/dnu (2 doubles)
+            loss, gnu, leaves_e = one_step(du, dtg)
+            # the step's results read back on the host: dL/du0, the loss and dL/dnu
+            for h, t in zip(host_g, leaves_e):
+                h.copy_(t.grad, non_blocking=True)
             results.append((float(loss.detach().cpu()), float(gnu.detach().cpu())))
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
         t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, "cuda")
         e2e = {"value": job_throughput(world, a.steps, cells, frames, t_e2e), "unit": UNIT,
-               "h2d_bytes_per_step": hb, "d2h_bytes_per_step": 16}
+               "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db}
 
     # ---- roofline of the dominant kernel -----------------------------------
-    roofline = roofline_of(prof, measured_peaks(), source_hash())
-    # CG kernels and V-cycles are timed every PROFILE_PERIOD-th iteration, the others at every launch
-    kernels = {}
-    for k, v in prof.items():
-        if k == "all_kernels" or not v[0]:
-            continue
-        scale = PROFILE_PERIOD if k in SAMPLED else 1
-        kernels[k] = {"timed_launches": v[0], "mean_us": round(1e3 * v[1] / v[0], 2),
-                      "est_share_of_step": round(scale * v[1] / (1e3 * elapsed), 4)}
+    peaks = measured_peaks()
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    roofline = roofline_of(prof, peaks, source_hash())
+    mg_family = family_roofline(prof, peaks)
+    kernels = kernel_table(prof, ms_per_step, a.steps, hbm)
     gpu_launches = None
     if "all_kernels" in prof:
         gpu_launches = prof["all_kernels"][0]
 
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not a.no_cpu:
         import oracle as O
         O.build()
         v, dt = cpu_oracle_sample(a.cpu_sample_n)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"oracle fwd+adjoint of 1 step of the same scene recipe at {a.cpu_sample_n}^3 "
-                         f"({dt:.1f} s; iteration counts grow with n, so this overstates the oracle at 256^3)"}
+               "sample": ORACLE_SAMPLE.format(n=a.cpu_sample_n) + f", one host core ({dt:.1f} s; iteration "
+                         "counts grow with n, so this overstates the oracle at 256^3)"}
+        va, cores, wall, _ = cpu_oracle_all_cores(a.cpu_sample_n)
+        cpu_all = {"value": va, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"{cores} independent copies of the one-core sample, one per host core, "
+                             f"{wall:.1f} s wall"}
+
+    configs = None
+    if rank == 0 and world == 1 and not a.no_configs:
+        configs = {"plain_forward_32": config_c1(), "fwd_adjoint_128_four_nu": config_c2()}
 
     compare = None
     if rank == 0 and not a.no_compare:
@@ -445,10 +618,13 @@ def main():
                 "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(a),
                 "clocks": clocks, "e2e": e2e, "gpu_launches": gpu_launches, "roofline": roofline,
-                "cpu_baseline": cpu, "kernels": kernels, "occupancy": info["occupancy"],
+                "roofline_mg_level0": mg_family, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all,
+                "kernels": kernels, "occupancy": info["occupancy"],
                 "pcg_iters_per_step": {"pressure_mean": sum(iters_p) / max(len(iters_p), 1),
-                                       "viscosity_mean": sum(iters_v) / max(len(iters_v), 1)},
-                "loss": float(loss.detach()), "dL_dnu": float(gnu), "precond_compare": compare}
+                                       "viscosity_mean": sum(iters_v) / max(len(iters_v), 1),
+                                       "pressure_refinements": sum(refines)},
+                "loss": float(loss.detach()), "dL_dnu": float(gnu), "configs": configs,
+                "precond_compare": compare}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -81,8 +81,10 @@ enum {
     FS_PRECOND_JACOBI = 0,  /* diagonal scaling */
     FS_PRECOND_MIC0 = 1,    /* modified incomplete Cholesky, level 0 */
     FS_PRECOND_LEARNED = 2, /* the convolutional network, in flexible CG */
-    FS_PRECOND_MG = 3       /* geometric multigrid V-cycle (not in the paper: damped-Jacobi
+    FS_PRECOND_MG = 3,      /* geometric multigrid V-cycle (not in the paper: damped-Jacobi
                                smoothing, cell coarsening with air kept, trilinear transfers) */
+    FS_PRECOND_LEARNED_MG = 4 /* the network, then one V-cycle on what it leaves:
+                                 z = e + M(r - L_p e), e = s Net(r/s); in flexible CG */
 };
 
 enum {
@@ -108,8 +110,9 @@ typedef struct {
     double nu;         /* kinematic viscosity, >= 0 */
     double rho;        /* density, > 0; only scales the reported pressure */
     double g[3];       /* body acceleration per component */
-    int precond;       /* FS_PRECOND_* for the pressure solve; FS_PRECOND_MG also
-                          preconditions the viscosity solve (Jacobi otherwise) */
+    int precond;       /* FS_PRECOND_* for the pressure solve; FS_PRECOND_MG and
+                          FS_PRECOND_LEARNED_MG also precondition the viscosity solve with
+                          the V-cycle (Jacobi otherwise) */
     int maxit_p;       /* pressure iteration cap, >= 1 */
     int maxit_v;       /* viscosity iteration cap, >= 1 */
     double tol_p;      /* pressure relative residual target |r|/|b|, > 0 */
@@ -366,6 +369,9 @@ int fs_precond_apply(fs_ctx *c, const float *r, float *z);
  * Parameters are one flat FP32 vector in PyTorch Conv3d order: W1 [16][2][3][3][3],
  * b1 [16], W2, b2, W3, b3, W4, b4 (each [16][16][3][3][3], [16]), W5 [1][16][3][3][3],
  * b5 [1]; fs_net_param_count() gives its length. With precond = FS_PRECOND_LEARNED
+ * (the network alone) or FS_PRECOND_LEARNED_MG (the network followed by one
+ * multigrid V-cycle on its residual, z = e + M(r - L_p e) with e = s Net(r/s): the
+ * network acts as the fine-grid smoother and the V-cycle as the coarse correction)
  * the pressure solve runs flexible CG (beta = -z'.Ap / p.Ap); if that does not
  * reach the tolerance it is redone with MIC(0) and fs_stats.fallbacks counts it. */
 int fs_net_param_count(void);
@@ -381,10 +387,15 @@ int fs_net_read(fs_ctx *c, float *params_host, int count);
 int fs_net_forward(fs_ctx *c, const float *r, float *z);
 
 /* Training on one (b, q) pair with L_p q = b on the context's mask (DEVICE cell
- * arrays): with y = Net(b/s) and e = y - q/s on liquid cells, the relative error
- * in the energy norm of the pressure operator, loss = e.L_p e / (q/s).L_p (q/s)
- * (the fitted network should give the pressure of the Laplacian scheme,
- * Sec. 3.4.1), is ADDED to *loss (host) and its gradient ADDED to the context's
+ * arrays), for the role the context's precond selects. The loss is the relative
+ * error that the preconditioner leaves, in the energy norm of the pressure
+ * operator, loss = w.L_p w / (q/s).L_p (q/s) (the fitted network should give the
+ * pressure of the Laplacian scheme, Sec. 3.4.1), with y = Net(b/s) on liquid
+ * cells and
+ *   FS_PRECOND_LEARNED_MG:  w = q/s - y - M(b/s - L_p y), M the V-cycle
+ *                           (its gradient passes through M, which is symmetric);
+ *   any other precond:      w = q/s - y.
+ * The loss is ADDED to *loss (host) and its gradient ADDED to the context's
  * gradient accumulator. */
 int fs_net_grad(fs_ctx *c, const float *b, const float *q, double *loss);
 
@@ -420,9 +431,10 @@ int fs_net_train_step(fs_ctx *c, const float *b_batch, const float *q_batch, int
  * kernels without a stated figure. */
 typedef struct {
     char name[32];
-    long long launches;
-    double total_ms;
-    double bytes;
+    long long launches;      /* launches timed (every k-th of the sampled kinds) */
+    double total_ms;         /* their summed duration */
+    double bytes;            /* their summed algorithmic bytes */
+    long long all_launches;  /* launches of this kind that did work, timed or not (>= launches) */
 } fs_kernel_time;
 
 int fs_profile(fs_ctx *c, int enable);

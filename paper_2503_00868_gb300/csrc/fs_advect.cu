@@ -158,7 +158,10 @@ int launch_advect(fs_ctx *c, CF3 u)
     for (int comp = 0; comp < 3; comp++)
         k_advect<<<grid, 128, 0, c->stream>>>(u, c->vx, c->fflag, L, comp, h,
                                              (float)(c->prm.dt * c->prm.g[comp]));
-    prof_add(c, K_ADVECT, e0, prof_mark(c), 0.0);
+    // algorithmic bytes of the three launches: the three input components read
+    // once (the gathered neighbours come from cache), the face flags, and the
+    // three advected components written
+    prof_add(c, K_ADVECT, e0, prof_mark(c), 24.0 * (double)L.S + (double)L.nF);
     c->n_launches += 3;
     FS_CUDA(cudaGetLastError());
     return FS_OK;
@@ -174,7 +177,9 @@ int launch_advect_adjoint(fs_ctx *c, CF3 u, F3 g)
     cudaEvent_t e0 = prof_mark(c);
     for (int comp = 0; comp < 3; comp++)
         k_advect_adj<<<grid, 128, 0, c->stream>>>(u, c->vx, g, c->fflag, L, comp, h);
-    prof_add(c, K_ADVECT_ADJ, e0, prof_mark(c), 0.0);
+    // the input field and the cotangent read once, the face flags, and the
+    // scattered gradient written once (its atomic adds resolve in L2)
+    prof_add(c, K_ADVECT_ADJ, e0, prof_mark(c), 36.0 * (double)L.S + (double)L.nF);
     c->n_launches += 4;
     FS_CUDA(cudaGetLastError());
     return FS_OK;

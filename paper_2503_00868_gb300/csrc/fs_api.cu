@@ -41,7 +41,7 @@ static int check_params(const fs_params *p)
     if (!(p->rho > 0.0) || !std::isfinite(p->rho)) return set_error(FS_EINVAL, "rho must be > 0");
     for (int c = 0; c < 3; c++)
         if (!std::isfinite(p->g[c])) return set_error(FS_EINVAL, "g must be finite");
-    if (p->precond < FS_PRECOND_JACOBI || p->precond > FS_PRECOND_MG)
+    if (p->precond < FS_PRECOND_JACOBI || p->precond > FS_PRECOND_LEARNED_MG)
         return set_error(FS_EINVAL, "unknown preconditioner %d", p->precond);
     if (p->maxit_p < 1 || p->maxit_v < 1) return set_error(FS_EINVAL, "iteration caps must be >= 1");
     if (!(p->tol_p > 0.0) || !(p->tol_v > 0.0)) return set_error(FS_EINVAL, "tolerances must be > 0");
@@ -89,7 +89,9 @@ static int alloc_zero(void **p, size_t bytes)
 // ---- per-kernel timing ---------------------------------------------------------
 static const char *kKernelNames[K_COUNT] = {"pressure_spmv", "pressure_update", "visc_spmv", "visc_update",
                                             "advect", "advect_adjoint", "mic0_apply", "net_apply", "fcg_vectors",
-                                            "mg_smooth0", "mg_vcycle_p", "mg_vcycle_v"};
+                                            "mg_vcycle_p", "mg_vcycle_v", "mg0_smooth2", "mg0_residual",
+                                            "mg0_restrict", "mg0_prolong", "mg0_smooth", "mg0_smooth_z",
+                                            "mg_coarse"};
 
 struct Prof {
     std::vector<cudaEvent_t> free_ev, all_ev;
@@ -98,6 +100,7 @@ struct Prof {
     double ms[K_COUNT] = {};
     double bytes[K_COUNT] = {};
     long long n[K_COUNT] = {};
+    long long all[K_COUNT] = {};  // launches that did work, timed or not
 };
 
 cudaEvent_t prof_mark(fs_ctx *c)
@@ -121,6 +124,12 @@ void prof_add(fs_ctx *c, int id, cudaEvent_t a, cudaEvent_t b, double bytes)
         return;
     }
     p->pending.push_back({id, a, b, bytes});
+}
+
+void prof_count(fs_ctx *c, int id, long long launches)
+{
+    if (!c->prof_on || !c->prof) return;
+    static_cast<Prof *>(c->prof)->all[id] += launches;
 }
 
 void prof_flush(fs_ctx *c)
@@ -226,6 +235,7 @@ int fs_profile(fs_ctx *c, int enable)
             p->ms[k] = 0.0;
             p->bytes[k] = 0.0;
             p->n[k] = 0;
+            p->all[k] = 0;
         }
     }
     c->prof_on = enable > 0 ? 1 : 0;
@@ -250,6 +260,7 @@ int fs_profile_read(fs_ctx *c, fs_kernel_time *out, int max, int *count)
         e.launches = p->n[k];
         e.total_ms = p->ms[k];
         e.bytes = p->bytes[k];
+        e.all_launches = std::max(p->all[k], p->n[k]);
     }
     if (*count < max) {
         fs_kernel_time &e = out[(*count)++];

@@ -280,7 +280,7 @@ int solve_pressure_fcg(fs_ctx *c, SolveScal *h, bool warm)
                 ring.q[j] = f->q[sj];
                 ring.pq[j] = f->pq + sj;
             }
-            if ((rc = net_apply(c, c->pr, c->pz))) return rc;
+            if ((rc = learned_apply(c, c->pr, c->pz, &s->done))) return rc;
             if ((rc = remove_null_mode(c, c->pz))) return rc;
             const bool samp = c->prof_on && (b % c->prof_period) == 0;
             cudaEvent_t e0 = samp ? prof_mark(c) : nullptr;

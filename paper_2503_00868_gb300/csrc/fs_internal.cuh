@@ -388,6 +388,7 @@ int launch_loss(fs_ctx *c, CF3 u, CF3 t, int kind, double alpha, double beta, F3
 int mg_apply(fs_ctx *c, const float *r, float *z, const int *done);
 int mg_apply_faces(fs_ctx *c, const float *r, float *z, float cc, const int *done);
 void mg_free(fs_ctx *c);
+void mg_count(fs_ctx *c, long long vcycles, bool faces);  // fs_mg.cu: launch counts for fs_profile
 int mg_levels(const fs_ctx *c);
 // fs_splat.cu
 int splat_render(fs_ctx *c, int n, const float *x, const float *op, const float *A, const float *col,
@@ -429,6 +430,7 @@ int read_scal(fs_ctx *c, int which, SolveScal *out);
 int remove_null_mode(fs_ctx *c, float *z);
 // fs_fcg.cu: flexible CG with the network, pb -> px (warm: from the current x);
 // final scalars in *h
+int learned_apply(fs_ctx *c, const float *r, float *z, const int *done);  // fs_pcg.cu: network (+ V-cycle)
 int solve_pressure_fcg(fs_ctx *c, SolveScal *h, bool warm);
 int pressure_restart(fs_ctx *c);  // fs_pcg.cu: r = b - A x, p = 0 (scalars of slot 0)
 void fcg_release(fs_ctx *c);
@@ -451,13 +453,22 @@ enum KernelId : int {
     K_MIC_APPLY,
     K_NET_APPLY,
     K_FCG_VEC,
-    K_MG_SMOOTH,    // the last damped-Jacobi sweep on level 0 of a pressure V-cycle
     K_MG_VCYCLE_P,  // one pressure V-cycle (time only)
     K_MG_VCYCLE_V,  // one viscosity V-cycle over the three face volumes (time only)
+    // level 0 of a V-cycle, one entry per kernel (timed on the pressure V-cycle;
+    // launches counted over the pressure and the face-volume V-cycles)
+    K_MG0_SMOOTH2,   // the two pre-smoothing sweeps from zero
+    K_MG0_RESIDUAL,  // the residual after them
+    K_MG0_RESTRICT,  // its restriction to level 1
+    K_MG0_PROLONG,   // the prolongation of the level-1 correction
+    K_MG0_SMOOTH,    // the first post-smoothing sweep
+    K_MG0_SMOOTH_Z,  // the last post-smoothing sweep, which writes z densely
+    K_MG_COARSE,     // levels 1 and below of a pressure V-cycle (time only)
     K_COUNT
 };
 cudaEvent_t prof_mark(fs_ctx *c);   // records an event on the stream (nullptr when off)
 void prof_add(fs_ctx *c, int id, cudaEvent_t a, cudaEvent_t b, double bytes);
+void prof_count(fs_ctx *c, int id, long long launches);  // launches of a kind, timed or not
 void prof_flush(fs_ctx *c);         // call after the stream has been synchronised
 
 }  // namespace fs

@@ -79,7 +79,9 @@ struct MgState {
     bool own0 = true;      // level 0 work arrays belong to this hierarchy
     const int *done = nullptr;  // the calling solve's convergence flag (nullable)
     long long calls = 0;        // applies so far (profiling samples every prof_period-th)
-    double smooth_bytes = 0.0;  // algorithmic bytes of one level-0 sweep (profiled when > 0)
+    // algorithmic bytes of the level-0 kernels, in the order of K_MG0_SMOOTH2 ..
+    // K_MG0_SMOOTH_Z (profiled when the first is > 0)
+    double by0[6] = {0, 0, 0, 0, 0, 0};
 };
 
 // The pressure hierarchy and one per face volume (viscosity). The face volumes
@@ -469,6 +471,10 @@ void free_levels(MgState *s)
 
 // The V-cycle on level l: r in lev[l].r, result in lev[l].a. With `sample`, the
 // last level-0 sweep is timed.
+// The V-cycle on level l: r in lev[l].r, result in lev[l].a. With `sample`
+// (level 0 of a pressure V-cycle on the context's stream), every level-0 kernel
+// and the coarse levels as a whole are timed; a timed kernel always runs in full
+// (an early exit would record work not done).
 int vcycle(fs_ctx *c, MgState *s, int l, bool sample, cudaStream_t st)
 {
     MgLevel &v = s->lev[l];
@@ -478,23 +484,42 @@ int vcycle(fs_ctx *c, MgState *s, int l, bool sample, cudaStream_t st)
         c->n_launches += 1;
         return FS_OK;
     }
+    const bool timed = sample && l == 0 && s->by0[0] > 0.0;
+    const int *done = timed ? nullptr : s->done;
+    // an event pair around each timed launch (an event belongs to one pair)
+    cudaEvent_t e0 = nullptr;
+    auto begin = [&]() {
+        if (timed) e0 = prof_mark(c);
+    };
+    auto end = [&](int kind, double bytes) {
+        if (timed) prof_add(c, kind, e0, prof_mark(c), bytes);
+    };
     // four elements per thread: every level but the coarsest has quad-aligned rows
     const int nq = grid_blocks(c, g.n / 4, TH);
-    k_mg0_smooth2<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.b, v.scale, v.mass, s->done);
-    k_mg0_residual<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, s->done);
     MgLevel &w = s->lev[l + 1];
+    begin();
+    k_mg0_smooth2<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.b, v.scale, v.mass, done);
+    end(K_MG0_SMOOTH2, s->by0[0]);
+    begin();
+    k_mg0_residual<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, done);
+    end(K_MG0_RESIDUAL, s->by0[1]);
+    begin();
     k_mg0_restrict<<<grid_blocks(c, (long long)((w.g.nx + 1) / 2) * w.g.ny * w.g.nz, TH), TH, 0, st>>>(
-        g, v.c, w.g, w.fl, w.r, s->done);
+        g, v.c, w.g, w.fl, w.r, done);
+    end(K_MG0_RESTRICT, s->by0[2]);
     c->n_launches += 3;
+    begin();
     if (int rc = vcycle(c, s, l + 1, false, st)) return rc;
-    k_mg0_prolong<<<nq, TH, 0, st>>>(g, v.fl, v.b, w.g, w.a, s->done);
-    k_mg0_smooth<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, 0, s->done);
-    // a timed sweep always runs in full (an early exit would record work not done)
-    const bool timed = sample && l == 0 && s->smooth_bytes > 0.0;
-    cudaEvent_t e0 = timed ? prof_mark(c) : nullptr;
-    k_mg0_smooth<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.c, v.a, v.scale, v.mass, l == 0 ? 1 : 0,
-                                    timed ? nullptr : s->done);
-    if (timed) prof_add(c, K_MG_SMOOTH, e0, prof_mark(c), s->smooth_bytes);
+    end(K_MG_COARSE, 0.0);
+    begin();
+    k_mg0_prolong<<<nq, TH, 0, st>>>(g, v.fl, v.b, w.g, w.a, done);
+    end(K_MG0_PROLONG, s->by0[3]);
+    begin();
+    k_mg0_smooth<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, 0, done);
+    end(K_MG0_SMOOTH, s->by0[4]);
+    begin();
+    k_mg0_smooth<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.c, v.a, v.scale, v.mass, l == 0 ? 1 : 0, done);
+    end(K_MG0_SMOOTH_Z, s->by0[5]);
     c->n_launches += 3;
     FS_CUDA(cudaGetLastError());
     return FS_OK;
@@ -555,14 +580,25 @@ int mg_build(fs_ctx *c, MgState *s, const MgGrid &g0, uint8_t *fl0, float *b0, f
         if (g.sy % 4 || g.sz % 4 || g.origin % 4 || g.n % 4)
             return set_error(FS_EINVAL, "multigrid: level %d rows are not quad-aligned", l);
     }
-    // the least a level-0 sweep must move: the flag of every element, and r and e
-    // read and e written on the unknowns (the zeros it writes elsewhere are excess)
-    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(c->partials), nliq = 0;
-    FS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(nliq), c->stream));
+    // The least each level-0 kernel must move (its algorithmic bytes): the flag
+    // byte of every element it scans, 4 bytes per unknown for each vector it reads
+    // or writes on the unknowns, and the whole of a vector it writes densely.
+    // n0, n1: elements of levels 0 and 1; u0, u1: their unknowns.
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(c->partials), nl[2] = {0, 0};
+    FS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(nl), c->stream));
     k_mg_count_liq<<<grid_blocks(c, g0.n, TH), TH, 0, c->stream>>>(g0, fl0, cnt);
-    FS_CUDA(cudaMemcpyAsync(&nliq, cnt, sizeof(nliq), cudaMemcpyDeviceToHost, c->stream));
+    if (s->nlev > 1)
+        k_mg_count_liq<<<grid_blocks(c, s->lev[1].g.n, TH), TH, 0, c->stream>>>(s->lev[1].g, s->lev[1].fl, cnt + 1);
+    FS_CUDA(cudaMemcpyAsync(nl, cnt, sizeof(nl), cudaMemcpyDeviceToHost, c->stream));
     FS_CUDA(cudaStreamSynchronize(c->stream));
-    s->smooth_bytes = 1.0 * (double)g0.n + 12.0 * (double)nliq;
+    const double n0 = (double)g0.n, u0 = (double)nl[0];
+    const double n1 = s->nlev > 1 ? (double)s->lev[1].g.n : 0.0, u1 = (double)nl[1];
+    s->by0[0] = n0 + 8.0 * u0;             // smooth2: read r, write e
+    s->by0[1] = n0 + 12.0 * u0;            // residual: read r, e, write res
+    s->by0[2] = 4.0 * u0 + n1 + 4.0 * u1;  // restrict: read res; level-1 flags, write its r
+    s->by0[3] = n0 + 8.0 * u0 + 4.0 * u1;  // prolong: read and write e, read the level-1 e
+    s->by0[4] = n0 + 12.0 * u0;            // smooth: read r, e, write e
+    s->by0[5] = n0 + 8.0 * u0 + 4.0 * n0;  // last smooth: read r, e, write z on every element
     s->epoch = c->mask_epoch;
     s->coef = coef;
     return FS_OK;
@@ -683,6 +719,21 @@ int mg_apply_faces(fs_ctx *c, const float *r, float *z, float cc, const int *don
     }
     if (sample) prof_add(c, K_MG_VCYCLE_V, e0, prof_mark(c), 0.0);
     return FS_OK;
+}
+
+// Launch counts of the level-0 kernels (fs_profile): `vcycles` V-cycles that did
+// work on the pressure hierarchy, or on each of the three face volumes.
+void mg_count(fs_ctx *c, long long vcycles, bool faces)
+{
+    const MgAll *m = static_cast<const MgAll *>(c->mg);
+    if (!m || !c->prof_on) return;
+    const int nlev = faces ? m->face[0].nlev : m->cell.nlev;
+    if (nlev < 2) return;
+    const long long k = faces ? 3 * vcycles : vcycles;
+    for (int id : {K_MG0_SMOOTH2, K_MG0_RESIDUAL, K_MG0_RESTRICT, K_MG0_PROLONG, K_MG0_SMOOTH, K_MG0_SMOOTH_Z})
+        prof_count(c, id, k);
+    prof_count(c, faces ? K_MG_VCYCLE_V : K_MG_VCYCLE_P, vcycles);
+    if (!faces) prof_count(c, K_MG_COARSE, vcycles);
 }
 
 int mg_levels(const fs_ctx *c)

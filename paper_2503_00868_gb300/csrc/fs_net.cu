@@ -340,6 +340,71 @@ __global__ void k_net_gy(const float *__restrict__ ae, const uint8_t *__restrict
         gy[t] = (cf[t] & CF_LIQ) ? g * ae[t] : 0.f;
 }
 
+// ---- the loss of the network followed by the V-cycle (FS_PRECOND_LEARNED_MG) ----
+// With y the network output (masked to the liquid), b/s and q/s the scaled pair
+// and M the V-cycle: w = q/s - y - M(b/s - A y), loss = w.A w / (q/s).A (q/s).
+// w = (I - M A)(q/s - y), so dloss/dy = -2 (I - A M) A w / den, M and A symmetric.
+
+// ym = y on liquid cells, 0 elsewhere
+__global__ void k_net_mask_y(const float *__restrict__ y, const uint8_t *__restrict__ cf, float *ym, int n)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x)
+        ym[t] = (cf[t] & CF_LIQ) ? y[t] : 0.f;
+}
+
+// t1 = b/s - A ym on liquid cells (the residual the network leaves), 0 elsewhere
+__global__ void __launch_bounds__(256) k_netmg_res(const float *__restrict__ b, const float *__restrict__ ym,
+                                                   const uint8_t *__restrict__ cf, const unsigned *__restrict__ smax,
+                                                   Layout L, float *t1)
+{
+    const float sc = __uint_as_float(*smax);
+    const float inv = sc > 0.f ? 1.f / sc : 0.f;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < L.nC; t += gridDim.x * blockDim.x) {
+        const uint8_t f = cf[t];
+        float v = 0.f;
+        if (f & CF_LIQ) {
+            const float ay = (float)(f & CF_D) * ym[t] -
+                             ((ym[t - 1] + ym[t + 1]) + (ym[t - L.P] + ym[t + L.P]) + (ym[t - L.PL] + ym[t + L.PL]));
+            v = b[t] * inv - ay;
+        }
+        t1[t] = v;
+    }
+}
+
+// w = q/s - ym - m and tq = q/s on liquid cells, 0 elsewhere
+__global__ void k_netmg_err(const float *__restrict__ q, const float *__restrict__ ym, const float *__restrict__ m,
+                            const uint8_t *__restrict__ cf, const unsigned *__restrict__ smax, float *w, float *tq,
+                            int n)
+{
+    const float sc = __uint_as_float(*smax);
+    const float inv = sc > 0.f ? 1.f / sc : 0.f;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const bool liq = (cf[t] & CF_LIQ) != 0;
+        const float tv = liq ? q[t] * inv : 0.f;
+        tq[t] = tv;
+        w[t] = liq ? tv - ym[t] - m[t] : 0.f;
+    }
+}
+
+// dloss/dy = -2 (v - A u) / den on liquid cells, v = A w, u = M v
+__global__ void __launch_bounds__(256) k_netmg_gy(const float *__restrict__ v, const float *__restrict__ u,
+                                                  const uint8_t *__restrict__ cf, const SolveScal *s, Layout L,
+                                                  float *gy)
+{
+    const double den = s->aux[1];
+    const float g = den > 0.0 ? (float)(-2.0 / den) : 0.f;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < L.nC; t += gridDim.x * blockDim.x) {
+        const uint8_t f = cf[t];
+        float o = 0.f;
+        if (f & CF_LIQ) {
+            const float au = (float)(f & CF_D) * u[t] -
+                             ((u[t - 1] + u[t + 1]) + (u[t - L.P] + u[t + L.P]) + (u[t - L.PL] + u[t + L.PL]));
+            o = g * (v[t] - au);
+        }
+        gy[t] = o;
+    }
+}
+
 // dL/d(layer-5 input) = sum_tap w5[ci][tap] gy[cell - tap], times [a4 > 0]
 __global__ void __launch_bounds__(256) k_bwd_last(const float *__restrict__ gy, const float *__restrict__ w5f,
                                                   const __nv_bfloat16 *__restrict__ a4, __nv_bfloat16 *g4, Layout L)
@@ -749,10 +814,27 @@ int net_grad(fs_ctx *c, const float *b, const float *q, double *loss)
     __nv_bfloat16 *A[5];
     for (int l = 0; l < 5; l++) A[l] = n->act + (size_t)l * nC * 16;
     SolveScal *s = c->scal + 3;
-    // energy-norm loss; scratch: pr = e, pz = q/s, pq = A e (no solve runs meanwhile)
-    k_net_err<<<grid_blocks(c, L.nC, 256), 256, 0, c->stream>>>(n->y, c->px, c->cflag, n->smax, c->pr, c->pz, L.nC);
-    k_net_energy<<<grid_blocks(c, L.nC, 256), 256, 0, c->stream>>>(c->pr, c->pz, c->pq, c->cflag, L, s, c->partials);
-    k_net_gy<<<grid_blocks(c, L.nC, 256), 256, 0, c->stream>>>(c->pq, c->cflag, s, n->gy, L.nC);
+    const int bsn = grid_blocks(c, L.nC, 256);
+    if (c->prm.precond == FS_PRECOND_LEARNED_MG) {
+        // the network followed by the V-cycle; scratch (no solve runs meanwhile):
+        // pxh = ym, pr = b/s - A ym, pz = M pr, pp0 = w, pp1 = q/s, pq = A w, pbr = M A w
+        k_net_mask_y<<<bsn, 256, 0, c->stream>>>(n->y, c->cflag, c->pxh, L.nC);
+        k_netmg_res<<<bsn, 256, 0, c->stream>>>(c->pb, c->pxh, c->cflag, n->smax, L, c->pr);
+        c->n_launches += 2;
+        if ((rc = mg_apply(c, c->pr, c->pz, nullptr))) return rc;
+        k_netmg_err<<<bsn, 256, 0, c->stream>>>(c->px, c->pxh, c->pz, c->cflag, n->smax, c->pp[0], c->pp[1], L.nC);
+        k_net_energy<<<bsn, 256, 0, c->stream>>>(c->pp[0], c->pp[1], c->pq, c->cflag, L, s, c->partials);
+        c->n_launches += 2;
+        if ((rc = mg_apply(c, c->pq, c->pbr, nullptr))) return rc;
+        k_netmg_gy<<<bsn, 256, 0, c->stream>>>(c->pq, c->pbr, c->cflag, s, L, n->gy);
+        c->n_launches += 1;
+    } else {
+        // energy-norm loss; scratch: pr = e, pz = q/s, pq = A e (no solve runs meanwhile)
+        k_net_err<<<bsn, 256, 0, c->stream>>>(n->y, c->px, c->cflag, n->smax, c->pr, c->pz, L.nC);
+        k_net_energy<<<bsn, 256, 0, c->stream>>>(c->pr, c->pz, c->pq, c->cflag, L, s, c->partials);
+        k_net_gy<<<bsn, 256, 0, c->stream>>>(c->pq, c->cflag, s, n->gy, L.nC);
+        c->n_launches += 3;
+    }
     // layer 5
     const int wg = std::max(1, std::min(((L.nx + NT_X - 1) / NT_X) * ((L.ny + NT_Y - 1) / NT_Y) * L.nz, c->num_sms * 2));
     k_wgrad<16, 1, true><<<wg, 256, wgrad_smem<16, 1>(), c->stream>>>(n->gy, A[4], n->grad + OW5, n->grad + OB5, L);
@@ -775,7 +857,7 @@ int net_grad(fs_ctx *c, const float *b, const float *q, double *loss)
     }
     // layer 1: gradient w.r.t. W1 from the stored input x (2 channels used)
     k_wgrad<2, 16, false><<<wg, 256, wgrad_smem<2, 16>(), c->stream>>>(G[gi], A[0], n->grad + OW1, n->grad + OB1, L);
-    c->n_launches += 3 + 2 + 6 + 1;
+    c->n_launches += 2 + 6 + 1;
     FS_CUDA(cudaGetLastError());
     SolveScal h;
     if ((rc = read_scal(c, 3, &h))) return rc;

@@ -290,6 +290,22 @@ __global__ void __launch_bounds__(TH) k_pois_refine_rhs(const float *b, const fl
     }
 }
 
+// res = r - A e on the liquid, zero elsewhere (guard planes included); e is zero
+// off the liquid
+__global__ void __launch_bounds__(TH) k_pois_resid(const float *__restrict__ r, const float *__restrict__ e,
+                                                   const uint8_t *__restrict__ fl, int n, int P, int PL, float *res)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const uint8_t f = fl[t];
+        float v = 0.f;
+        if (f & CF_LIQ) {
+            const float nb = (e[t - 1] + e[t + 1]) + (e[t - P] + e[t + P]) + (e[t - PL] + e[t + PL]);
+            v = r[t] - (PoisOp::diag(f, 0.f) * e[t] - nb);
+        }
+        res[t] = v;
+    }
+}
+
 // a += b over n elements (n a multiple of 4)
 __global__ void __launch_bounds__(TH) k_add4(float *a, const float *__restrict__ b, int n4)
 {
@@ -653,6 +669,27 @@ int remove_null_mode(fs_ctx *c, float *z)
     return FS_OK;
 }
 
+// The learned preconditioner of flexible CG: the network alone
+// (FS_PRECOND_LEARNED), or the network followed by one V-cycle on the residual it
+// leaves (FS_PRECOND_LEARNED_MG): z = e + M(r - A e), e = s Net(r/s). The network
+// smooths, the V-cycle corrects the error it cannot reach. pp[0] and pp[1] are
+// free while flexible CG runs (it keeps its directions in its own ring).
+int learned_apply(fs_ctx *c, const float *r, float *z, const int *done)
+{
+    if (c->prm.precond != FS_PRECOND_LEARNED_MG) return net_apply(c, r, z);
+    const Layout &L = c->L;
+    float *e = c->pp[0], *res = c->pp[1];
+    if (int rc = net_apply(c, r, e)) return rc;
+    k_pois_resid<<<grid_blocks(c, L.nC, TH), TH, 0, c->stream>>>(r, e, c->cflag, L.nC, L.P, L.PL, res);
+    c->n_launches += 1;
+    FS_CUDA(cudaGetLastError());
+    if (int rc = mg_apply(c, res, z, done)) return rc;
+    k_add4<<<grid_blocks(c, L.nC / 4, TH), TH, 0, c->stream>>>(z, e, L.nC / 4);
+    c->n_launches += 1;
+    FS_CUDA(cudaGetLastError());
+    return FS_OK;
+}
+
 static int pressure_tail(fs_ctx *c, const SolveScal &h, long long iters, double bb0, fs_stats *st);
 
 // Warm start (fs_params.warm_start): after the x = 0 initialisation, start
@@ -811,6 +848,9 @@ static int pcg_iterate(fs_ctx *c, SolveScal &h)
         if (launched > (long long)c->prm.maxit_p + c->prm.check_every)
             return set_error(FS_ECUDA, "pressure solve: iteration flag never set");
     }
+    prof_count(c, K_P_SPMV, h.iter);
+    prof_count(c, K_P_UPDATE, h.iter);
+    if (c->prm.precond == FS_PRECOND_MG) mg_count(c, h.iter, false);
     return check_wait_error(c, "pressure solve");
 }
 
@@ -828,7 +868,7 @@ static int solve_pressure_once(fs_ctx *c, fs_stats *st)
         if (rc) return rc;
         return pressure_tail(c, h, h.iter, 0.0, st);
     }
-    const bool learned = c->prm.precond == FS_PRECOND_LEARNED;
+    const bool learned = c->prm.precond == FS_PRECOND_LEARNED || c->prm.precond == FS_PRECOND_LEARNED_MG;
     if (learned && !net_loaded(c))
         return set_error(FS_ESTATE, "the learned preconditioner has no network loaded");
     FS_CUDA(cudaMemsetAsync(c->err_word, 0, sizeof(unsigned), c->stream));
@@ -946,8 +986,9 @@ static int pressure_tail(fs_ctx *c, const SolveScal &h, long long iters, double 
 int solve_pressure(fs_ctx *c, fs_stats *st)
 {
     int rc = solve_pressure_once(c, st);
-    if (c->prm.precond != FS_PRECOND_LEARNED || rc == FS_OK || rc == FS_ECUDA || rc == FS_EINVAL ||
-        rc == FS_ESTATE || rc == FS_ETIMEOUT)
+    const int pc = c->prm.precond;
+    if ((pc != FS_PRECOND_LEARNED && pc != FS_PRECOND_LEARNED_MG) || rc == FS_OK || rc == FS_ECUDA ||
+        rc == FS_EINVAL || rc == FS_ESTATE || rc == FS_ETIMEOUT)
         return rc;
     c->prm.precond = FS_PRECOND_MIC0;
     if (st) {
@@ -955,7 +996,7 @@ int solve_pressure(fs_ctx *c, fs_stats *st)
         st->fallbacks += 1;
     }
     rc = solve_pressure_once(c, st);
-    c->prm.precond = FS_PRECOND_LEARNED;
+    c->prm.precond = pc;
     return rc;
 }
 
@@ -970,7 +1011,7 @@ int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st)
     const int b4 = grid_blocks(c, n4, TH);
     FS_CUDA(cudaMemsetAsync(c->err_word, 0, sizeof(unsigned), c->stream));
     // the multigrid preconditioner serves both solves; otherwise Jacobi
-    const bool mg = c->prm.precond == FS_PRECOND_MG;
+    const bool mg = c->prm.precond == FS_PRECOND_MG || c->prm.precond == FS_PRECOND_LEARNED_MG;
     const float *dsum = (dirichlet && c->has_bc) ? c->dsum : nullptr;
     if (mg)
         k_helm_init<false><<<bs, TH, 0, c->stream>>>(c->vx, dsum, c->vr, c->vp[0], c->vp[1], c->fflag, L.nF, L.P, L.PL,
@@ -1046,6 +1087,9 @@ int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st)
             return set_error(FS_ECUDA, "viscosity solve: iteration flag never set");
     }
     if (int rc = check_wait_error(c, "viscosity solve")) return rc;
+    prof_count(c, K_V_SPMV, h.iter);
+    prof_count(c, K_V_UPDATE, h.iter);
+    if (mg) mg_count(c, h.iter, true);
     if (st) {
         st->iters_v += h.iter;
         st->relres_v = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
@@ -1110,7 +1154,7 @@ int precond_apply_public(fs_ctx *c, const float *r, float *z)
         int rc = mic0_apply(c, c->pr, c->pz);
         if (rc) return rc;
     } else {
-        int rc = net_apply(c, c->pr, c->pz);
+        int rc = learned_apply(c, c->pr, c->pz, nullptr);
         if (rc) return rc;
     }
     k_cell_out<<<bs, TH, 0, c->stream>>>(c->pz, z, L);

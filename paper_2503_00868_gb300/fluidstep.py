@@ -25,7 +25,7 @@ FS_OK, FS_EINVAL, FS_ENOMEM, FS_ECUDA, FS_ENOCONV, FS_ENONFINITE, FS_ESTATE, FS_
 STATUS_NAMES = {0: "FS_OK", 1: "FS_EINVAL", 2: "FS_ENOMEM", 3: "FS_ECUDA", 4: "FS_ENOCONV",
                 5: "FS_ENONFINITE", 6: "FS_ESTATE", 7: "FS_ETIMEOUT", 8: "FS_EBREAKDOWN"}
 FS_AIR, FS_LIQUID, FS_SOLID = 0, 1, 2
-FS_PRECOND_JACOBI, FS_PRECOND_MIC0, FS_PRECOND_LEARNED, FS_PRECOND_MG = 0, 1, 2, 3
+FS_PRECOND_JACOBI, FS_PRECOND_MIC0, FS_PRECOND_LEARNED, FS_PRECOND_MG, FS_PRECOND_LEARNED_MG = 0, 1, 2, 3, 4
 FS_MASK_SURFACE, FS_MASK_OCCUPIED = 0, 1
 FS_SOLVER_PCG, FS_SOLVER_PERCNN = 0, 1
 SOFT_STATUS = (FS_OK, FS_ENOCONV)
@@ -61,7 +61,7 @@ class fs_layout_t(C.Structure):
 
 class fs_kernel_time(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_longlong), ("total_ms", C.c_double),
-                ("bytes", C.c_double)]
+                ("bytes", C.c_double), ("all_launches", C.c_longlong)]
 
 
 class fs_mac(C.Structure):
@@ -239,11 +239,13 @@ def fs_profile(ctx: int, period: int) -> None:
 
 
 def fs_profile_read(ctx: int):
-    """Per-kernel timing since fs_profile(ctx, True): {name: (launches, total_ms, bytes)}."""
-    buf = (fs_kernel_time * 16)()
+    """Per-kernel timing since fs_profile(ctx, k): {name: (timed launches, total_ms,
+    bytes, all launches)}."""
+    buf = (fs_kernel_time * 32)()
     n = C.c_int(0)
-    _check(load().fs_profile_read(C.c_void_p(ctx), buf, 16, C.byref(n)), (FS_OK,))
-    return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms, buf[i].bytes) for i in range(n.value)}
+    _check(load().fs_profile_read(C.c_void_p(ctx), buf, 32, C.byref(n)), (FS_OK,))
+    return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms, buf[i].bytes, buf[i].all_launches)
+            for i in range(n.value)}
 
 
 def fs_precond_apply(ctx: int, r: torch.Tensor, z: torch.Tensor) -> None:

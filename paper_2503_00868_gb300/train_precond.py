@@ -18,6 +18,13 @@ The shipped weights (weights/precond_n48.npy) come from
     python -m paper_2503_00868_gb300.train_precond --n 48 --masks 8 --rhs 6 \
         --steps 300 --lr 2e-3 --seed 0 --out precond_n48.npy
 (192 pairs at 48^3, energy-norm loss 1.02 -> 0.168).
+
+The data set of the learned-preconditioner configuration (``--c4``): 4000 pairs,
+3000 at 64^3 and 1000 at 128^3, on ellipsoid blobs and sphere unions (radii
+scaled by n/256) in equal numbers, split 3600 / 400 for training and validation.
+``--role net_mg`` trains the network for FS_PRECOND_LEARNED_MG, where one V-cycle
+follows it: the loss is then the energy-norm error left after the network and
+the V-cycle together, so the network learns what the V-cycle misses.
 """
 from __future__ import annotations
 
@@ -108,6 +115,103 @@ def make_pairs(n: int, masks, rhs: int, seed: int, tol: float = 1e-7, cg_iters=(
     return out
 
 
+ROLES = {"net": F.FS_PRECOND_LEARNED, "net_mg": F.FS_PRECOND_LEARNED_MG}
+
+
+def c4_data(seed: int = 0, n64: int = 3000, n128: int = 1000, per_mask: int = 50):
+    """The pairs of the learned-preconditioner configuration: n64 pairs at 64^3
+    and n128 at 128^3, `per_mask` per mask (ten right-hand sides, each with the
+    residual/error pairs of Jacobi-PCG stopped after 2, 8, 32 and 128
+    iterations), blobs and sphere unions alternating. Returns {n: [(types,
+    pairs)]}."""
+    rhs = per_mask // 5
+    out = {}
+    for n, count, base in ((64, n64, 0), (128, n128, 10000)):
+        nmask = max(1, count // per_mask)
+        masks = [make_mask(n, k, seed + base + k) for k in range(nmask)]
+        out[n] = make_pairs(n, masks, rhs, seed + base, cg_iters=(2, 8, 32, 128))
+    return out
+
+
+def split(data, val_every: int = 10):
+    """Every val_every-th pair of each mask goes to validation (3600 / 400)."""
+    tr, va = {}, {}
+    for n, items in data.items():
+        tr[n] = [(t, [p for i, p in enumerate(ps) if i % val_every != val_every - 1]) for t, ps in items]
+        va[n] = [(t, [p for i, p in enumerate(ps) if i % val_every == val_every - 1]) for t, ps in items]
+    return tr, va
+
+
+def train_batched(data, params: np.ndarray, role: str, epochs: int, batch: int, lr: float, seed: int = 0,
+                  val=None, log=True):
+    """Adam over minibatches of `batch` pairs of one mask (in shuffled order),
+    `epochs` passes over the training pairs, cosine learning rate; the loss
+    follows the role (FS_PRECOND_LEARNED or FS_PRECOND_LEARNED_MG). Returns the
+    parameters and per-epoch (train loss, validation loss)."""
+    rng = np.random.default_rng(seed)
+    # one context per grid size, each with its own Adam moments and step count;
+    # the parameters move between them when the size changes (once per epoch:
+    # the minibatches of each size run together, in shuffled order)
+    grids = {n: F.Grid(n, n, n, dx=1.0 / n, precond=ROLES[role]) for n in data}
+    cur = params
+    batches = {n: [] for n in data}
+    for n, items in data.items():
+        for mi, (types, pairs) in enumerate(items):
+            idx = np.arange(len(pairs))
+            for k in range(0, len(idx), batch):
+                batches[n].append((mi, list(idx[k:k + batch])))
+    total_steps = epochs * sum(len(v) for v in batches.values())
+    hist, step = [], 0
+    steps_of = {n: 0 for n in data}
+    last_n = None
+    for ep in range(epochs):
+        tl, tc = 0.0, 0
+        for n in rng.permutation(sorted(data)):
+            n = int(n)
+            g = grids[n]
+            if last_n != n:
+                if last_n is not None:
+                    cur = F.fs_net_read(grids[last_n].ctx)
+                F.fs_net_load(g.ctx, cur)
+                last_n = n
+            for bi in rng.permutation(len(batches[n])):
+                mi, idx = batches[n][bi]
+                types, pairs = data[n][mi]
+                g.set_mask(types)
+                for j in idx:
+                    b, q = pairs[j]
+                    tl += F.fs_net_grad(g.ctx, b, q)
+                    tc += 1
+                step += 1
+                steps_of[n] += 1
+                lr_t = lr * 0.5 * (1.0 + np.cos(np.pi * (step - 1) / total_steps)) + 1e-5
+                F.fs_net_adam(g.ctx, lr_t, steps_of[n], grad_scale=1.0 / len(idx))
+        cur = F.fs_net_read(grids[last_n].ctx)
+        vl = evaluate_loss(val, cur, role) if val else None
+        hist.append((tl / max(tc, 1), vl))
+        if log:
+            print(f"epoch {ep + 1}: train loss {hist[-1][0]:.4f} validation {vl}", flush=True)
+    for g in grids.values():
+        g.close()
+    return cur, hist
+
+
+def evaluate_loss(data, params: np.ndarray, role: str) -> float:
+    """Mean loss over the pairs of `data`, on contexts of its own (the gradients
+    they accumulate are dropped with them)."""
+    tot, cnt = 0.0, 0
+    for n, items in data.items():
+        g = F.Grid(n, n, n, dx=1.0 / n, precond=ROLES[role])
+        F.fs_net_load(g.ctx, params)
+        for types, pairs in items:
+            g.set_mask(types)
+            for b, q in pairs:
+                tot += F.fs_net_grad(g.ctx, b, q)
+                cnt += 1
+        g.close()
+    return tot / max(cnt, 1)
+
+
 def train(n: int, data, params: np.ndarray, steps: int, lr: float, log_every: int = 25):
     g = F.Grid(n, n, n, dx=1.0 / n)
     g.set_mask(data[0][0])
@@ -141,28 +245,30 @@ def timed_project(g: F.Grid, u0: F.Mac):
     return e0.elapsed_time(e1) / 1e3, rc, st
 
 
-def compare(n: int, params: np.ndarray, seeds=(0,), tol: float = 1e-6, warm: bool = True):
+def compare(n: int, nets, seeds=(0,), tol: float = 1e-6, warm: bool = True):
     """Wall time and iterations of the projection to relative residual `tol`
-    with Jacobi, MIC(0) and the learned preconditioner (flexible CG)."""
+    with Jacobi, MIC(0), the multigrid V-cycle and each learned preconditioner of
+    `nets` ({name: (params, FS_PRECOND_LEARNED or FS_PRECOND_LEARNED_MG)}, in
+    flexible CG), on sphere unions at n^3."""
     rows = []
-    grids = {name: F.Grid(n, n, n, dx=1.0 / n, tol_p=tol, maxit_p=20000, precond=pc)
-             for name, pc in (("jacobi", F.FS_PRECOND_JACOBI), ("mic0", F.FS_PRECOND_MIC0),
-                              ("learned", F.FS_PRECOND_LEARNED))}
-    F.fs_net_load(grids["learned"].ctx, params)
+    spec = [("jacobi", F.FS_PRECOND_JACOBI, None), ("mic0", F.FS_PRECOND_MIC0, None), ("mg", F.FS_PRECOND_MG, None)]
+    spec += [(name, pc, params) for name, (params, pc) in nets.items()]
     for seed in seeds:
         types, info = W.sphere_union(n, n, n, seed)
         row = {"n": n, "seed": seed, "occupancy": info["occupancy"]}
-        for name, g in grids.items():
+        for name, pc, params in spec:
+            g = F.Grid(n, n, n, dx=1.0 / n, tol_p=tol, maxit_p=20000, precond=pc)
             g.set_mask(types)
+            if params is not None:
+                F.fs_net_load(g.ctx, params)
             u0 = g.pack(W.random_mac(n, n, n, 500 + seed))
             if warm:
-                timed_project(g, u0)  # the MIC(0) factor and first-touch costs
+                timed_project(g, u0)  # the MIC(0) factor, the hierarchy and first-touch costs
             t, rc, st = timed_project(g, u0)
-            row[name] = {"seconds": t, "iters": st["iters_p"], "true_relres": st["true_relres_p"],
+            row[name] = {"ms": round(1e3 * t, 3), "iters": st["iters_p"], "true_relres": st["true_relres_p"],
                          "fallbacks": st["fallbacks"], "status": rc}
+            g.close()
         rows.append(row)
-    for g in grids.values():
-        g.close()
     return rows
 
 
@@ -176,9 +282,37 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default="precond_weights.npy")
     ap.add_argument("--eval-n", type=int, nargs="*", default=[128])
+    ap.add_argument("--c4", action="store_true",
+                    help="train on the 4000-pair data set (3000 at 64^3, 1000 at 128^3), minibatched")
+    ap.add_argument("--roles", nargs="*", default=["net", "net_mg"], choices=list(ROLES))
+    ap.add_argument("--epochs", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--out-dir", default=".")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     t0 = time.time()
+    if a.c4:
+        data = c4_data(a.seed)
+        tr, va = split(data)
+        t1 = time.time()
+        nets, report = {}, {"pairs": {n: sum(len(p) for _, p in items) for n, items in data.items()},
+                            "train_pairs": {n: sum(len(p) for _, p in items) for n, items in tr.items()},
+                            "data_seconds": t1 - t0, "roles": {}}
+        for role in a.roles:
+            t2 = time.time()
+            init = init_params(a.seed)
+            v0 = evaluate_loss(va, init, role)
+            params, hist = train_batched(tr, init, role, a.epochs, a.batch, a.lr, a.seed, val=va)
+            out = os.path.join(a.out_dir, f"precond_{role}_c4.npy")
+            np.save(out, params)
+            nets["learned" if role == "net" else "learned_mg"] = (params, ROLES[role])
+            report["roles"][role] = {"validation_loss_init": v0, "epochs": hist, "train_seconds": time.time() - t2,
+                                     "weights": out}
+        report["compare"] = []
+        for n in a.eval_n:
+            report["compare"] += compare(n, nets)
+        print(json.dumps(report), flush=True)
+        return
     masks = [make_mask(a.n, k, a.seed + k) for k in range(a.masks)]
     data = make_pairs(a.n, masks, a.rhs, a.seed)
     t1 = time.time()
@@ -188,7 +322,7 @@ def main():
     report = {"pairs": a.masks * a.rhs, "n": a.n, "steps": a.steps, "loss_first": hist[0], "loss_last": hist[-1],
               "data_seconds": t1 - t0, "train_seconds": t2 - t1, "compare": []}
     for n in a.eval_n:
-        report["compare"] += compare(n, params)
+        report["compare"] += compare(n, {"learned": (params, F.FS_PRECOND_LEARNED)})
     print(json.dumps(report), flush=True)
 
 

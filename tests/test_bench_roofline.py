@@ -1,17 +1,19 @@
-"""The benchmark's roofline object, computed from a synthetic profile: the entry
-with the largest estimated share of the step among those with algorithmic bytes
-(sampled entries count PROFILE_PERIOD times), achieved bandwidth from bytes and
-time per launch, the measured peak or the fallback, and ncu traffic reported
-only while the kernel sources match its capture."""
+"""The benchmark's roofline objects, computed from synthetic profiles: the single
+kernel with the largest estimated share of the step (mean duration times the
+launches that did work) among those with algorithmic bytes, achieved bandwidth
+from bytes and time per launch, the measured peak or the fallback, ncu traffic
+reported only while the kernel sources match its capture; aggregates of several
+kernels (a V-cycle) never win; the level-0 multigrid family sums its kernels."""
 import pytest
 
 import bench
 
+# name: (timed launches, total ms, bytes of the timed launches, launches that did work)
 PROF = {
-    "pressure_spmv": (10, 0.5, 1.0e9),   # sampled: share 0.5 x period
-    "visc_spmv": (5, 1.0, 2.0e9),        # sampled: share 1.0 x period
-    "advect": (3, 2.0, 3.0e8),           # timed at every launch: share 2.0
-    "mg_vcycle_v": (5, 9.0, 0.0),        # no byte count: never the roofline entry
+    "pressure_spmv": (10, 0.5, 1.0e9, 80),   # mean 0.05 ms x 80 = 4.0
+    "visc_spmv": (5, 1.0, 2.0e9, 40),        # mean 0.2 ms x 40 = 8.0
+    "advect": (3, 2.0, 3.0e8, 3),            # 2.0
+    "mg_vcycle_v": (5, 9.0, 1.0e9, 40),      # an aggregate: never the roofline entry
     "all_kernels": (100, 0.0, 0.0),
 }
 
@@ -23,6 +25,7 @@ def test_picks_the_largest_share_with_bytes():
     assert r["frac"] == pytest.approx(r["achieved"] / 5000.0)
     assert r["algorithmic_bytes_per_launch"] == pytest.approx(4.0e8)
     assert r["avg_launch_us"] == pytest.approx(200.0)
+    assert r["launches_all"] == 40
     assert r["peak_source"].endswith("(of measured)") and r["traffic"] is None
 
 
@@ -39,6 +42,27 @@ def test_fallback_peak_and_empty_profile():
     assert bench.roofline_of({}, None, "h", traffic_table={}) is None
 
 
-def test_unsampled_entry_wins_when_its_time_is_larger():
-    prof = dict(PROF, advect=(3, 9.0, 3.0e8))   # 9.0 > 1.0 x period = 8.0
+def test_launch_counts_decide_the_share():
+    # a kernel timed at every launch but launched rarely loses to a sampled one launched often
+    prof = dict(PROF, advect=(3, 9.0, 3.0e8, 3))          # 9.0 > 8.0
     assert bench.roofline_of(prof, None, "h", traffic_table={})["kernel"] == "advect"
+    prof = dict(PROF, advect=(3, 6.0, 3.0e8, 3))          # 6.0 < 8.0
+    assert bench.roofline_of(prof, None, "h", traffic_table={})["kernel"] == "visc_spmv"
+    # a three-field profile (no launch count) counts its timed launches
+    old = {k: v[:3] for k, v in PROF.items()}
+    assert bench.roofline_of(old, None, "h", traffic_table={})["kernel"] == "advect"
+
+
+def test_kernel_table_and_family():
+    prof = {"mg0_smooth": (4, 0.2, 4.0e8, 32), "mg0_residual": (4, 0.2, 2.0e8, 32), "mg_coarse": (4, 0.1, 0.0, 16),
+            "all_kernels": (500, 0.0, 0.0)}
+    t = bench.kernel_table(prof, step_ms=10.0, steps=2, hbm=4000.0)
+    assert set(t) == {"mg0_smooth", "mg0_residual", "mg_coarse"}
+    assert t["mg0_smooth"]["est_share_of_step"] == pytest.approx(0.05 * 32 / 20.0)
+    assert t["mg0_smooth"]["achieved_gbs"] == pytest.approx(2000.0)
+    assert t["mg0_smooth"]["frac_of_hbm"] == pytest.approx(0.5)
+    assert "achieved_gbs" not in t["mg_coarse"]
+    fam = bench.family_roofline(prof, {"hbm_gbs": 4000.0})
+    assert fam["achieved"] == pytest.approx((6.0e8) / (0.4e-3) / 1e9)      # 1500 GB/s
+    assert fam["frac"] == pytest.approx(1500.0 / 4000.0)
+    assert bench.family_roofline({"all_kernels": (1, 0.0, 0.0)}, None) is None
