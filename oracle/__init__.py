@@ -49,7 +49,7 @@ class _Grid(C.Structure):
                 ("maxit_p", C.c_int), ("maxit_v", C.c_int),
                 ("precond", C.c_int),
                 ("mic_tau", C.c_double), ("mic_sigma", C.c_double),
-                ("percnn_w", C.POINTER(C.c_double)), ("percnn_k", C.c_int)]
+                ("percnn_w", C.POINTER(C.c_double)), ("percnn_k", C.c_int), ("advect_grad", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -77,6 +77,7 @@ def lib():
                 "or_advect": [G, _P3, _P3],
                 "or_advect_adjoint": [G, _P3, _P3, _P3],
                 "or_advect_samples": [G, C.c_int, _P3, _D],
+                "or_advect_adjoint_upwind": [G, _P3, _P3, _P3],
                 "or_visc_apply": [G, _P3, _P3],
                 "or_visc_solve": [G, _P3, _P3, C.POINTER(Stats)],
                 "or_divergence": [G, _P3, _D],
@@ -137,7 +138,7 @@ class Grid:
 
     def __init__(self, types, dx, dt, nu, g=(0.0, 0.0, 0.0), bc=None, tol_p=1e-13,
                  tol_v=1e-13, maxit_p=100000, maxit_v=100000, precond=PC_JACOBI,
-                 mic_tau=0.97, mic_sigma=0.25):
+                 mic_tau=0.97, mic_sigma=0.25, advect_grad=0):
         self.types = np.ascontiguousarray(types, dtype=np.uint8)
         self.nz, self.ny, self.nx = self.types.shape
         self.bc = None if bc is None else tuple(_f64(a) for a in bc)
@@ -150,6 +151,7 @@ class Grid:
         self.maxit_p, self.maxit_v = int(maxit_p), int(maxit_v)
         self.precond = int(precond)
         self.mic_tau, self.mic_sigma = float(mic_tau), float(mic_sigma)
+        self.advect_grad = int(advect_grad)   # 0 exact adjoint of advection, 1 the upwind surrogate
 
     def shapes(self):
         return face_shapes(self.nx, self.ny, self.nz)
@@ -173,6 +175,7 @@ class Grid:
         pw = getattr(self, "percnn_w", None)
         s.percnn_w = _ptr(pw) if pw is not None else _D()
         s.percnn_k = int(getattr(self, "percnn_k", 0)) if pw is not None else 0
+        s.advect_grad = self.advect_grad
         self._keep = s
         return C.byref(s)
 
@@ -195,6 +198,16 @@ def advect(g: Grid, u):
     out = g.zeros()
     lib().or_advect(g.cstruct(), _p3(u), _p3(out))
     return out
+
+
+def advect_adjoint_upwind(g: Grid, u, ga):
+    """The upwind surrogate of the reverse of advection (Sec. 3.4.1): gu =
+    ga + the transport terms -dt ga_c dv_c/de (upwind differences of the
+    convected field v), routed to the velocity components seen at each face."""
+    u, ga = _field(g, u), _field(g, ga)
+    gu = g.zeros()
+    lib().or_advect_adjoint_upwind(g.cstruct(), _p3(u), _p3(ga), _p3(gu))
+    return gu
 
 
 def advect_samples(g: Grid, u, c: int):

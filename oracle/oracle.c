@@ -67,6 +67,7 @@ typedef struct {
     double mic_tau, mic_sigma;
     const double *percnn_w;     /* 27 taps [dz][dy][dx]; with percnn_k > 0 the projection */
     int percnn_k;               /* solves the pressure by that many recurrent sub-steps */
+    int advect_grad;            /* reverse of advection: 0 the exact adjoint, 1 the upwind surrogate */
 } or_grid;
 
 typedef struct {
@@ -331,6 +332,76 @@ void or_advect_adjoint(const or_grid *g, const double *const u[3],
                     }
                 }
     }
+}
+
+/* The paper's surrogate for the reverse pass of convection (Sec. 3.4.1): the
+ * derivative of the convected velocity v with respect to the velocity component
+ * i that transports it is taken as -dt dv/di, with dv/di by a first-order
+ * upwind difference, instead of differentiating the back-trace. Reading taken
+ * (the passage gives only that derivative): the cotangent of each convected
+ * fluid face f of component c passes unchanged to the same face of the input
+ * (the value the face carries), and each velocity component e seen at f
+ * (ubar_e of the back-trace: the own component, or the mean of four faces of
+ * another) receives -dt ga_c(f) dv_c/de at f. dv_c/de is the index-space
+ * difference of the convected field v along e divided by dx, taken on the
+ * upstream side of ubar_e (the side the flow comes from: the lower neighbour
+ * when ubar_e > 0, else the upper one), and zero where that neighbour is
+ * outside the face array. v is the
+ * convected field (or_advect of u); ACCUMULATES into gu. */
+void or_advect_adjoint_upwind(const or_grid *g, const double *const u[3],
+                              const double *const ga[3], double *const gu[3])
+{
+    double h = g->dt / g->dx;
+    long nf[3];
+    double *va[3];
+    for (int c = 0; c < 3; c++) {
+        int d[3];
+        face_dims(g, c, d);
+        nf[c] = (long)d[0] * d[1] * d[2];
+        va[c] = (double *)calloc((size_t)nf[c], sizeof(double));
+    }
+    or_advect(g, u, va);
+    for (int c = 0; c < 3; c++) {
+        int d[3];
+        face_dims(g, c, d);
+        for (int k = 0; k < d[2]; k++)
+            for (int j = 0; j < d[1]; j++)
+                for (int i = 0; i < d[0]; i++) {
+                    long f = fidx(d, i, j, k);
+                    if (face_class(g, c, i, j, k) != FC_FLUID) continue;
+                    double w = ga[c][f];
+                    if (w == 0.0) continue;
+                    gu[c][f] += w; /* the value term */
+                    double vel[3];
+                    face_velocity(g, c, i, j, k, u, vel);
+                    int idx[3] = {i, j, k};
+                    for (int e = 0; e < 3; e++) {
+                        /* upwind difference of v_c along e, in index units */
+                        int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+                        if (vel[e] > 0.0) lo[e] -= 1; else hi[e] += 1;
+                        if (lo[e] < 0 || hi[e] >= d[e]) continue;
+                        (void)idx;
+                        double dv = va[c][fidx(d, hi[0], hi[1], hi[2])] - va[c][fidx(d, lo[0], lo[1], lo[2])];
+                        double gv = -h * dv * w; /* d/d ubar_e */
+                        if (e == c) {
+                            gu[c][f] += gv;
+                        } else {
+                            int de[3];
+                            face_dims(g, e, de);
+                            int L[3] = {i, j, k}, R[3] = {i, j, k};
+                            L[c] -= 1;
+                            int Lp[3] = {L[0], L[1], L[2]}, Rp[3] = {R[0], R[1], R[2]};
+                            Lp[e] += 1;
+                            Rp[e] += 1;
+                            gu[e][fidx(de, L[0], L[1], L[2])] += 0.25 * gv;
+                            gu[e][fidx(de, Lp[0], Lp[1], Lp[2])] += 0.25 * gv;
+                            gu[e][fidx(de, R[0], R[1], R[2])] += 0.25 * gv;
+                            gu[e][fidx(de, Rp[0], Rp[1], Rp[2])] += 0.25 * gv;
+                        }
+                    }
+                }
+    }
+    for (int c = 0; c < 3; c++) free(va[c]);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -861,7 +932,10 @@ void or_adjoint_step(const or_grid *g, const double *const u_in[3], const double
     *g_nu += -g->dt * s;
     /* advection adjoint (body force is an additive constant) */
     for (int c = 0; c < 3; c++) memset(g_in[c], 0, (size_t)nfaces(g, c) * sizeof(double));
-    or_advect_adjoint(g, u_in, (const double *const *)gb, g_in);
+    if (g->advect_grad == 1)
+        or_advect_adjoint_upwind(g, u_in, (const double *const *)gb, g_in);
+    else
+        or_advect_adjoint(g, u_in, (const double *const *)gb, g_in);
     free3(ua); free3(uv); free3(gv); free3(gb); free3(lu);
 }
 
