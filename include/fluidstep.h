@@ -88,6 +88,12 @@ enum {
 };
 
 enum {
+    FS_ADVECT_GRAD_EXACT = 0,  /* the exact discrete adjoint of the back-trace */
+    FS_ADVECT_GRAD_UPWIND = 1  /* the paper's surrogate (Sec. 3.4.1): -dt dv/de by first-order upwind
+                                  differences of the convected field v, the cotangent passed through */
+};
+
+enum {
     FS_SOLVER_PCG = 0,      /* preconditioned CG to tol_p (precond selects the preconditioner) */
     FS_SOLVER_PERCNN = 1    /* K recurrent convolutional sub-steps (fs_percnn_load), Sec. 3.4.1 */
 };
@@ -132,6 +138,11 @@ typedef struct {
                              projection (fs_step, fs_project, fs_adjoint_step) by the recurrent
                              convolutional solver; its map is symmetric, so the adjoint step
                              applies the same projection to the cotangent */
+    int advect_grad;      /* reverse of advection in fs_adjoint_step: FS_ADVECT_GRAD_EXACT (default)
+                             or FS_ADVECT_GRAD_UPWIND (the paper's surrogate gradient: each fluid
+                             face's cotangent passes through, and each velocity component e seen
+                             at the face receives -dt times the cotangent times the upwind
+                             difference of the convected field along e, over dx) */
 } fs_params;
 
 typedef struct {

@@ -139,6 +139,63 @@ __global__ void __launch_bounds__(128) k_advect_adj(CF3 u, const float *__restri
     }
 }
 
+// The paper's upwind surrogate of the reverse of convection (Sec. 3.4.1): the
+// cotangent w of a fluid face f of component c passes to the same face, and
+// each velocity component e seen at f (the own one, or the mean of four faces
+// of another) receives -h w (v_c(hi) - v_c(lo)), the first-order upwind
+// difference of the convected field v along e, taken on the side the flow
+// comes from (lo = f - 1 when the velocity along e is > 0, else hi = f + 1) and
+// zero when that neighbour is outside the component's array. A fixed face holds
+// its prescribed value in v, an air face 0. One launch per component.
+__global__ void __launch_bounds__(128) k_advect_adj_upwind(CF3 u, const float *__restrict__ va,
+                                                           const float *__restrict__ bc, const float *__restrict__ gb,
+                                                           F3 g, const uint8_t *__restrict__ ff, Layout L, int c,
+                                                           float h)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, k = blockIdx.z;
+    if (i >= L.P) return;
+    const int idx = (k * L.R + j) * L.P + i;
+    const int t = L.face_origin(c) + idx;
+    if (!(ff[t] & FF_FLUID)) return;
+    const float w = gb[t];
+    if (w == 0.f) return;
+    float *gcp = g.c[c];
+    atomicAdd(gcp + idx, w);  // the value term
+    const int offs[3] = {1, L.P, L.PL};
+    float vel[3];
+    vel[c] = u.c[c][idx];
+#pragma unroll
+    for (int e = 0; e < 3; e++) {
+        if (e == c) continue;
+        const float *ue = u.c[e];
+        const int l = idx - offs[c], oe = offs[e];
+        vel[e] = 0.25f * ((ue[l] + ue[l + oe]) + (ue[idx] + ue[idx + oe]));
+    }
+    int dims[3] = {L.nx, L.ny, L.nz};
+    dims[c] += 1;
+    const int pos[3] = {i, j, k};
+    auto conv = [&](int tt) { return (ff[tt] & FF_FIXED) ? bc[tt] : va[tt]; };
+#pragma unroll
+    for (int e = 0; e < 3; e++) {
+        const bool up = vel[e] > 0.f;
+        const int lo = up ? pos[e] - 1 : pos[e], hi = up ? pos[e] : pos[e] + 1;
+        if (lo < 0 || hi >= dims[e]) continue;
+        const int tl = t + (lo - pos[e]) * offs[e], th = t + (hi - pos[e]) * offs[e];
+        const float gv = -h * (conv(th) - conv(tl)) * w;
+        if (e == c) {
+            atomicAdd(gcp + idx, gv);
+        } else {
+            float *ge = g.c[e];
+            const int l = idx - offs[c], oe = offs[e];
+            const float q = 0.25f * gv;
+            atomicAdd(ge + l, q);
+            atomicAdd(ge + l + oe, q);
+            atomicAdd(ge + idx, q);
+            atomicAdd(ge + idx + oe, q);
+        }
+    }
+}
+
 __global__ void k_zero3(F3 g, int n)
 {
     const int c = blockIdx.y;
@@ -174,6 +231,16 @@ int launch_advect_adjoint(fs_ctx *c, CF3 u, F3 g)
     dim3 gz(grid_blocks(c, L.S / 4, 256), 3);
     k_zero3<<<gz, 256, 0, c->stream>>>(g, L.S);
     dim3 grid((L.P + 127) / 128, L.R, L.Z);
+    if (c->prm.advect_grad == FS_ADVECT_GRAD_UPWIND) {
+        // the convected field, into a free face-space vector (vx holds the cotangent)
+        for (int comp = 0; comp < 3; comp++)
+            k_advect<<<grid, 128, 0, c->stream>>>(u, c->vq, c->fflag, L, comp, h, (float)(c->prm.dt * c->prm.g[comp]));
+        for (int comp = 0; comp < 3; comp++)
+            k_advect_adj_upwind<<<grid, 128, 0, c->stream>>>(u, c->vq, c->bc, c->vx, g, c->fflag, L, comp, h);
+        c->n_launches += 7;
+        FS_CUDA(cudaGetLastError());
+        return FS_OK;
+    }
     cudaEvent_t e0 = prof_mark(c);
     for (int comp = 0; comp < 3; comp++)
         k_advect_adj<<<grid, 128, 0, c->stream>>>(u, c->vx, g, c->fflag, L, comp, h);

@@ -50,6 +50,8 @@ static int check_params(const fs_params *p)
     if (!(p->mic_tau >= 0.0 && p->mic_tau <= 1.0)) return set_error(FS_EINVAL, "mic_tau must be in [0, 1]");
     if (!(p->mic_sigma >= 0.0 && p->mic_sigma < 1.0)) return set_error(FS_EINVAL, "mic_sigma must be in [0, 1)");
     if (p->warm_start != 0 && p->warm_start != 1) return set_error(FS_EINVAL, "warm_start must be 0 or 1");
+    if (p->advect_grad != FS_ADVECT_GRAD_EXACT && p->advect_grad != FS_ADVECT_GRAD_UPWIND)
+        return set_error(FS_EINVAL, "unknown advect_grad %d", p->advect_grad);
     if (p->pressure_solver != FS_SOLVER_PCG && p->pressure_solver != FS_SOLVER_PERCNN)
         return set_error(FS_EINVAL, "unknown pressure solver %d", p->pressure_solver);
     return FS_OK;
@@ -205,6 +207,7 @@ void fs_default_params(fs_params *p)
     p->mic_tau = 0.97;
     p->mic_sigma = 0.25;
     p->warm_start = 0;
+    p->advect_grad = FS_ADVECT_GRAD_EXACT;
     p->pressure_solver = FS_SOLVER_PCG;
 }
 

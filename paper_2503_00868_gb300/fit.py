@@ -33,7 +33,8 @@ from . import workloads as W
 from .rollout import forward_states, rollout_loss
 
 PRECONDS = {"jacobi": F.FS_PRECOND_JACOBI, "mic0": F.FS_PRECOND_MIC0, "learned": F.FS_PRECOND_LEARNED,
-            "mg": F.FS_PRECOND_MG}
+            "mg": F.FS_PRECOND_MG, "learned_mg": F.FS_PRECOND_LEARNED_MG}
+ADVECT_GRADS = {"exact": F.FS_ADVECT_GRAD_EXACT, "upwind": F.FS_ADVECT_GRAD_UPWIND}
 
 
 def river_scene(nx: int, ny: int, nz: int, seed: int, inflow_speed: float = 0.5, depth: float = 0.25):
@@ -57,10 +58,10 @@ def make_grid(nx: int, ny: int, nz: int, types, bc, precond: str = "jacobi", nu:
     g.set_mask(types, g.pack(bc))
     if percnn_kernel is not None:
         F.fs_percnn_load(g.ctx, percnn_kernel, percnn_k)
-    if precond == "learned":
+    if precond in ("learned", "learned_mg"):
         if weights is None:
-            from .train_precond import default_weights
-            weights = default_weights()
+            from .train_precond import default_weights, role_weights
+            weights = default_weights() if precond == "learned" else role_weights("net_mg")
         F.fs_net_load(g.ctx, weights)
     return g
 
@@ -130,6 +131,39 @@ def compare_pressure_solvers(nx: int = 64, ny: int = 48, nz: int = 64, frames: i
     return out
 
 
+def compare_gradient_paths(nx: int = 64, ny: int = 48, nz: int = 64, frames: int = 12, iters: int = 30,
+                           seed: int = 0) -> dict:
+    """The fit with the reverse of convection by the exact discrete adjoint and by
+    the paper's upwind surrogate (Sec. 3.4.1), against the same targets: the
+    loss after each update and the fitted nu of each, and at the starting point
+    the agreement of the two gradients (cosine of dL/du0, ratio of dL/dnu)."""
+    types, bc, info = river_scene(nx, ny, nz, seed)
+    ref = make_grid(nx, ny, nz, types, bc, "mg", tol_p=1e-6, maxit_p=20000)
+    u_base = ref.pack(bc)
+    d = W.blurred_noise_mac(nx, ny, nz, seed + 7)
+    sc = 0.05 / max(float(np.std(np.concatenate([x.ravel() for x in d]))), 1e-12)
+    targets = synthetic_targets(ref, u_base, ref.pack([x * sc for x in d]), 1e-2, frames)
+    out = {"grid": [nx, ny, nz], "frames": frames, "iters": iters, "runs": {}, "start": {}}
+    grads = {}
+    for name, ag in ADVECT_GRADS.items():
+        g = make_grid(nx, ny, nz, types, bc, "mg", tol_p=1e-6, maxit_p=20000, advect_grad=ag)
+        leaves = [t.clone().requires_grad_(True) for t in u_base]
+        nu = torch.tensor(1e-3, requires_grad=True)
+        loss = rollout_loss(g, F.Mac(*leaves), nu, frames, targets, 4)
+        loss.backward()
+        grads[name] = (torch.cat([t.grad.reshape(-1).double() for t in leaves]), float(nu.grad))
+        t0 = time.time()
+        res = fit(g, u_base, targets, frames, iters, 1e-3)
+        torch.cuda.synchronize()
+        out["runs"][name] = {"loss": [round(h[0], 8) for h in res["history"]], "nu_fit": res["nu"],
+                             "s_per_iter": (time.time() - t0) / iters}
+        g.close()
+    ge, gu = grads["exact"], grads["upwind"]
+    out["start"] = {"cosine_dL_du0": float((ge[0] @ gu[0]) / (ge[0].norm() * gu[0].norm())),
+                    "dL_dnu_exact": ge[1], "dL_dnu_upwind": gu[1]}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--nx", type=int, default=192)
@@ -142,15 +176,21 @@ def main():
     ap.add_argument("--nu-true", type=float, default=1e-2)
     ap.add_argument("--nu0", type=float, default=1e-3)
     ap.add_argument("--delta-sigma", type=float, default=0.05, help="std of the true correction, m/s")
+    ap.add_argument("--advect-grad", default="exact", choices=sorted(ADVECT_GRADS))
     ap.add_argument("--compare-pressure-solvers", action="store_true",
                     help="run the PCG / fitted recurrent solver / Jacobi sub-step comparison instead")
+    ap.add_argument("--compare-gradient-paths", action="store_true",
+                    help="run the exact-adjoint / upwind-surrogate comparison instead")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     if a.compare_pressure_solvers:
         print(json.dumps(compare_pressure_solvers(seed=a.seed)), flush=True)
         return
+    if a.compare_gradient_paths:
+        print(json.dumps(compare_gradient_paths(seed=a.seed)), flush=True)
+        return
     types, bc, info = river_scene(a.nx, a.ny, a.nz, a.seed)
-    grid = make_grid(a.nx, a.ny, a.nz, types, bc, a.precond, maxit_p=20000)
+    grid = make_grid(a.nx, a.ny, a.nz, types, bc, a.precond, maxit_p=20000, advect_grad=ADVECT_GRADS[a.advect_grad])
     u_base = grid.pack(bc)
     dt_np = W.blurred_noise_mac(a.nx, a.ny, a.nz, a.seed + 7)
     scale = a.delta_sigma / max(float(np.std(np.concatenate([x.ravel() for x in dt_np]))), 1e-12)
@@ -168,6 +208,7 @@ def main():
     cells = a.nx * a.ny * a.nz
     steps = a.iters * a.frames * 3  # forward, recompute, adjoint
     print(json.dumps({"grid": [a.nx, a.ny, a.nz], "frames": a.frames, "iters": a.iters, "precond": a.precond,
+                      "advect_grad": a.advect_grad,
                       "occupancy": info["occupancy"], "nu_true": a.nu_true, "nu_fit": res["nu"],
                       "loss_first": res["history"][0][0], "loss_last": res["history"][-1][0],
                       "targets_s": t1 - t0, "fit_s": t2 - t1, "s_per_iter": (t2 - t1) / max(a.iters, 1),

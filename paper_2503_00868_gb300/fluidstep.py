@@ -28,6 +28,7 @@ FS_AIR, FS_LIQUID, FS_SOLID = 0, 1, 2
 FS_PRECOND_JACOBI, FS_PRECOND_MIC0, FS_PRECOND_LEARNED, FS_PRECOND_MG, FS_PRECOND_LEARNED_MG = 0, 1, 2, 3, 4
 FS_MASK_SURFACE, FS_MASK_OCCUPIED = 0, 1
 FS_SOLVER_PCG, FS_SOLVER_PERCNN = 0, 1
+FS_ADVECT_GRAD_EXACT, FS_ADVECT_GRAD_UPWIND = 0, 1
 SOFT_STATUS = (FS_OK, FS_ENOCONV)
 
 
@@ -42,7 +43,7 @@ class fs_params(C.Structure):
                 ("g", C.c_double * 3), ("precond", C.c_int), ("maxit_p", C.c_int), ("maxit_v", C.c_int),
                 ("tol_p", C.c_double), ("tol_v", C.c_double), ("check_every", C.c_int),
                 ("spin_limit", C.c_int), ("mic_tau", C.c_double), ("mic_sigma", C.c_double),
-                ("warm_start", C.c_int), ("pressure_solver", C.c_int)]
+                ("warm_start", C.c_int), ("pressure_solver", C.c_int), ("advect_grad", C.c_int)]
 
 
 class fs_stats(C.Structure):

@@ -48,6 +48,13 @@ def default_weights() -> np.ndarray:
     return np.load(DEFAULT_WEIGHTS).astype(np.float32)
 
 
+def role_weights(role: str) -> np.ndarray:
+    """The network trained for a role on the 4000-pair data set (``--c4``):
+    "net" (FS_PRECOND_LEARNED) or "net_mg" (FS_PRECOND_LEARNED_MG)."""
+    path = os.path.join(os.path.dirname(DEFAULT_WEIGHTS), f"precond_{role}_c4.npy")
+    return np.load(path).astype(np.float32)
+
+
 def init_params(seed: int) -> np.ndarray:
     """He-initialised conv weights, a small last layer; zero biases and zero
     weights on the cell-type channel. Training keeps those offsets at zero, so the

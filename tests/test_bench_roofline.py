@@ -54,13 +54,13 @@ def test_launch_counts_decide_the_share():
 
 
 def test_kernel_table_and_family():
-    prof = {"mg0_smooth": (4, 0.2, 4.0e8, 32), "mg0_residual": (4, 0.2, 2.0e8, 32), "mg_coarse": (4, 0.1, 0.0, 16),
+    prof = {"mg0_smooth2": (4, 0.2, 4.0e8, 32), "mg0_residual": (4, 0.2, 2.0e8, 32), "mg_coarse": (4, 0.1, 0.0, 16),
             "all_kernels": (500, 0.0, 0.0)}
     t = bench.kernel_table(prof, step_ms=10.0, steps=2, hbm=4000.0)
-    assert set(t) == {"mg0_smooth", "mg0_residual", "mg_coarse"}
-    assert t["mg0_smooth"]["est_share_of_step"] == pytest.approx(0.05 * 32 / 20.0)
-    assert t["mg0_smooth"]["achieved_gbs"] == pytest.approx(2000.0)
-    assert t["mg0_smooth"]["frac_of_hbm"] == pytest.approx(0.5)
+    assert set(t) == {"mg0_smooth2", "mg0_residual", "mg_coarse"}
+    assert t["mg0_smooth2"]["est_share_of_step"] == pytest.approx(0.05 * 32 / 20.0)
+    assert t["mg0_smooth2"]["achieved_gbs"] == pytest.approx(2000.0)
+    assert t["mg0_smooth2"]["frac_of_hbm"] == pytest.approx(0.5)
     assert "achieved_gbs" not in t["mg_coarse"]
     fam = bench.family_roofline(prof, {"hbm_gbs": 4000.0})
     assert fam["achieved"] == pytest.approx((6.0e8) / (0.4e-3) / 1e9)      # 1500 GB/s
