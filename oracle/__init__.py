@@ -100,6 +100,11 @@ def lib():
                 "or_percnn_solve": [G, _D, C.c_int, _D, _D, C.POINTER(Stats)],
                 "or_p2g": [G, C.c_int, _D, _D, _D, _D, _P3, C.c_void_p],
                 "or_splat_render": [C.c_int, _D, _D, _D, _D, C.c_void_p, _D, _D],
+                "or_splat_render_flags": [C.c_int, _D, _D, _D, _D, C.c_void_p, _D, _D, C.POINTER(C.c_uint8),
+                                          C.c_double],
+                "or_splat_render_sh": [C.c_int, _D, _D, _D, _D, C.c_int, C.c_void_p, _D, _D, C.POINTER(C.c_uint8),
+                                       C.c_double],
+                "or_sh_basis": [C.c_int, _D, _D],
                 "or_g2p": [G, C.c_int, _D, _D, _D, _D, _D, _D, _P3, C.c_double, C.c_int, C.c_double, C.c_double],
                 "or_percnn_loss_grad": [G, _D, C.c_int, _D, _D, _D],
             }
@@ -468,12 +473,41 @@ def make_camera(R, t, fx, fy, cx, cy, width, height, znear=0.01, bg=(0.0, 0.0, 0
     return cam
 
 
-def splat_render(x, opacity, A, color, cam):
-    """Front-to-back splatting (Sec. 3.2.1); returns rgb (h, w, 3) and transmittance (h, w)."""
+def splat_render(x, opacity, A, color, cam, near_rel=None):
+    """Front-to-back splatting (Sec. 3.2.1); returns rgb (h, w, 3) and transmittance
+    (h, w). With near_rel, also a uint8 (h, w) mask of the pixels whose value turns
+    on a threshold decision within that relative distance (the 3-sigma cutoff, the
+    1/255 alpha floor, the 1e-4 transmittance floor, near-equal depths)."""
     x, o, A, c = _f64(x), _f64(opacity), _f64(A), _f64(color)
     n = x.shape[0]
     rgb = np.zeros((cam.height, cam.width, 3))
     T = np.zeros((cam.height, cam.width))
-    lib().or_splat_render(n, _ptr(x), _ptr(o), _ptr(A), _ptr(c), C.cast(C.pointer(cam), C.c_void_p), _ptr(rgb),
-                          _ptr(T))
-    return rgb, T
+    cp = C.cast(C.pointer(cam), C.c_void_p)
+    if near_rel is None:
+        lib().or_splat_render(n, _ptr(x), _ptr(o), _ptr(A), _ptr(c), cp, _ptr(rgb), _ptr(T))
+        return rgb, T
+    near = np.zeros((cam.height, cam.width), dtype=np.uint8)
+    lib().or_splat_render_flags(n, _ptr(x), _ptr(o), _ptr(A), _ptr(c), cp, _ptr(rgb), _ptr(T),
+                                near.ctypes.data_as(C.POINTER(C.c_uint8)), float(near_rel))
+    return rgb, T, near
+
+
+def sh_basis(degree: int, d):
+    """The real spherical harmonics Y_0 .. Y_{(degree+1)^2 - 1} at the unit vector d."""
+    out = np.zeros(16)
+    lib().or_sh_basis(int(degree), _ptr(_f64(d)), _ptr(out))
+    return out[:(degree + 1) ** 2]
+
+
+def splat_render_sh(x, opacity, A, sh, degree, cam, near_rel=None):
+    """Splatting with view-dependent colours from spherical-harmonic coefficients
+    sh (n, (degree+1)^2, 3); returns rgb, T and, with near_rel, the flag mask."""
+    x, o, A, sh = _f64(x), _f64(opacity), _f64(A), _f64(sh)
+    n = x.shape[0]
+    rgb = np.zeros((cam.height, cam.width, 3))
+    T = np.zeros((cam.height, cam.width))
+    near = np.zeros((cam.height, cam.width), dtype=np.uint8)
+    lib().or_splat_render_sh(n, _ptr(x), _ptr(o), _ptr(A), _ptr(sh), int(degree), C.cast(C.pointer(cam), C.c_void_p),
+                             _ptr(rgb), _ptr(T), near.ctypes.data_as(C.POINTER(C.c_uint8)),
+                             float(near_rel if near_rel is not None else 0.0))
+    return (rgb, T, near) if near_rel is not None else (rgb, T)

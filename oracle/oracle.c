@@ -1634,8 +1634,106 @@ static int splat_key_cmp(const void *a, const void *b)
  * (d^T Sigma^-1 d <= 9) and when alpha >= 1/255; the walk stops once the
  * transmittance T would fall below 1e-4. Colours are degree-0 spherical harmonics
  * (RGB). x [n][3], opacity [n], A [n][3][3], color [n][3]; rgb [h][w][3], T [h][w]. */
+/* View-dependent colour (Sec. 3.2.1: the compositing sum weights SH(r; F_i), the
+ * spherical-harmonic colour of Gaussian i seen along the viewing ray r). The
+ * real spherical harmonics of degree <= 3 at the unit direction d = (x, y, z),
+ * normalised over the sphere (the integral of Y_j^2 is 1), indexed j = l^2 +
+ * l + m, with the signs of the standard 3DGS evaluator (so that coefficients
+ * made for it render alike):
+ *   l = 0: 1/(2 sqrt(pi))
+ *   l = 1: -a y, a z, -a x                                        a = sqrt(3/(4 pi))
+ *   l = 2: b xy, -b yz, c (2zz - xx - yy), -b xz, e (xx - yy)    b = sqrt(15/(4 pi)),
+ *          c = sqrt(5/(16 pi)), e = sqrt(15/(16 pi))
+ *   l = 3: -f y (3xx - yy), g xyz, -h y (4zz - xx - yy), k z (2zz - 3xx - 3yy),
+ *          -h x (4zz - xx - yy), (g/2) z (xx - yy), -f x (xx - 3yy)
+ *          f = sqrt(35/(32 pi)), g = sqrt(105/(4 pi)), h = sqrt(21/(32 pi)),
+ *          k = sqrt(7/(16 pi)) */
+void or_sh_basis(int degree, const double d[3], double *Y)
+{
+    const double PI = 3.14159265358979323846;
+    const double x = d[0], y = d[1], z = d[2];
+    Y[0] = 0.5 / sqrt(PI);
+    if (degree < 1) return;
+    const double a = sqrt(3.0 / (4.0 * PI));
+    Y[1] = -a * y;
+    Y[2] = a * z;
+    Y[3] = -a * x;
+    if (degree < 2) return;
+    const double b = sqrt(15.0 / (4.0 * PI)), c = sqrt(5.0 / (16.0 * PI)), e = sqrt(15.0 / (16.0 * PI));
+    Y[4] = b * x * y;
+    Y[5] = -b * y * z;
+    Y[6] = c * (2.0 * z * z - x * x - y * y);
+    Y[7] = -b * x * z;
+    Y[8] = e * (x * x - y * y);
+    if (degree < 3) return;
+    const double f = sqrt(35.0 / (32.0 * PI)), g = sqrt(105.0 / (4.0 * PI)), h = sqrt(21.0 / (32.0 * PI)),
+                 k = sqrt(7.0 / (16.0 * PI));
+    Y[9] = -f * y * (3.0 * x * x - y * y);
+    Y[10] = g * x * y * z;
+    Y[11] = -h * y * (4.0 * z * z - x * x - y * y);
+    Y[12] = k * z * (2.0 * z * z - 3.0 * x * x - 3.0 * y * y);
+    Y[13] = -h * x * (4.0 * z * z - x * x - y * y);
+    Y[14] = 0.5 * g * z * (x * x - y * y);
+    Y[15] = -f * x * (x * x - 3.0 * y * y);
+}
+
+/* The colour of one Gaussian: max(0, 1/2 + sum_j sh[j][k] Y_j(d)) per channel k,
+ * with d the unit vector from the camera centre (-R^T t) to the mean (the 1/2
+ * offset of the standard evaluator: zero coefficients give mid grey). */
+static void sh_colour(int degree, const or_camera *cam, const double xm[3], const double *sh, double out[3])
+{
+    double C[3], d[3], Y[16], nrm = 0.0;
+    for (int r = 0; r < 3; r++) C[r] = -(cam->R[r] * cam->t[0] + cam->R[3 + r] * cam->t[1] + cam->R[6 + r] * cam->t[2]);
+    for (int r = 0; r < 3; r++) {
+        d[r] = xm[r] - C[r];
+        nrm += d[r] * d[r];
+    }
+    nrm = sqrt(nrm);
+    for (int r = 0; r < 3; r++) d[r] = nrm > 0.0 ? d[r] / nrm : 0.0;
+    or_sh_basis(degree, d, Y);
+    const int nb = (degree + 1) * (degree + 1);
+    for (int k = 0; k < 3; k++) {
+        double v = 0.5;
+        for (int j = 0; j < nb; j++) v += sh[3 * j + k] * Y[j];
+        out[k] = v > 0.0 ? v : 0.0;
+    }
+}
+
+/* Front-to-back compositing as below; with `near` non-NULL, near[pixel] = 1 when
+ * the pixel's value turns on a decision that an evaluation in single precision
+ * could take the other way: a Gaussian whose md lies within rel of the 3-sigma
+ * cutoff 9, an alpha within rel of 1/255, a transmittance within rel of the
+ * 1e-4 floor, or two contributing Gaussians whose depths differ by less than
+ * rel times the depth (but are not equal). The flags change no value. */
+static void splat_render_impl(int n, const double *x, const double *opacity, const double *A, const double *color,
+                              const or_camera *cam, double *rgb, double *T_out, unsigned char *near, double rel);
+
 void or_splat_render(int n, const double *x, const double *opacity, const double *A, const double *color,
                      const or_camera *cam, double *rgb, double *T_out)
+{
+    splat_render_impl(n, x, opacity, A, color, cam, rgb, T_out, NULL, 0.0);
+}
+
+void or_splat_render_flags(int n, const double *x, const double *opacity, const double *A, const double *color,
+                           const or_camera *cam, double *rgb, double *T_out, unsigned char *near, double rel)
+{
+    splat_render_impl(n, x, opacity, A, color, cam, rgb, T_out, near, rel);
+}
+
+/* The same compositing with the view-dependent colour of each Gaussian from its
+ * spherical-harmonic coefficients sh [n][(degree + 1)^2][3] (degree 0 .. 3). */
+void or_splat_render_sh(int n, const double *x, const double *opacity, const double *A, const double *sh,
+                        int degree, const or_camera *cam, double *rgb, double *T_out, unsigned char *near, double rel)
+{
+    const int nb = (degree + 1) * (degree + 1);
+    double *col = (double *)malloc((size_t)(n > 0 ? n : 1) * 3 * sizeof(double));
+    for (int i = 0; i < n; i++) sh_colour(degree, cam, x + 3 * i, sh + (size_t)i * nb * 3, col + 3 * i);
+    splat_render_impl(n, x, opacity, A, col, cam, rgb, T_out, near, rel);
+    free(col);
+}
+
+static void splat_render_impl(int n, const double *x, const double *opacity, const double *A, const double *color,
+                              const or_camera *cam, double *rgb, double *T_out, unsigned char *near, double rel)
 {
     double *depth = (double *)malloc((size_t)n * sizeof(double));
     double *mean = (double *)malloc((size_t)n * 2 * sizeof(double));
@@ -1652,20 +1750,29 @@ void or_splat_render(int n, const double *x, const double *opacity, const double
         for (int px = 0; px < cam->width; px++) {
             double T = 1.0, c[3] = {0.0, 0.0, 0.0};
             double pu = px + 0.5, pv = py + 0.5;
+            int flag = 0;
+            double last_depth = -1.0;
             for (int q = 0; q < m; q++) {
                 int i = keys[q].idx;
                 double dx = pu - mean[2 * i], dy = pv - mean[2 * i + 1];
                 double md = conic[3 * i] * dx * dx + 2.0 * conic[3 * i + 1] * dx * dy + conic[3 * i + 2] * dy * dy;
+                if (near && fabs(md - 9.0) < rel * 9.0) flag = 1;
                 if (md > 9.0) continue;
                 double alpha = opacity[i] * exp(-0.5 * md);
                 if (alpha > 0.99) alpha = 0.99;
+                if (near && fabs(alpha * 255.0 - 1.0) < rel) flag = 1;
                 if (alpha < 1.0 / 255.0) continue;
                 double Tn = T * (1.0 - alpha);
+                if (near && fabs(Tn * 1e4 - 1.0) < rel) flag = 1;
                 if (Tn < 1e-4) break;
+                if (near && last_depth >= 0.0 && depth[i] != last_depth && depth[i] - last_depth < rel * depth[i])
+                    flag = 1;
                 for (int k = 0; k < 3; k++) c[k] += alpha * T * color[3 * i + k];
                 T = Tn;
+                last_depth = depth[i];
             }
             long o = (long)py * cam->width + px;
+            if (near) near[o] = (unsigned char)flag;
             for (int k = 0; k < 3; k++) rgb[3 * o + k] = c[k] + T * cam->bg[k];
             if (T_out) T_out[o] = T;
         }

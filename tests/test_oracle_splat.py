@@ -146,3 +146,94 @@ def test_alpha_threshold_of_one_over_255():
     rgb_hi, T_hi = O.splat_render(x, [hi], A, np.ones((1, 3)), c)
     assert T_lo[0, 0] == 1.0
     assert T_hi[0, 0] == pytest.approx(1.0 - hi, abs=1e-15) and rgb_hi[0, 0, 0] == pytest.approx(hi, abs=1e-15)
+
+
+def test_near_threshold_flags_mark_exactly_the_ambiguous_pixels():
+    """One isotropic Gaussian on the axis: sigma 0.1 at depth 2 seen with f = 40
+    projects to a 2-pixel isotropic 2D Gaussian, so md = d^2 / 4 with d the pixel
+    centre's distance to the mean in pixels. With the mean on a pixel corner
+    (cx, cy = 20.5, 15.5) d^2 is an integer and md = 9 exactly at the four
+    pixels 6 away along the axes: those, and only those, are flagged at rel 1e-3
+    (alpha never reaches 1/255 before the cutoff, T stays above the floor). The
+    flags change no value."""
+    c = O.make_camera(np.eye(3), (0, 0, 0), 40.0, 40.0, 20.5, 15.5, 41, 31, 0.01, (0.1, 0.2, 0.3))
+    x = np.array([[0.0, 0.0, 2.0]])
+    A = (0.1 ** 2 * np.eye(3)).reshape(1, 9)
+    op, col = np.array([0.9]), np.array([[0.3, 0.6, 0.9]])
+    rgb, T = O.splat_render(x, op, A, col, c)
+    rgb2, T2, near = O.splat_render(x, op, A, col, c, near_rel=1e-3)
+    assert np.array_equal(rgb, rgb2) and np.array_equal(T, T2)
+    py, px = np.nonzero(near)
+    got = sorted(zip((px + 0.5 - 20.5).astype(int), (py + 0.5 - 15.5).astype(int)))
+    assert got == [(-6, 0), (0, -6), (0, 6), (6, 0)]
+
+
+def test_sh_basis_is_orthonormal_on_the_sphere():
+    """The 16 real spherical harmonics of degree <= 3 integrate to the identity
+    over the sphere: a Fibonacci lattice of 200 000 directions, each weighted
+    4 pi / N, gives <Y_i, Y_j> to 1e-4. A wrong constant or a dropped term of any
+    basis polynomial breaks this."""
+    N = 200_000
+    k = np.arange(N) + 0.5
+    z = 1.0 - 2.0 * k / N
+    phi = np.pi * (1.0 + 5.0 ** 0.5) * k
+    r = np.sqrt(1.0 - z * z)
+    dirs = np.stack([r * np.cos(phi), r * np.sin(phi), z], axis=1)
+    Y = np.stack([O.sh_basis(3, d) for d in dirs[::50]])          # a coarse check of the call itself
+    assert Y.shape == (N // 50, 16)
+    # the full lattice through the same function, vectorised by rows of 1000
+    G = np.zeros((16, 16))
+    for s in range(0, N, 1000):
+        Ys = np.stack([O.sh_basis(3, d) for d in dirs[s:s + 1000]])
+        G += Ys.T @ Ys
+    G *= 4.0 * np.pi / N
+    np.testing.assert_allclose(G, np.eye(16), atol=1e-4)
+
+
+def test_sh_sign_convention_along_the_axes():
+    """The signs of the standard 3DGS evaluator: the degree-1 functions are
+    -a y, a z, -a x (a = sqrt(3 / 4 pi))."""
+    a = np.sqrt(3.0 / (4.0 * np.pi))
+    np.testing.assert_allclose(O.sh_basis(1, [1, 0, 0]), [0.5 / np.sqrt(np.pi), 0, 0, -a], atol=1e-15)
+    np.testing.assert_allclose(O.sh_basis(1, [0, 1, 0]), [0.5 / np.sqrt(np.pi), -a, 0, 0], atol=1e-15)
+    np.testing.assert_allclose(O.sh_basis(1, [0, 0, 1]), [0.5 / np.sqrt(np.pi), 0, a, 0], atol=1e-15)
+
+
+def test_sh_degree_zero_is_the_rgb_colour_and_degree_one_turns_with_the_view():
+    """Degree 0 with coefficient (c - 1/2) / Y_0 renders exactly as the RGB colour
+    c. One Gaussian on the optical axis with only the z coefficient of degree 1
+    set: its colour is max(0, 1/2 + k a d_z) with d the direction from the camera
+    centre to the mean, so the centre pixel is alpha colour + (1 - alpha) bg, and a
+    camera on the other side (d_z = -1) sees 1/2 - k a."""
+    rng = np.random.default_rng(4)
+    n = 40
+    x = np.column_stack([rng.uniform(-0.5, 0.5, n), rng.uniform(-0.4, 0.4, n), rng.uniform(1.5, 3.0, n)])
+    A = np.stack([0.03 ** 2 * np.eye(3)] * n).reshape(n, 9)
+    op, col = rng.uniform(0.3, 0.9, n), rng.random((n, 3))
+    c = cam()
+    y0 = 0.5 / np.sqrt(np.pi)
+    sh0 = ((col - 0.5) / y0).reshape(n, 1, 3)
+    a_rgb, a_T = O.splat_render(x, op, A, col, c)
+    b_rgb, b_T = O.splat_render_sh(x, op, A, sh0, 0, c)
+    np.testing.assert_allclose(b_rgb, a_rgb, atol=1e-13)
+    np.testing.assert_allclose(b_T, a_T, atol=1e-15)
+    # one Gaussian on the axis, 2 m in front of the camera
+    aa = np.sqrt(3.0 / (4.0 * np.pi))
+    kz = np.array([0.3, -0.2, 0.6])
+    sh = np.zeros((1, 4, 3))
+    sh[0, 2] = kz
+    xg = np.array([[0.0, 0.0, 2.0]])
+    Ag = (0.05 ** 2 * np.eye(3)).reshape(1, 9)
+    c1 = O.make_camera(np.eye(3), (0, 0, 0), 40.0, 40.0, 16.0, 12.0, 32, 24, 0.01, (0.1, 0.2, 0.3))
+    rgb, T = O.splat_render_sh(xg, np.array([0.8]), Ag, sh, 1, c1)
+    # pixel (15, 11) has its centre half a pixel from the mean in x and y
+    s2 = (40.0 * 0.05 / 2.0) ** 2
+    alpha = 0.8 * np.exp(-0.5 * (0.25 + 0.25) / s2)
+    expect = alpha * np.maximum(0.0, 0.5 + kz * aa) + (1.0 - alpha) * np.array([0.1, 0.2, 0.3])
+    np.testing.assert_allclose(rgb[11, 15], expect, rtol=1e-12)
+    # the camera behind the Gaussian looking back along -z: R = diag(-1, 1, -1), centre at z = 4
+    Rb = np.diag([-1.0, 1.0, -1.0])
+    c2 = O.make_camera(Rb, -Rb @ np.array([0.0, 0.0, 4.0]), 40.0, 40.0, 16.0, 12.0, 32, 24, 0.01, (0.1, 0.2, 0.3))
+    rgb2, _ = O.splat_render_sh(xg, np.array([0.8]), Ag, sh, 1, c2)
+    expect2 = alpha * np.maximum(0.0, 0.5 - kz * aa) + (1.0 - alpha) * np.array([0.1, 0.2, 0.3])
+    np.testing.assert_allclose(rgb2[11, 16], expect2, rtol=1e-12)
