@@ -291,7 +291,8 @@ typedef struct {
  *   with S = J R A_i R^T J^T the projected covariance (J the pinhole Jacobian at the
  *   mean) and d the pixel centre's offset from the projected mean, kept inside the
  *   3-sigma ellipse and when alpha >= 1/255; the walk stops once the transmittance
- *   would fall below 1e-4. Colours are degree-0 spherical harmonics (RGB).
+ *   would fall below 1e-4. Colours are RGB (degree-0 spherical harmonics;
+ *   fs_splat_render_sh takes higher degrees).
  *   x [n][3], opacity [n] in [0, 1], A [n][3][3] covariances, color [n][3]: DEVICE;
  *   cam: HOST; rgb_out [height][width][3], T_out (nullable) [height][width]: DEVICE.
  * A must be symmetric positive definite. Does not need a mask. Synchronises the
@@ -300,6 +301,18 @@ typedef struct {
  * scratch cannot grow. */
 int fs_splat_render(fs_ctx *c, int n, const float *x, const float *opacity, const float *A, const float *color,
                     const fs_camera *cam, float *rgb_out, float *T_out);
+
+/* fs_splat_render with view-dependent colours (Sec. 3.2.1: the compositing sum
+ * weights SH(r; F_i), the spherical-harmonic colour of Gaussian i seen along the
+ * ray): c_i = max(0, 1/2 + sum_j sh[i][j] Y_j(d_i)) per channel, with d_i the
+ * unit vector from the camera centre -R^T t to the mean and Y_j, j = l^2 + l + m,
+ * the real spherical harmonics of degree l <= sh_degree, normalised over the
+ * sphere, in the sign convention of the standard 3DGS evaluator (degree 1:
+ * -a y, a z, -a x with a = sqrt(3 / (4 pi))).
+ *   sh [n][(sh_degree + 1)^2][3]: DEVICE; sh_degree in [0, 3]; the rest as in
+ *   fs_splat_render. Degree 0 with sh[i][0] = (c_i - 1/2) / Y_0 gives colour c_i. */
+int fs_splat_render_sh(fs_ctx *c, int n, const float *x, const float *opacity, const float *A, const float *sh,
+                       int sh_degree, const fs_camera *cam, float *rgb_out, float *T_out);
 
 /* Counters of the last fs_splat_render on this context, as host values (no GPU
  * work): entries = the number of (Gaussian, tile) pairs binned, max_tile = the

@@ -564,14 +564,8 @@ int fs_pbd_project(fs_ctx *c, fs_mac *u, int hold_surface, int iters, double eps
     return launch_pbd_project(c, f3(u), hold_surface ? 1 : 0, iters, eps, div_norm);
 }
 
-int fs_splat_render(fs_ctx *c, int n, const float *x, const float *opacity, const float *A, const float *color,
-                    const fs_camera *cam, float *rgb_out, float *T_out)
+static int check_camera(const fs_camera *cam)
 {
-    if (!c) return set_error(FS_EINVAL, "NULL context");
-    g_err[0] = 0;
-    if (n < 0) return set_error(FS_EINVAL, "n must be >= 0");
-    if (n > 0 && (!x || !opacity || !A || !color)) return set_error(FS_EINVAL, "Gaussian array is NULL");
-    if (!cam || !rgb_out) return set_error(FS_EINVAL, "cam / rgb_out is NULL");
     if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384)
         return set_error(FS_EINVAL, "image size must be in [1, 16384]");
     const double *vals[] = {cam->R, cam->t, &cam->fx, &cam->fy, &cam->cx, &cam->cy, &cam->znear, cam->bg};
@@ -580,7 +574,32 @@ int fs_splat_render(fs_ctx *c, int n, const float *x, const float *opacity, cons
         for (int k = 0; k < cnt[a]; k++)
             if (!std::isfinite(vals[a][k])) return set_error(FS_EINVAL, "camera parameters must be finite");
     if (!(cam->znear > 0.0)) return set_error(FS_EINVAL, "znear must be > 0");
-    return splat_render(c, n, x, opacity, A, color, cam, rgb_out, T_out);
+    return FS_OK;
+}
+
+int fs_splat_render_sh(fs_ctx *c, int n, const float *x, const float *opacity, const float *A, const float *sh,
+                       int sh_degree, const fs_camera *cam, float *rgb_out, float *T_out)
+{
+    if (!c) return set_error(FS_EINVAL, "NULL context");
+    g_err[0] = 0;
+    if (n < 0) return set_error(FS_EINVAL, "n must be >= 0");
+    if (sh_degree < 0 || sh_degree > 3) return set_error(FS_EINVAL, "sh_degree must be in [0, 3]");
+    if (n > 0 && (!x || !opacity || !A || !sh)) return set_error(FS_EINVAL, "Gaussian array is NULL");
+    if (!cam || !rgb_out) return set_error(FS_EINVAL, "cam / rgb_out is NULL");
+    if (int rc = check_camera(cam)) return rc;
+    return splat_render(c, n, x, opacity, A, nullptr, sh, sh_degree, cam, rgb_out, T_out);
+}
+
+int fs_splat_render(fs_ctx *c, int n, const float *x, const float *opacity, const float *A, const float *color,
+                    const fs_camera *cam, float *rgb_out, float *T_out)
+{
+    if (!c) return set_error(FS_EINVAL, "NULL context");
+    g_err[0] = 0;
+    if (n < 0) return set_error(FS_EINVAL, "n must be >= 0");
+    if (n > 0 && (!x || !opacity || !A || !color)) return set_error(FS_EINVAL, "Gaussian array is NULL");
+    if (!cam || !rgb_out) return set_error(FS_EINVAL, "cam / rgb_out is NULL");
+    if (int rc = check_camera(cam)) return rc;
+    return splat_render(c, n, x, opacity, A, color, nullptr, 0, cam, rgb_out, T_out);
 }
 
 int fs_splat_stats(const fs_ctx *c, unsigned long long *entries, unsigned long long *max_tile)

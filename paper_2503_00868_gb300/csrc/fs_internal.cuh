@@ -392,7 +392,7 @@ void mg_count(fs_ctx *c, long long vcycles, bool faces);  // fs_mg.cu: launch co
 int mg_levels(const fs_ctx *c);
 // fs_splat.cu
 int splat_render(fs_ctx *c, int n, const float *x, const float *op, const float *A, const float *col,
-                 const fs_camera *cam, float *rgb, float *T);
+                 const float *sh, int deg, const fs_camera *cam, float *rgb, float *T);
 void splat_free(fs_ctx *c);
 void splat_stats(const fs_ctx *c, unsigned long long *entries, unsigned long long *max_tile);
 // fs_apic.cu

@@ -86,10 +86,60 @@ __device__ __forceinline__ int ht_slot(unsigned *hk, unsigned t, bool insert)
     return -1;
 }
 
+// View-dependent colour (Sec. 3.2.1, SH(r; F_i)): max(0, 1/2 + sum_j sh[j] Y_j(d))
+// per channel, with the real spherical harmonics Y_j of degree <= 3 in the sign
+// convention of the standard 3DGS evaluator and d the unit vector from the camera
+// centre to the mean. The constants are the normalisations of the basis:
+// sqrt(3/4pi), sqrt(15/4pi), sqrt(5/16pi), sqrt(15/16pi), sqrt(35/32pi),
+// sqrt(105/4pi), sqrt(21/32pi), sqrt(7/16pi).
+__device__ __forceinline__ void sh_colour(int deg, const float *__restrict__ sh, float dx, float dy, float dz,
+                                          float out[3])
+{
+    constexpr float Y0 = 0.28209479177387814f, A1 = 0.4886025119029199f;
+    constexpr float B2 = 1.0925484305920792f, C2 = 0.31539156525252005f, E2 = 0.5462742152960396f;
+    constexpr float F3 = 0.5900435899266435f, G3 = 2.890611442640554f, H3 = 0.4570457994644658f,
+                    K3 = 0.3731763325901154f;
+    float Y[16];
+    Y[0] = Y0;
+    if (deg >= 1) {
+        Y[1] = -A1 * dy;
+        Y[2] = A1 * dz;
+        Y[3] = -A1 * dx;
+    }
+    if (deg >= 2) {
+        const float xx = dx * dx, yy = dy * dy, zz = dz * dz;
+        Y[4] = B2 * dx * dy;
+        Y[5] = -B2 * dy * dz;
+        Y[6] = C2 * (2.f * zz - xx - yy);
+        Y[7] = -B2 * dx * dz;
+        Y[8] = E2 * (xx - yy);
+        if (deg >= 3) {
+            Y[9] = -F3 * dy * (3.f * xx - yy);
+            Y[10] = G3 * dx * dy * dz;
+            Y[11] = -H3 * dy * (4.f * zz - xx - yy);
+            Y[12] = K3 * dz * (2.f * zz - 3.f * xx - 3.f * yy);
+            Y[13] = -H3 * dx * (4.f * zz - xx - yy);
+            Y[14] = 0.5f * G3 * dz * (xx - yy);
+            Y[15] = -F3 * dx * (xx - 3.f * yy);
+        }
+    }
+    const int nb = (deg + 1) * (deg + 1);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        float v = 0.5f;
+        for (int j = 0; j < nb; j++) v += sh[3 * j + k] * Y[j];
+        out[k] = fmaxf(v, 0.f);
+    }
+}
+
+// Projection, colour and tile counting of each Gaussian. The colour is col[i]
+// (RGB) or, with sh non-null, the spherical-harmonic colour of degree `deg`
+// seen from the camera centre.
 __global__ void __launch_bounds__(256) k_sp_project(int n, const float *__restrict__ x,
                                                     const float *__restrict__ op, const float *__restrict__ A,
-                                                    const float *__restrict__ col, Cam cam, SplatRecord *rec,
-                                                    int4 *rect, float *depth, unsigned *tcount, int ntx, int nty)
+                                                    const float *__restrict__ col, const float *__restrict__ sh,
+                                                    int deg, Cam cam, SplatRecord *rec, int4 *rect, float *depth,
+                                                    unsigned *tcount, int ntx, int nty)
 {
     __shared__ unsigned hk[SP_HT], hc[SP_HT];
     for (int base = blockIdx.x * 256; base < n; base += gridDim.x * 256) {  // uniform over the block
@@ -137,9 +187,26 @@ __global__ void __launch_bounds__(256) k_sp_project(int n, const float *__restri
                 q.cb = -S[1] / det;
                 q.cc = S[0] / det;
                 q.opacity = op[i];
-                q.r = col[3 * i];
-                q.g = col[3 * i + 1];
-                q.b = col[3 * i + 2];
+                if (sh) {
+                    // the camera centre -R^T t and the unit direction to the mean
+                    float d[3], nrm = 0.f;
+#pragma unroll
+                    for (int r = 0; r < 3; r++) {
+                        const float cr = -(cam.R[r] * cam.t[0] + cam.R[3 + r] * cam.t[1] + cam.R[6 + r] * cam.t[2]);
+                        d[r] = x[3 * i + r] - cr;
+                        nrm += d[r] * d[r];
+                    }
+                    const float inv = nrm > 0.f ? rsqrtf(nrm) : 0.f;
+                    float cv[3];
+                    sh_colour(deg, sh + (size_t)i * (deg + 1) * (deg + 1) * 3, d[0] * inv, d[1] * inv, d[2] * inv, cv);
+                    q.r = cv[0];
+                    q.g = cv[1];
+                    q.b = cv[2];
+                } else {
+                    q.r = col[3 * i];
+                    q.g = col[3 * i + 1];
+                    q.b = col[3 * i + 2];
+                }
                 rec[i] = q;
                 depth[i] = z;
                 // the 3-sigma ellipse lies in mean +- 3 sqrt(diag S); pixel centres at p + 1/2
@@ -446,7 +513,7 @@ void splat_free(fs_ctx *c)
 }
 
 int splat_render(fs_ctx *c, int n, const float *x, const float *op, const float *A, const float *col,
-                 const fs_camera *camh, float *rgb, float *T)
+                 const float *sh, int deg, const fs_camera *camh, float *rgb, float *T)
 {
     SplatState *s = static_cast<SplatState *>(c->splat);
     if (!s) {
@@ -484,7 +551,8 @@ int splat_render(fs_ctx *c, int n, const float *x, const float *op, const float 
     FS_CUDA(cudaMemsetAsync(s->tfill, 0, (size_t)nt * 4, c->stream));
     const int gb = grid_blocks(c, n > 0 ? n : 1, 256);
     if (n > 0)
-        k_sp_project<<<gb, 256, 0, c->stream>>>(n, x, op, A, col, cam, s->rec, s->rect, s->depth, s->tcount, ntx, nty);
+        k_sp_project<<<gb, 256, 0, c->stream>>>(n, x, op, A, col, sh, deg, cam, s->rec, s->rect, s->depth,
+                                                s->tcount, ntx, nty);
     unsigned long long *total_d = reinterpret_cast<unsigned long long *>(c->partials);
     k_sp_scan<<<1, 1024, 0, c->stream>>>(s->tcount, s->toff, nt, total_d);
     c->n_launches += 2;

@@ -91,6 +91,8 @@ _SIGS = {
     "fs_divergence": ([C.c_void_p, C.POINTER(fs_mac), C.c_void_p], C.c_int),
     "fs_splat_render": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                          C.c_void_p, C.c_void_p], C.c_int),
+    "fs_splat_render_sh": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                            C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "fs_splat_stats": ([C.c_void_p, C.POINTER(C.c_ulonglong), C.POINTER(C.c_ulonglong)], C.c_int),
     "fs_p2g": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(fs_mac),
                 C.POINTER(fs_mac)], C.c_int),
@@ -301,6 +303,30 @@ def fs_splat_render(ctx: int, x: torch.Tensor, opacity: torch.Tensor, A: torch.T
                                   C.c_void_p(opacity.data_ptr()), C.c_void_p(A.data_ptr()),
                                   C.c_void_p(color.data_ptr()), C.byref(cam), C.c_void_p(rgb_out.data_ptr()),
                                   C.c_void_p(T_out.data_ptr()) if T_out is not None else None), (FS_OK,))
+
+
+def fs_splat_render_sh(ctx: int, x: torch.Tensor, opacity: torch.Tensor, A: torch.Tensor, sh: torch.Tensor,
+                       degree: int, cam: fs_camera, rgb_out: torch.Tensor, T_out: Optional[torch.Tensor] = None) -> None:
+    """Like fs_splat_render with colours from spherical-harmonic coefficients sh
+    (n, (degree+1)^2, 3) float32 CUDA, degree 0 .. 3."""
+    n = x.shape[0]
+    nb = (int(degree) + 1) ** 2
+    if sh.dtype != torch.float32 or not sh.is_cuda or not sh.is_contiguous() or tuple(sh.shape) != (n, nb, 3):
+        raise ValueError(f"sh must be a contiguous float32 CUDA tensor of shape ({n}, {nb}, 3)")
+    for t, cols in ((x, 3), (A, 9), (opacity.reshape(-1, 1), 1)):
+        _parts(t, cols)
+        if t.shape[0] != n:
+            raise ValueError("x, opacity, A and sh must have the same number of rows")
+    if T_out is not None and (T_out.shape != (cam.height, cam.width) or T_out.dtype != torch.float32
+                              or not T_out.is_cuda):
+        raise ValueError("T_out must be a float32 CUDA tensor of shape (height, width)")
+    if rgb_out.shape != (cam.height, cam.width, 3) or rgb_out.dtype != torch.float32 or not rgb_out.is_cuda:
+        raise ValueError("rgb_out must be a float32 CUDA tensor of shape (height, width, 3)")
+    _check(load().fs_splat_render_sh(C.c_void_p(ctx), int(n), C.c_void_p(x.data_ptr()),
+                                     C.c_void_p(opacity.data_ptr()), C.c_void_p(A.data_ptr()),
+                                     C.c_void_p(sh.data_ptr()), int(degree), C.byref(cam),
+                                     C.c_void_p(rgb_out.data_ptr()),
+                                     C.c_void_p(T_out.data_ptr()) if T_out is not None else None), (FS_OK,))
 
 
 def fs_splat_stats(ctx: int) -> dict:

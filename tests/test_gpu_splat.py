@@ -5,10 +5,14 @@ depth ties that fall back to index order), and pixel windows of the full-size
 workload (1920 x 1080, one Gaussian per liquid cell of a 128^3 blob).
 
 The GPU projects in FP32 and the oracle in FP64, so a pixel whose Mahalanobis
-distance sits on the 3-sigma cutoff, whose alpha sits on 1/255, or whose
-transmittance sits on the 1e-4 floor can fall on the other side; each such flip
-moves a pixel by at most about exp(-4.5) ~ 0.011 (times a colour <= 1). The
-tests bound the share of pixels off by more than 1e-4 and the worst pixel."""
+distance sits on the 3-sigma cutoff, whose alpha sits on 1/255, whose
+transmittance sits on the 1e-4 floor, or whose contributors have nearly equal
+depths can fall on the other side of that decision. The oracle flags exactly
+those pixels (a relative distance of 1e-3 to the threshold); every other pixel
+must agree to 1e-4 in colour and transmittance, with no allowance. A flagged
+pixel may move by one flip (at most about exp(-4.5) ~ 0.011 at the cutoff,
+times a colour <= 1; a reordering of near-equal depths by the difference of two
+contributions) and is bounded by 0.05; flagged pixels stay a small share."""
 import numpy as np
 import pytest
 import torch
@@ -51,11 +55,18 @@ def render_gpu(ctx, x, op, A, col, cam):
     return rgb.cpu().numpy().astype(np.float64), T.cpu().numpy().astype(np.float64)
 
 
-def compare(g, o, share=0.99, tol=1e-4, worst=0.05):
+NEAR = 1e-3   # relative distance to a threshold under which the oracle flags a pixel
+
+
+def compare(g, o, tol=1e-4, worst=0.05, flagged_share=0.5):
+    """o = (rgb, T, near) from the oracle with near_rel = NEAR"""
     d = np.maximum(np.abs(g[0] - o[0]).max(-1), np.abs(g[1] - o[1]))
+    near = o[2].astype(bool)
     assert np.isfinite(d).all()
-    assert np.mean(d <= tol) >= share, (np.mean(d <= tol), d.max())
+    if (~near).any():
+        assert d[~near].max() <= tol, (d[~near].max(), int((d[~near] > tol).sum()))
     assert d.max() <= worst, d.max()
+    assert near.mean() <= flagged_share, near.mean()
 
 
 def camera_space_scene(n, seed, R, t, zlo=1.5, zhi=4.0, spread=0.6, sig=0.05):
@@ -77,7 +88,7 @@ def test_ragged_image_under_a_rotated_camera(ctx):
     R, t = Rx @ Ry, np.array([0.1, -0.05, 0.3])
     x, op, A, col = camera_space_scene(3000, 0, R, t)
     cg, co = cams(R, t, 70.0, 72.0, 51.3, 36.8, 101, 75)
-    compare(render_gpu(ctx, x, op, A, col, cg), O.splat_render(x, op, A, col, co))
+    compare(render_gpu(ctx, x, op, A, col, cg), O.splat_render(x, op, A, col, co, near_rel=NEAR))
 
 
 def test_empty_scene_and_culled_gaussians(ctx):
@@ -88,9 +99,9 @@ def test_empty_scene_and_culled_gaussians(ctx):
     x = np.array([[0, 0, -2.0], [0, 0, 0.005], [0, 0, 2.0]])
     A = np.stack([0.01 * np.eye(3), 0.01 * np.eye(3), np.outer([0, 0, 1.0], [0, 0, 1.0])])
     g = render_gpu(ctx, x, np.full(3, 0.9), A, np.ones((3, 3)), cg)
-    o = O.splat_render(x, np.full(3, 0.9), A, np.ones((3, 3)), co)
+    o = O.splat_render(x, np.full(3, 0.9), A, np.ones((3, 3)), co, near_rel=NEAR)
     assert np.all(o[1] == 1.0) and np.all(g[1] == 1.0)
-    compare(g, o, share=1.0, tol=1e-6, worst=1e-6)
+    compare(g, o, tol=1e-6, worst=1e-6, flagged_share=0.0)
 
 
 def test_tiles_beyond_shared_memory_with_depth_ties(ctx):
@@ -107,7 +118,7 @@ def test_tiles_beyond_shared_memory_with_depth_ties(ctx):
     cg, co = cams(np.eye(3), np.zeros(3), 300.0, 300.0, 48.0, 40.0, 96, 80)
     g = render_gpu(ctx, x, op, A, col, cg)
     assert F.fs_splat_stats(ctx.ctx)["max_tile"] > 4096  # the global-memory sort ran
-    compare(g, O.splat_render(x, op, A, col, co))
+    compare(g, O.splat_render(x, op, A, col, co, near_rel=NEAR))
 
 
 def test_full_size_workload_windows(ctx):
@@ -122,8 +133,8 @@ def test_full_size_workload_windows(ctx):
     # one on its silhouette: the oracle renders them by shifting the principal point
     for x0, y0 in ((944, 300), (700, 500), (1000, 20), (1350, 400)):
         co = O.make_camera(R, t, fx, fy, cx - x0, cy - y0, 24, 16, 0.01, (0.1, 0.2, 0.3))
-        o = O.splat_render(x, op, A, col, co)
-        compare((rgb[y0:y0 + 16, x0:x0 + 24], T[y0:y0 + 16, x0:x0 + 24]), o, share=0.98)
+        o = O.splat_render(x, op, A, col, co, near_rel=NEAR)
+        compare((rgb[y0:y0 + 16, x0:x0 + 24], T[y0:y0 + 16, x0:x0 + 24]), o)
 
 
 def test_camera_argument_errors(ctx):
@@ -136,3 +147,50 @@ def test_camera_argument_errors(ctx):
     cg.znear, cg.fx = 0.01, float("nan")
     with pytest.raises(F.FluidStepError):
         F.fs_splat_render(ctx.ctx, z, torch.ones(1, device="cuda"), torch.zeros(1, 9, device="cuda"), z, cg, rgb)
+
+
+def render_gpu_sh(ctx, x, op, A, sh, deg, cam):
+    dev = lambda a, k: torch.tensor(np.asarray(a, np.float32).reshape(-1, k), device="cuda").contiguous()
+    rgb = torch.full((cam.height, cam.width, 3), float("nan"), device="cuda")
+    T = torch.full((cam.height, cam.width), float("nan"), device="cuda")
+    shd = torch.tensor(np.asarray(sh, np.float32), device="cuda").contiguous()
+    F.fs_splat_render_sh(ctx.ctx, dev(x, 3), dev(op, 1).reshape(-1), dev(A, 9), shd, deg, cam, rgb, T)
+    torch.cuda.synchronize()
+    return rgb.cpu().numpy().astype(np.float64), T.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("deg", [1, 3])
+def test_view_dependent_colour_matches_oracle(ctx, deg):
+    """Spherical-harmonic colours of degree 1 and 3 (random coefficients), a
+    ragged image under a rotated and translated camera, against the oracle's
+    evaluation of the same basis; then the same scene from a camera on the other
+    side, where the colours change."""
+    th = 0.5
+    Ry = np.array([[np.cos(th), 0, np.sin(th)], [0, 1, 0], [-np.sin(th), 0, np.cos(th)]])
+    R, t = Ry, np.array([0.2, -0.1, 0.4])
+    x, op, A, _ = camera_space_scene(2500, 3, R, t)
+    rng = np.random.default_rng(9)
+    nb = (deg + 1) ** 2
+    sh = f32(rng.normal(0.0, 0.4, (x.shape[0], nb, 3)))
+    cg, co = cams(R, t, 70.0, 72.0, 51.3, 36.8, 101, 75)
+    g = render_gpu_sh(ctx, x, op, A, sh, deg, cg)
+    o = O.splat_render_sh(x, op, A, sh, deg, co, near_rel=NEAR)
+    compare(g, o)
+    # the camera turned half a turn about the y axis, on the far side of the scene
+    Rb = np.array([[-1.0, 0, 0], [0, 1, 0], [0, 0, -1.0]]) @ R
+    centre = -R.T @ t + 2 * (R.T @ np.array([0.0, 0.0, 2.75]))
+    tb = -Rb @ centre
+    cgb, cob = cams(Rb, tb, 70.0, 72.0, 51.3, 36.8, 101, 75)
+    gb = render_gpu_sh(ctx, x, op, A, sh, deg, cgb)
+    ob = O.splat_render_sh(x, op, A, sh, deg, cob, near_rel=NEAR)
+    compare(gb, ob)
+    assert np.abs(ob[0] - o[0][:, ::-1]).max() > 0.05   # not the mirror image: the colours turned
+
+
+def test_sh_degree_is_validated(ctx):
+    cg, _ = cams(np.eye(3), np.zeros(3), 40.0, 40.0, 20.0, 15.0, 40, 30)
+    z = torch.zeros(1, 3, device="cuda")
+    rgb = torch.zeros(30, 40, 3, device="cuda")
+    with pytest.raises((F.FluidStepError, ValueError)):
+        F.fs_splat_render_sh(ctx.ctx, z, torch.ones(1, device="cuda"), torch.zeros(1, 9, device="cuda"),
+                             torch.zeros(1, 25, 3, device="cuda"), 4, cg, rgb)
