@@ -334,9 +334,10 @@ def workload_config(a):
 def precond_compare(n, seeds=(0,)):
     """Projection of an unblurred N(0,1) MAC field (the stress right-hand side) on
     a union of 8 spheres at n^3, to relative residual 1e-6, with Jacobi, MIC(0),
-    the multigrid V-cycle and the shipped learned network (flexible CG): device
-    wall time of fs_project
-    (CUDA events, after one warm-up solve), iterations, true residual."""
+    the multigrid V-cycle, the shipped learned network alone, and the network
+    trained for the smoother role in front of one V-cycle (flexible CG; its layers
+    on mma.sync and on tcgen05): device wall time of fs_project (CUDA events,
+    after one warm-up solve), iterations, true residual, and the network's share."""
     import torch
     from paper_2503_00868_gb300 import fluidstep as F
     from paper_2503_00868_gb300 import train_precond as T
@@ -344,7 +345,8 @@ def precond_compare(n, seeds=(0,)):
     out = {"workload": f"projection of a divergent N(0,1) MAC field on a union of 8 spheres at {n}^3, "
                        "tol 1e-6, maxit 20000", "rows": []}
     pcs = (("jacobi", F.FS_PRECOND_JACOBI), ("mic0", F.FS_PRECOND_MIC0), ("mg", F.FS_PRECOND_MG),
-           ("learned", F.FS_PRECOND_LEARNED))
+           ("learned", F.FS_PRECOND_LEARNED), ("learned_mg", F.FS_PRECOND_LEARNED_MG),
+           ("learned_mg_tcgen05", F.FS_PRECOND_LEARNED_MG))
     for seed in seeds:
         types, info = W.sphere_union(n, n, n, seed)
         row = {"seed": seed, "occupancy": info["occupancy"]}
@@ -353,6 +355,9 @@ def precond_compare(n, seeds=(0,)):
             g.set_mask(types)
             if pc == F.FS_PRECOND_LEARNED:
                 F.fs_net_load(g.ctx, T.default_weights())
+            elif pc == F.FS_PRECOND_LEARNED_MG:
+                F.fs_net_load(g.ctx, T.role_weights("net_mg"))
+                F.fs_net_kernel(g.ctx, 1 if name.endswith("tcgen05") else 0)
             u0 = g.pack(W.random_mac(n, n, n, 500 + seed))
             ts = []
             for rep in range(2):
@@ -366,6 +371,19 @@ def precond_compare(n, seeds=(0,)):
                 ts.append(e0.elapsed_time(e1))
             row[name] = {"ms": round(ts[-1], 3), "iters": st["iters_p"], "true_relres": st["true_relres_p"],
                          "fallbacks": st["fallbacks"], "restarts": st["restarts_p"], "status": rc}
+            if pc in (F.FS_PRECOND_LEARNED, F.FS_PRECOND_LEARNED_MG):
+                # the network's applications in a third, profiled solve (every one timed):
+                # useful flops on the visited tiles over their time, against the bf16 peak
+                g.profile(1)
+                g.project(F.Mac(*(t.clone() for t in u0)))
+                na = g.profile_read().get("net_apply")
+                g.profile(0)
+                if na and na[0]:
+                    tfl = na[2] / (na[1] * 1e-3) / 1e12
+                    peak = (measured_peaks() or {}).get("bf16_tflops", 1900.0)
+                    row[name]["net"] = {"applies": na[0], "ms_per_apply": round(na[1] / na[0], 4),
+                                        "useful_tflop_per_apply": na[2] / na[0] / 1e12, "achieved_tflops": tfl,
+                                        "frac_of_bf16_peak": tfl / peak}
             g.close()
         # the recurrent convolutional solver with the shipped fitted kernel: a fixed
         # 100 sub-steps, so its true residual is reported rather than reached

@@ -410,6 +410,16 @@ int fs_net_read(fs_ctx *c, float *params_host, int count);
 /* z = Net(r) on liquid cells; r, z DEVICE cell arrays (library layout). */
 int fs_net_forward(fs_ctx *c, const float *r, float *z);
 
+/* The kernels of the network's inference layers on this context (the learned
+ * preconditioners and fs_net_forward; training always uses the first):
+ *   0: warp-level mma.sync m16n8k16 BF16 MMAs, operands staged by ldmatrix;
+ *   1: tcgen05.mma (M = 128 cells, N = 16 channels, K = 16 per 3x3x3 tap) with
+ *      the accumulators in tensor memory, read back by tcgen05.ld.
+ * Both compute the same sums (FP32 accumulation of BF16 products, in a different
+ * order). FS_EINVAL for another value; a bounded wait for the MMAs that runs out
+ * makes the next solve or fs_net_forward return FS_ETIMEOUT. */
+int fs_net_kernel(fs_ctx *c, int which);
+
 /* Training on one (b, q) pair with L_p q = b on the context's mask (DEVICE cell
  * arrays), for the role the context's precond selects. The loss is the relative
  * error that the preconditioner leaves, in the energy norm of the pressure

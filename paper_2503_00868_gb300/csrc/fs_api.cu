@@ -676,6 +676,14 @@ int fs_net_read(fs_ctx *c, float *params_host, int count)
     return net_read(c, params_host);
 }
 
+int fs_net_kernel(fs_ctx *c, int which)
+{
+    if (!c) return set_error(FS_EINVAL, "NULL context");
+    g_err[0] = 0;
+    if (which != 0 && which != 1) return set_error(FS_EINVAL, "which must be 0 (mma.sync) or 1 (tcgen05)");
+    return net_kernel(c, which);
+}
+
 int fs_net_forward(fs_ctx *c, const float *r, float *z)
 {
     int rc = need_mask(c);

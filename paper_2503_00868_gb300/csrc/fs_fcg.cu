@@ -296,7 +296,7 @@ int solve_pressure_fcg(fs_ctx *c, SolveScal *h, bool warm)
         }
         FS_CUDA(cudaGetLastError());
     }
-    return FS_OK;
+    return check_wait_error(c, "flexible CG");
 }
 
 }  // namespace fs

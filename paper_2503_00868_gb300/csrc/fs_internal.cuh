@@ -413,6 +413,8 @@ int net_alloc(fs_ctx *c, bool training);
 void net_free(fs_ctx *c);
 int net_load(fs_ctx *c, const float *params, int count, bool host);
 int net_read(fs_ctx *c, float *params_host);
+int net_kernel(fs_ctx *c, int which);  // fs_net.cu: inference layers, 0 mma.sync, 1 tcgen05
+int check_wait_error(fs_ctx *c, const char *what);  // fs_pcg.cu: bounded-wait errors of the last solve
 int net_apply(fs_ctx *c, const float *r, float *z);   // cell space
 int net_grad(fs_ctx *c, const float *b, const float *q, double *loss);  // public layout
 int net_adam(fs_ctx *c, double lr, double beta1, double beta2, double eps, int step, double gscale,

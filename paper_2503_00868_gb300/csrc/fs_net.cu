@@ -59,6 +59,10 @@ struct NetState {
     int *tlist;           // conv tiles sorted by distance to the liquid (0 .. 5 = farther)
     uint8_t *tdist;       // per conv tile: Chebyshev distance to the nearest liquid cell, capped at 5
     int tcount[6];        // tiles within distance d of the liquid
+    int *tlist_tc;        // tiles of the tensor-core layer (TC_M x TC_NY of one plane), sorted the same way
+    int tcount_tc[6];
+    int kernel;           // inference layers: 0 mma.sync (k_conv), 1 tcgen05 (k_conv_tc)
+    double last_flops;    // useful flops of the last inference, on the tiles it visited
     long long tlist_epoch;  // mask epoch the list was built for (-1: none)
     __nv_bfloat16 *wt;    // layers 2-4 backward-data: [3][27 tap][16 ci][16 co], tap flipped
     __nv_bfloat16 *act;   // [6][nC][16]: x (2 ch used), a1, a2, a3, a4, spare
@@ -250,6 +254,245 @@ __global__ void __launch_bounds__(256) k_conv(ConvArgs a)
             }
         }
     }
+}
+
+// ---- the same layer on the fifth-generation tensor cores (tcgen05, TMEM) ----------
+// Inference only. A tile is TC_NY = 2 rows of TC_M = 128 cells along x of one
+// plane; each row is one M = 128, N = 16 GEMM over K = 27 taps x 16 channels,
+// issued as 27 tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulators in TMEM,
+// one 16-column accumulator per row) by one thread. The input tile (3 planes x
+// TC_NY + 2 rows x TC_M + 2 cells, 16 channels) is staged in shared memory split
+// by channel half: region [plane][row][half][x][8 channels], so that a tap's A
+// operand is the same region read from a start shifted by the tap's offset, in
+// the canonical K-major layout without swizzling (8-row core matrices of 16 bytes
+// per row, 128 bytes apart along M; the second 8 channels TC_HALF bytes further
+// along K). The weights of a tap are [half][out channel][8 in channels], 512
+// bytes. The accumulators are read back with tcgen05.ld (warp w owns lanes 32w
+// .. 32w + 31, one cell each) for the bias, ReLU and bf16 store.
+//
+// The layout keeps every address inside the block's shared memory even if the
+// two descriptor strides were read the other way round (the whole operand spans
+// less than the allocation either way), and every wait on the MMA's completion
+// is bounded: on timeout the block records an error bit and stops.
+constexpr int TC_M = 128, TC_NY = 2, TC_XW = TC_M + 2, TC_ROWS = TC_NY + 2;
+constexpr int TC_HALF = TC_XW * 16;                          // 2080 bytes: one channel half of a row
+constexpr int TC_ROWB = 2 * TC_HALF;                         // 4160 bytes per (plane, row)
+constexpr int TC_A_BYTES = 3 * TC_ROWS * TC_ROWB;            // 49920
+constexpr int TC_B_BYTES = 27 * 512;                         // 13824
+constexpr int TC_A_SPAN = TC_A_BYTES + 16 * TC_HALF + 1024;  // bound of either stride reading
+constexpr size_t TC_SMEM = 1024 + (size_t)TC_A_SPAN + TC_B_BYTES;
+constexpr unsigned TC_SPIN = 1u << 24;
+constexpr unsigned ERR_TC = 8u;
+static_assert(TC_A_SPAN + TC_B_BYTES + 1024 <= 200 * 1024, "tcgen05 conv: shared memory");
+
+__device__ __forceinline__ uint32_t tc_smem(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
+// offsets in units of 16 bytes, descriptor version 1, no swizzling
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulate (bits 4-5 = 1), A and B
+// BF16 (bits 7-9 = 1, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at
+// bits 24-28
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(16 >> 3) << 17) |
+                              ((uint32_t)(TC_M >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(TC_IDESC), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ bool tc_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// 16 FP32 columns of the warp's lane quarter, one lane per thread
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 16; k++) v[k] = __uint_as_float(r[k]);
+}
+
+// tiles of the tensor-core layer: TC_M x TC_NY cells of one plane, index
+// (k * ntyc + ty) * ntxc + tx
+__device__ __forceinline__ void tc_tile(int tb, const Layout &L, int &i0, int &j0, int &k)
+{
+    const int ntxc = (L.nx + TC_M - 1) / TC_M, ntyc = (L.ny + TC_NY - 1) / TC_NY;
+    i0 = (tb % ntxc) * TC_M;
+    j0 = ((tb / ntxc) % ntyc) * TC_NY;
+    k = tb / (ntxc * ntyc);
+}
+
+template <int IN, int OUT>
+__global__ void __launch_bounds__(128) k_conv_tc(ConvArgs a, unsigned *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem_tc[];
+    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_tc) + 1023) & ~(uintptr_t)1023);
+    unsigned char *sa = base;                 // input tile, TC_A_BYTES (TC_A_SPAN reserved)
+    unsigned char *sb = base + TC_A_SPAN;     // weights, TC_B_BYTES
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int stop;
+    const Layout &L = a.L;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // weights: [tap][half][co][8 ci] from [tap][co][16 ci]
+    for (int e = tid; e < 27 * 16 * 2; e += blockDim.x) {
+        const int tap = e >> 5, co = (e >> 1) & 15, half = e & 1;
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(a.wts) + (tap * 16 + co) * 2 + half);
+        *reinterpret_cast<uint4 *>(sb + tap * 512 + half * 256 + co * 16) = v;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem(&tmem_base)),
+                     "r"(32)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc_smem(&mbar)), "r"(1) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        stop = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    float bv[16];
+#pragma unroll
+    for (int k = 0; k < 16; k++) bv[k] = 0.f;
+    if (OUT == OUT_RELU) {
+#pragma unroll
+        for (int k = 0; k < 16; k++) bv[k] = a.bias[k];
+    } else {
+        bv[0] = a.bias[0];
+    }
+    float sc = 1.f, inv = 0.f;
+    if (IN == IN_R || OUT == OUT_Z) {
+        sc = __uint_as_float(*a.smax);
+        inv = sc > 0.f ? 1.f / sc : 0.f;
+    }
+    const uint32_t sa_u = tc_smem(sa), sb_u = tc_smem(sb), bar_u = tc_smem(&mbar);
+    const int ntxc = (L.nx + TC_M - 1) / TC_M, ntyc = (L.ny + TC_NY - 1) / TC_NY;
+    const int total = a.tiles ? a.ntiles : ntxc * ntyc * L.nz;
+    uint32_t phase = 0;
+    for (int idx = blockIdx.x; idx < total; idx += gridDim.x) {
+        const int tb = a.tiles ? __ldg(a.tiles + idx) : idx;
+        int i0, j0, kz;
+        tc_tile(tb, L, i0, j0, kz);
+        // stage the input tile: plane kz - 1 + pz, row j0 - 1 + ry, cell i0 - 1 + x
+        for (int e = tid; e < 3 * TC_ROWS * TC_XW; e += blockDim.x) {
+            const int x = e % TC_XW, ry = (e / TC_XW) % TC_ROWS, pz = e / (TC_XW * TC_ROWS);
+            const int gi = i0 - 1 + x, gj = j0 - 1 + ry, gk = kz - 1 + pz;
+            uint4 h0 = make_uint4(0u, 0u, 0u, 0u), h1 = h0;
+            if (in_grid(L, gi, gj, gk)) {
+                const int t = cell_t(L, gi, gj, gk);
+                if (IN == IN_ACT) {
+                    h0 = __ldg(reinterpret_cast<const uint4 *>(a.in + (size_t)t * 16));
+                    h1 = __ldg(reinterpret_cast<const uint4 *>(a.in + (size_t)t * 16) + 1);
+                } else {
+                    const uint8_t f = a.cf[t];
+                    const __nv_bfloat162 xv = __floats2bfloat162_rn((f & CF_LIQ) ? a.r[t] * inv : 0.f, type_code(f));
+                    h0.x = *reinterpret_cast<const uint32_t *>(&xv);
+                }
+            }
+            unsigned char *row = sa + (pz * TC_ROWS + ry) * TC_ROWB + x * 16;
+            *reinterpret_cast<uint4 *>(row) = h0;
+            *reinterpret_cast<uint4 *>(row + TC_HALF) = h1;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+#pragma unroll 1
+            for (int yr = 0; yr < TC_NY; yr++) {
+#pragma unroll 1
+                for (int tap = 0; tap < 27; tap++) {
+                    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+                    const uint32_t aaddr = sa_u + (uint32_t)((dz * TC_ROWS + yr + dy) * TC_ROWB + dx * 16);
+                    tc_mma(tmem + (uint32_t)(16 * yr), tc_desc(aaddr, TC_HALF, 128), tc_desc(sb_u + tap * 512, 256, 128),
+                           tap > 0 ? 1u : 0u);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_u)
+                         : "memory");
+        }
+        // every thread waits for the MMAs (bounded)
+        bool ok = false;
+        for (unsigned n = 0; n < TC_SPIN && !ok; n++) ok = tc_try_wait(bar_u, phase);
+        if (!ok) {
+            if (lane == 0) atomicOr(err, ERR_TC);
+            stop = 1;
+        }
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (stop) break;
+        // epilogue: lane tid of row yr = cell (i0 + tid, j0 + yr, kz)
+#pragma unroll 1
+        for (int yr = 0; yr < TC_NY; yr++) {
+            float acc[16];
+            tc_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(16 * yr), acc);
+            const int gi = i0 + tid, gj = j0 + yr;
+            if (gi >= L.nx || gj >= L.ny) continue;
+            const size_t t = (size_t)cell_t(L, gi, gj, kz);
+            if (OUT == OUT_Z) {
+                const float yv = acc[0] + bv[0];
+                if (a.y) a.y[t] = yv;
+                if (a.z) a.z[t] = (a.cf[t] & CF_LIQ) ? sc * yv : 0.f;
+            } else {
+                uint32_t pk[8];
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(fmaxf(acc[2 * k] + bv[2 * k], 0.f),
+                                                                    fmaxf(acc[2 * k + 1] + bv[2 * k + 1], 0.f));
+                    pk[k] = *reinterpret_cast<const uint32_t *>(&b2);
+                }
+                uint4 *o = reinterpret_cast<uint4 *>(a.out + t * 16);
+                o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();  // TMEM read and the shared tile consumed before the next tile
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    if (stop) {  // the MMAs of a timed-out tile may still run: wait for them again (bounded) before freeing TMEM
+        bool ok = false;
+        for (unsigned n = 0; n < TC_SPIN && !ok; n++) ok = tc_try_wait(bar_u, phase ^ 1u);
+    }
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32) : "memory");
 }
 
 // Chebyshev distance from each conv tile (32 x 8 cells of one plane) to the
@@ -577,6 +820,11 @@ static int conv_tiles(const Layout &L) { return ((L.nx + NT_X - 1) / NT_X) * ((L
 template <int CIN, int COUT>
 static size_t wgrad_smem() { return ((size_t)NT_X * NT_Y * COUT + (size_t)TCELLS * CIN) * 4; }
 
+static int conv_tiles_tc(const Layout &L)
+{
+    return ((L.nx + TC_M - 1) / TC_M) * ((L.ny + TC_NY - 1) / TC_NY) * L.nz;
+}
+
 int net_alloc(fs_ctx *c, bool training)
 {
     if (c->net && (!training || net(c)->gact)) return FS_OK;
@@ -606,7 +854,8 @@ int net_alloc(fs_ctx *c, bool training)
         (rc = alloc((void **)&n->smax, 16)) || (rc = alloc((void **)&n->y, nC * 4)) ||
         (rc = alloc((void **)&n->wf1, 27 * 16 * 16 * 2)) || (rc = alloc((void **)&n->wf5, 27 * 16 * 16 * 2)) ||
         (rc = alloc((void **)&n->tdist, (size_t)conv_tiles(c->L))) ||
-        (rc = alloc((void **)&n->tlist, (size_t)conv_tiles(c->L) * sizeof(int))))
+        (rc = alloc((void **)&n->tlist, (size_t)conv_tiles(c->L) * sizeof(int))) ||
+        (rc = alloc((void **)&n->tlist_tc, (size_t)conv_tiles_tc(c->L) * sizeof(int))))
         return rc;
     // inference needs two activation buffers; training keeps all five layer inputs
     const int nact = training ? 6 : 2;
@@ -625,6 +874,12 @@ int net_alloc(fs_ctx *c, bool training)
         FS_CUDA(cudaFuncSetAttribute(k_conv<IN_ACT, OUT_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs));
         FS_CUDA(cudaFuncSetAttribute(k_conv<IN_ACT, OUT_Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs));
         FS_CUDA(cudaFuncSetAttribute(k_conv<IN_ACT, OUT_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, cs));
+        FS_CUDA(cudaFuncSetAttribute(k_conv_tc<IN_R, OUT_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)TC_SMEM));
+        FS_CUDA(cudaFuncSetAttribute(k_conv_tc<IN_ACT, OUT_RELU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)TC_SMEM));
+        FS_CUDA(cudaFuncSetAttribute(k_conv_tc<IN_ACT, OUT_Z>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)TC_SMEM));
         FS_CUDA(cudaFuncSetAttribute(k_wgrad<16, 16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)wgrad_smem<16, 16>()));
         FS_CUDA(cudaFuncSetAttribute(k_wgrad<16, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -641,7 +896,7 @@ void net_free(fs_ctx *c)
     NetState *n = net(c);
     if (!n) return;
     void *ptrs[] = {n->master, n->grad, n->m, n->v, n->w1f, n->w5f, n->wf, n->wt, n->act, n->gact,
-                    n->y, n->gy, n->smax, n->wf1, n->wf5, n->tdist, n->tlist};
+                    n->y, n->gy, n->smax, n->wf1, n->wf5, n->tdist, n->tlist, n->tlist_tc};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete n;
@@ -709,6 +964,28 @@ static int net_tile_list(fs_ctx *c)
         n->tcount[dd] = (int)list.size();
     }
     FS_CUDA(cudaMemcpy(n->tlist, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice));
+    // the tensor-core layer's tiles (TC_M x TC_NY of one plane, inside one row of
+    // conv tiles since NT_Y is a multiple of TC_NY): the distance of the nearest
+    // conv tile they overlap
+    const int ntx = (L.nx + NT_X - 1) / NT_X, nty = (L.ny + NT_Y - 1) / NT_Y;
+    const int ntxc = (L.nx + TC_M - 1) / TC_M, ntyc = (L.ny + TC_NY - 1) / TC_NY, ntc = conv_tiles_tc(L);
+    std::vector<uint8_t> dc((size_t)ntc, 5);
+    for (int t = 0; t < ntc; t++) {
+        const int i0 = (t % ntxc) * TC_M, j0 = ((t / ntxc) % ntyc) * TC_NY, k = t / (ntxc * ntyc);
+        const int ty = j0 / NT_Y;
+        uint8_t m = 5;
+        for (int tx = i0 / NT_X; tx <= std::min(ntx - 1, (i0 + TC_M - 1) / NT_X); tx++)
+            m = std::min(m, d[(size_t)((k * nty + ty) * ntx + tx)]);
+        dc[(size_t)t] = m;
+    }
+    std::vector<int> lc;
+    lc.reserve((size_t)ntc);
+    for (int dd = 0; dd <= 5; dd++) {
+        for (int t = 0; t < ntc; t++)
+            if (dc[(size_t)t] == dd) lc.push_back(t);
+        n->tcount_tc[dd] = (int)lc.size();
+    }
+    FS_CUDA(cudaMemcpy(n->tlist_tc, lc.data(), lc.size() * sizeof(int), cudaMemcpyHostToDevice));
     n->tlist_epoch = c->mask_epoch;
     return FS_OK;
 }
@@ -725,6 +1002,19 @@ static void conv_launch(fs_ctx *c, int in, int out, const ConvArgs &a, int tiles
         k_conv<IN_ACT, OUT_Z><<<g, 256, sm, c->stream>>>(a);
     else
         k_conv<IN_ACT, OUT_BWD><<<g, 256, sm, c->stream>>>(a);
+    c->n_launches += 1;
+}
+
+// The tensor-core layer: two blocks per SM (the shared tile and its margin).
+static void conv_launch_tc(fs_ctx *c, int in, int out, const ConvArgs &a, int tiles)
+{
+    const int g = std::max(1, std::min(tiles, c->num_sms * 2));
+    if (in == IN_R)
+        k_conv_tc<IN_R, OUT_RELU><<<g, 128, TC_SMEM, c->stream>>>(a, c->err_word);
+    else if (out == OUT_RELU)
+        k_conv_tc<IN_ACT, OUT_RELU><<<g, 128, TC_SMEM, c->stream>>>(a, c->err_word);
+    else
+        k_conv_tc<IN_ACT, OUT_Z><<<g, 128, TC_SMEM, c->stream>>>(a, c->err_word);
     c->n_launches += 1;
 }
 
@@ -746,11 +1036,20 @@ static int net_forward(fs_ctx *c, const float *r, float *z, float *y, bool keep)
     __nv_bfloat16 *A[6];
     for (int l = 0; l < 6; l++) A[l] = n->act + (keep ? (size_t)l : (size_t)(l & 1)) * nC * 16;
     const int all = conv_tiles(L);
-    auto tiles_for = [&](int layer) { return keep ? all : n->tcount[5 - layer]; };  // layer 1 .. 5
+    const bool tc = !keep && n->kernel == 1;  // inference on the tcgen05 layer
+    auto tiles_for = [&](int layer) {         // layer 1 .. 5
+        return keep ? all : (tc ? n->tcount_tc[5 - layer] : n->tcount[5 - layer]);
+    };
+    auto launch = [&](int in, int out, const ConvArgs &ca) {
+        if (tc)
+            conv_launch_tc(c, in, out, ca, ca.ntiles);
+        else
+            conv_launch(c, in, out, ca, ca.ntiles);
+    };
     ConvArgs a{};
     a.cf = c->cflag;
     a.smax = n->smax;
-    a.tiles = keep ? nullptr : n->tlist;
+    a.tiles = keep ? nullptr : (tc ? n->tlist_tc : n->tlist);
     a.L = L;
     // layer 1: input built from r; keep: x -> A[0], a1 -> A[1]
     a.r = r;
@@ -759,7 +1058,7 @@ static int net_forward(fs_ctx *c, const float *r, float *z, float *y, bool keep)
     a.xin = keep ? A[0] : nullptr;
     a.out = keep ? A[1] : A[0];
     a.ntiles = tiles_for(1);
-    conv_launch(c, IN_R, OUT_RELU, a, a.ntiles);
+    launch(IN_R, OUT_RELU, a);
     __nv_bfloat16 *cur = a.out;
     a.xin = nullptr;
     a.r = nullptr;
@@ -771,7 +1070,7 @@ static int net_forward(fs_ctx *c, const float *r, float *z, float *y, bool keep)
         a.bias = n->master + bias_off[l];
         a.out = nxt;
         a.ntiles = tiles_for(2 + l);
-        conv_launch(c, IN_ACT, OUT_RELU, a, a.ntiles);
+        launch(IN_ACT, OUT_RELU, a);
         cur = nxt;
     }
     a.in = cur;
@@ -781,8 +1080,13 @@ static int net_forward(fs_ctx *c, const float *r, float *z, float *y, bool keep)
     a.y = y;
     a.z = z;
     a.ntiles = tiles_for(5);
-    conv_launch(c, IN_ACT, OUT_Z, a, a.ntiles);
+    launch(IN_ACT, OUT_Z, a);
     FS_CUDA(cudaGetLastError());
+    // the useful flops of the layers, on the cells of the tiles they visit (both
+    // tilings hold 256 cells a tile): 2 x 27 x (2 x 16 + 3 x 16 x 16 + 16 x 1) per cell
+    n->last_flops = 0.0;
+    const double fl[5] = {2.0 * 27 * 2 * 16, 2.0 * 27 * 16 * 16, 2.0 * 27 * 16 * 16, 2.0 * 27 * 16 * 16, 2.0 * 27 * 16};
+    for (int l = 1; l <= 5; l++) n->last_flops += fl[l - 1] * 256.0 * (double)tiles_for(l);
     return FS_OK;
 }
 
@@ -792,8 +1096,16 @@ int net_apply(fs_ctx *c, const float *r, float *z)
     if (!n || !n->loaded) return set_error(FS_ESTATE, "the learned preconditioner has no network loaded");
     cudaEvent_t e0 = prof_mark(c);
     int rc = net_forward(c, r, z, nullptr, false);
-    prof_add(c, K_NET_APPLY, e0, prof_mark(c), 0.0);
+    prof_add(c, K_NET_APPLY, e0, prof_mark(c), n->last_flops);  // flops, not bytes: a tensor-core entry
     return rc;
+}
+
+int net_kernel(fs_ctx *c, int which)
+{
+    int rc = net_alloc(c, false);
+    if (rc) return rc;
+    net(c)->kernel = which;
+    return FS_OK;
 }
 
 // Forward + backward for one (b, q) pair (public-layout cell arrays); adds the

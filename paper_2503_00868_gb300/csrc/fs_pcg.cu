@@ -608,7 +608,7 @@ int zmarch_slots(const fs_ctx *c, bool face)
 
 // A bounded wait of a TMA-fed kernel or of the MIC(0) wavefront that ran out
 // leaves a bit in the error word.
-static int check_wait_error(fs_ctx *c, const char *what)
+int check_wait_error(fs_ctx *c, const char *what)
 {
     unsigned herr = 0;
     FS_CUDA(cudaMemcpyAsync(&herr, c->err_word, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
@@ -619,6 +619,8 @@ static int check_wait_error(fs_ctx *c, const char *what)
                          c->prm.spin_limit);
     }
     if (herr & ERR_TMA) return set_error(FS_ETIMEOUT, "%s: a wait for a tensor copy ran out", what);
+    if (herr & 8u)  // the bit of the tensor-core network layer
+        return set_error(FS_ETIMEOUT, "%s: a wait for the network's tensor-core MMAs ran out", what);
     return FS_OK;
 }
 
@@ -1139,6 +1141,7 @@ int precond_apply_public(fs_ctx *c, const float *r, float *z)
     const int bs = grid_blocks(c, L.S, TH);
     k_cell_in<<<bs, TH, 0, c->stream>>>(r, c->pr, c->cflag, L);
     c->n_launches += 1;
+    FS_CUDA(cudaMemsetAsync(c->err_word, 0, sizeof(unsigned), c->stream));
     if (c->prm.precond == FS_PRECOND_JACOBI) {
         k_jacobi<<<grid_blocks(c, L.nC, TH), TH, 0, c->stream>>>(c->pr, c->pz, c->cflag, L.nC);
         c->n_launches += 1;
@@ -1167,6 +1170,7 @@ int precond_apply_public(fs_ctx *c, const float *r, float *z)
         c->mic_ready = 0;  // the factor may be incomplete: refactor on the next use
         return set_error(FS_ETIMEOUT, "MIC(0) sweep: a wait on a predecessor tile ran out");
     }
+    if (herr & 8u) return set_error(FS_ETIMEOUT, "network: a wait for the tensor-core MMAs ran out");
     return FS_OK;
 }
 

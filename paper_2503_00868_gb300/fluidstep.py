@@ -109,6 +109,7 @@ _SIGS = {
     "fs_net_load": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int], C.c_int),
     "fs_net_read": ([C.c_void_p, C.c_void_p, C.c_int], C.c_int),
     "fs_net_forward": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "fs_net_kernel": ([C.c_void_p, C.c_int], C.c_int),
     "fs_net_grad": ([C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)], C.c_int),
     "fs_net_grad_read": ([C.c_void_p, C.c_void_p, C.c_int], C.c_int),
     "fs_net_adam": ([C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int],
@@ -424,6 +425,11 @@ def fs_net_read(ctx: int) -> np.ndarray:
 
 def fs_net_forward(ctx: int, r: torch.Tensor, z: torch.Tensor) -> None:
     _check(load().fs_net_forward(C.c_void_p(ctx), _cell(r), _cell(z)), (FS_OK,))
+
+
+def fs_net_kernel(ctx: int, which: int) -> None:
+    """Inference layers: 0 mma.sync, 1 tcgen05 (tensor memory)."""
+    _check(load().fs_net_kernel(C.c_void_p(ctx), int(which)), (FS_OK,))
 
 
 def fs_net_grad(ctx: int, b: torch.Tensor, q: torch.Tensor) -> float:
