@@ -476,8 +476,10 @@ def make_camera(R, t, fx, fy, cx, cy, width, height, znear=0.01, bg=(0.0, 0.0, 0
 def splat_render(x, opacity, A, color, cam, near_rel=None):
     """Front-to-back splatting (Sec. 3.2.1); returns rgb (h, w, 3) and transmittance
     (h, w). With near_rel, also a uint8 (h, w) mask of the pixels whose value turns
-    on a threshold decision within that relative distance (the 3-sigma cutoff, the
-    1/255 alpha floor, the 1e-4 transmittance floor, near-equal depths)."""
+    on a threshold decision within that relative distance, by enough to show (the
+    3-sigma cutoff and the 1/255 alpha floor where the Gaussian's share there
+    exceeds 2e-5, the 1e-4 transmittance floor, depths within 4e-6 of each
+    other)."""
     x, o, A, c = _f64(x), _f64(opacity), _f64(A), _f64(color)
     n = x.shape[0]
     rgb = np.zeros((cam.height, cam.width, 3))

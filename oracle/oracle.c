@@ -1701,10 +1701,12 @@ static void sh_colour(int degree, const or_camera *cam, const double xm[3], cons
 
 /* Front-to-back compositing as below; with `near` non-NULL, near[pixel] = 1 when
  * the pixel's value turns on a decision that an evaluation in single precision
- * could take the other way: a Gaussian whose md lies within rel of the 3-sigma
- * cutoff 9, an alpha within rel of 1/255, a transmittance within rel of the
- * 1e-4 floor, or two contributing Gaussians whose depths differ by less than
- * rel times the depth (but are not equal). The flags change no value. */
+ * could take the other way, by enough to show: a Gaussian whose md lies within
+ * rel of the 3-sigma cutoff 9, or whose alpha lies within rel of 1/255, while
+ * its contribution at the threshold times the transmittance exceeds 2e-5; a
+ * transmittance within rel of the 1e-4 floor; or two contributing Gaussians whose
+ * depths differ (but are not equal) by less than 4e-6 of the depth, a few
+ * single-precision roundings. The flags change no value. */
 static void splat_render_impl(int n, const double *x, const double *opacity, const double *A, const double *color,
                               const or_camera *cam, double *rgb, double *T_out, unsigned char *near, double rel);
 
@@ -1756,16 +1758,19 @@ static void splat_render_impl(int n, const double *x, const double *opacity, con
                 int i = keys[q].idx;
                 double dx = pu - mean[2 * i], dy = pv - mean[2 * i + 1];
                 double md = conic[3 * i] * dx * dx + 2.0 * conic[3 * i + 1] * dx * dy + conic[3 * i + 2] * dy * dy;
-                if (near && fabs(md - 9.0) < rel * 9.0) flag = 1;
+                if (near && fabs(md - 9.0) < rel * 9.0) {
+                    double a_cut = opacity[i] * exp(-4.5);
+                    if ((a_cut > 0.99 ? 0.99 : a_cut) * T > 2e-5) flag = 1;
+                }
                 if (md > 9.0) continue;
                 double alpha = opacity[i] * exp(-0.5 * md);
                 if (alpha > 0.99) alpha = 0.99;
-                if (near && fabs(alpha * 255.0 - 1.0) < rel) flag = 1;
+                if (near && fabs(alpha * 255.0 - 1.0) < rel && T / 255.0 > 2e-5) flag = 1;
                 if (alpha < 1.0 / 255.0) continue;
                 double Tn = T * (1.0 - alpha);
                 if (near && fabs(Tn * 1e4 - 1.0) < rel) flag = 1;
                 if (Tn < 1e-4) break;
-                if (near && last_depth >= 0.0 && depth[i] != last_depth && depth[i] - last_depth < rel * depth[i])
+                if (near && last_depth >= 0.0 && depth[i] != last_depth && depth[i] - last_depth < 4e-6 * depth[i])
                     flag = 1;
                 for (int k = 0; k < 3; k++) c[k] += alpha * T * color[3 * i + k];
                 T = Tn;

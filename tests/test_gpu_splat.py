@@ -8,8 +8,10 @@ The GPU projects in FP32 and the oracle in FP64, so a pixel whose Mahalanobis
 distance sits on the 3-sigma cutoff, whose alpha sits on 1/255, whose
 transmittance sits on the 1e-4 floor, or whose contributors have nearly equal
 depths can fall on the other side of that decision. The oracle flags exactly
-those pixels (a relative distance of 1e-3 to the threshold); every other pixel
-must agree to 1e-4 in colour and transmittance, with no allowance. A flagged
+those pixels (a relative distance of 1e-3 to a threshold, where the Gaussian's
+share there could move the pixel by more than 2e-5; depths within 4e-6 of each
+other); every other pixel must agree to 1e-4 in colour and transmittance, with
+no allowance. A flagged
 pixel may move by one flip (at most about exp(-4.5) ~ 0.011 at the cutoff,
 times a colour <= 1; a reordering of near-equal depths by the difference of two
 contributions) and is bounded by 0.05; flagged pixels stay a small share."""
@@ -58,7 +60,7 @@ def render_gpu(ctx, x, op, A, col, cam):
 NEAR = 1e-3   # relative distance to a threshold under which the oracle flags a pixel
 
 
-def compare(g, o, tol=1e-4, worst=0.05, flagged_share=0.5):
+def compare(g, o, tol=1e-4, worst=0.05, flagged_share=0.25):
     """o = (rgb, T, near) from the oracle with near_rel = NEAR"""
     d = np.maximum(np.abs(g[0] - o[0]).max(-1), np.abs(g[1] - o[1]))
     near = o[2].astype(bool)
