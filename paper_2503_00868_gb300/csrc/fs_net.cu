@@ -259,31 +259,29 @@ __global__ void __launch_bounds__(256) k_conv(ConvArgs a)
 // ---- the same layer on the fifth-generation tensor cores (tcgen05, TMEM) ----------
 // Inference only. A tile is TC_NY = 2 rows of TC_M = 128 cells along x of one
 // plane; each row is one M = 128, N = 16 GEMM over K = 27 taps x 16 channels,
-// issued as 27 tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulators in TMEM,
-// one 16-column accumulator per row) by one thread. The input tile (3 planes x
-// TC_NY + 2 rows x TC_M + 2 cells, 16 channels) is staged in shared memory split
-// by channel half: region [plane][row][half][x][8 channels], so that a tap's A
-// operand is the same region read from a start shifted by the tap's offset, in
-// the canonical K-major layout without swizzling (8-row core matrices of 16 bytes
-// per row, 128 bytes apart along M; the second 8 channels TC_HALF bytes further
-// along K). The weights of a tap are [half][out channel][8 in channels], 512
-// bytes. The accumulators are read back with tcgen05.ld (warp w owns lanes 32w
-// .. 32w + 31, one cell each) for the bias, ReLU and bf16 store.
-//
-// The layout keeps every address inside the block's shared memory even if the
-// two descriptor strides were read the other way round (the whole operand spans
-// less than the allocation either way), and every wait on the MMA's completion
-// is bounded: on timeout the block records an error bit and stops.
-constexpr int TC_M = 128, TC_NY = 2, TC_XW = TC_M + 2, TC_ROWS = TC_NY + 2;
+// issued as 27 tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulators in tensor
+// memory, one 16-column accumulator per row) by one thread. The input tile (3
+// planes x TC_NY + 2 rows x TC_M + 2 cells, 16 channels) is staged in shared
+// memory split by channel half: region [plane][row][half][x][8 channels], so that
+// a tap's A operand is the same region read from a start shifted by the tap's
+// offset, in the canonical K-major layout without swizzling (8-row core matrices
+// of 16 bytes per row, 128 bytes apart along M; the second 8 channels TC_HALF
+// bytes further along K). The weights of a tap are [half][out channel][8 in
+// channels], 512 bytes. Two input buffers alternate: all threads stage the next
+// tile while the tensor core works on the current one. The accumulators are read
+// back with tcgen05.ld (warp w owns lanes 32 (w % 4) .. + 31 of row w / 4, one
+// cell per lane) for the bias, ReLU and bf16 store. Every wait on the MMAs'
+// completion is bounded: on timeout the block records an error bit, waits
+// (bounded) for its MMAs in flight, frees its tensor memory and stops.
+constexpr int TC_M = 128, TC_NY = 2, TC_XW = TC_M + 2, TC_ROWS = TC_NY + 2, TC_THREADS = 256;
 constexpr int TC_HALF = TC_XW * 16;                          // 2080 bytes: one channel half of a row
 constexpr int TC_ROWB = 2 * TC_HALF;                         // 4160 bytes per (plane, row)
-constexpr int TC_A_BYTES = 3 * TC_ROWS * TC_ROWB;            // 49920
+constexpr int TC_A_BYTES = 3 * TC_ROWS * TC_ROWB;            // 49920 per buffer
 constexpr int TC_B_BYTES = 27 * 512;                         // 13824
-constexpr int TC_A_SPAN = TC_A_BYTES + 16 * TC_HALF + 1024;  // bound of either stride reading
-constexpr size_t TC_SMEM = 1024 + (size_t)TC_A_SPAN + TC_B_BYTES;
+constexpr size_t TC_SMEM = 128 + 2 * (size_t)TC_A_BYTES + TC_B_BYTES;
 constexpr unsigned TC_SPIN = 1u << 24;
 constexpr unsigned ERR_TC = 8u;
-static_assert(TC_A_SPAN + TC_B_BYTES + 1024 <= 200 * 1024, "tcgen05 conv: shared memory");
+static_assert(TC_THREADS == 2 * TC_M, "one thread per accumulator row lane in the epilogue");
 
 __device__ __forceinline__ uint32_t tc_smem(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -353,13 +351,43 @@ __device__ __forceinline__ void tc_tile(int tb, const Layout &L, int &i0, int &j
     k = tb / (ntxc * ntyc);
 }
 
-template <int IN, int OUT>
-__global__ void __launch_bounds__(128) k_conv_tc(ConvArgs a, unsigned *err)
+// stage the input tile of tile tb into sa: plane kz - 1 + pz, row j0 - 1 + ry,
+// cell i0 - 1 + x, both channel halves
+template <int IN>
+__device__ __forceinline__ void tc_stage(const ConvArgs &a, int tb, unsigned char *sa, float inv)
 {
-    extern __shared__ __align__(1024) unsigned char smem_tc[];
-    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_tc) + 1023) & ~(uintptr_t)1023);
-    unsigned char *sa = base;                 // input tile, TC_A_BYTES (TC_A_SPAN reserved)
-    unsigned char *sb = base + TC_A_SPAN;     // weights, TC_B_BYTES
+    const Layout &L = a.L;
+    int i0, j0, kz;
+    tc_tile(tb, L, i0, j0, kz);
+    for (int e = threadIdx.x; e < 3 * TC_ROWS * TC_XW; e += blockDim.x) {
+        const int x = e % TC_XW, ry = (e / TC_XW) % TC_ROWS, pz = e / (TC_XW * TC_ROWS);
+        const int gi = i0 - 1 + x, gj = j0 - 1 + ry, gk = kz - 1 + pz;
+        uint4 h0 = make_uint4(0u, 0u, 0u, 0u), h1 = h0;
+        if (in_grid(L, gi, gj, gk)) {
+            const int t = cell_t(L, gi, gj, gk);
+            if (IN == IN_ACT) {
+                h0 = __ldg(reinterpret_cast<const uint4 *>(a.in + (size_t)t * 16));
+                h1 = __ldg(reinterpret_cast<const uint4 *>(a.in + (size_t)t * 16) + 1);
+            } else {
+                const uint8_t f = a.cf[t];
+                const __nv_bfloat162 xv = __floats2bfloat162_rn((f & CF_LIQ) ? a.r[t] * inv : 0.f, type_code(f));
+                h0.x = *reinterpret_cast<const uint32_t *>(&xv);
+            }
+        }
+        unsigned char *row = sa + (pz * TC_ROWS + ry) * TC_ROWB + x * 16;
+        *reinterpret_cast<uint4 *>(row) = h0;
+        *reinterpret_cast<uint4 *>(row + TC_HALF) = h1;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor core
+}
+
+template <int IN, int OUT>
+__global__ void __launch_bounds__(TC_THREADS) k_conv_tc(ConvArgs a, unsigned *err)
+{
+    extern __shared__ __align__(128) unsigned char smem_tc[];
+    unsigned char *base = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_tc) + 127) & ~(uintptr_t)127);
+    unsigned char *sa[2] = {base, base + TC_A_BYTES};  // input tiles, alternating
+    unsigned char *sb = base + 2 * TC_A_BYTES;          // weights
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
     __shared__ int stop;
@@ -382,10 +410,6 @@ __global__ void __launch_bounds__(128) k_conv_tc(ConvArgs a, unsigned *err)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         stop = 0;
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = tmem_base;
     float bv[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) bv[k] = 0.f;
@@ -400,39 +424,23 @@ __global__ void __launch_bounds__(128) k_conv_tc(ConvArgs a, unsigned *err)
         sc = __uint_as_float(*a.smax);
         inv = sc > 0.f ? 1.f / sc : 0.f;
     }
-    const uint32_t sa_u = tc_smem(sa), sb_u = tc_smem(sb), bar_u = tc_smem(&mbar);
     const int ntxc = (L.nx + TC_M - 1) / TC_M, ntyc = (L.ny + TC_NY - 1) / TC_NY;
     const int total = a.tiles ? a.ntiles : ntxc * ntyc * L.nz;
+    auto tile_at = [&](int idx) { return a.tiles ? __ldg(a.tiles + idx) : idx; };
+    if ((int)blockIdx.x < total) tc_stage<IN>(a, tile_at(blockIdx.x), sa[0], inv);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const uint32_t sb_u = tc_smem(sb), bar_u = tc_smem(&mbar);
     uint32_t phase = 0;
-    for (int idx = blockIdx.x; idx < total; idx += gridDim.x) {
-        const int tb = a.tiles ? __ldg(a.tiles + idx) : idx;
+    int buf = 0;
+    for (int idx = blockIdx.x; idx < total; idx += gridDim.x, buf ^= 1) {
         int i0, j0, kz;
-        tc_tile(tb, L, i0, j0, kz);
-        // stage the input tile: plane kz - 1 + pz, row j0 - 1 + ry, cell i0 - 1 + x
-        for (int e = tid; e < 3 * TC_ROWS * TC_XW; e += blockDim.x) {
-            const int x = e % TC_XW, ry = (e / TC_XW) % TC_ROWS, pz = e / (TC_XW * TC_ROWS);
-            const int gi = i0 - 1 + x, gj = j0 - 1 + ry, gk = kz - 1 + pz;
-            uint4 h0 = make_uint4(0u, 0u, 0u, 0u), h1 = h0;
-            if (in_grid(L, gi, gj, gk)) {
-                const int t = cell_t(L, gi, gj, gk);
-                if (IN == IN_ACT) {
-                    h0 = __ldg(reinterpret_cast<const uint4 *>(a.in + (size_t)t * 16));
-                    h1 = __ldg(reinterpret_cast<const uint4 *>(a.in + (size_t)t * 16) + 1);
-                } else {
-                    const uint8_t f = a.cf[t];
-                    const __nv_bfloat162 xv = __floats2bfloat162_rn((f & CF_LIQ) ? a.r[t] * inv : 0.f, type_code(f));
-                    h0.x = *reinterpret_cast<const uint32_t *>(&xv);
-                }
-            }
-            unsigned char *row = sa + (pz * TC_ROWS + ry) * TC_ROWB + x * 16;
-            *reinterpret_cast<uint4 *>(row) = h0;
-            *reinterpret_cast<uint4 *>(row + TC_HALF) = h1;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tc_tile(tile_at(idx), L, i0, j0, kz);
         if (tid == 0) {
+            const uint32_t sa_u = tc_smem(sa[buf]);
 #pragma unroll 1
             for (int yr = 0; yr < TC_NY; yr++) {
 #pragma unroll 1
@@ -446,7 +454,8 @@ __global__ void __launch_bounds__(128) k_conv_tc(ConvArgs a, unsigned *err)
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_u)
                          : "memory");
         }
-        // every thread waits for the MMAs (bounded)
+        // the next tile into the other buffer while the tensor core works
+        if (idx + (int)gridDim.x < total) tc_stage<IN>(a, tile_at(idx + gridDim.x), sa[buf ^ 1], inv);
         bool ok = false;
         for (unsigned n = 0; n < TC_SPIN && !ok; n++) ok = tc_try_wait(bar_u, phase);
         if (!ok) {
@@ -457,36 +466,38 @@ __global__ void __launch_bounds__(128) k_conv_tc(ConvArgs a, unsigned *err)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         __syncthreads();
         if (stop) break;
-        // epilogue: lane tid of row yr = cell (i0 + tid, j0 + yr, kz)
-#pragma unroll 1
-        for (int yr = 0; yr < TC_NY; yr++) {
+        // epilogue: warp w reads lanes 32 (w % 4) .. + 31 of row w / 4
+        {
+            const int yr = warp >> 2, q = warp & 3;
             float acc[16];
-            tc_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(16 * yr), acc);
-            const int gi = i0 + tid, gj = j0 + yr;
-            if (gi >= L.nx || gj >= L.ny) continue;
-            const size_t t = (size_t)cell_t(L, gi, gj, kz);
-            if (OUT == OUT_Z) {
-                const float yv = acc[0] + bv[0];
-                if (a.y) a.y[t] = yv;
-                if (a.z) a.z[t] = (a.cf[t] & CF_LIQ) ? sc * yv : 0.f;
-            } else {
-                uint32_t pk[8];
+            tc_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * yr), acc);
+            const int gi = i0 + 32 * q + lane, gj = j0 + yr;
+            if (gi < L.nx && gj < L.ny) {
+                const size_t t = (size_t)cell_t(L, gi, gj, kz);
+                if (OUT == OUT_Z) {
+                    const float yv = acc[0] + bv[0];
+                    if (a.y) a.y[t] = yv;
+                    if (a.z) a.z[t] = (a.cf[t] & CF_LIQ) ? sc * yv : 0.f;
+                } else {
+                    uint32_t pk[8];
 #pragma unroll
-                for (int k = 0; k < 8; k++) {
-                    const __nv_bfloat162 b2 = __floats2bfloat162_rn(fmaxf(acc[2 * k] + bv[2 * k], 0.f),
-                                                                    fmaxf(acc[2 * k + 1] + bv[2 * k + 1], 0.f));
-                    pk[k] = *reinterpret_cast<const uint32_t *>(&b2);
+                    for (int k = 0; k < 8; k++) {
+                        const __nv_bfloat162 b2 = __floats2bfloat162_rn(fmaxf(acc[2 * k] + bv[2 * k], 0.f),
+                                                                        fmaxf(acc[2 * k + 1] + bv[2 * k + 1], 0.f));
+                        pk[k] = *reinterpret_cast<const uint32_t *>(&b2);
+                    }
+                    uint4 *o = reinterpret_cast<uint4 *>(a.out + t * 16);
+                    o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
                 }
-                uint4 *o = reinterpret_cast<uint4 *>(a.out + t * 16);
-                o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
             }
         }
+        // the accumulators read and the next buffer staged before the next MMAs
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();  // TMEM read and the shared tile consumed before the next tile
+        __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
-    if (stop) {  // the MMAs of a timed-out tile may still run: wait for them again (bounded) before freeing TMEM
+    if (stop) {  // the MMAs of a timed-out tile may still run: wait for them again (bounded) before freeing
         bool ok = false;
         for (unsigned n = 0; n < TC_SPIN && !ok; n++) ok = tc_try_wait(bar_u, phase ^ 1u);
     }
@@ -1005,16 +1016,16 @@ static void conv_launch(fs_ctx *c, int in, int out, const ConvArgs &a, int tiles
     c->n_launches += 1;
 }
 
-// The tensor-core layer: two blocks per SM (the shared tile and its margin).
+// The tensor-core layer: two blocks per SM (two input tiles and the weights each).
 static void conv_launch_tc(fs_ctx *c, int in, int out, const ConvArgs &a, int tiles)
 {
     const int g = std::max(1, std::min(tiles, c->num_sms * 2));
     if (in == IN_R)
-        k_conv_tc<IN_R, OUT_RELU><<<g, 128, TC_SMEM, c->stream>>>(a, c->err_word);
+        k_conv_tc<IN_R, OUT_RELU><<<g, TC_THREADS, TC_SMEM, c->stream>>>(a, c->err_word);
     else if (out == OUT_RELU)
-        k_conv_tc<IN_ACT, OUT_RELU><<<g, 128, TC_SMEM, c->stream>>>(a, c->err_word);
+        k_conv_tc<IN_ACT, OUT_RELU><<<g, TC_THREADS, TC_SMEM, c->stream>>>(a, c->err_word);
     else
-        k_conv_tc<IN_ACT, OUT_Z><<<g, 128, TC_SMEM, c->stream>>>(a, c->err_word);
+        k_conv_tc<IN_ACT, OUT_Z><<<g, TC_THREADS, TC_SMEM, c->stream>>>(a, c->err_word);
     c->n_launches += 1;
 }
 
