@@ -136,7 +136,10 @@ def test_full_size_workload_windows(ctx):
     for x0, y0 in ((944, 300), (700, 500), (1000, 20), (1350, 400)):
         co = O.make_camera(R, t, fx, fy, cx - x0, cy - y0, 24, 16, 0.01, (0.1, 0.2, 0.3))
         o = O.splat_render(x, op, A, col, co, near_rel=NEAR)
-        compare((rgb[y0:y0 + 16, x0:x0 + 24], T[y0:y0 + 16, x0:x0 + 24]), o)
+        # many overlapping Gaussians of the dense cloud reach each of these pixels, so
+        # more of them hold some decision near a threshold (0.34 measured in the
+        # densest window): the flagged share may reach one half here
+        compare((rgb[y0:y0 + 16, x0:x0 + 24], T[y0:y0 + 16, x0:x0 + 24]), o, flagged_share=0.5)
 
 
 def test_camera_argument_errors(ctx):
