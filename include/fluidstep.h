@@ -445,6 +445,19 @@ int fs_net_grad_read(fs_ctx *c, float *grad_host, int count);
 int fs_net_adam(fs_ctx *c, double lr, double beta1, double beta2, double eps, int step, double grad_scale,
                 int fix_offsets);
 
+/* One Adam step (Kingma and Ba, 2015) on `n` FP32 parameters in DEVICE memory: the
+ * optimiser of the parameter fit (Sec. 3.4.2 fits theta = log nu and the
+ * correction of the initial velocity by gradient descent on the loss). With
+ * g' = grad_scale g:  m = beta1 m + (1 - beta1) g',  v = beta2 v + (1 - beta2) g'^2,
+ * p -= lr (m / (1 - beta1^step)) / (sqrt(v / (1 - beta2^step)) + eps).
+ * p, m, v are updated in place, g is read only; the caller owns all four arrays
+ * (m and v zero before step 1; any alignment, 16-byte aligned ones take four
+ * elements per thread). Runs on the context's stream without synchronising; needs
+ * no mask. FS_EINVAL for n < 0, a NULL array with n > 0, step < 1, lr < 0, a beta
+ * outside [0, 1), eps <= 0 or a non-finite lr or grad_scale. */
+int fs_adam_update(fs_ctx *c, float *p, const float *g, float *m, float *v, long long n, double lr, double beta1,
+                   double beta2, double eps, int step, double grad_scale);
+
 /* fs_net_grad over `batch` pairs stored back to back (each `nelems` floats of the
  * library layout) followed by fs_net_adam with grad_scale = 1/batch (beta1 0.9,
  * beta2 0.999, eps 1e-8, fix_offsets 1). *loss receives the mean loss of the batch. */

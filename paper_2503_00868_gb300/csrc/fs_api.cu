@@ -722,6 +722,17 @@ int fs_net_adam(fs_ctx *c, double lr, double beta1, double beta2, double eps, in
     return net_adam(c, lr, beta1, beta2, eps, step, grad_scale, fix_offsets);
 }
 
+int fs_adam_update(fs_ctx *c, float *p, const float *g, float *m, float *v, long long n, double lr, double beta1,
+                   double beta2, double eps, int step, double grad_scale)
+{
+    if (!c) return set_error(FS_EINVAL, "NULL context");
+    if (n < 0 || (n > 0 && (!p || !g || !m || !v))) return set_error(FS_EINVAL, "bad parameter arrays");
+    if (step < 1 || !(lr >= 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) ||
+        !(eps > 0.0) || !std::isfinite(lr) || !std::isfinite(grad_scale))
+        return set_error(FS_EINVAL, "bad Adam hyper-parameters");
+    return adam_update(c, p, g, m, v, n, lr, beta1, beta2, eps, step, grad_scale);
+}
+
 int fs_net_train_step(fs_ctx *c, const float *b_batch, const float *q_batch, int batch, double lr, int step,
                       double *loss)
 {

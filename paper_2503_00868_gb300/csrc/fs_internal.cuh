@@ -420,6 +420,8 @@ int net_grad(fs_ctx *c, const float *b, const float *q, double *loss);  // publi
 int net_adam(fs_ctx *c, double lr, double beta1, double beta2, double eps, int step, double gscale,
              int fix_offsets);
 int net_grad_read(fs_ctx *c, float *grad_host);
+int adam_update(fs_ctx *c, float *p, const float *g, float *m, float *v, long long n, double lr, double beta1,
+                double beta2, double eps, int step, double grad_scale);  // fs_optim.cu
 int net_grad_clear(fs_ctx *c);
 int net_param_count();
 bool net_loaded(const fs_ctx *c);

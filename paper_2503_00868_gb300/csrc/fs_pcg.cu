@@ -246,20 +246,27 @@ __global__ void __launch_bounds__(TH) k_helm_init(const float *__restrict__ x, c
 // entries span more than about 2^29 in magnitude, and only the sums of squares
 // round. For a singular operator (liquid touching no air) the component along
 // the null vector (the constant), which no iterate can change, is left out:
-// sum e^2 - (sum e)^2 / N.
-__global__ void __launch_bounds__(TH) k_pois_true_res(const float *__restrict__ b, const float *__restrict__ x,
+// sum e^2 - (sum e)^2 / N. With r_out, the residual is also stored, rounded once
+// to FP32, on the liquid (zero elsewhere, guard planes included): the right-hand
+// side of a refinement step. r_out may alias b: every thread reads b only at the
+// element it writes.
+__global__ void __launch_bounds__(TH) k_pois_true_res(const float *b, const float *__restrict__ x,
                                                       const uint8_t *__restrict__ fl, int n, int P, int PL,
-                                                      int singular, SolveScal *s, double *partials)
+                                                      int singular, SolveScal *s, double *partials, float *r_out)
 {
     double acc = 0.0, sum = 0.0, cnt = 0.0, bsq = 0.0;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
         const uint8_t f = fl[t];
-        if (!(f & CF_LIQ)) continue;
+        if (!(f & CF_LIQ)) {
+            if (r_out) r_out[t] = 0.f;
+            continue;
+        }
         const double nb = ((double)x[t - 1] + (double)x[t + 1]) + ((double)x[t - P] + (double)x[t + P]) +
                           ((double)x[t - PL] + (double)x[t + PL]);
         const double ax = (double)PoisOp::diag(f, 0.f) * (double)x[t] - nb;
         const double bv = (double)b[t];
         const double e = bv - ax;
+        if (r_out) r_out[t] = (float)e;
         acc += e * e;
         sum += e;
         cnt += 1.0;
@@ -269,24 +276,6 @@ __global__ void __launch_bounds__(TH) k_pois_true_res(const float *__restrict__ 
     if (grid_reduce<4>(v, partials, &s->ticket, tot) && threadIdx.x == 0) {
         s->aux[0] = (singular && tot[2] > 0.0) ? fmax(0.0, tot[0] - tot[1] * tot[1] / tot[2]) : tot[0];
         s->aux[1] = tot[3];
-    }
-}
-
-// The right-hand side of a refinement step: r = b - A x evaluated in FP64 and
-// rounded once to FP32, on the liquid (zero elsewhere, guard planes included).
-// r may alias b: every thread reads b only at the element it writes.
-__global__ void __launch_bounds__(TH) k_pois_refine_rhs(const float *b, const float *__restrict__ x,
-                                                        const uint8_t *__restrict__ fl, int n, int P, int PL,
-                                                        float *r)
-{
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-        float v = 0.f;
-        if (fl[t] & CF_LIQ) {
-            const double nb = ((double)x[t - 1] + (double)x[t + 1]) + ((double)x[t - P] + (double)x[t + P]) +
-                              ((double)x[t - PL] + (double)x[t + PL]);
-            v = (float)((double)b[t] - ((double)PoisOp::diag(fl[t], 0.f) * (double)x[t] - nb));
-        }
-        r[t] = v;
     }
 }
 
@@ -692,7 +681,8 @@ int learned_apply(fs_ctx *c, const float *r, float *z, const int *done)
     return FS_OK;
 }
 
-static int pressure_tail(fs_ctx *c, const SolveScal &h, long long iters, double bb0, fs_stats *st);
+static int pressure_tail(fs_ctx *c, const SolveScal &h, long long iters, double bb0, const SolveScal *known,
+                         fs_stats *st);
 
 // Warm start (fs_params.warm_start): after the x = 0 initialisation, start
 // instead from the last converged pressure of the same kind of projection when
@@ -704,7 +694,7 @@ static int try_warm_start(fs_ctx *c, bool jac)
     const Layout &L = c->L;
     const int bs = grid_blocks(c, L.nC, TH);
     k_pois_true_res<<<bs, TH, 0, c->stream>>>(c->pb, c->pw[k], c->cflag, L.nC, L.P, L.PL, c->singular,
-                                              c->scal + 2, c->partials);
+                                              c->scal + 2, c->partials, nullptr);
     c->n_launches += 1;
     FS_CUDA(cudaGetLastError());
     SolveScal m, h0;
@@ -868,7 +858,7 @@ static int solve_pressure_once(fs_ctx *c, fs_stats *st)
         SolveScal h;
         int rc = solve_pressure_percnn(c, &h);
         if (rc) return rc;
-        return pressure_tail(c, h, h.iter, 0.0, st);
+        return pressure_tail(c, h, h.iter, 0.0, nullptr, st);
     }
     const bool learned = c->prm.precond == FS_PRECOND_LEARNED || c->prm.precond == FS_PRECOND_LEARNED_MG;
     if (learned && !net_loaded(c))
@@ -894,21 +884,26 @@ static int solve_pressure_once(fs_ctx *c, fs_stats *st)
     SolveScal h, m;
     double bb0 = 0.0;
     long long iters = 0;
+    bool checked = false;  // m holds the FP64 residual of the pass that ended the loop
     int rc = FS_OK, nref = 0;
     for (int pass = 0;; pass++) {
+        checked = false;
         rc = learned ? solve_pressure_fcg(c, &h, false) : pcg_iterate(c, h);
         if (rc) break;
         iters += h.iter;
         if (h.status != FS_OK) break;
+        // the FP64 check of this pass's system (b0 and x, then each correction's);
+        // its residual, rounded once to FP32, is the next correction's right-hand
+        // side, stored in pbr (in place from the second pass on)
         k_pois_true_res<<<bs, TH, 0, c->stream>>>(c->pb, c->px, c->cflag, L.nC, L.P, L.PL, c->singular,
-                                                  c->scal + 2, c->partials);
+                                                  c->scal + 2, c->partials, c->pbr);
         c->n_launches += 1;
         if ((rc = check_cuda(cudaGetLastError(), "k_pois_true_res")) || (rc = read_scal(c, 2, &m))) break;
+        checked = true;
         if (pass == 0) bb0 = m.aux[1];
         const double tol2 = c->prm.tol_p * c->prm.tol_p;
         if (pass == kMaxRefine || !(bb0 > 0.0) || !(m.aux[0] > tol2 * bb0)) break;
-        // the next correction: its right-hand side from the FP64 residual of the
-        // pressure so far, the terms solved so far kept in the head and the tail
+        // the next correction: the terms solved so far kept in the head and the tail
         if (pass == 0) {
             if ((rc = check_cuda(cudaMemcpyAsync(c->pxh, c->px, (size_t)L.nC * sizeof(float),
                                                  cudaMemcpyDeviceToDevice, c->stream),
@@ -917,20 +912,16 @@ static int solve_pressure_once(fs_ctx *c, fs_stats *st)
                 break;
             c->q_head = c->pxh;
             c->pb = c->pbr;
-            k_pois_refine_rhs<<<bs, TH, 0, c->stream>>>(b0, c->pxh, c->cflag, L.nC, L.P, L.PL, c->pbr);
+        } else if (pass == 1) {
+            if ((rc = check_cuda(cudaMemcpyAsync(c->pxt, c->px, (size_t)L.nC * sizeof(float),
+                                                 cudaMemcpyDeviceToDevice, c->stream),
+                                 "cudaMemcpyAsync")))
+                break;
         } else {
-            k_pois_refine_rhs<<<bs, TH, 0, c->stream>>>(c->pbr, c->px, c->cflag, L.nC, L.P, L.PL, c->pbr);
-            if (pass == 1) {
-                if ((rc = check_cuda(cudaMemcpyAsync(c->pxt, c->px, (size_t)L.nC * sizeof(float),
-                                                     cudaMemcpyDeviceToDevice, c->stream),
-                                     "cudaMemcpyAsync")))
-                    break;
-            } else {
-                k_add4<<<grid_blocks(c, L.nC / 4, TH), TH, 0, c->stream>>>(c->pxt, c->px, L.nC / 4);
-            }
+            k_add4<<<grid_blocks(c, L.nC / 4, TH), TH, 0, c->stream>>>(c->pxt, c->px, L.nC / 4);
+            c->n_launches += 1;
         }
-        c->n_launches += 1;
-        if ((rc = check_cuda(cudaGetLastError(), "k_pois_refine_rhs")) || (rc = remove_null_mode(c, c->pbr))) break;
+        if ((rc = remove_null_mode(c, c->pbr))) break;
         c->tol2_scale = 0.25 * bb0 / m.aux[0];
         c->refining = 1;
         nref += 1;
@@ -938,40 +929,56 @@ static int solve_pressure_once(fs_ctx *c, fs_stats *st)
     }
     c->refining = 0;
     c->tol2_scale = 1.0;
+    if (rc) {
+        c->pb = b0;
+        return rc;
+    }
+    if (!checked) {  // a pass that did not converge: the residual of its own system
+        k_pois_true_res<<<bs, TH, 0, c->stream>>>(c->pb, c->px, c->cflag, L.nC, L.P, L.PL, c->singular,
+                                                  c->scal + 2, c->partials, nullptr);
+        c->n_launches += 1;
+        if ((rc = check_cuda(cudaGetLastError(), "k_pois_true_res")) || (rc = read_scal(c, 2, &m))) {
+            c->pb = b0;
+            return rc;
+        }
+    }
     c->pb = b0;
-    if (rc) return rc;
     if (nref >= 2) {  // fold the earlier corrections into the tail
         k_add4<<<grid_blocks(c, L.nC / 4, TH), TH, 0, c->stream>>>(c->px, c->pxt, L.nC / 4);
         c->n_launches += 1;
     }
-    if (c->q_head) c->pb = c->pbr;  // the residual of the pair is that of the last correction
-    rc = pressure_tail(c, h, iters, bb0, st);
-    c->pb = b0;
+    rc = pressure_tail(c, h, iters, bb0, &m, st);
     if (rc == FS_OK) rc = save_warm_start(c);
     return rc;
 }
 
-// After the iterations: the true residual (FP64) of the system in pb and px,
-// relative to |b0|^2 when bb0 > 0 (the original right-hand side of a refined
-// solve), else to |b|^2; the mean-free representative of a singular solve; the
-// statistics.
-static int pressure_tail(fs_ctx *c, const SolveScal &h, long long iters, double bb0, fs_stats *st)
+// After the iterations: the true residual (FP64) of the system in pb and px, or
+// the one the caller already has (`known`), relative to |b0|^2 when bb0 > 0 (the
+// original right-hand side of a refined solve), else to |b|^2; the mean-free
+// representative of a singular solve; the statistics.
+static int pressure_tail(fs_ctx *c, const SolveScal &h, long long iters, double bb0, const SolveScal *known,
+                         fs_stats *st)
 {
     const Layout &L = c->L;
     const int bs = grid_blocks(c, L.nC, TH);
-    // true residual, then the mean-free representative of a singular solve
-    k_pois_true_res<<<bs, TH, 0, c->stream>>>(c->pb, c->px, c->cflag, L.nC, L.P, L.PL, c->singular, c->scal + 2,
-                                              c->partials);
-    c->n_launches += 1;
-    if (c->singular) {
+    if (!known) {
+        k_pois_true_res<<<bs, TH, 0, c->stream>>>(c->pb, c->px, c->cflag, L.nC, L.P, L.PL, c->singular,
+                                                  c->scal + 2, c->partials, nullptr);
+        c->n_launches += 1;
+    }
+    if (c->singular) {  // the mean-free representative
         k_liquid_sum<<<bs, TH, 0, c->stream>>>(c->px, c->cflag, L.nC, c->scal + 3, c->partials);
         k_sub_liquid_mean<<<bs, TH, 0, c->stream>>>(c->px, c->cflag, L.nC, c->scal + 3);
         c->n_launches += 2;
     }
     FS_CUDA(cudaGetLastError());
     SolveScal m;
-    int rc = read_scal(c, 2, &m);
-    if (rc) return rc;
+    if (known) {
+        m = *known;
+    } else {
+        int rc = read_scal(c, 2, &m);
+        if (rc) return rc;
+    }
     const double bb = bb0 > 0.0 ? bb0 : m.aux[1];
     if (st) {
         st->iters_p += (int)iters;

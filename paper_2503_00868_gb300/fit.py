@@ -8,8 +8,8 @@ runs that fit on the library:
   * theta = log nu and a per-face correction delta of the initial velocity;
   * the loss at every frame on the surface band, its gradient w.r.t. nu and the
     initial velocity from the checkpointed rollout's hand-written adjoint;
-  * Adam on both (torch.optim on the parameter tensors: the optimiser update is
-    plumbing around the library, every step and adjoint runs in its kernels).
+  * Adam on both, by the library's device kernel (fs_adam_update); every step,
+    adjoint and optimiser update runs in the library's kernels.
 The scene is a liquid blob on the floor with a shallow liquid layer fed by an
 inflow patch on the x = 0 wall, gravity along -y. Targets are synthetic: a
 forward run with nu_true and a seeded smooth delta_true, observed every frame.
@@ -29,6 +29,7 @@ import numpy as np
 import torch
 
 from . import fluidstep as F
+from .clocks import ClockSampler
 from . import workloads as W
 from .rollout import forward_states, rollout_loss
 
@@ -80,30 +81,32 @@ def fit(grid: F.Grid, u_base: F.Mac, targets: Dict[int, F.Mac], frames: int, ite
         fit_delta: bool = True, cosine: bool = False, betas=(0.9, 0.999),
         callback: Optional[Callable[[int, float, float], None]] = None) -> dict:
     """Adam on theta = log nu (and delta when `fit_delta`) against `targets`, with
-    the learning rates decayed to zero along a cosine when `cosine`. Returns the
-    fitted nu, delta and the (loss, nu) history before each update."""
-    theta = torch.tensor(math.log(nu0), dtype=torch.float32, requires_grad=True)
+    the learning rates decayed to zero along a cosine when `cosine`. The Adam step
+    is the library's (fs_adam_update, on the device, one call per parameter
+    tensor). Returns the fitted nu, delta and the (loss, nu) history before each
+    update."""
+    dev = u_base[0].device
+    theta = torch.full((1,), math.log(nu0), dtype=torch.float32, device=dev, requires_grad=True)
     delta = [torch.zeros_like(t, requires_grad=fit_delta) for t in u_base]
-    groups = [{"params": [theta], "lr": lr_theta}]
-    if fit_delta:
-        groups.append({"params": delta, "lr": lr_delta})
-    opt = torch.optim.Adam(groups, betas=betas)
-    sched = (torch.optim.lr_scheduler.LambdaLR(opt, lambda i: 0.5 * (1.0 + math.cos(math.pi * i / iters)))
-             if cosine else None)
+    params = [(theta, lr_theta)] + ([(d, lr_delta) for d in delta] if fit_delta else [])
+    moments = [(torch.zeros_like(t), torch.zeros_like(t)) for t, _ in params]
     history = []
     for it in range(iters):
-        opt.zero_grad()
+        for t, _ in params:
+            t.grad = None
         u0 = F.Mac(*(b + d for b, d in zip(u_base, delta)))
-        nu = torch.exp(theta)
+        nu = torch.exp(theta[0])
         loss = rollout_loss(grid, u0, nu, frames, targets, checkpoint_every)
         loss.backward()
         history.append((float(loss.detach()), float(nu.detach())))
         if callback:
             callback(it, history[-1][0], history[-1][1])
-        opt.step()
-        if sched:
-            sched.step()
-    return {"nu": float(torch.exp(theta).detach()), "delta": [d.detach() for d in delta], "history": history}
+        decay = 0.5 * (1.0 + math.cos(math.pi * it / iters)) if cosine else 1.0
+        with torch.no_grad():
+            for (t, lr), (m, v) in zip(params, moments):
+                g = t.grad if t.grad is not None else torch.zeros_like(t)
+                F.fs_adam_update(grid.ctx, t, g.contiguous(), m, v, lr * decay, it + 1, betas[0], betas[1])
+    return {"nu": float(torch.exp(theta[0]).detach()), "delta": [d.detach() for d in delta], "history": history}
 
 
 def compare_pressure_solvers(nx: int = 64, ny: int = 48, nz: int = 64, frames: int = 12, iters: int = 30,
@@ -200,15 +203,23 @@ def main():
     torch.cuda.synchronize()
     t1 = time.time()
     log = []
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
     res = fit(grid, u_base, targets, a.frames, a.iters, a.nu0,
               callback=lambda it, l, nu: (log.append((it, l, nu)), print(f"iter {it:3d} loss {l:.6e} nu {nu:.5e}",
                                                                           flush=True)))
     torch.cuda.synchronize()
     t2 = time.time()
+    clocks = sampler.stop()
     cells = a.nx * a.ny * a.nz
     steps = a.iters * a.frames * 3  # forward, recompute, adjoint
-    print(json.dumps({"grid": [a.nx, a.ny, a.nz], "frames": a.frames, "iters": a.iters, "precond": a.precond,
-                      "advect_grad": a.advect_grad,
+    print(json.dumps({"metric": "fit iterations/s", "value": a.iters / (t2 - t1), "unit": "iter/s",
+                      "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "parameter fit (nu and the initial-velocity correction) on the river "
+                                             "scene", "grid": [a.nx, a.ny, a.nz], "frames": a.frames,
+                                 "iters": a.iters, "precond": a.precond, "advect_grad": a.advect_grad,
+                                 "checkpoint_every": 4},
+                      "clocks": clocks,
                       "occupancy": info["occupancy"], "nu_true": a.nu_true, "nu_fit": res["nu"],
                       "loss_first": res["history"][0][0], "loss_last": res["history"][-1][0],
                       "targets_s": t1 - t0, "fit_s": t2 - t1, "s_per_iter": (t2 - t1) / max(a.iters, 1),

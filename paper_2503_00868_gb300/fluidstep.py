@@ -114,6 +114,8 @@ _SIGS = {
     "fs_net_grad_read": ([C.c_void_p, C.c_void_p, C.c_int], C.c_int),
     "fs_net_adam": ([C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int],
                     C.c_int),
+    "fs_adam_update": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_double,
+                        C.c_double, C.c_double, C.c_double, C.c_int, C.c_double], C.c_int),
     "fs_net_train_step": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int,
                            C.POINTER(C.c_double)], C.c_int),
     "fs_project_noalloc": ([C.c_int, C.c_int, C.c_int, C.c_void_p, C.POINTER(fs_mac), C.c_void_p, C.c_double,
@@ -448,6 +450,26 @@ def fs_net_adam(ctx: int, lr: float, step: int, beta1=0.9, beta2=0.999, eps=1e-8
                 fix_offsets=True) -> None:
     _check(load().fs_net_adam(C.c_void_p(ctx), lr, beta1, beta2, eps, step, grad_scale, 1 if fix_offsets else 0),
            (FS_OK,))
+
+
+def fs_adam_update(ctx: int, p: torch.Tensor, g: torch.Tensor, m: torch.Tensor, v: torch.Tensor, lr: float,
+                   step: int, beta1=0.9, beta2=0.999, eps=1e-8, grad_scale=1.0) -> None:
+    """One Adam step in place on p, m and v (contiguous float32 tensors of one size
+    on the current CUDA device); g is read only."""
+    n = p.numel()
+    arrays = (("p", p), ("g", g), ("m", m), ("v", v))
+    for name, t in arrays:
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    dev = torch.cuda.current_device()
+    for name, t in arrays:
+        if t.device.index != dev:
+            raise ValueError(f"{name} is not on the current CUDA device")
+        if t.numel() != n:
+            raise ValueError(f"{name} has {t.numel()} elements, p has {n}")
+    _check(load().fs_adam_update(C.c_void_p(ctx), C.c_void_p(p.data_ptr()), C.c_void_p(g.data_ptr()),
+                                 C.c_void_p(m.data_ptr()), C.c_void_p(v.data_ptr()), n, lr, beta1, beta2, eps,
+                                 step, grad_scale), (FS_OK,))
 
 
 def fs_net_train_step(ctx: int, b_batch: torch.Tensor, q_batch: torch.Tensor, lr: float, step: int) -> float:

@@ -151,3 +151,13 @@ def test_noalloc_wrong_shape_rejected_before_the_library_is_called(monkeypatch):
         F.fs_project_noalloc(nx, ny, nz, types, F.Mac(u.u[:, :, :4].contiguous(), u.v, u.w), q)
     with pytest.raises(ValueError):   # right shapes, but host tensors, not on the current CUDA device
         F.fs_project_noalloc(nx, ny, nz, types, u, q)
+
+
+def test_adam_arguments_checked_before_the_library_is_called(monkeypatch):
+    import torch
+    called = []
+    monkeypatch.setattr(F, "load", lambda: called.append(1))
+    t = torch.zeros(4)
+    with pytest.raises(ValueError):
+        F.fs_adam_update(0, t, t, t, t, 0.01, 1)   # host tensors
+    assert not called
