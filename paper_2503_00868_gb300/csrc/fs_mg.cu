@@ -69,6 +69,10 @@ struct MgLevel {
     float mass = 0.f;   // identity term (1 for the Helmholtz operator)
     uint8_t *fl = nullptr;
     float *r = nullptr, *a = nullptr, *b = nullptr, *c = nullptr;  // right-hand side and three work arrays
+    int *ql = nullptr;  // active quads (every level but the coarsest)
+    int nqa = 0;
+    int *pl = nullptr;  // active restriction pairs of this level as the coarse one (levels >= 1)
+    int npa = 0;
 };
 
 struct MgState {
@@ -143,44 +147,63 @@ __device__ __forceinline__ float sweep1(uint8_t f, float c, float nb, float rv, 
     return liq(f) ? c + wt[f & CF_D] * (rv - m * c - scale * ((float)(f & CF_D) * c - nb)) : 0.f;
 }
 
-__global__ void __launch_bounds__(256) k_mg0_smooth(MgGrid g, const uint8_t *__restrict__ fl,
-                                                    const float *__restrict__ r, const float *__restrict__ ein,
-                                                    float *eout, float scale, float m, int dense, const int *done)
+// The kernels below walk a level's list of active quads (those holding an
+// unknown, built with the hierarchy), each thread striding through it with the
+// next entry fetched one step ahead: no flag load stands between a thread and its
+// data loads, and the quads without an unknown cost nothing.
+#define MG_FOR_LIST(list, na)                                                                            \
+    for (int mg_i = blockIdx.x * blockDim.x + threadIdx.x, mg_st = gridDim.x * blockDim.x,               \
+             q = mg_i < (na) ? __ldg((list) + mg_i) : 0, mg_next = 0;                                    \
+         mg_i < (na) && ((mg_next = mg_i + mg_st < (na) ? __ldg((list) + mg_i + mg_st) : 0), true);     \
+         mg_i += mg_st, q = mg_next)
+
+// one damped Jacobi sweep on quad q: eout from ein
+__device__ __forceinline__ void smooth_q(const MgGrid &g, const uint8_t *__restrict__ fl, const float *__restrict__ r,
+                                         const float *__restrict__ ein, float *eout, const float *wt, float scale,
+                                         float m, int q)
+{
+    const int t = q << 2;
+    const uchar4 f = ldf4(fl, t);
+    const float4 c = ld4g(ein, t), rv = ld4g(r, t);
+    const float4 dn = ld4g(ein, t - g.sy), up = ld4g(ein, t + g.sy);
+    const float4 bk = ld4g(ein, t - g.sz), fw = ld4g(ein, t + g.sz);
+    const float lf = __ldg(ein + t - 1), rt = __ldg(ein + t + 4);
+    float4 v;
+    v.x = sweep1(f.x, c.x, (lf + c.y) + (dn.x + up.x) + (bk.x + fw.x), rv.x, wt, scale, m);
+    v.y = sweep1(f.y, c.y, (c.x + c.z) + (dn.y + up.y) + (bk.y + fw.y), rv.y, wt, scale, m);
+    v.z = sweep1(f.z, c.z, (c.y + c.w) + (dn.z + up.z) + (bk.z + fw.z), rv.z, wt, scale, m);
+    v.w = sweep1(f.w, c.w, (c.z + rt) + (dn.w + up.w) + (bk.w + fw.w), rv.w, wt, scale, m);
+    *reinterpret_cast<float4 *>(eout + t) = v;
+}
+
+// One sweep over the active quads. With `dense` (the level-0 output, the solver's
+// z), the quads without an unknown are written with zeros too, in a second loop
+// over the whole array that reads the flags only.
+__global__ void __launch_bounds__(256) k_mg0_smooth(MgGrid g, const int *__restrict__ qlist, int na,
+                                                    const uint8_t *__restrict__ fl, const float *__restrict__ r,
+                                                    const float *__restrict__ ein, float *eout, float scale, float m,
+                                                    int dense, const int *done)
 {
     if (done && *(volatile const int *)done) return;  // the solve has converged
     __shared__ float wt[8];
     fill_wtab(wt, scale, m);
+    MG_FOR_LIST(qlist, na) smooth_q(g, fl, r, ein, eout, wt, scale, m, q);
+    if (!dense) return;
     const int nq = g.n >> 2;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
-        const int t = q << 2;
-        const uchar4 f = ldf4(fl, t);
-        if (!any_liq(f)) {
-            if (dense) *reinterpret_cast<float4 *>(eout + t) = make_float4(0.f, 0.f, 0.f, 0.f);
-            continue;
-        }
-        const float4 c = ld4g(ein, t), rv = ld4g(r, t);
-        const float4 dn = ld4g(ein, t - g.sy), up = ld4g(ein, t + g.sy);
-        const float4 bk = ld4g(ein, t - g.sz), fw = ld4g(ein, t + g.sz);
-        const float lf = __ldg(ein + t - 1), rt = __ldg(ein + t + 4);
-        float4 v;
-        v.x = sweep1(f.x, c.x, (lf + c.y) + (dn.x + up.x) + (bk.x + fw.x), rv.x, wt, scale, m);
-        v.y = sweep1(f.y, c.y, (c.x + c.z) + (dn.y + up.y) + (bk.y + fw.y), rv.y, wt, scale, m);
-        v.z = sweep1(f.z, c.z, (c.y + c.w) + (dn.z + up.z) + (bk.z + fw.z), rv.z, wt, scale, m);
-        v.w = sweep1(f.w, c.w, (c.z + rt) + (dn.w + up.w) + (bk.w + fw.w), rv.w, wt, scale, m);
-        *reinterpret_cast<float4 *>(eout + t) = v;
-    }
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x)
+        if (!any_liq(ldf4(fl, q << 2))) *reinterpret_cast<float4 *>(eout + (q << 2)) = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-__global__ void __launch_bounds__(256) k_mg0_residual(MgGrid g, const uint8_t *__restrict__ fl,
-                                                      const float *__restrict__ r, const float *__restrict__ ev,
-                                                      float *res, float scale, float m, const int *done)
+__global__ void __launch_bounds__(256) k_mg0_residual(MgGrid g, const int *__restrict__ qlist, int na,
+                                                      const uint8_t *__restrict__ fl, const float *__restrict__ r,
+                                                      const float *__restrict__ ev, float *res, float scale, float m,
+                                                      const int *done)
 {
     if (done && *(volatile const int *)done) return;  // the solve has converged
-    const int nq = g.n >> 2;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    MG_FOR_LIST(qlist, na)
+    {
         const int t = q << 2;
         const uchar4 f = ldf4(fl, t);
-        if (!any_liq(f)) continue;
         const float4 c = ld4g(ev, t), rv = ld4g(r, t);
         const float4 dn = ld4g(ev, t - g.sy), up = ld4g(ev, t + g.sy);
         const float4 bk = ld4g(ev, t - g.sz), fw = ld4g(ev, t + g.sz);
@@ -198,18 +221,17 @@ __global__ void __launch_bounds__(256) k_mg0_residual(MgGrid g, const uint8_t *_
 }
 
 // the first two sweeps from e = 0: e1 = omega D^-1 r on the fly, then one sweep
-__global__ void __launch_bounds__(256) k_mg0_smooth2(MgGrid g, const uint8_t *__restrict__ fl,
-                                                     const float *__restrict__ r, float *eo, float scale, float m,
-                                                     const int *done)
+__global__ void __launch_bounds__(256) k_mg0_smooth2(MgGrid g, const int *__restrict__ qlist, int na,
+                                                     const uint8_t *__restrict__ fl, const float *__restrict__ r,
+                                                     float *eo, float scale, float m, const int *done)
 {
     if (done && *(volatile const int *)done) return;  // the solve has converged
     __shared__ float wt[8];
     fill_wtab(wt, scale, m);
-    const int nq = g.n >> 2;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    MG_FOR_LIST(qlist, na)
+    {
         const int t = q << 2;
         const uchar4 f = ldf4(fl, t);
-        if (!any_liq(f)) continue;
         auto e1q = [&](int u) {  // e1 on the quad at u
             const uchar4 fu = ldf4(fl, u);
             const float4 ru = ld4g(r, u);
@@ -232,20 +254,20 @@ __global__ void __launch_bounds__(256) k_mg0_smooth2(MgGrid g, const uint8_t *__
     }
 }
 
-// e_fine += P e_coarse on the unknowns of a quad (in place). The quad's elements
-// i .. i + 3 (i a multiple of 4) take their x samples from coarse I0 - 1 .. I0 + 2
-// (I0 = i / 2); indices past the coarse halo are clamped to it (a sample that
-// only padding elements use).
-__global__ void __launch_bounds__(256) k_mg0_prolong(MgGrid gf, const uint8_t *__restrict__ fl, float *ef,
-                                                     MgGrid gc, const float *__restrict__ ec, const int *done)
+// e_fine += P e_coarse on the unknowns of an active quad (in place). The quad's
+// elements i .. i + 3 (i a multiple of 4) take their x samples from coarse
+// I0 - 1 .. I0 + 2 (I0 = i / 2); indices past the coarse halo are clamped to it
+// (a sample that only padding elements use).
+__global__ void __launch_bounds__(256) k_mg0_prolong(MgGrid gf, const int *__restrict__ qlist, int na,
+                                                     const uint8_t *__restrict__ fl, float *ef, MgGrid gc,
+                                                     const float *__restrict__ ec, const int *done)
 {
     if (done && *(volatile const int *)done) return;  // the solve has converged
-    const int nq = gf.n >> 2;
     const int qrow = gf.sy >> 2;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    MG_FOR_LIST(qlist, na)
+    {
         const int t = q << 2;
         const uchar4 f = ldf4(fl, t);
-        if (!any_liq(f)) continue;
         const int row = q / qrow, e = (q - row * qrow) << 2;
         const int i = e - gf.ioff, j = row % gf.rpp - gf.joff, k = row / gf.rpp - gf.koff;
         const int I0 = i >> 1, J = j >> 1, K = k >> 1;
@@ -276,25 +298,24 @@ __global__ void __launch_bounds__(256) k_mg0_prolong(MgGrid gf, const uint8_t *_
     }
 }
 
-// Restriction from a quad-aligned level: one thread per pair of coarse cells
-// (2m, 2m + 1) of an interior coarse row. Per fine row of the 4 x 4 window it reads the aligned
+// Restriction from a quad-aligned level over the coarse level's list of active
+// pairs: entry t0 is the element of coarse cell (2m, J, K), and the pair (2m,
+// 2m + 1) holds at least one unknown. Per fine row of the 4 x 4 window it reads the aligned
 // quad 4m .. 4m + 3 and the scalars at 4m - 1 and 4m + 4 (excluded at or past nx,
 // where the next row begins), and forms both cells' x weights from them.
 __global__ void __launch_bounds__(256) k_mg0_restrict(MgGrid gf, const float *__restrict__ res, MgGrid gc,
+                                                      const int *__restrict__ plist, int np,
                                                       const uint8_t *__restrict__ flc, float *rc, const int *done)
 {
     if (done && *(volatile const int *)done) return;  // the solve has converged
-    const int npair = (gc.nx + 1) >> 1;
-    const long long items = (long long)npair * gc.ny * gc.nz;
     const float w[4] = {0.25f, 0.75f, 0.75f, 0.25f};
-    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < items;
-         it += (long long)gridDim.x * blockDim.x) {
-        const int m = (int)(it % npair);
-        const long long jk = it / npair;
-        const int J = (int)(jk % gc.ny), K = (int)(jk / gc.ny);
-        const int I0 = 2 * m, t0 = gc.idx(I0, J, K);
+    MG_FOR_LIST(plist, np)
+    {
+        const int t0 = q;
+        const int rel = t0 - gc.origin;
+        const int K = rel / gc.sz, J = (rel - K * gc.sz) / gc.sy, I0 = rel - K * gc.sz - J * gc.sy;
+        const int m = I0 >> 1;
         const bool l0 = liq(flc[t0]), l1 = I0 + 1 < gc.nx && liq(flc[t0 + 1]);
-        if (!l0 && !l1) continue;
         float a0 = 0.f, a1 = 0.f;
         for (int c = 0; c < 4; c++) {
             const int k = 2 * K - 1 + c;
@@ -314,6 +335,62 @@ __global__ void __launch_bounds__(256) k_mg0_restrict(MgGrid gf, const float *__
         }
         if (l0) rc[t0] = 0.125f * a0;
         if (l1) rc[t0 + 1] = 0.125f * a1;
+    }
+}
+
+// ---- lists of the active quads and restriction pairs ------------------------------
+
+// Appends, in warp order, the indices of the items for which `keep` holds: one
+// atomic per warp. The list's order follows the scheduling of the warps, which
+// changes nothing computed (every item is independent).
+__device__ __forceinline__ void warp_append(bool keep, int item, int *list, int *count)
+{
+    const unsigned lane = threadIdx.x & 31, act = __activemask();
+    const unsigned bal = __ballot_sync(act, keep);
+    if (!bal) return;
+    const int leader = __ffs(act) - 1;
+    int base = 0;
+    if ((int)lane == leader) base = atomicAdd(count, __popc(bal));
+    base = __shfl_sync(act, base, leader);
+    if (keep) list[base + __popc(bal & ((1u << lane) - 1u))] = item;
+}
+
+// quads of a level with an unknown (count only when list is null)
+__global__ void k_mg_list_quads(MgGrid g, const uint8_t *__restrict__ fl, int *list, int *count)
+{
+    const int nq = g.n >> 2;
+    const int n32 = (nq + 31) & ~31;  // whole warps take part in the ballot
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n32; q += gridDim.x * blockDim.x) {
+        const bool keep = q < nq && any_liq(ldf4(fl, q << 2));
+        if (list)
+            warp_append(keep, q, list, count);
+        else if (keep)
+            atomicAdd(count, 1);
+    }
+}
+
+// restriction pairs of a coarse level with an unknown: the element of the pair's
+// first cell (count only when list is null)
+__global__ void k_mg_list_pairs(MgGrid gc, const uint8_t *__restrict__ flc, int *list, int *count)
+{
+    const int npair = (gc.nx + 1) >> 1;
+    const long long items = (long long)npair * gc.ny * gc.nz;
+    const long long i32 = (items + 31) & ~31ll;
+    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < i32;
+         it += (long long)gridDim.x * blockDim.x) {
+        bool keep = false;
+        int t0 = 0;
+        if (it < items) {
+            const int m = (int)(it % npair);
+            const long long jk = it / npair;
+            const int J = (int)(jk % gc.ny), K = (int)(jk / gc.ny);
+            t0 = gc.idx(2 * m, J, K);
+            keep = liq(flc[t0]) || (2 * m + 1 < gc.nx && liq(flc[t0 + 1]));
+        }
+        if (list)
+            warp_append(keep, t0, list, count);
+        else if (keep)
+            atomicAdd(count, 1);
     }
 }
 
@@ -451,6 +528,12 @@ MgGrid coarse_grid(int nx, int ny, int nz)
 
 void free_levels(MgState *s)
 {
+    for (int l = 0; l < s->nlev; l++) {
+        cudaFree(s->lev[l].ql);
+        cudaFree(s->lev[l].pl);
+        s->lev[l].ql = s->lev[l].pl = nullptr;
+        s->lev[l].nqa = s->lev[l].npa = 0;
+    }
     for (int l = 1; l < s->nlev; l++) {
         MgLevel &v = s->lev[l];
         cudaFree(v.fl);
@@ -495,30 +578,31 @@ int vcycle(fs_ctx *c, MgState *s, int l, bool sample, cudaStream_t st)
         if (timed) prof_add(c, kind, e0, prof_mark(c), bytes);
     };
     // four elements per thread: every level but the coarsest has quad-aligned rows
-    const int nq = grid_blocks(c, g.n / 4, TH);
+    const int dense = l == 0 ? 1 : 0;
+    const int nb = grid_blocks(c, v.nqa, TH);                    // the active quads
+    const int nbz = grid_blocks(c, dense ? g.n / 4 : v.nqa, TH);  // and all quads for the dense sweep
     MgLevel &w = s->lev[l + 1];
     begin();
-    k_mg0_smooth2<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.b, v.scale, v.mass, done);
+    k_mg0_smooth2<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.b, v.scale, v.mass, done);
     end(K_MG0_SMOOTH2, s->by0[0]);
     begin();
-    k_mg0_residual<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, done);
+    k_mg0_residual<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.b, v.c, v.scale, v.mass, done);
     end(K_MG0_RESIDUAL, s->by0[1]);
     begin();
-    k_mg0_restrict<<<grid_blocks(c, (long long)((w.g.nx + 1) / 2) * w.g.ny * w.g.nz, TH), TH, 0, st>>>(
-        g, v.c, w.g, w.fl, w.r, done);
+    k_mg0_restrict<<<grid_blocks(c, w.npa, TH), TH, 0, st>>>(g, v.c, w.g, w.pl, w.npa, w.fl, w.r, done);
     end(K_MG0_RESTRICT, s->by0[2]);
     c->n_launches += 3;
     begin();
     if (int rc = vcycle(c, s, l + 1, false, st)) return rc;
     end(K_MG_COARSE, 0.0);
     begin();
-    k_mg0_prolong<<<nq, TH, 0, st>>>(g, v.fl, v.b, w.g, w.a, done);
+    k_mg0_prolong<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.b, w.g, w.a, done);
     end(K_MG0_PROLONG, s->by0[3]);
     begin();
-    k_mg0_smooth<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.b, v.c, v.scale, v.mass, 0, done);
+    k_mg0_smooth<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.b, v.c, v.scale, v.mass, 0, done);
     end(K_MG0_SMOOTH, s->by0[4]);
     begin();
-    k_mg0_smooth<<<nq, TH, 0, st>>>(g, v.fl, v.r, v.c, v.a, v.scale, v.mass, l == 0 ? 1 : 0, done);
+    k_mg0_smooth<<<nbz, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.c, v.a, v.scale, v.mass, dense, done);
     end(K_MG0_SMOOTH_Z, s->by0[5]);
     c->n_launches += 3;
     FS_CUDA(cudaGetLastError());
@@ -580,10 +664,53 @@ int mg_build(fs_ctx *c, MgState *s, const MgGrid &g0, uint8_t *fl0, float *b0, f
         if (g.sy % 4 || g.sz % 4 || g.origin % 4 || g.n % 4)
             return set_error(FS_EINVAL, "multigrid: level %d rows are not quad-aligned", l);
     }
-    // The least each level-0 kernel must move (its algorithmic bytes): the flag
-    // byte of every element it scans, 4 bytes per unknown for each vector it reads
-    // or writes on the unknowns, and the whole of a vector it writes densely.
-    // n0, n1: elements of levels 0 and 1; u0, u1: their unknowns.
+    // the lists of active quads (every level but the coarsest) and of active
+    // restriction pairs (every level but the finest): counted, allocated, filled
+    int *icnt = reinterpret_cast<int *>(c->partials);
+    auto make_list = [&](bool pairs, int l, int **list, int *count) -> int {
+        const MgGrid &g = s->lev[l].g;
+        const long long items = pairs ? (long long)((g.nx + 1) >> 1) * g.ny * g.nz : g.n / 4;
+        const int blocks = grid_blocks(c, items, TH);
+        for (int pass = 0; pass < 2; pass++) {
+            FS_CUDA(cudaMemsetAsync(icnt, 0, sizeof(int), c->stream));
+            if (pairs)
+                k_mg_list_pairs<<<blocks, TH, 0, c->stream>>>(g, s->lev[l].fl, pass ? *list : nullptr, icnt);
+            else
+                k_mg_list_quads<<<blocks, TH, 0, c->stream>>>(g, s->lev[l].fl, pass ? *list : nullptr, icnt);
+            c->n_launches += 1;
+            FS_CUDA(cudaGetLastError());
+            int n = 0;
+            FS_CUDA(cudaMemcpyAsync(&n, icnt, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+            FS_CUDA(cudaStreamSynchronize(c->stream));
+            if (pass == 0) {
+                *count = n;
+                if (cudaMalloc(list, sizeof(int) * (size_t)std::max(n, 1)) != cudaSuccess) {
+                    *list = nullptr;
+                    return FS_ENOMEM;
+                }
+            } else if (n != *count) {
+                return set_error(FS_ECUDA, "multigrid: active lists of level %d disagree", l);
+            }
+        }
+        return FS_OK;
+    };
+    for (int l = 0; l < s->nlev; l++) {
+        MgLevel &v = s->lev[l];
+        int rc = FS_OK;
+        if (l + 1 < s->nlev) rc = make_list(false, l, &v.ql, &v.nqa);
+        if (!rc && l >= 1) rc = make_list(true, l, &v.pl, &v.npa);
+        if (rc == FS_ENOMEM) return fail("active lists");
+        if (rc) {
+            free_levels(s);
+            return rc;
+        }
+    }
+    // The least each level-0 kernel must move (its algorithmic bytes): the list
+    // entry and the flags of each active quad (or pair) it visits, every flag byte
+    // of an array it scans whole, 4 bytes per unknown for each vector it reads or
+    // writes on the unknowns, and the whole of a vector it writes densely.
+    // n0: elements of level 0; q0: its active quads; p1: level 1's active pairs;
+    // u0, u1: the unknowns of levels 0 and 1.
     unsigned long long *cnt = reinterpret_cast<unsigned long long *>(c->partials), nl[2] = {0, 0};
     FS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(nl), c->stream));
     k_mg_count_liq<<<grid_blocks(c, g0.n, TH), TH, 0, c->stream>>>(g0, fl0, cnt);
@@ -591,14 +718,14 @@ int mg_build(fs_ctx *c, MgState *s, const MgGrid &g0, uint8_t *fl0, float *b0, f
         k_mg_count_liq<<<grid_blocks(c, s->lev[1].g.n, TH), TH, 0, c->stream>>>(s->lev[1].g, s->lev[1].fl, cnt + 1);
     FS_CUDA(cudaMemcpyAsync(nl, cnt, sizeof(nl), cudaMemcpyDeviceToHost, c->stream));
     FS_CUDA(cudaStreamSynchronize(c->stream));
-    const double n0 = (double)g0.n, u0 = (double)nl[0];
-    const double n1 = s->nlev > 1 ? (double)s->lev[1].g.n : 0.0, u1 = (double)nl[1];
-    s->by0[0] = n0 + 8.0 * u0;             // smooth2: read r, write e
-    s->by0[1] = n0 + 12.0 * u0;            // residual: read r, e, write res
-    s->by0[2] = 4.0 * u0 + n1 + 4.0 * u1;  // restrict: read res; level-1 flags, write its r
-    s->by0[3] = n0 + 8.0 * u0 + 4.0 * u1;  // prolong: read and write e, read the level-1 e
-    s->by0[4] = n0 + 12.0 * u0;            // smooth: read r, e, write e
-    s->by0[5] = n0 + 8.0 * u0 + 4.0 * n0;  // last smooth: read r, e, write z on every element
+    const double n0 = (double)g0.n, u0 = (double)nl[0], u1 = (double)nl[1];
+    const double q0 = (double)s->lev[0].nqa, p1 = s->nlev > 1 ? (double)s->lev[1].npa : 0.0;
+    s->by0[0] = 8.0 * q0 + 8.0 * u0;             // smooth2: read r, write e
+    s->by0[1] = 8.0 * q0 + 12.0 * u0;            // residual: read r, e, write res
+    s->by0[2] = 6.0 * p1 + 4.0 * u0 + 4.0 * u1;  // restrict: pair list and flags, read res, write level-1 r
+    s->by0[3] = 8.0 * q0 + 8.0 * u0 + 4.0 * u1;  // prolong: read and write e, read the level-1 e
+    s->by0[4] = 8.0 * q0 + 12.0 * u0;            // smooth: read r, e, write e
+    s->by0[5] = n0 + 4.0 * q0 + 8.0 * u0 + 4.0 * n0;  // last smooth: every flag, read r, e, write z densely
     s->epoch = c->mask_epoch;
     s->coef = coef;
     return FS_OK;
