@@ -390,6 +390,7 @@ int mg_apply_faces(fs_ctx *c, const float *r, float *z, float cc, const int *don
 void mg_free(fs_ctx *c);
 void mg_count(fs_ctx *c, long long vcycles, bool faces);  // fs_mg.cu: launch counts for fs_profile
 int mg_levels(const fs_ctx *c);
+bool mg_rz(fs_ctx *c, bool faces, const float *r, const float *z, int first, SolveScal *s);  // fs_mg.cu
 // fs_splat.cu
 int splat_render(fs_ctx *c, int n, const float *x, const float *op, const float *A, const float *col,
                  const float *sh, int deg, const fs_camera *cam, float *rgb, float *T);

@@ -305,9 +305,11 @@ int build_mask(fs_ctx *c, const uint8_t *types_dense, const fs_mac *bc)
     unsigned long long *cnt = reinterpret_cast<unsigned long long *>(c->partials);
     FS_CUDA(cudaMemsetAsync(c->err_word, 0, sizeof(unsigned), c->stream));
     FS_CUDA(cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), c->stream));
-    // the preconditioned residuals start from zero off the unknowns of the new
-    // mask: the multigrid V-cycle writes them only on tiles that hold an unknown
+    // the buffers the multigrid V-cycle writes its result into start from zero
+    // off the unknowns of the new mask: it writes them only on quads that hold an
+    // unknown, and every other writer leaves them zero off the unknowns
     if (c->pz) FS_CUDA(cudaMemsetAsync(c->pz, 0, (size_t)L.nC * sizeof(float), c->stream));
+    if (c->pbr) FS_CUDA(cudaMemsetAsync(c->pbr, 0, (size_t)L.nC * sizeof(float), c->stream));
     if (c->vz) FS_CUDA(cudaMemsetAsync(c->vz, 0, (size_t)L.nF * sizeof(float), c->stream));
     k_cell_types<<<grid_blocks(c, L.nC, th), th, 0, c->stream>>>(L, types_dense, c->cflag, c->err_word);
     k_cell_flags<<<grid_blocks(c, L.S, th), th, 0, c->stream>>>(L, c->cflag);

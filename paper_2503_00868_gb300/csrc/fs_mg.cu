@@ -22,11 +22,14 @@
 // in one block. Every step is linear in r with symmetric smoothing and restriction
 // proportional to the transposed prolongation, so M is symmetric, as CG needs.
 //
-// The sweeps, the residual and the transfers take four elements per thread over a
-// level's whole array and skip the quads without an unknown. The work arrays are
-// zeroed when the hierarchy is built and written only on quads that hold an
-// unknown (with zeros on their other elements), so a stencil at the edge of the
-// liquid reads zeros; the level-0 output (the solver's z) is written densely.
+// The sweeps, the residual and the transfers take four elements per thread and
+// walk a list of a level's quads that hold an unknown (built with the hierarchy).
+// Every array a V-cycle writes is written only on those quads (with zeros on
+// their other elements) and is zero on every other quad: the work arrays are
+// zeroed when the hierarchy is built, and the level-0 output (the solver's z) is
+// a context buffer that is zeroed with each new mask and that every writer
+// leaves zero off the unknowns. So a stencil at the edge of the liquid reads
+// zeros, and the solver's operator apply reads z = 0 off the unknowns.
 //
 // The same V-cycle preconditions the implicit viscosity solve, one velocity
 // component at a time: each face volume is a box of unknown faces (FF_FLUID),
@@ -36,7 +39,9 @@
 // 4^-l cc L_l with m = 1 (m = 0 for the pressure).
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <new>
+#include <vector>
 
 #include "fs_internal.cuh"
 
@@ -82,6 +87,8 @@ struct MgState {
     float coef = 0.f;      // operator coefficient it was built for
     bool own0 = true;      // level 0 work arrays belong to this hierarchy
     const int *done = nullptr;  // the calling solve's convergence flag (nullable)
+    int cl = 0;                 // first level of the single-cluster launch (0: none)
+    int ctas = 0;               // CTAs of that cluster
     long long calls = 0;        // applies so far (profiling samples every prof_period-th)
     // algorithmic bytes of the level-0 kernels, in the order of K_MG0_SMOOTH2 ..
     // K_MG0_SMOOTH_Z (profiled when the first is > 0)
@@ -112,14 +119,18 @@ __device__ __forceinline__ float lap(const float *__restrict__ e, int t, uint8_t
     return (float)(f & CF_D) * e[t] - ((e[t - 1] + e[t + 1]) + (e[t - g.sy] + e[t + g.sy]) + (e[t - g.sz] + e[t + g.sz]));
 }
 
-// omega / (m + scale d) for d = 0..7 (zero where the diagonal vanishes)
+// omega / (m + scale d), zero where the diagonal vanishes
+__device__ __forceinline__ float wtab_entry(float scale, float m, int d)
+{
+    const float dg = m + scale * (float)d;
+    return dg > 0.f ? MG_OMEGA / dg : 0.f;
+}
+
+// the table for d = 0..7 in shared memory
 __device__ __forceinline__ void fill_wtab(float *wt, float scale, float m)
 {
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
-    if (tid < 8) {
-        const float dg = m + scale * (float)tid;
-        wt[tid] = dg > 0.f ? MG_OMEGA / dg : 0.f;
-    }
+    if (tid < 8) wt[tid] = wtab_entry(scale, m, tid);
     __syncthreads();
 }
 
@@ -131,10 +142,6 @@ __device__ __forceinline__ void fill_wtab(float *wt, float scale, float m)
 // with one is read whole (its row is interior, so every neighbour load is inside
 // the array) and written whole, with zeros on the elements that are not unknowns.
 
-__device__ __forceinline__ float4 ld4g(const float *__restrict__ p, int t)
-{
-    return __ldg(reinterpret_cast<const float4 *>(p + t));
-}
 __device__ __forceinline__ uchar4 ldf4(const uint8_t *__restrict__ p, int t)
 {
     return __ldg(reinterpret_cast<const uchar4 *>(p + t));
@@ -157,17 +164,37 @@ __device__ __forceinline__ float sweep1(uint8_t f, float c, float nb, float rv, 
          mg_i < (na) && ((mg_next = mg_i + mg_st < (na) ? __ldg((list) + mg_i + mg_st) : 0), true);     \
          mg_i += mg_st, q = mg_next)
 
+// Vector loads of the item functions: through the non-coherent path for a launch
+// that does not write what it reads (CG = false), or at L2 (CG = true) for the
+// cluster launch, whose CTAs read what others wrote before a cluster barrier.
+template <bool CG>
+__device__ __forceinline__ float4 ldv4(const float *p, int t)
+{
+    if constexpr (CG)
+        return __ldcg(reinterpret_cast<const float4 *>(p + t));
+    else
+        return __ldg(reinterpret_cast<const float4 *>(p + t));
+}
+template <bool CG>
+__device__ __forceinline__ float ldv1(const float *p, int t)
+{
+    if constexpr (CG)
+        return __ldcg(p + t);
+    else
+        return __ldg(p + t);
+}
+
 // one damped Jacobi sweep on quad q: eout from ein
-__device__ __forceinline__ void smooth_q(const MgGrid &g, const uint8_t *__restrict__ fl, const float *__restrict__ r,
-                                         const float *__restrict__ ein, float *eout, const float *wt, float scale,
-                                         float m, int q)
+template <bool CG>
+__device__ __forceinline__ void smooth_q(const MgGrid &g, const uint8_t *__restrict__ fl, const float *r,
+                                         const float *ein, float *eout, const float *wt, float scale, float m, int q)
 {
     const int t = q << 2;
     const uchar4 f = ldf4(fl, t);
-    const float4 c = ld4g(ein, t), rv = ld4g(r, t);
-    const float4 dn = ld4g(ein, t - g.sy), up = ld4g(ein, t + g.sy);
-    const float4 bk = ld4g(ein, t - g.sz), fw = ld4g(ein, t + g.sz);
-    const float lf = __ldg(ein + t - 1), rt = __ldg(ein + t + 4);
+    const float4 c = ldv4<CG>(ein, t), rv = ldv4<CG>(r, t);
+    const float4 dn = ldv4<CG>(ein, t - g.sy), up = ldv4<CG>(ein, t + g.sy);
+    const float4 bk = ldv4<CG>(ein, t - g.sz), fw = ldv4<CG>(ein, t + g.sz);
+    const float lf = ldv1<CG>(ein, t - 1), rt = ldv1<CG>(ein, t + 4);
     float4 v;
     v.x = sweep1(f.x, c.x, (lf + c.y) + (dn.x + up.x) + (bk.x + fw.x), rv.x, wt, scale, m);
     v.y = sweep1(f.y, c.y, (c.x + c.z) + (dn.y + up.y) + (bk.y + fw.y), rv.y, wt, scale, m);
@@ -176,22 +203,145 @@ __device__ __forceinline__ void smooth_q(const MgGrid &g, const uint8_t *__restr
     *reinterpret_cast<float4 *>(eout + t) = v;
 }
 
-// One sweep over the active quads. With `dense` (the level-0 output, the solver's
-// z), the quads without an unknown are written with zeros too, in a second loop
-// over the whole array that reads the flags only.
+// res = r - A e on quad q
+template <bool CG>
+__device__ __forceinline__ void resid_q(const MgGrid &g, const uint8_t *__restrict__ fl, const float *r,
+                                        const float *ev, float *res, float scale, float m, int q)
+{
+    const int t = q << 2;
+    const uchar4 f = ldf4(fl, t);
+    const float4 c = ldv4<CG>(ev, t), rv = ldv4<CG>(r, t);
+    const float4 dn = ldv4<CG>(ev, t - g.sy), up = ldv4<CG>(ev, t + g.sy);
+    const float4 bk = ldv4<CG>(ev, t - g.sz), fw = ldv4<CG>(ev, t + g.sz);
+    const float lf = ldv1<CG>(ev, t - 1), rt = ldv1<CG>(ev, t + 4);
+    auto one = [&](uint8_t fe, float ce, float nb, float re) {
+        return liq(fe) ? re - m * ce - scale * ((float)(fe & CF_D) * ce - nb) : 0.f;
+    };
+    float4 v;
+    v.x = one(f.x, c.x, (lf + c.y) + (dn.x + up.x) + (bk.x + fw.x), rv.x);
+    v.y = one(f.y, c.y, (c.x + c.z) + (dn.y + up.y) + (bk.y + fw.y), rv.y);
+    v.z = one(f.z, c.z, (c.y + c.w) + (dn.z + up.z) + (bk.z + fw.z), rv.z);
+    v.w = one(f.w, c.w, (c.z + rt) + (dn.w + up.w) + (bk.w + fw.w), rv.w);
+    *reinterpret_cast<float4 *>(res + t) = v;
+}
+
+// the first two sweeps from e = 0 on quad q: e1 = omega D^-1 r on the fly, then one sweep
+template <bool CG>
+__device__ __forceinline__ void smooth2_q(const MgGrid &g, const uint8_t *__restrict__ fl, const float *r, float *eo,
+                                          const float *wt, float scale, float m, int q)
+{
+    const int t = q << 2;
+    const uchar4 f = ldf4(fl, t);
+    auto e1q = [&](int u) {  // e1 on the quad at u
+        const uchar4 fu = ldf4(fl, u);
+        const float4 ru = ldv4<CG>(r, u);
+        return make_float4(liq(fu.x) ? wt[fu.x & CF_D] * ru.x : 0.f, liq(fu.y) ? wt[fu.y & CF_D] * ru.y : 0.f,
+                           liq(fu.z) ? wt[fu.z & CF_D] * ru.z : 0.f, liq(fu.w) ? wt[fu.w & CF_D] * ru.w : 0.f);
+    };
+    auto e1s = [&](int u) {
+        const uint8_t fu = fl[u];
+        return liq(fu) ? wt[fu & CF_D] * ldv1<CG>(r, u) : 0.f;
+    };
+    const float4 c = e1q(t), rv = ldv4<CG>(r, t);
+    const float4 dn = e1q(t - g.sy), up = e1q(t + g.sy), bk = e1q(t - g.sz), fw = e1q(t + g.sz);
+    const float lf = e1s(t - 1), rt = e1s(t + 4);
+    float4 v;
+    v.x = sweep1(f.x, c.x, (lf + c.y) + (dn.x + up.x) + (bk.x + fw.x), rv.x, wt, scale, m);
+    v.y = sweep1(f.y, c.y, (c.x + c.z) + (dn.y + up.y) + (bk.y + fw.y), rv.y, wt, scale, m);
+    v.z = sweep1(f.z, c.z, (c.y + c.w) + (dn.z + up.z) + (bk.z + fw.z), rv.z, wt, scale, m);
+    v.w = sweep1(f.w, c.w, (c.z + rt) + (dn.w + up.w) + (bk.w + fw.w), rv.w, wt, scale, m);
+    *reinterpret_cast<float4 *>(eo + t) = v;
+}
+
+// e_fine += P e_coarse on the unknowns of an active quad q (in place). The quad's
+// elements i .. i + 3 (i a multiple of 4) take their x samples from coarse
+// I0 - 1 .. I0 + 2 (I0 = i / 2); indices past the coarse halo are clamped to it
+// (a sample that only padding elements use).
+template <bool CG>
+__device__ __forceinline__ void prolong_q(const MgGrid &gf, const uint8_t *__restrict__ fl, float *ef,
+                                          const MgGrid &gc, const float *ec, int q)
+{
+    const int qrow = gf.sy >> 2;
+    const int t = q << 2;
+    const uchar4 f = ldf4(fl, t);
+    const int row = q / qrow, e = (q - row * qrow) << 2;
+    const int i = e - gf.ioff, j = row % gf.rpp - gf.joff, k = row / gf.rpp - gf.koff;
+    const int I0 = i >> 1, J = j >> 1, K = k >> 1;
+    const int J2 = (j & 1) ? J + 1 : J - 1, K2 = (k & 1) ? K + 1 : K - 1;
+    const int xs[4] = {max(I0 - 1, -1), I0, min(I0 + 1, gc.nx), min(I0 + 2, gc.nx)};
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    const int jj[2] = {J, J2}, kk[2] = {K, K2};
+    const float wy[2] = {0.75f, 0.25f};
+#pragma unroll
+    for (int b = 0; b < 2; b++)
+#pragma unroll
+        for (int a = 0; a < 2; a++) {
+            const int base = gc.idx(0, jj[a], kk[b]);
+            const float w = wy[a] * wy[b];
+            const float cm = ldv1<CG>(ec, base + xs[0]), c0 = ldv1<CG>(ec, base + xs[1]);
+            const float c1 = ldv1<CG>(ec, base + xs[2]), c2 = ldv1<CG>(ec, base + xs[3]);
+            s0 += w * (0.75f * c0 + 0.25f * cm);
+            s1 += w * (0.75f * c0 + 0.25f * c1);
+            s2 += w * (0.75f * c1 + 0.25f * c0);
+            s3 += w * (0.75f * c1 + 0.25f * c2);
+        }
+    float4 v = CG ? __ldcg(reinterpret_cast<const float4 *>(ef + t)) : *reinterpret_cast<const float4 *>(ef + t);
+    if (liq(f.x)) v.x += s0;
+    if (liq(f.y)) v.y += s1;
+    if (liq(f.z)) v.z += s2;
+    if (liq(f.w)) v.w += s3;
+    *reinterpret_cast<float4 *>(ef + t) = v;
+}
+
+// Restriction of an active pair of the coarse level: t0 is the element of coarse
+// cell (2m, J, K), and the pair (2m, 2m + 1) holds at least one unknown. Per fine
+// row of the 4 x 4 window it reads the aligned quad 4m .. 4m + 3 and the scalars
+// at 4m - 1 and 4m + 4 (excluded at or past nx, where the next row begins), and
+// forms both cells' x weights from them.
+template <bool CG>
+__device__ __forceinline__ void restrict_pair(const MgGrid &gf, const float *res, const MgGrid &gc,
+                                              const uint8_t *__restrict__ flc, float *rc, int t0)
+{
+    const float w[4] = {0.25f, 0.75f, 0.75f, 0.25f};
+    const int rel = t0 - gc.origin;
+    const int K = rel / gc.sz, J = (rel - K * gc.sz) / gc.sy, I0 = rel - K * gc.sz - J * gc.sy;
+    const int m = I0 >> 1;
+    const bool l0 = liq(flc[t0]), l1 = I0 + 1 < gc.nx && liq(flc[t0 + 1]);
+    float a0 = 0.f, a1 = 0.f;
+    // unrolled, so the 16 row loads are issued together
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        const int k = 2 * K - 1 + c;
+        if (k < 0 || k >= gf.nz) continue;
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+            const int j = 2 * J - 1 + b;
+            if (j < 0 || j >= gf.ny) continue;
+            const int row = gf.idx(0, j, k) + 4 * m;  // a multiple of 4
+            const float4 qd = ldv4<CG>(res, row);
+            const float lf = m > 0 ? ldv1<CG>(res, row - 1) : 0.f;
+            const float rt = 4 * m + 4 < gf.nx ? ldv1<CG>(res, row + 4) : 0.f;
+            const float wyz = w[c] * w[b];
+            // coarse 2m: fine 4m - 1 .. 4m + 2; coarse 2m + 1: fine 4m + 1 .. 4m + 4
+            a0 += wyz * (0.25f * lf + 0.75f * qd.x + 0.75f * qd.y + 0.25f * qd.z);
+            a1 += wyz * (0.25f * qd.y + 0.75f * qd.z + 0.75f * qd.w + 0.25f * rt);
+        }
+    }
+    if (l0) rc[t0] = 0.125f * a0;
+    if (l1) rc[t0 + 1] = 0.125f * a1;
+}
+
+// ---- one launch per step ------------------------------------------------------
+
 __global__ void __launch_bounds__(256) k_mg0_smooth(MgGrid g, const int *__restrict__ qlist, int na,
                                                     const uint8_t *__restrict__ fl, const float *__restrict__ r,
                                                     const float *__restrict__ ein, float *eout, float scale, float m,
-                                                    int dense, const int *done)
+                                                    const int *done)
 {
     if (done && *(volatile const int *)done) return;  // the solve has converged
     __shared__ float wt[8];
     fill_wtab(wt, scale, m);
-    MG_FOR_LIST(qlist, na) smooth_q(g, fl, r, ein, eout, wt, scale, m, q);
-    if (!dense) return;
-    const int nq = g.n >> 2;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x)
-        if (!any_liq(ldf4(fl, q << 2))) *reinterpret_cast<float4 *>(eout + (q << 2)) = make_float4(0.f, 0.f, 0.f, 0.f);
+    MG_FOR_LIST(qlist, na) smooth_q<false>(g, fl, r, ein, eout, wt, scale, m, q);
 }
 
 __global__ void __launch_bounds__(256) k_mg0_residual(MgGrid g, const int *__restrict__ qlist, int na,
@@ -200,27 +350,9 @@ __global__ void __launch_bounds__(256) k_mg0_residual(MgGrid g, const int *__res
                                                       const int *done)
 {
     if (done && *(volatile const int *)done) return;  // the solve has converged
-    MG_FOR_LIST(qlist, na)
-    {
-        const int t = q << 2;
-        const uchar4 f = ldf4(fl, t);
-        const float4 c = ld4g(ev, t), rv = ld4g(r, t);
-        const float4 dn = ld4g(ev, t - g.sy), up = ld4g(ev, t + g.sy);
-        const float4 bk = ld4g(ev, t - g.sz), fw = ld4g(ev, t + g.sz);
-        const float lf = __ldg(ev + t - 1), rt = __ldg(ev + t + 4);
-        auto one = [&](uint8_t fe, float ce, float nb, float re) {
-            return liq(fe) ? re - m * ce - scale * ((float)(fe & CF_D) * ce - nb) : 0.f;
-        };
-        float4 v;
-        v.x = one(f.x, c.x, (lf + c.y) + (dn.x + up.x) + (bk.x + fw.x), rv.x);
-        v.y = one(f.y, c.y, (c.x + c.z) + (dn.y + up.y) + (bk.y + fw.y), rv.y);
-        v.z = one(f.z, c.z, (c.y + c.w) + (dn.z + up.z) + (bk.z + fw.z), rv.z);
-        v.w = one(f.w, c.w, (c.z + rt) + (dn.w + up.w) + (bk.w + fw.w), rv.w);
-        *reinterpret_cast<float4 *>(res + t) = v;
-    }
+    MG_FOR_LIST(qlist, na) resid_q<false>(g, fl, r, ev, res, scale, m, q);
 }
 
-// the first two sweeps from e = 0: e1 = omega D^-1 r on the fly, then one sweep
 __global__ void __launch_bounds__(256) k_mg0_smooth2(MgGrid g, const int *__restrict__ qlist, int na,
                                                      const uint8_t *__restrict__ fl, const float *__restrict__ r,
                                                      float *eo, float scale, float m, const int *done)
@@ -228,171 +360,98 @@ __global__ void __launch_bounds__(256) k_mg0_smooth2(MgGrid g, const int *__rest
     if (done && *(volatile const int *)done) return;  // the solve has converged
     __shared__ float wt[8];
     fill_wtab(wt, scale, m);
-    MG_FOR_LIST(qlist, na)
-    {
-        const int t = q << 2;
-        const uchar4 f = ldf4(fl, t);
-        auto e1q = [&](int u) {  // e1 on the quad at u
-            const uchar4 fu = ldf4(fl, u);
-            const float4 ru = ld4g(r, u);
-            return make_float4(liq(fu.x) ? wt[fu.x & CF_D] * ru.x : 0.f, liq(fu.y) ? wt[fu.y & CF_D] * ru.y : 0.f,
-                               liq(fu.z) ? wt[fu.z & CF_D] * ru.z : 0.f, liq(fu.w) ? wt[fu.w & CF_D] * ru.w : 0.f);
-        };
-        auto e1s = [&](int u) {
-            const uint8_t fu = fl[u];
-            return liq(fu) ? wt[fu & CF_D] * __ldg(r + u) : 0.f;
-        };
-        const float4 c = e1q(t), rv = ld4g(r, t);
-        const float4 dn = e1q(t - g.sy), up = e1q(t + g.sy), bk = e1q(t - g.sz), fw = e1q(t + g.sz);
-        const float lf = e1s(t - 1), rt = e1s(t + 4);
-        float4 v;
-        v.x = sweep1(f.x, c.x, (lf + c.y) + (dn.x + up.x) + (bk.x + fw.x), rv.x, wt, scale, m);
-        v.y = sweep1(f.y, c.y, (c.x + c.z) + (dn.y + up.y) + (bk.y + fw.y), rv.y, wt, scale, m);
-        v.z = sweep1(f.z, c.z, (c.y + c.w) + (dn.z + up.z) + (bk.z + fw.z), rv.z, wt, scale, m);
-        v.w = sweep1(f.w, c.w, (c.z + rt) + (dn.w + up.w) + (bk.w + fw.w), rv.w, wt, scale, m);
-        *reinterpret_cast<float4 *>(eo + t) = v;
-    }
+    MG_FOR_LIST(qlist, na) smooth2_q<false>(g, fl, r, eo, wt, scale, m, q);
 }
 
-// e_fine += P e_coarse on the unknowns of an active quad (in place). The quad's
-// elements i .. i + 3 (i a multiple of 4) take their x samples from coarse
-// I0 - 1 .. I0 + 2 (I0 = i / 2); indices past the coarse halo are clamped to it
-// (a sample that only padding elements use).
 __global__ void __launch_bounds__(256) k_mg0_prolong(MgGrid gf, const int *__restrict__ qlist, int na,
                                                      const uint8_t *__restrict__ fl, float *ef, MgGrid gc,
                                                      const float *__restrict__ ec, const int *done)
 {
     if (done && *(volatile const int *)done) return;  // the solve has converged
-    const int qrow = gf.sy >> 2;
-    MG_FOR_LIST(qlist, na)
-    {
-        const int t = q << 2;
-        const uchar4 f = ldf4(fl, t);
-        const int row = q / qrow, e = (q - row * qrow) << 2;
-        const int i = e - gf.ioff, j = row % gf.rpp - gf.joff, k = row / gf.rpp - gf.koff;
-        const int I0 = i >> 1, J = j >> 1, K = k >> 1;
-        const int J2 = (j & 1) ? J + 1 : J - 1, K2 = (k & 1) ? K + 1 : K - 1;
-        const int xs[4] = {max(I0 - 1, -1), I0, min(I0 + 1, gc.nx), min(I0 + 2, gc.nx)};
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-        const int jj[2] = {J, J2}, kk[2] = {K, K2};
-        const float wy[2] = {0.75f, 0.25f};
-#pragma unroll
-        for (int b = 0; b < 2; b++)
-#pragma unroll
-            for (int a = 0; a < 2; a++) {
-                const int base = gc.idx(0, jj[a], kk[b]);
-                const float w = wy[a] * wy[b];
-                const float cm = __ldg(ec + base + xs[0]), c0 = __ldg(ec + base + xs[1]);
-                const float c1 = __ldg(ec + base + xs[2]), c2 = __ldg(ec + base + xs[3]);
-                s0 += w * (0.75f * c0 + 0.25f * cm);
-                s1 += w * (0.75f * c0 + 0.25f * c1);
-                s2 += w * (0.75f * c1 + 0.25f * c0);
-                s3 += w * (0.75f * c1 + 0.25f * c2);
-            }
-        float4 v = *reinterpret_cast<const float4 *>(ef + t);
-        if (liq(f.x)) v.x += s0;
-        if (liq(f.y)) v.y += s1;
-        if (liq(f.z)) v.z += s2;
-        if (liq(f.w)) v.w += s3;
-        *reinterpret_cast<float4 *>(ef + t) = v;
-    }
+    MG_FOR_LIST(qlist, na) prolong_q<false>(gf, fl, ef, gc, ec, q);
 }
 
-// Restriction from a quad-aligned level over the coarse level's list of active
-// pairs: entry t0 is the element of coarse cell (2m, J, K), and the pair (2m,
-// 2m + 1) holds at least one unknown. Per fine row of the 4 x 4 window it reads the aligned
-// quad 4m .. 4m + 3 and the scalars at 4m - 1 and 4m + 4 (excluded at or past nx,
-// where the next row begins), and forms both cells' x weights from them.
+// restriction over the coarse level's list of active pairs
 __global__ void __launch_bounds__(256) k_mg0_restrict(MgGrid gf, const float *__restrict__ res, MgGrid gc,
                                                       const int *__restrict__ plist, int np,
                                                       const uint8_t *__restrict__ flc, float *rc, const int *done)
 {
     if (done && *(volatile const int *)done) return;  // the solve has converged
-    const float w[4] = {0.25f, 0.75f, 0.75f, 0.25f};
-    MG_FOR_LIST(plist, np)
-    {
-        const int t0 = q;
-        const int rel = t0 - gc.origin;
-        const int K = rel / gc.sz, J = (rel - K * gc.sz) / gc.sy, I0 = rel - K * gc.sz - J * gc.sy;
-        const int m = I0 >> 1;
-        const bool l0 = liq(flc[t0]), l1 = I0 + 1 < gc.nx && liq(flc[t0 + 1]);
-        float a0 = 0.f, a1 = 0.f;
-        for (int c = 0; c < 4; c++) {
-            const int k = 2 * K - 1 + c;
-            if (k < 0 || k >= gf.nz) continue;
-            for (int b = 0; b < 4; b++) {
-                const int j = 2 * J - 1 + b;
-                if (j < 0 || j >= gf.ny) continue;
-                const int row = gf.idx(0, j, k) + 4 * m;  // a multiple of 4
-                const float4 qd = ld4g(res, row);
-                const float lf = m > 0 ? __ldg(res + row - 1) : 0.f;
-                const float rt = 4 * m + 4 < gf.nx ? __ldg(res + row + 4) : 0.f;
-                const float wyz = w[c] * w[b];
-                // coarse 2m: fine 4m - 1 .. 4m + 2; coarse 2m + 1: fine 4m + 1 .. 4m + 4
-                a0 += wyz * (0.25f * lf + 0.75f * qd.x + 0.75f * qd.y + 0.25f * qd.z);
-                a1 += wyz * (0.25f * qd.y + 0.75f * qd.z + 0.75f * qd.w + 0.25f * rt);
-            }
-        }
-        if (l0) rc[t0] = 0.125f * a0;
-        if (l1) rc[t0 + 1] = 0.125f * a1;
-    }
+    MG_FOR_LIST(plist, np) restrict_pair<false>(gf, res, gc, flc, rc, q);
 }
 
 // ---- lists of the active quads and restriction pairs ------------------------------
+// Sorted and deterministic: block b owns items [b LB_ITEMS, (b + 1) LB_ITEMS), four
+// consecutive items per thread; a first pass counts each block's kept items, the
+// host scans the counts, and a second pass writes each block's items in order
+// at its offset.
+constexpr int LB_TH = 256, LB_PER = 4, LB_ITEMS = LB_TH * LB_PER;
 
-// Appends, in warp order, the indices of the items for which `keep` holds: one
-// atomic per warp. The list's order follows the scheduling of the warps, which
-// changes nothing computed (every item is independent).
-__device__ __forceinline__ void warp_append(bool keep, int item, int *list, int *count)
-{
-    const unsigned lane = threadIdx.x & 31, act = __activemask();
-    const unsigned bal = __ballot_sync(act, keep);
-    if (!bal) return;
-    const int leader = __ffs(act) - 1;
-    int base = 0;
-    if ((int)lane == leader) base = atomicAdd(count, __popc(bal));
-    base = __shfl_sync(act, base, leader);
-    if (keep) list[base + __popc(bal & ((1u << lane) - 1u))] = item;
-}
-
-// quads of a level with an unknown (count only when list is null)
-__global__ void k_mg_list_quads(MgGrid g, const uint8_t *__restrict__ fl, int *list, int *count)
-{
-    const int nq = g.n >> 2;
-    const int n32 = (nq + 31) & ~31;  // whole warps take part in the ballot
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n32; q += gridDim.x * blockDim.x) {
-        const bool keep = q < nq && any_liq(ldf4(fl, q << 2));
-        if (list)
-            warp_append(keep, q, list, count);
-        else if (keep)
-            atomicAdd(count, 1);
+struct QuadPred {  // a quad of the level holds an unknown
+    MgGrid g;
+    const uint8_t *fl;
+    __device__ long long items() const { return g.n >> 2; }
+    __device__ bool keep(long long q, int &out) const
+    {
+        out = (int)q;
+        return any_liq(ldf4(fl, (int)q << 2));
     }
+};
+struct PairPred {  // a restriction pair (2m, 2m + 1) of the coarse level holds an unknown
+    MgGrid g;
+    const uint8_t *fl;
+    __device__ long long items() const { return (long long)((g.nx + 1) >> 1) * g.ny * g.nz; }
+    __device__ bool keep(long long it, int &out) const
+    {
+        const int npair = (g.nx + 1) >> 1;
+        const int m = (int)(it % npair);
+        const long long jk = it / npair;
+        const int J = (int)(jk % g.ny), K = (int)(jk / g.ny);
+        out = g.idx(2 * m, J, K);
+        return liq(fl[out]) || (2 * m + 1 < g.nx && liq(fl[out + 1]));
+    }
+};
+
+template <class P>
+__global__ void __launch_bounds__(LB_TH) k_list_build(P pred, const int *__restrict__ offsets, int *count, int *list)
+{
+    __shared__ int warp_tot[LB_TH / 32];
+    const long long n = pred.items();
+    const long long base = (long long)blockIdx.x * LB_ITEMS + (long long)threadIdx.x * LB_PER;
+    int ids[LB_PER];
+    int kept = 0;
+#pragma unroll
+    for (int k = 0; k < LB_PER; k++) {
+        int id = 0;
+        const bool keep = base + k < n && pred.keep(base + k, id);
+        ids[k] = keep ? id : -1;
+        kept += keep ? 1 : 0;
+    }
+    // inclusive scan of the kept counts over the block (warp shuffles, then warps)
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = kept;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int k = 0; k < LB_TH / 32; k++) {
+        if (k < w) before += warp_tot[k];
+        total += warp_tot[k];
+    }
+    if (!list) {  // counting pass
+        if (threadIdx.x == 0) count[blockIdx.x] = total;
+        return;
+    }
+    int pos = offsets[blockIdx.x] + before + incl - kept;
+#pragma unroll
+    for (int k = 0; k < LB_PER; k++)
+        if (ids[k] >= 0) list[pos++] = ids[k];
 }
 
-// restriction pairs of a coarse level with an unknown: the element of the pair's
-// first cell (count only when list is null)
-__global__ void k_mg_list_pairs(MgGrid gc, const uint8_t *__restrict__ flc, int *list, int *count)
-{
-    const int npair = (gc.nx + 1) >> 1;
-    const long long items = (long long)npair * gc.ny * gc.nz;
-    const long long i32 = (items + 31) & ~31ll;
-    for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < i32;
-         it += (long long)gridDim.x * blockDim.x) {
-        bool keep = false;
-        int t0 = 0;
-        if (it < items) {
-            const int m = (int)(it % npair);
-            const long long jk = it / npair;
-            const int J = (int)(jk % gc.ny), K = (int)(jk / gc.ny);
-            t0 = gc.idx(2 * m, J, K);
-            keep = liq(flc[t0]) || (2 * m + 1 < gc.nx && liq(flc[t0 + 1]));
-        }
-        if (list)
-            warp_append(keep, t0, list, count);
-        else if (keep)
-            atomicAdd(count, 1);
-    }
-}
+// ---- set-up ------------------------------------------------------------------
 
 // coarse flags from the level above: air if any child is air, else liquid if any
 // child is liquid; the halo stays solid (zero)
@@ -436,39 +495,168 @@ __global__ void k_mg_count(MgGrid g, uint8_t *fl)
     }
 }
 
-// coarsest level: MG_COARSE_SWEEPS damped Jacobi sweeps from zero, in shared memory
-__global__ void __launch_bounds__(TH) k_mg_coarse(MgGrid g, const uint8_t *__restrict__ fl,
-                                                  const float *__restrict__ r, float *e, float scale, float m, const int *done)
+// The coarsest level: MG_COARSE_SWEEPS damped Jacobi sweeps from zero in the
+// shared memory `sm` of one block (13 bytes per element), the result written to
+// e on every element; wt is the level's weight table. Each sweep reads only the
+// previous one, so the result does not depend on the block size.
+template <bool CG>
+__device__ void coarse_block(const MgGrid &g, const uint8_t *__restrict__ fl, const float *r, float *e,
+                             const float *wt, float scale, float m, float *sm)
 {
-    if (done && *(volatile const int *)done) return;  // the solve has converged
-    extern __shared__ float sm[];
-    __shared__ float wt[8];
     float *e0 = sm, *e1 = sm + g.n, *rs = sm + 2 * g.n;
     uint8_t *fs = reinterpret_cast<uint8_t *>(sm + 3 * g.n);
-    if (threadIdx.x < 8) {
-        const float dg = m + scale * (float)threadIdx.x;
-        wt[threadIdx.x] = dg > 0.f ? MG_OMEGA / dg : 0.f;
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < g.n; t += TH) {
+    for (int t = threadIdx.x; t < g.n; t += blockDim.x) {
         const uint8_t f = fl[t];
+        const float rv = ldv1<CG>(r, t);
         fs[t] = f;
-        rs[t] = liq(f) ? r[t] : 0.f;
-        e0[t] = liq(f) ? wt[f & CF_D] * r[t] : 0.f;
+        rs[t] = liq(f) ? rv : 0.f;
+        e0[t] = liq(f) ? wt[f & CF_D] * rv : 0.f;
         e1[t] = 0.f;
     }
     __syncthreads();
     for (int s = 1; s < MG_COARSE_SWEEPS; s++) {
         const float *ein = (s & 1) ? e0 : e1;
         float *eout = (s & 1) ? e1 : e0;
-        for (int t = threadIdx.x; t < g.n; t += TH) {
+        for (int t = threadIdx.x; t < g.n; t += blockDim.x) {
             const uint8_t f = fs[t];
             eout[t] = liq(f) ? ein[t] + wt[f & CF_D] * (rs[t] - m * ein[t] - scale * lap(ein, t, f, g)) : 0.f;
         }
         __syncthreads();
     }
     const float *res = (MG_COARSE_SWEEPS & 1) ? e0 : e1;  // the last sweep's output
-    for (int t = threadIdx.x; t < g.n; t += TH) e[t] = res[t];
+    for (int t = threadIdx.x; t < g.n; t += blockDim.x) e[t] = res[t];
+}
+
+constexpr int COARSE_TH = 1024;  // threads of the block that solves the coarsest level
+
+__global__ void __launch_bounds__(COARSE_TH) k_mg_coarse(MgGrid g, const uint8_t *__restrict__ fl,
+                                                         const float *__restrict__ r, float *e, float scale, float m,
+                                                         const int *done)
+{
+    if (done && *(volatile const int *)done) return;  // the solve has converged
+    extern __shared__ float sm[];
+    __shared__ float wt[8];
+    fill_wtab(wt, scale, m);
+    coarse_block<false>(g, fl, r, e, wt, scale, m, sm);
+}
+
+// ---- the small levels in one cluster -------------------------------------------
+// The levels whose active quads number at most MGC_MAX_QUADS take one launch of a
+// single thread-block cluster (MGC_CTAS CTAs of MGC_TH threads): the same steps as
+// the per-level kernels, level by level, with the cluster's hardware barrier in
+// place of each kernel boundary. What one CTA writes another reads after the
+// barrier (release, then acquire at cluster scope), through L2 (ld.global.cg:
+// no SM's L1 can hold a stale copy). CTA 0 solves the coarsest level.
+constexpr int MGC_TH = 1024;
+constexpr int MGC_MAXLEV = 8;
+constexpr int MGC_MAX_QUADS = 49152;
+
+struct MgcLevel {
+    MgGrid g;
+    const uint8_t *fl;
+    float *r, *a, *b, *c;
+    const int *ql, *pl;
+    int nqa, npa;
+    float scale, mass;
+};
+
+struct MgClusterArgs {
+    MgcLevel lev[MGC_MAXLEV];
+    int nlev;
+    const int *done;
+};
+
+__device__ __forceinline__ void cluster_barrier()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ int cluster_rank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return (int)r;
+}
+__device__ __forceinline__ int cluster_ctas()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return (int)r;
+}
+
+// The V-cycle on a.lev[0] .. a.lev[nlev - 1]: r in lev[0].r, result in lev[0].a.
+__global__ void __launch_bounds__(MGC_TH) k_mg_cluster(const MgClusterArgs a)
+{
+    if (a.done && *(volatile const int *)a.done) return;  // the solve has converged (every CTA alike)
+    extern __shared__ float sm[];
+    __shared__ float wts[MGC_MAXLEV][8];
+    for (int i = threadIdx.x; i < MGC_MAXLEV * 8; i += blockDim.x)
+        if (i / 8 < a.nlev) wts[i / 8][i % 8] = wtab_entry(a.lev[i / 8].scale, a.lev[i / 8].mass, i % 8);
+    __syncthreads();
+    const int tid = cluster_rank() * blockDim.x + threadIdx.x, st = cluster_ctas() * blockDim.x;
+    for (int l = 0; l + 1 < a.nlev; l++) {
+        const MgcLevel &L = a.lev[l], &W = a.lev[l + 1];
+        for (int i = tid; i < L.nqa; i += st)
+            smooth2_q<true>(L.g, L.fl, L.r, L.b, wts[l], L.scale, L.mass, __ldg(L.ql + i));
+        cluster_barrier();
+        for (int i = tid; i < L.nqa; i += st) resid_q<true>(L.g, L.fl, L.r, L.b, L.c, L.scale, L.mass, __ldg(L.ql + i));
+        cluster_barrier();
+        for (int i = tid; i < W.npa; i += st) restrict_pair<true>(L.g, L.c, W.g, W.fl, W.r, __ldg(W.pl + i));
+        cluster_barrier();
+    }
+    if (cluster_rank() == 0) {
+        const MgcLevel &L = a.lev[a.nlev - 1];
+        coarse_block<true>(L.g, L.fl, L.r, L.a, wts[a.nlev - 1], L.scale, L.mass, sm);
+    }
+    cluster_barrier();
+    for (int l = a.nlev - 2; l >= 0; l--) {
+        const MgcLevel &L = a.lev[l], &W = a.lev[l + 1];
+        for (int i = tid; i < L.nqa; i += st) prolong_q<true>(L.g, L.fl, L.b, W.g, W.a, __ldg(L.ql + i));
+        cluster_barrier();
+        for (int i = tid; i < L.nqa; i += st)
+            smooth_q<true>(L.g, L.fl, L.r, L.b, L.c, wts[l], L.scale, L.mass, __ldg(L.ql + i));
+        cluster_barrier();
+        for (int i = tid; i < L.nqa; i += st)
+            smooth_q<true>(L.g, L.fl, L.r, L.c, L.a, wts[l], L.scale, L.mass, __ldg(L.ql + i));
+        if (l > 0) cluster_barrier();
+    }
+}
+
+// r.z over the active quads of one or three level-0 lists (r is zero off the
+// unknowns, so no other quad adds to it), in the lists' fixed order: beta =
+// rz_new / rz (first: beta = 0), as the dense pass of the solver does.
+struct RzLists {
+    const int *ql[3];
+    int n[3];
+    long long base[3];
+    int nv;
+};
+
+__global__ void __launch_bounds__(TH) k_mg_rz(RzLists L, const float *__restrict__ r, const float *__restrict__ z,
+                                             int first, SolveScal *s, double *partials)
+{
+    if (s->done) return;
+    KSum acc;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, st = gridDim.x * blockDim.x;
+    for (int v = 0; v < L.nv; v++) {
+        const float4 *r4 = reinterpret_cast<const float4 *>(r + L.base[v]);
+        const float4 *z4 = reinterpret_cast<const float4 *>(z + L.base[v]);
+        for (int i = tid; i < L.n[v]; i += st) {
+            const int q = __ldg(L.ql[v] + i);
+            const float4 a = __ldg(r4 + q), b = __ldg(z4 + q);
+            acc.add(a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w);
+        }
+    }
+    KSum v[1] = {acc};
+    double tot[1];
+    if (grid_reduce<1>(v, partials, &s->ticket, tot) && threadIdx.x == 0) {
+        if (!isfinite(tot[0])) {
+            s->done = 1;
+            s->status = FS_ENONFINITE;
+            return;
+        }
+        s->beta = first ? 0.0 : tot[0] / s->rz;
+        s->rz = tot[0];
+    }
 }
 
 // number of unknown cells of a level (once per mask, for the profiled byte count)
@@ -558,12 +746,72 @@ void free_levels(MgState *s)
 // (level 0 of a pressure V-cycle on the context's stream), every level-0 kernel
 // and the coarse levels as a whole are timed; a timed kernel always runs in full
 // (an early exit would record work not done).
+// levels cl .. nlev - 1 of a hierarchy in one cluster launch
+int launch_cluster(fs_ctx *c, MgState *s, int cl, cudaStream_t st)
+{
+    MgClusterArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.nlev = s->nlev - cl;
+    for (int l = cl; l < s->nlev; l++) {
+        const MgLevel &v = s->lev[l];
+        a.lev[l - cl] = MgcLevel{v.g, v.fl, v.r, v.a, v.b, v.c, v.ql, v.pl, v.nqa, v.npa, v.scale, v.mass};
+    }
+    a.done = s->done;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(s->ctas);
+    cfg.blockDim = dim3(MGC_TH);
+    cfg.dynamicSmemBytes = coarse_smem(s->lev[s->nlev - 1].g);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = s->ctas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    FS_CUDA(cudaLaunchKernelEx(&cfg, k_mg_cluster, a));
+    c->n_launches += 1;
+    return FS_OK;
+}
+
+// CTAs of the single-cluster launch on this device: 16 where the device allows
+// that non-portable size, else 8, else 0 (no cluster launch)
+int cluster_ctas_here()
+{
+    static int cached = -1;
+    if (cached >= 0) return cached;
+    cached = 0;
+    if (cudaFuncSetAttribute(k_mg_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        cudaGetLastError();
+    for (int n : {16, 8}) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(n);
+        cfg.blockDim = dim3(MGC_TH);
+        cfg.dynamicSmemBytes = (size_t)MG_COARSE_CELLS * 13 + 16;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = n;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, k_mg_cluster, &cfg) == cudaSuccess && clusters > 0) {
+            cached = n;
+            break;
+        }
+        cudaGetLastError();
+    }
+    return cached;
+}
+
 int vcycle(fs_ctx *c, MgState *s, int l, bool sample, cudaStream_t st)
 {
+    if (s->cl > 0 && l == s->cl) return launch_cluster(c, s, l, st);
     MgLevel &v = s->lev[l];
     const MgGrid &g = v.g;
     if (l == s->nlev - 1) {
-        k_mg_coarse<<<1, TH, coarse_smem(g), st>>>(g, v.fl, v.r, v.a, v.scale, v.mass, s->done);
+        k_mg_coarse<<<1, COARSE_TH, coarse_smem(g), st>>>(g, v.fl, v.r, v.a, v.scale, v.mass, s->done);
         c->n_launches += 1;
         return FS_OK;
     }
@@ -578,9 +826,7 @@ int vcycle(fs_ctx *c, MgState *s, int l, bool sample, cudaStream_t st)
         if (timed) prof_add(c, kind, e0, prof_mark(c), bytes);
     };
     // four elements per thread: every level but the coarsest has quad-aligned rows
-    const int dense = l == 0 ? 1 : 0;
-    const int nb = grid_blocks(c, v.nqa, TH);                    // the active quads
-    const int nbz = grid_blocks(c, dense ? g.n / 4 : v.nqa, TH);  // and all quads for the dense sweep
+    const int nb = grid_blocks(c, v.nqa, TH);  // the active quads
     MgLevel &w = s->lev[l + 1];
     begin();
     k_mg0_smooth2<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.b, v.scale, v.mass, done);
@@ -599,10 +845,10 @@ int vcycle(fs_ctx *c, MgState *s, int l, bool sample, cudaStream_t st)
     k_mg0_prolong<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.b, w.g, w.a, done);
     end(K_MG0_PROLONG, s->by0[3]);
     begin();
-    k_mg0_smooth<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.b, v.c, v.scale, v.mass, 0, done);
+    k_mg0_smooth<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.b, v.c, v.scale, v.mass, done);
     end(K_MG0_SMOOTH, s->by0[4]);
     begin();
-    k_mg0_smooth<<<nbz, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.c, v.a, v.scale, v.mass, dense, done);
+    k_mg0_smooth<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.c, v.a, v.scale, v.mass, done);
     end(K_MG0_SMOOTH_Z, s->by0[5]);
     c->n_launches += 3;
     FS_CUDA(cudaGetLastError());
@@ -666,33 +912,54 @@ int mg_build(fs_ctx *c, MgState *s, const MgGrid &g0, uint8_t *fl0, float *b0, f
     }
     // the lists of active quads (every level but the coarsest) and of active
     // restriction pairs (every level but the finest): counted, allocated, filled
-    int *icnt = reinterpret_cast<int *>(c->partials);
     auto make_list = [&](bool pairs, int l, int **list, int *count) -> int {
         const MgGrid &g = s->lev[l].g;
         const long long items = pairs ? (long long)((g.nx + 1) >> 1) * g.ny * g.nz : g.n / 4;
-        const int blocks = grid_blocks(c, items, TH);
-        for (int pass = 0; pass < 2; pass++) {
-            FS_CUDA(cudaMemsetAsync(icnt, 0, sizeof(int), c->stream));
-            if (pairs)
-                k_mg_list_pairs<<<blocks, TH, 0, c->stream>>>(g, s->lev[l].fl, pass ? *list : nullptr, icnt);
-            else
-                k_mg_list_quads<<<blocks, TH, 0, c->stream>>>(g, s->lev[l].fl, pass ? *list : nullptr, icnt);
-            c->n_launches += 1;
-            FS_CUDA(cudaGetLastError());
-            int n = 0;
-            FS_CUDA(cudaMemcpyAsync(&n, icnt, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-            FS_CUDA(cudaStreamSynchronize(c->stream));
-            if (pass == 0) {
-                *count = n;
-                if (cudaMalloc(list, sizeof(int) * (size_t)std::max(n, 1)) != cudaSuccess) {
-                    *list = nullptr;
-                    return FS_ENOMEM;
-                }
-            } else if (n != *count) {
-                return set_error(FS_ECUDA, "multigrid: active lists of level %d disagree", l);
-            }
+        const int blocks = (int)std::max(1LL, (items + LB_ITEMS - 1) / LB_ITEMS);
+        int *dcnt = nullptr;
+        std::vector<int> hcnt(blocks);
+        if (cudaMalloc(&dcnt, sizeof(int) * (size_t)blocks * 2) != cudaSuccess) {
+            cudaGetLastError();
+            return FS_ENOMEM;
         }
-        return FS_OK;
+        auto launch = [&](const int *offs, int *out) {
+            if (pairs)
+                k_list_build<<<blocks, LB_TH, 0, c->stream>>>(PairPred{g, s->lev[l].fl}, offs, dcnt, out);
+            else
+                k_list_build<<<blocks, LB_TH, 0, c->stream>>>(QuadPred{g, s->lev[l].fl}, offs, dcnt, out);
+            c->n_launches += 1;
+        };
+        int rc = FS_OK;
+        launch(nullptr, nullptr);
+        if ((rc = check_cuda(cudaGetLastError(), "k_list_build")) ||
+            (rc = check_cuda(cudaMemcpyAsync(hcnt.data(), dcnt, sizeof(int) * (size_t)blocks,
+                                             cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync")) ||
+            (rc = check_cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize"))) {
+            cudaFree(dcnt);
+            return rc;
+        }
+        int total = 0;
+        for (int b = 0; b < blocks; b++) {  // exclusive scan of the block counts
+            const int n = hcnt[b];
+            hcnt[b] = total;
+            total += n;
+        }
+        *count = total;
+        if (cudaMalloc(list, sizeof(int) * (size_t)std::max(total, 1)) != cudaSuccess) {
+            cudaGetLastError();
+            *list = nullptr;
+            cudaFree(dcnt);
+            return FS_ENOMEM;
+        }
+        if (!(rc = check_cuda(cudaMemcpyAsync(dcnt + blocks, hcnt.data(), sizeof(int) * (size_t)blocks,
+                                              cudaMemcpyHostToDevice, c->stream), "cudaMemcpyAsync"))) {
+            launch(dcnt + blocks, *list);
+            rc = check_cuda(cudaGetLastError(), "k_list_build");
+        }
+        // the host counts must outlive the copy above
+        if (!rc) rc = check_cuda(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+        cudaFree(dcnt);
+        return rc;
     };
     for (int l = 0; l < s->nlev; l++) {
         MgLevel &v = s->lev[l];
@@ -705,11 +972,21 @@ int mg_build(fs_ctx *c, MgState *s, const MgGrid &g0, uint8_t *fl0, float *b0, f
             return rc;
         }
     }
+    // the small levels in one cluster launch: from the first level below level 0
+    // whose active quads fit the cluster's threads a few times over, when at
+    // least one level above the coarsest is among them
+    s->cl = 0;
+    s->ctas = cluster_ctas_here();
+    if (s->ctas > 0)
+        for (int l = 1; l + 1 < s->nlev; l++)
+            if (s->lev[l].nqa <= MGC_MAX_QUADS && s->nlev - l <= MGC_MAXLEV) {
+                s->cl = l;
+                break;
+            }
     // The least each level-0 kernel must move (its algorithmic bytes): the list
-    // entry and the flags of each active quad (or pair) it visits, every flag byte
-    // of an array it scans whole, 4 bytes per unknown for each vector it reads or
-    // writes on the unknowns, and the whole of a vector it writes densely.
-    // n0: elements of level 0; q0: its active quads; p1: level 1's active pairs;
+    // entry and the flags of each active quad (or pair) it visits and 4 bytes per
+    // unknown for each vector it reads or writes on the unknowns.
+    // q0: the active quads of level 0; p1: level 1's active pairs;
     // u0, u1: the unknowns of levels 0 and 1.
     unsigned long long *cnt = reinterpret_cast<unsigned long long *>(c->partials), nl[2] = {0, 0};
     FS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(nl), c->stream));
@@ -718,14 +995,14 @@ int mg_build(fs_ctx *c, MgState *s, const MgGrid &g0, uint8_t *fl0, float *b0, f
         k_mg_count_liq<<<grid_blocks(c, s->lev[1].g.n, TH), TH, 0, c->stream>>>(s->lev[1].g, s->lev[1].fl, cnt + 1);
     FS_CUDA(cudaMemcpyAsync(nl, cnt, sizeof(nl), cudaMemcpyDeviceToHost, c->stream));
     FS_CUDA(cudaStreamSynchronize(c->stream));
-    const double n0 = (double)g0.n, u0 = (double)nl[0], u1 = (double)nl[1];
+    const double u0 = (double)nl[0], u1 = (double)nl[1];
     const double q0 = (double)s->lev[0].nqa, p1 = s->nlev > 1 ? (double)s->lev[1].npa : 0.0;
     s->by0[0] = 8.0 * q0 + 8.0 * u0;             // smooth2: read r, write e
     s->by0[1] = 8.0 * q0 + 12.0 * u0;            // residual: read r, e, write res
     s->by0[2] = 6.0 * p1 + 4.0 * u0 + 4.0 * u1;  // restrict: pair list and flags, read res, write level-1 r
     s->by0[3] = 8.0 * q0 + 8.0 * u0 + 4.0 * u1;  // prolong: read and write e, read the level-1 e
     s->by0[4] = 8.0 * q0 + 12.0 * u0;            // smooth: read r, e, write e
-    s->by0[5] = n0 + 4.0 * q0 + 8.0 * u0 + 4.0 * n0;  // last smooth: every flag, read r, e, write z densely
+    s->by0[5] = 8.0 * q0 + 12.0 * u0;            // last smooth: read r, e, write z
     s->epoch = c->mask_epoch;
     s->coef = coef;
     return FS_OK;
@@ -861,6 +1138,30 @@ void mg_count(fs_ctx *c, long long vcycles, bool faces)
         prof_count(c, id, k);
     prof_count(c, faces ? K_MG_VCYCLE_V : K_MG_VCYCLE_P, vcycles);
     if (!faces) prof_count(c, K_MG_COARSE, vcycles);
+}
+
+// r.z over the active quads of the pressure hierarchy's level 0 (or of the three
+// face volumes'); false when the hierarchy has no lists (a level 0 that is its
+// own coarsest level), and the caller takes the dense pass
+bool mg_rz(fs_ctx *c, bool faces, const float *r, const float *z, int first, SolveScal *s)
+{
+    const MgAll *m = static_cast<const MgAll *>(c->mg);
+    if (!m) return false;
+    RzLists L;
+    std::memset(&L, 0, sizeof(L));
+    long long total = 0;
+    L.nv = faces ? 3 : 1;
+    for (int v = 0; v < L.nv; v++) {
+        const MgState &h = faces ? m->face[v] : m->cell;
+        if (h.nlev < 2 || h.epoch != c->mask_epoch || !h.lev[0].ql) return false;
+        L.ql[v] = h.lev[0].ql;
+        L.n[v] = h.lev[0].nqa;
+        L.base[v] = faces ? (long long)c->L.face_origin(v) - c->L.PL : 0;
+        total += L.n[v];
+    }
+    k_mg_rz<<<grid_blocks(c, total, TH), TH, 0, c->stream>>>(L, r, z, first, s, c->partials);
+    c->n_launches += 1;
+    return cudaPeekAtLastError() == cudaSuccess;
 }
 
 int mg_levels(const fs_ctx *c)

@@ -762,6 +762,12 @@ static int pcg_iterate(fs_ctx *c, SolveScal &h)
     auto apply_m = [&]() -> int {
         return c->prm.precond == FS_PRECOND_MG ? mg_apply(c, c->pr, c->pz, &s->done) : mic0_apply(c, c->pr, c->pz);
     };
+    // r.z: over the V-cycle's active quads with multigrid, else a dense pass
+    auto rz = [&](int first) {
+        if (!(c->prm.precond == FS_PRECOND_MG && mg_rz(c, false, c->pr, c->pz, first, s)))
+            k_rz<<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(c->pr, c->pz, n4, first, s, c->partials);
+        c->n_launches += 1;
+    };
     if (jac)
         k_pois_init<true><<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(
             c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, n4, tol2, c->prm.maxit_p, s, c->partials);
@@ -774,8 +780,7 @@ static int pcg_iterate(fs_ctx *c, SolveScal &h)
         int rc = apply_m();
         if (rc) return rc;
         if ((rc = remove_null_mode(c, c->pz))) return rc;
-        k_rz<<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(c->pr, c->pz, n4, 1, s, c->partials);
-        c->n_launches += 1;
+        rz(1);
     }
     c->n_launches += 1;
     FS_CUDA(cudaGetLastError());
@@ -827,8 +832,7 @@ static int pcg_iterate(fs_ctx *c, SolveScal &h)
                 int rc = apply_m();
                 if (rc) return rc;
                 if ((rc = remove_null_mode(c, c->pz))) return rc;
-                k_rz<<<b4, TH, 0, c->stream>>>(c->pr, c->pz, n4, 0, s, c->partials);
-                c->n_launches += 1;
+                rz(0);
             }
             cur ^= 1;
         }
@@ -1033,7 +1037,8 @@ int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st)
     // z = M r and r.z (first: beta = 0)
     auto precondition = [&](int first) -> int {
         if (int rc = mg_apply_faces(c, c->vr, c->vz, cc, &s->done)) return rc;
-        k_rz<<<b4, TH, 0, c->stream>>>(c->vr, c->vz, n4, first, s, c->partials);
+        if (!mg_rz(c, true, c->vr, c->vz, first, s))  // over the active quads, else a dense pass
+            k_rz<<<b4, TH, 0, c->stream>>>(c->vr, c->vz, n4, first, s, c->partials);
         c->n_launches += 1;
         FS_CUDA(cudaGetLastError());
         return FS_OK;
