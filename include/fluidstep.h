@@ -151,8 +151,10 @@ typedef struct {
     int iters_v;           /* viscosity iterations, summed over the call's solves */
     double relres_p;       /* last pressure solve: recursive |r|/|b| at exit */
     double relres_v;       /* last viscosity solve: recursive |r|/|b| at exit */
-    double true_relres_p;  /* last pressure solve: |b - A q|/|b| recomputed at exit in FP64
-                              (A q of the FP32 pressure, b - A q and both norms in FP64) */
+    double true_relres_p;  /* last pressure solve: |b - A q|/|b| recomputed at exit to FP64
+                              accuracy (b - A q of the FP32 pressure summed from its exact
+                              terms by cascaded error-free FP32 sums, the norms in
+                              compensated pairs merged in FP64) */
     int fallbacks;         /* pressure solves redone with MIC(0) after the learned one failed */
     int restarts_p;        /* refinement steps of the pressure solves (summed over the call):
                               when the recursive residual meets tol_p but the FP64 residual

@@ -240,39 +240,93 @@ __global__ void __launch_bounds__(TH) k_helm_init(const float *__restrict__ x, c
         init_scalars(s, tot[0], tot[1], tot[2], tol2, maxit);
 }
 
+// Error-free sum (Knuth's TwoSum): a + b = s + e exactly, s = fl(a + b).
+__device__ __forceinline__ float two_sum(float a, float b, float &e)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+    return s;
+}
+
+// A running sum carried as hi + lo + rest: each term enters by TwoSum into hi,
+// its error by TwoSum into lo, and that error into rest (cascaded summation, as
+// accurate as about three times the FP32 precision).
+struct Sum3 {
+    float hi = 0.f, lo = 0.f, rest = 0.f;
+    __device__ __forceinline__ void add(float v)
+    {
+        float e1, e2;
+        hi = two_sum(hi, v, e1);
+        lo = two_sum(lo, e1, e2);
+        rest += e2;
+    }
+};
+
+// A compensated sum of non-negligible terms given as pairs (h, l): h by TwoSum
+// into s, the errors and l into c.
+struct Sum2 {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float h, float l)
+    {
+        float e;
+        s = two_sum(s, h, e);
+        c += e + l;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 // |b - A x|^2 over the liquid -> s->aux[0] and |b|^2 -> s->aux[1], the final
-// convergence check. It is evaluated in FP64 throughout: A x of the FP32
-// iterate (integer stencil weights) and b - A x are then exact unless the
-// entries span more than about 2^29 in magnitude, and only the sums of squares
-// round. For a singular operator (liquid touching no air) the component along
-// the null vector (the constant), which no iterate can change, is left out:
-// sum e^2 - (sum e)^2 / N. With r_out, the residual is also stored, rounded once
-// to FP32, on the liquid (zero elsewhere, guard planes included): the right-hand
-// side of a refinement step. r_out may alias b: every thread reads b only at the
-// element it writes.
+// convergence check, to FP64 accuracy without FP64 arithmetic per element (this
+// GPU runs FP64 at a small fraction of its FP32 rate). The residual of the FP32
+// iterate, e = b - d x + sum of the six neighbours, is summed from its eight
+// exact terms (d x as a product and its FMA error) by cascaded error-free sums
+// (Sum3), so it is known to about 2^-70 of the terms' size, where FP64 would
+// round at 2^-53; it is then held as a pair e_hi + e_lo (48 significant bits of
+// e itself), squared as a pair (the product and its FMA error), and e^2, e and
+// b^2 are summed per thread in compensated pairs (Sum2), converted to FP64 and
+// merged in FP64 across the grid. For a singular operator (liquid touching no
+// air) the component along the null vector (the constant), which no iterate can
+// change, is left out: sum e^2 - (sum e)^2 / N. With r_out, the residual is also
+// stored, rounded once to FP32, on the liquid (zero elsewhere, guard planes
+// included): the right-hand side of a refinement step. r_out may alias b: every
+// thread reads b only at the element it writes.
 __global__ void __launch_bounds__(TH) k_pois_true_res(const float *b, const float *__restrict__ x,
                                                       const uint8_t *__restrict__ fl, int n, int P, int PL,
                                                       int singular, SolveScal *s, double *partials, float *r_out)
 {
-    double acc = 0.0, sum = 0.0, cnt = 0.0, bsq = 0.0;
+    Sum2 acc, sum, bsq;
+    int cnt = 0;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
         const uint8_t f = fl[t];
         if (!(f & CF_LIQ)) {
             if (r_out) r_out[t] = 0.f;
             continue;
         }
-        const double nb = ((double)x[t - 1] + (double)x[t + 1]) + ((double)x[t - P] + (double)x[t + P]) +
-                          ((double)x[t - PL] + (double)x[t + PL]);
-        const double ax = (double)PoisOp::diag(f, 0.f) * (double)x[t] - nb;
-        const double bv = (double)b[t];
-        const double e = bv - ax;
-        if (r_out) r_out[t] = (float)e;
-        acc += e * e;
-        sum += e;
-        cnt += 1.0;
-        bsq += bv * bv;
+        const float d = PoisOp::diag(f, 0.f), xc = x[t], bv = b[t];
+        const float dx = d * xc, dxe = fmaf(d, xc, -dx);  // d x = dx + dxe exactly
+        Sum3 r;
+        r.add(bv);
+        r.add(-dx);
+        r.add(-dxe);
+        r.add(x[t - 1]);
+        r.add(x[t + 1]);
+        r.add(x[t - P]);
+        r.add(x[t + P]);
+        r.add(x[t - PL]);
+        r.add(x[t + PL]);
+        float el;
+        const float eh = two_sum(r.hi, r.lo, el);
+        el += r.rest;  // e = eh + el
+        if (r_out) r_out[t] = eh + el;
+        const float sq = eh * eh;
+        acc.add(sq, fmaf(eh, eh, -sq) + 2.f * eh * el);
+        sum.add(eh, el);
+        const float bb = bv * bv;
+        bsq.add(bb, fmaf(bv, bv, -bb));
+        cnt += 1;
     }
-    double v[4] = {acc, sum, cnt, bsq}, tot[4];
+    double v[4] = {acc.value(), sum.value(), (double)cnt, bsq.value()}, tot[4];
     if (grid_reduce<4>(v, partials, &s->ticket, tot) && threadIdx.x == 0) {
         s->aux[0] = (singular && tot[2] > 0.0) ? fmax(0.0, tot[0] - tot[1] * tot[1] / tot[2]) : tot[0];
         s->aux[1] = tot[3];
