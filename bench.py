@@ -57,6 +57,11 @@ NCU_TRAFFIC = {
     # when the kernel ends are not counted
     "visc_spmv": {"bytes_per_launch": 342685440 + 134320896, "source": "5e31bb1c3ef8787b"},
     "visc_update": {"bytes_per_launch": 387683584 + 125340416, "source": "5e31bb1c3ef8787b"},
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_mg0_smooth2 on the
+    # benchmark's 256^3 blob, one level-0 launch (profiles/mg0_kernels_256_ncu.md); the entry
+    # names its own files: the V-cycle kernels and the mask layout they read
+    "mg0_smooth2": {"bytes_per_launch": 50603776 + 3720704, "source": "4cfc780494228df8",
+                    "files": ("fs_mg.cu", "fs_mask.cu")},
 }
 KERNEL_FILES = ("fs_stencil.cuh", "fs_tma.cuh", "fs_mask.cu")
 
@@ -144,7 +149,8 @@ def roofline_of(prof, peaks, src_hash, traffic_table=None):
     name, (launches, ms, by, alln) = top
     achieved = (by / launches) / (ms / launches * 1e-3) / 1e9
     tr = traffic_table.get(name)
-    traffic = tr["bytes_per_launch"] if tr and tr.get("source") == src_hash else None
+    want = source_hash(tr["files"]) if tr and "files" in tr else src_hash
+    traffic = tr["bytes_per_launch"] if tr and tr.get("source") == want else None
     return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": traffic,
             "algorithmic_bytes_per_launch": by / launches, "launches": launches, "launches_all": alln,

@@ -217,8 +217,20 @@ int fs_step(fs_ctx *c, const fs_mac *u_in, fs_mac *u_out, fs_mac *u_visc, fs_sta
 
 /* Pressure projection alone (Sec. 3.2.2, Poisson pressure equation), in place on u.
  * q_out: nullable DEVICE cell array (library layout) receiving q, where the
- * pressure is p = rho * q / dt (q is mean-free when the operator is singular). */
+ * pressure is p = rho * q / dt (q is mean-free when the operator is singular).
+ * After a refined solve the solver keeps q as a pair of FP32 terms
+ * (fs_pressure_pair); q_out is their sum rounded to FP32. */
 int fs_project(fs_ctx *c, fs_mac *u, float *q_out, fs_stats *st);
+
+/* The last projection's q as the pair of FP32 terms the solver keeps it in,
+ * q = q_hi + q_lo (the paper has no counterpart: a precision detail of this
+ * solver). After an iterative refinement (fs_stats.restarts_p > 0) the pair is the
+ * first solution and the sum of the corrections, which q_out rounds to one FP32
+ * value; otherwise q_lo = 0. fs_stats.true_relres_p is the residual of the pair.
+ * q_hi, q_lo: DEVICE cell arrays in the library layout (as q_out of fs_project),
+ * must not alias. Before any solve both read zero. FS_EINVAL for a NULL or aliased
+ * array, FS_ESTATE before fs_set_mask. */
+int fs_pressure_pair(fs_ctx *c, float *q_hi, float *q_lo);
 
 /* Reverse mode of fs_step (derived from the step; Sec. 3.4.2 optimises through
  * it). Given the step input u_in and the cotangent g_out = dL/du_out, writes

@@ -722,6 +722,15 @@ int fs_net_adam(fs_ctx *c, double lr, double beta1, double beta2, double eps, in
     return net_adam(c, lr, beta1, beta2, eps, step, grad_scale, fix_offsets);
 }
 
+int fs_pressure_pair(fs_ctx *c, float *q_hi, float *q_lo)
+{
+    int rc = need_mask(c);
+    if (rc) return rc;
+    if (!q_hi || !q_lo) return set_error(FS_EINVAL, "NULL argument");
+    if (q_hi == q_lo) return set_error(FS_EINVAL, "q_hi and q_lo must not alias");
+    return pressure_pair(c, q_hi, q_lo);
+}
+
 int fs_adam_update(fs_ctx *c, float *p, const float *g, float *m, float *v, long long n, double lr, double beta1,
                    double beta2, double eps, int step, double grad_scale)
 {

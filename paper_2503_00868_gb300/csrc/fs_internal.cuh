@@ -206,6 +206,15 @@ __device__ __forceinline__ double warp_sum(double v)
 
 // Compensated FP32 accumulation (Kahan): keeps per-thread partial sums of FP32
 // products accurate to about one FP32 rounding before the FP64 tree.
+// Error-free sum (Knuth's TwoSum): a + b = s + e exactly, s = fl(a + b).
+__device__ __forceinline__ float two_sum(float a, float b, float &e)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+    return s;
+}
+
 struct KSum {
     float s = 0.f, c = 0.f;
     __device__ __forceinline__ void add(float x)
@@ -390,6 +399,7 @@ int mg_apply_faces(fs_ctx *c, const float *r, float *z, float cc, const int *don
 void mg_free(fs_ctx *c);
 void mg_count(fs_ctx *c, long long vcycles, bool faces);  // fs_mg.cu: launch counts for fs_profile
 int mg_levels(const fs_ctx *c);
+int pressure_pair(fs_ctx *c, float *q_hi, float *q_lo);  // fs_pcg.cu
 bool mg_rz(fs_ctx *c, bool faces, const float *r, const float *z, int first, SolveScal *s);  // fs_mg.cu
 // fs_splat.cu
 int splat_render(fs_ctx *c, int n, const float *x, const float *op, const float *A, const float *col,

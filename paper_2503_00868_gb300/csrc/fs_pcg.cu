@@ -240,15 +240,6 @@ __global__ void __launch_bounds__(TH) k_helm_init(const float *__restrict__ x, c
         init_scalars(s, tot[0], tot[1], tot[2], tol2, maxit);
 }
 
-// Error-free sum (Knuth's TwoSum): a + b = s + e exactly, s = fl(a + b).
-__device__ __forceinline__ float two_sum(float a, float b, float &e)
-{
-    const float s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-    return s;
-}
-
 // A running sum carried as hi + lo + rest: each term enters by TwoSum into hi,
 // its error by TwoSum into lo, and that error into rest (cascaded summation, as
 // accurate as about three times the FP32 precision).
@@ -950,9 +941,9 @@ static int solve_pressure_once(fs_ctx *c, fs_stats *st)
         if (rc) break;
         iters += h.iter;
         if (h.status != FS_OK) break;
-        // the FP64 check of this pass's system (b0 and x, then each correction's);
-        // its residual, rounded once to FP32, is the next correction's right-hand
-        // side, stored in pbr (in place from the second pass on)
+        // the check of this pass's system (b0 and x, then each correction's); its
+        // residual, rounded once to FP32, is the next correction's right-hand side,
+        // stored in pbr (in place from the second pass on)
         k_pois_true_res<<<bs, TH, 0, c->stream>>>(c->pb, c->px, c->cflag, L.nC, L.P, L.PL, c->singular,
                                                   c->scal + 2, c->partials, c->pbr);
         c->n_launches += 1;
@@ -1237,6 +1228,25 @@ int precond_apply_public(fs_ctx *c, const float *r, float *z)
         return set_error(FS_ETIMEOUT, "MIC(0) sweep: a wait on a predecessor tile ran out");
     }
     if (herr & 8u) return set_error(FS_ETIMEOUT, "network: a wait for the tensor-core MMAs ran out");
+    return FS_OK;
+}
+
+// the pressure as its two FP32 terms, public layout (q2 nullable: zeros)
+__global__ void __launch_bounds__(TH) k_pair_out(const float *__restrict__ q, const float *__restrict__ q2, float *hi,
+                                                 float *lo, Layout L)
+{
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < L.S; idx += gridDim.x * blockDim.x) {
+        hi[idx] = q[L.PL + idx];
+        lo[idx] = q2 ? q2[L.PL + idx] : 0.f;
+    }
+}
+
+int pressure_pair(fs_ctx *c, float *q_hi, float *q_lo)
+{
+    const Layout &L = c->L;
+    k_pair_out<<<grid_blocks(c, L.S, TH), TH, 0, c->stream>>>(c->px, c->q_head, q_hi, q_lo, L);
+    c->n_launches += 1;
+    FS_CUDA(cudaGetLastError());
     return FS_OK;
 }
 

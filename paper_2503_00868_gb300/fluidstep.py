@@ -116,6 +116,7 @@ _SIGS = {
                     C.c_int),
     "fs_adam_update": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_double,
                         C.c_double, C.c_double, C.c_double, C.c_int, C.c_double], C.c_int),
+    "fs_pressure_pair": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "fs_net_train_step": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_int,
                            C.POINTER(C.c_double)], C.c_int),
     "fs_project_noalloc": ([C.c_int, C.c_int, C.c_int, C.c_void_p, C.POINTER(fs_mac), C.c_void_p, C.c_double,
@@ -221,6 +222,11 @@ def fs_project(ctx: int, u: Mac, q_out: Optional[torch.Tensor] = None):
     q = C.c_void_p(q_out.data_ptr()) if q_out is not None else None
     rc = _check(load().fs_project(C.c_void_p(ctx), _ref(_mac(u)), q, C.byref(st)))
     return rc, st.as_dict()
+
+
+def fs_pressure_pair(ctx: int, q_hi: torch.Tensor, q_lo: torch.Tensor) -> None:
+    """The last projection's q as its two FP32 terms (cell arrays, library layout)."""
+    _check(load().fs_pressure_pair(C.c_void_p(ctx), _cell(q_hi), _cell(q_lo)), (FS_OK,))
 
 
 def fs_adjoint_step(ctx: int, u_in: Mac, u_visc: Optional[Mac], g_out: Mac, g_in: Mac):

@@ -66,3 +66,13 @@ def test_kernel_table_and_family():
     assert fam["achieved"] == pytest.approx((6.0e8) / (0.4e-3) / 1e9)      # 1500 GB/s
     assert fam["frac"] == pytest.approx(1500.0 / 4000.0)
     assert bench.family_roofline({"all_kernels": (1, 0.0, 0.0)}, None) is None
+
+
+def test_traffic_entry_with_its_own_files():
+    # an entry that names its files is matched against their hash, not the global one
+    good = bench.source_hash(("fs_mg.cu", "fs_mask.cu"))
+    prof = {"mg0_smooth2": (3, 0.09, 3 * 6.7e7, 100)}
+    table = {"mg0_smooth2": {"bytes_per_launch": 5, "source": good, "files": ("fs_mg.cu", "fs_mask.cu")}}
+    assert bench.roofline_of(prof, None, "other", traffic_table=table)["traffic"] == 5
+    table["mg0_smooth2"]["source"] = "0" * 16
+    assert bench.roofline_of(prof, None, good, traffic_table=table)["traffic"] is None
