@@ -375,6 +375,43 @@ __device__ __forceinline__ bool grid_reduce(KSum (&v)[K], double *partials, unsi
     return true;
 }
 
+// grid_reduce over the blocks of several launches that run at once (the face
+// volumes' V-cycles on their streams): this block is number `block` of `nblocks`
+// in all; the partials are merged in that order by the last block to arrive, in
+// whichever launch it is.
+template <int K>
+__device__ __forceinline__ bool multi_reduce(KSum (&v)[K], double *partials, unsigned *ticket, double (&tot)[K],
+                                             int block, int nblocks)
+{
+    __shared__ int last;
+    float2 *pp = reinterpret_cast<float2 *>(partials);
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x, nthr = blockDim.x * blockDim.y;
+    if (ks_block<K>(v) && tid == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k++) pp[(size_t)block * K + k] = make_float2(v[k].s, v[k].c);
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == (unsigned)nblocks - 1;
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = KSum();
+    for (int b = tid; b < nblocks; b += nthr)
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const float2 q = __ldcg(&pp[(size_t)b * K + k]);
+            ks_merge(v[k].s, v[k].c, q.x, q.y);
+        }
+    __syncthreads();  // the shared staging of ks_block is reused
+    if (ks_block<K>(v) && tid == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k++) tot[k] = (double)v[k].s - (double)v[k].c;
+        *ticket = 0u;
+    }
+    return true;
+}
+
 // ---- launchers implemented in the .cu files --------------------------------
 // fs_mask.cu
 int build_mask(fs_ctx *c, const uint8_t *types_dense, const fs_mac *bc);
@@ -401,6 +438,12 @@ void mg_count(fs_ctx *c, long long vcycles, bool faces);  // fs_mg.cu: launch co
 int mg_levels(const fs_ctx *c);
 int pressure_pair(fs_ctx *c, float *q_hi, float *q_lo);  // fs_pcg.cu
 bool mg_rz(fs_ctx *c, bool faces, const float *r, const float *z, int first, SolveScal *s);  // fs_mg.cu
+// z = M r with r.z formed in the V-cycle's last level-0 sweep (beta = rz_new / rz,
+// first: beta = 0, as k_rz); false when the hierarchy has no such sweep (a level
+// 0 that is its own coarsest level): then z is formed but r.z is not
+bool mg_apply_rz(fs_ctx *c, const float *r, float *z, const int *done, SolveScal *s, int first, int &rc);
+bool mg_apply_faces_rz(fs_ctx *c, const float *r, float *z, float cc, const int *done, SolveScal *s, int first,
+                       int &rc);
 // fs_splat.cu
 int splat_render(fs_ctx *c, int n, const float *x, const float *op, const float *A, const float *col,
                  const float *sh, int deg, const fs_camera *cam, float *rgb, float *T);

@@ -88,6 +88,9 @@ struct MgState {
     bool own0 = true;      // level 0 work arrays belong to this hierarchy
     const int *done = nullptr;  // the calling solve's convergence flag (nullable)
     int cl = 0;                 // first level of the single-cluster launch (0: none)
+    // r.z in the last level-0 sweep of the current apply (rzs null: not formed)
+    SolveScal *rzs = nullptr;
+    int rz_first = 0, rz_boff = 0, rz_btot = 0;
     int ctas = 0;               // CTAs of that cluster
     long long calls = 0;        // applies so far (profiling samples every prof_period-th)
     // algorithmic bytes of the level-0 kernels, in the order of K_MG0_SMOOTH2 ..
@@ -184,10 +187,10 @@ __device__ __forceinline__ float ldv1(const float *p, int t)
         return __ldg(p + t);
 }
 
-// one damped Jacobi sweep on quad q: eout from ein
+// one damped Jacobi sweep on quad q: eout from ein; returns r.eout over the quad
 template <bool CG>
-__device__ __forceinline__ void smooth_q(const MgGrid &g, const uint8_t *__restrict__ fl, const float *r,
-                                         const float *ein, float *eout, const float *wt, float scale, float m, int q)
+__device__ __forceinline__ float smooth_q(const MgGrid &g, const uint8_t *__restrict__ fl, const float *r,
+                                          const float *ein, float *eout, const float *wt, float scale, float m, int q)
 {
     const int t = q << 2;
     const uchar4 f = ldf4(fl, t);
@@ -201,6 +204,7 @@ __device__ __forceinline__ void smooth_q(const MgGrid &g, const uint8_t *__restr
     v.z = sweep1(f.z, c.z, (c.y + c.w) + (dn.z + up.z) + (bk.z + fw.z), rv.z, wt, scale, m);
     v.w = sweep1(f.w, c.w, (c.z + rt) + (dn.w + up.w) + (bk.w + fw.w), rv.w, wt, scale, m);
     *reinterpret_cast<float4 *>(eout + t) = v;
+    return rv.x * v.x + rv.y * v.y + rv.z * v.z + rv.w * v.w;
 }
 
 // res = r - A e on quad q
@@ -333,15 +337,34 @@ __device__ __forceinline__ void restrict_pair(const MgGrid &gf, const float *res
 
 // ---- one launch per step ------------------------------------------------------
 
+// One sweep over the active quads. With rzs (the last sweep of a V-cycle's level
+// 0), it also forms r.eout, which is the solver's r.z: each block's compensated
+// sum goes to the partials as block boff + blockIdx.x of btot (the blocks of the
+// face volumes' launches together), and the last block to arrive sets beta =
+// rz_new / rz (first: 0) and rz, as the solver's separate r.z pass does.
 __global__ void __launch_bounds__(256) k_mg0_smooth(MgGrid g, const int *__restrict__ qlist, int na,
                                                     const uint8_t *__restrict__ fl, const float *__restrict__ r,
                                                     const float *__restrict__ ein, float *eout, float scale, float m,
-                                                    const int *done)
+                                                    const int *done, SolveScal *rzs, double *partials, int first,
+                                                    int boff, int btot)
 {
     if (done && *(volatile const int *)done) return;  // the solve has converged
     __shared__ float wt[8];
     fill_wtab(wt, scale, m);
-    MG_FOR_LIST(qlist, na) smooth_q<false>(g, fl, r, ein, eout, wt, scale, m, q);
+    KSum acc;
+    MG_FOR_LIST(qlist, na) acc.add(smooth_q<false>(g, fl, r, ein, eout, wt, scale, m, q));
+    if (!rzs || *(volatile const int *)&rzs->done) return;  // (a timed sweep runs after convergence too)
+    KSum v[1] = {acc};
+    double tot[1];
+    if (multi_reduce<1>(v, partials, &rzs->ticket, tot, boff + (int)blockIdx.x, btot) && threadIdx.x == 0) {
+        if (!isfinite(tot[0])) {
+            rzs->done = 1;
+            rzs->status = FS_ENONFINITE;
+            return;
+        }
+        rzs->beta = first ? 0.0 : tot[0] / rzs->rz;
+        rzs->rz = tot[0];
+    }
 }
 
 __global__ void __launch_bounds__(256) k_mg0_residual(MgGrid g, const int *__restrict__ qlist, int na,
@@ -845,10 +868,13 @@ int vcycle(fs_ctx *c, MgState *s, int l, bool sample, cudaStream_t st)
     k_mg0_prolong<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.b, w.g, w.a, done);
     end(K_MG0_PROLONG, s->by0[3]);
     begin();
-    k_mg0_smooth<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.b, v.c, v.scale, v.mass, done);
+    k_mg0_smooth<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.b, v.c, v.scale, v.mass, done, nullptr, nullptr,
+                                    0, 0, 0);
     end(K_MG0_SMOOTH, s->by0[4]);
     begin();
-    k_mg0_smooth<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.c, v.a, v.scale, v.mass, done);
+    SolveScal *rzs = l == 0 ? s->rzs : nullptr;  // r.z of the solver in the last level-0 sweep
+    k_mg0_smooth<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.c, v.a, v.scale, v.mass, done, rzs, c->partials,
+                                    s->rz_first, s->rz_boff, s->rz_btot);
     end(K_MG0_SMOOTH_Z, s->by0[5]);
     c->n_launches += 3;
     FS_CUDA(cudaGetLastError());
@@ -1008,9 +1034,14 @@ int mg_build(fs_ctx *c, MgState *s, const MgGrid &g0, uint8_t *fl0, float *b0, f
     return FS_OK;
 }
 
-int apply_on(fs_ctx *c, MgState *s, const float *r, float *z, const int *done, bool sample, cudaStream_t st)
+int apply_on(fs_ctx *c, MgState *s, const float *r, float *z, const int *done, bool sample, cudaStream_t st,
+             SolveScal *rzs = nullptr, int first = 0, int boff = 0, int btot = 0)
 {
     s->done = done;
+    s->rzs = rzs;
+    s->rz_first = first;
+    s->rz_boff = boff;
+    s->rz_btot = btot;
     MgLevel &l0 = s->lev[0];
     l0.r = const_cast<float *>(r);
     l0.a = z;
@@ -1050,26 +1081,47 @@ void mg_free(fs_ctx *c)
 }
 
 // z = M r on the cell space (r and z of length nC, zero off the liquid).
-int mg_apply(fs_ctx *c, const float *r, float *z, const int *done)
+// z = M r on the cell space; with rzs, r.z in the last level-0 sweep when the
+// hierarchy has one (*fused tells)
+static int apply_cell(fs_ctx *c, const float *r, float *z, const int *done, SolveScal *rzs, int first, bool *fused)
 {
+    if (fused) *fused = false;
     MgAll *m = state(c);
     if (!m) return set_error(FS_ENOMEM, "host allocation failed");
     const Layout &L = c->L;
     if (m->cell.epoch != c->mask_epoch)
         if (int rc = mg_build(c, &m->cell, level0_grid(L, L.nx, L.ny, L.nz), c->cflag, nullptr, nullptr, 1.f, 0.f))
             return rc;
+    const bool fuse = rzs && m->cell.nlev >= 2;
     const bool sample = c->prof_on && (m->cell.calls++ % std::max(1, c->prof_period)) == 0;
     cudaEvent_t e0 = sample ? prof_mark(c) : nullptr;
-    const int rc = apply_on(c, &m->cell, r, z, done, sample, c->stream);
+    const int rc = fuse ? apply_on(c, &m->cell, r, z, done, sample, c->stream, rzs, first, 0,
+                                   grid_blocks(c, m->cell.lev[0].nqa, TH))
+                        : apply_on(c, &m->cell, r, z, done, sample, c->stream);
     if (sample) prof_add(c, K_MG_VCYCLE_P, e0, prof_mark(c), 0.0);
+    if (fused) *fused = fuse && rc == FS_OK;
     return rc;
+}
+
+int mg_apply(fs_ctx *c, const float *r, float *z, const int *done)
+{
+    return apply_cell(c, r, z, done, nullptr, 0, nullptr);
+}
+
+bool mg_apply_rz(fs_ctx *c, const float *r, float *z, const int *done, SolveScal *s, int first, int &rc)
+{
+    bool fused = false;
+    rc = apply_cell(c, r, z, done, s, first, &fused);
+    return fused;
 }
 
 // z = M r on the face space for the Helmholtz operator I + cc L of the viscosity
 // solve, one V-cycle per velocity component (r and z of length nF, zero off the
 // unknown faces). With `done` set, every kernel returns at once once *done != 0.
-int mg_apply_faces(fs_ctx *c, const float *r, float *z, float cc, const int *done)
+static int apply_faces(fs_ctx *c, const float *r, float *z, float cc, const int *done, SolveScal *rzs, int first,
+                       bool *fused)
 {
+    if (fused) *fused = false;
     MgAll *m = state(c);
     if (!m) return set_error(FS_ENOMEM, "host allocation failed");
     const Layout &L = c->L;
@@ -1108,6 +1160,15 @@ int mg_apply_faces(fs_ctx *c, const float *r, float *z, float cc, const int *don
             s.coef = cc;
         }
     }
+    // r.z in the three last level-0 sweeps together: their blocks are numbered
+    // one after another for one reduction (volume k's from boff[k])
+    bool fuse = rzs != nullptr;
+    int boff[3] = {0, 0, 0}, btot = 0;
+    for (int k = 0; k < 3 && fuse; k++) {
+        fuse = m->face[k].nlev >= 2;
+        boff[k] = btot;
+        btot += grid_blocks(c, m->face[k].lev[0].nqa, TH);
+    }
     // volume 0 on the context's stream, 1 and 2 beside it (their sweeps share the
     // GPU, so none is timed alone: the profiled sweep is the pressure V-cycle's)
     FS_CUDA(cudaEventRecord(m->fork, c->stream));
@@ -1115,14 +1176,30 @@ int mg_apply_faces(fs_ctx *c, const float *r, float *z, float cc, const int *don
     for (int k = 2; k >= 0; k--) {
         const size_t base = (size_t)L.face_origin(k) - L.PL;
         cudaStream_t st = k == 0 ? c->stream : m->side[k - 1];
-        if (int rc = apply_on(c, &m->face[k], r + base, z + base, done, false, st)) return rc;
+        const int rc = fuse ? apply_on(c, &m->face[k], r + base, z + base, done, false, st, rzs, first, boff[k], btot)
+                            : apply_on(c, &m->face[k], r + base, z + base, done, false, st);
+        if (rc) return rc;
     }
     for (int k = 0; k < 2; k++) {
         FS_CUDA(cudaEventRecord(m->join[k], m->side[k]));
         FS_CUDA(cudaStreamWaitEvent(c->stream, m->join[k], 0));
     }
     if (sample) prof_add(c, K_MG_VCYCLE_V, e0, prof_mark(c), 0.0);
+    if (fused) *fused = fuse;
     return FS_OK;
+}
+
+int mg_apply_faces(fs_ctx *c, const float *r, float *z, float cc, const int *done)
+{
+    return apply_faces(c, r, z, cc, done, nullptr, 0, nullptr);
+}
+
+bool mg_apply_faces_rz(fs_ctx *c, const float *r, float *z, float cc, const int *done, SolveScal *s, int first,
+                       int &rc)
+{
+    bool fused = false;
+    rc = apply_faces(c, r, z, cc, done, s, first, &fused);
+    return fused;
 }
 
 // Launch counts of the level-0 kernels (fs_profile): `vcycles` V-cycles that did

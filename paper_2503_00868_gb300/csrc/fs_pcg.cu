@@ -813,6 +813,19 @@ static int pcg_iterate(fs_ctx *c, SolveScal &h)
             k_rz<<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(c->pr, c->pz, n4, first, s, c->partials);
         c->n_launches += 1;
     };
+    // z = M r and r.z: with multigrid (and no null mode to remove from z) r.z is
+    // formed in the V-cycle's last sweep
+    auto precondition = [&](int first) -> int {
+        int rc = FS_OK;
+        if (c->prm.precond == FS_PRECOND_MG && !c->singular) {
+            if (mg_apply_rz(c, c->pr, c->pz, &s->done, s, first, rc) || rc) return rc;
+        } else {
+            if ((rc = apply_m())) return rc;
+            if ((rc = remove_null_mode(c, c->pz))) return rc;
+        }
+        rz(first);
+        return FS_OK;
+    };
     if (jac)
         k_pois_init<true><<<grid_blocks(c, n4, TH), TH, 0, c->stream>>>(
             c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, n4, tol2, c->prm.maxit_p, s, c->partials);
@@ -821,12 +834,8 @@ static int pcg_iterate(fs_ctx *c, SolveScal &h)
             c->pb, c->px, c->pr, c->pp[0], c->pp[1], c->cflag, n4, tol2, c->prm.maxit_p, s, c->partials);
     if (!c->refining)
         if (int rc = try_warm_start(c, jac)) return rc;
-    if (!jac) {
-        int rc = apply_m();
-        if (rc) return rc;
-        if ((rc = remove_null_mode(c, c->pz))) return rc;
-        rz(1);
-    }
+    if (!jac)
+        if (int rc = precondition(1)) return rc;
     c->n_launches += 1;
     FS_CUDA(cudaGetLastError());
     const int bs = grid_blocks(c, L.nC, TH);
@@ -873,12 +882,8 @@ static int pcg_iterate(fs_ctx *c, SolveScal &h)
             prof_add(c, K_P_SPMV, e0, e1, by_spmv);
             prof_add(c, K_P_UPDATE, e2, e3, by_upd);
             c->n_launches += 2;
-            if (!jac) {
-                int rc = apply_m();
-                if (rc) return rc;
-                if ((rc = remove_null_mode(c, c->pz))) return rc;
-                rz(0);
-            }
+            if (!jac)
+                if (int rc = precondition(0)) return rc;
             cur ^= 1;
         }
         launched += check;
@@ -1081,7 +1086,8 @@ int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st)
     FS_CUDA(cudaGetLastError());
     // z = M r and r.z (first: beta = 0)
     auto precondition = [&](int first) -> int {
-        if (int rc = mg_apply_faces(c, c->vr, c->vz, cc, &s->done)) return rc;
+        int rc = FS_OK;
+        if (mg_apply_faces_rz(c, c->vr, c->vz, cc, &s->done, s, first, rc) || rc) return rc;  // r.z in the V-cycle
         if (!mg_rz(c, true, c->vr, c->vz, first, s))  // over the active quads, else a dense pass
             k_rz<<<b4, TH, 0, c->stream>>>(c->vr, c->vz, n4, first, s, c->partials);
         c->n_launches += 1;
