@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(256) k_mg0_smooth(MgGrid g, const int *__restr
     }
 }
 
-__global__ void __launch_bounds__(256) k_mg0_residual(MgGrid g, const int *__restrict__ qlist, int na,
+__global__ void __launch_bounds__(256, 8) k_mg0_residual(MgGrid g, const int *__restrict__ qlist, int na,
                                                       const uint8_t *__restrict__ fl, const float *__restrict__ r,
                                                       const float *__restrict__ ev, float *res, float scale, float m,
                                                       const int *done)
