@@ -17,7 +17,10 @@
 // V-cycle on level l for A_l e = r: two damped Jacobi sweeps from e = 0
 // (omega = 0.8), the residual, restriction (the transpose of cell-centred
 // trilinear prolongation, divided by 8), the V-cycle on level l + 1, prolongation
-// of its correction (weights 3/4 and 1/4 per axis), and two more sweeps. The
+// of its correction (weights 3/4 and 1/4 per axis), and two more sweeps; one
+// before and one after on a face volume's level 0, where the mass term of the
+// Helmholtz operator makes the smoothing strong enough that the second costs more
+// than the iterations it saves. The
 // coarsest level (small enough for shared memory) takes a fixed number of sweeps
 // in one block. Every step is linear in r with symmetric smoothing and restriction
 // proportional to the transposed prolongation, so M is symmetric, as CG needs.
@@ -88,6 +91,7 @@ struct MgState {
     bool own0 = true;      // level 0 work arrays belong to this hierarchy
     const int *done = nullptr;  // the calling solve's convergence flag (nullable)
     int cl = 0;                 // first level of the single-cluster launch (0: none)
+    bool one0 = false;          // one smoothing sweep each side on level 0 (the face volumes)
     // r.z in the last level-0 sweep of the current apply (rzs null: not formed)
     SolveScal *rzs = nullptr;
     int rz_first = 0, rz_boff = 0, rz_btot = 0;
@@ -335,6 +339,90 @@ __device__ __forceinline__ void restrict_pair(const MgGrid &gf, const float *res
     if (l1) rc[t0 + 1] = 0.125f * a1;
 }
 
+// one damped Jacobi sweep from zero and the residual it leaves, on quad q:
+// eb = e1 = omega D^-1 r at the quad, res = r - A e1 (e1 at the neighbours formed
+// on the fly)
+__device__ __forceinline__ void pre1_q(const MgGrid &g, const uint8_t *__restrict__ fl, const float *r, float *eb,
+                                       float *res, const float *wt, float scale, float m, int q)
+{
+    const int t = q << 2;
+    const uchar4 f = ldf4(fl, t);
+    auto e1q = [&](int u) {  // e1 on the quad at u
+        const uchar4 fu = ldf4(fl, u);
+        const float4 ru = ldv4<false>(r, u);
+        return make_float4(liq(fu.x) ? wt[fu.x & CF_D] * ru.x : 0.f, liq(fu.y) ? wt[fu.y & CF_D] * ru.y : 0.f,
+                           liq(fu.z) ? wt[fu.z & CF_D] * ru.z : 0.f, liq(fu.w) ? wt[fu.w & CF_D] * ru.w : 0.f);
+    };
+    auto e1s = [&](int u) {
+        const uint8_t fu = fl[u];
+        return liq(fu) ? wt[fu & CF_D] * ldv1<false>(r, u) : 0.f;
+    };
+    const float4 c = e1q(t), rv = ldv4<false>(r, t);
+    const float4 dn = e1q(t - g.sy), up = e1q(t + g.sy), bk = e1q(t - g.sz), fw = e1q(t + g.sz);
+    const float lf = e1s(t - 1), rt = e1s(t + 4);
+    auto one = [&](uint8_t fe, float ce, float nb, float re) {
+        return liq(fe) ? re - m * ce - scale * ((float)(fe & CF_D) * ce - nb) : 0.f;
+    };
+    float4 v;
+    v.x = one(f.x, c.x, (lf + c.y) + (dn.x + up.x) + (bk.x + fw.x), rv.x);
+    v.y = one(f.y, c.y, (c.x + c.z) + (dn.y + up.y) + (bk.y + fw.y), rv.y);
+    v.z = one(f.z, c.z, (c.y + c.w) + (dn.z + up.z) + (bk.z + fw.z), rv.z);
+    v.w = one(f.w, c.w, (c.z + rt) + (dn.w + up.w) + (bk.w + fw.w), rv.w);
+    *reinterpret_cast<float4 *>(eb + t) = c;
+    *reinterpret_cast<float4 *>(res + t) = v;
+}
+
+// Restriction of a column of RC coarse planes: t0 is the element of coarse cell
+// (2m, J, K0), K0 a multiple of RC. The x weights and then the y weights of each
+// fine plane 2 K0 - 1 .. 2 (K0 + RC) are formed once, and each coarse plane takes
+// the z-weighted sum of its four: a fine plane serves two coarse planes of the
+// column, where a thread per pair would read it twice.
+constexpr int RC = 4;
+template <bool CG>
+__device__ __forceinline__ void restrict_col(const MgGrid &gf, const float *res, const MgGrid &gc,
+                                             const uint8_t *__restrict__ flc, float *rc, int t0)
+{
+    const float w[4] = {0.25f, 0.75f, 0.75f, 0.25f};
+    const int rel = t0 - gc.origin;
+    const int K0 = rel / gc.sz, J = (rel - K0 * gc.sz) / gc.sy, I0 = rel - K0 * gc.sz - J * gc.sy;
+    const int m = I0 >> 1;
+    float y0[2 * RC + 2], y1[2 * RC + 2];
+#pragma unroll
+    for (int p = 0; p < 2 * RC + 2; p++) {
+        const int k = 2 * K0 - 1 + p;
+        float a0 = 0.f, a1 = 0.f;
+        if (k >= 0 && k < gf.nz) {
+#pragma unroll
+            for (int b = 0; b < 4; b++) {
+                const int j = 2 * J - 1 + b;
+                if (j < 0 || j >= gf.ny) continue;
+                const int row = gf.idx(0, j, k) + 4 * m;  // a multiple of 4
+                const float4 qd = ldv4<CG>(res, row);
+                const float lf = m > 0 ? ldv1<CG>(res, row - 1) : 0.f;
+                const float rt = 4 * m + 4 < gf.nx ? ldv1<CG>(res, row + 4) : 0.f;
+                // coarse 2m: fine 4m - 1 .. 4m + 2; coarse 2m + 1: fine 4m + 1 .. 4m + 4
+                a0 += w[b] * (0.25f * lf + 0.75f * qd.x + 0.75f * qd.y + 0.25f * qd.z);
+                a1 += w[b] * (0.25f * qd.y + 0.75f * qd.z + 0.75f * qd.w + 0.25f * rt);
+            }
+        }
+        y0[p] = a0;
+        y1[p] = a1;
+    }
+#pragma unroll
+    for (int kk = 0; kk < RC; kk++) {
+        if (K0 + kk >= gc.nz) break;
+        const int tk = t0 + kk * gc.sz;
+        float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            a0 += w[c] * y0[2 * kk + c];
+            a1 += w[c] * y1[2 * kk + c];
+        }
+        if (liq(flc[tk])) rc[tk] = 0.125f * a0;
+        if (I0 + 1 < gc.nx && liq(flc[tk + 1])) rc[tk + 1] = 0.125f * a1;
+    }
+}
+
 // ---- one launch per step ------------------------------------------------------
 
 // One sweep over the active quads. With rzs (the last sweep of a V-cycle's level
@@ -365,6 +453,16 @@ __global__ void __launch_bounds__(256) k_mg0_smooth(MgGrid g, const int *__restr
         rzs->beta = first ? 0.0 : tot[0] / rzs->rz;
         rzs->rz = tot[0];
     }
+}
+
+__global__ void __launch_bounds__(256) k_mg0_pre1(MgGrid g, const int *__restrict__ qlist, int na,
+                                                  const uint8_t *__restrict__ fl, const float *__restrict__ r,
+                                                  float *eb, float *res, float scale, float m, const int *done)
+{
+    if (done && *(volatile const int *)done) return;  // the solve has converged
+    __shared__ float wt[8];
+    fill_wtab(wt, scale, m);
+    MG_FOR_LIST(qlist, na) pre1_q(g, fl, r, eb, res, wt, scale, m, q);
 }
 
 __global__ void __launch_bounds__(256, 8) k_mg0_residual(MgGrid g, const int *__restrict__ qlist, int na,
@@ -851,32 +949,47 @@ int vcycle(fs_ctx *c, MgState *s, int l, bool sample, cudaStream_t st)
     // four elements per thread: every level but the coarsest has quad-aligned rows
     const int nb = grid_blocks(c, v.nqa, TH);  // the active quads
     MgLevel &w = s->lev[l + 1];
-    begin();
-    k_mg0_smooth2<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.b, v.scale, v.mass, done);
-    end(K_MG0_SMOOTH2, s->by0[0]);
-    begin();
-    k_mg0_residual<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.b, v.c, v.scale, v.mass, done);
-    end(K_MG0_RESIDUAL, s->by0[1]);
+    // one sweep each side on level 0 of a face volume (the viscosity solve), two
+    // elsewhere
+    const bool one = l == 0 && s->one0;
+    if (one) {  // the sweep from zero and the residual it leaves, in one pass
+        k_mg0_pre1<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.b, v.c, v.scale, v.mass, done);
+        c->n_launches += 1;
+    } else {
+        begin();
+        k_mg0_smooth2<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.b, v.scale, v.mass, done);
+        end(K_MG0_SMOOTH2, s->by0[0]);
+        begin();
+        k_mg0_residual<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.b, v.c, v.scale, v.mass, done);
+        end(K_MG0_RESIDUAL, s->by0[1]);
+        c->n_launches += 2;
+    }
     begin();
     k_mg0_restrict<<<grid_blocks(c, w.npa, TH), TH, 0, st>>>(g, v.c, w.g, w.pl, w.npa, w.fl, w.r, done);
     end(K_MG0_RESTRICT, s->by0[2]);
-    c->n_launches += 3;
+    c->n_launches += 1;
     begin();
     if (int rc = vcycle(c, s, l + 1, false, st)) return rc;
     end(K_MG_COARSE, 0.0);
     begin();
     k_mg0_prolong<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.b, w.g, w.a, done);
     end(K_MG0_PROLONG, s->by0[3]);
-    begin();
-    k_mg0_smooth<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.b, v.c, v.scale, v.mass, done, nullptr, nullptr,
-                                    0, 0, 0);
-    end(K_MG0_SMOOTH, s->by0[4]);
-    begin();
     SolveScal *rzs = l == 0 ? s->rzs : nullptr;  // r.z of the solver in the last level-0 sweep
-    k_mg0_smooth<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.c, v.a, v.scale, v.mass, done, rzs, c->partials,
+    const float *ez = v.c;                        // the input of the last sweep
+    if (one) {
+        ez = v.b;
+    } else {
+        begin();
+        k_mg0_smooth<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.b, v.c, v.scale, v.mass, done, nullptr,
+                                        nullptr, 0, 0, 0);
+        end(K_MG0_SMOOTH, s->by0[4]);
+        c->n_launches += 1;
+    }
+    begin();
+    k_mg0_smooth<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, ez, v.a, v.scale, v.mass, done, rzs, c->partials,
                                     s->rz_first, s->rz_boff, s->rz_btot);
     end(K_MG0_SMOOTH_Z, s->by0[5]);
-    c->n_launches += 3;
+    c->n_launches += 2;
     FS_CUDA(cudaGetLastError());
     return FS_OK;
 }
@@ -1154,6 +1267,7 @@ static int apply_faces(fs_ctx *c, const float *r, float *z, float cc, const int 
         if (s.epoch != c->mask_epoch) {
             const MgGrid g0 = level0_grid(L, L.nx + (k == 0), L.ny + (k == 1), L.nz + (k == 2));
             if (int rc = mg_build(c, &s, g0, c->fflag + base, m->fb + base, m->fc + base, cc, 1.f)) return rc;
+            s.one0 = true;
         } else if (s.coef != cc) {  // a new viscosity or time step: rescale the levels only
             float sc = cc;
             for (int l = 0; l < s.nlev; l++, sc *= 0.25f) s.lev[l].scale = sc;
@@ -1211,8 +1325,10 @@ void mg_count(fs_ctx *c, long long vcycles, bool faces)
     const int nlev = faces ? m->face[0].nlev : m->cell.nlev;
     if (nlev < 2) return;
     const long long k = faces ? 3 * vcycles : vcycles;
-    for (int id : {K_MG0_SMOOTH2, K_MG0_RESIDUAL, K_MG0_RESTRICT, K_MG0_PROLONG, K_MG0_SMOOTH, K_MG0_SMOOTH_Z})
-        prof_count(c, id, k);
+    const bool one = faces && m->face[0].one0;  // the face volumes' level 0 skips three of the six kinds
+    for (int id : {K_MG0_SMOOTH2, K_MG0_RESIDUAL, K_MG0_SMOOTH})
+        if (!one) prof_count(c, id, k);
+    for (int id : {K_MG0_RESTRICT, K_MG0_PROLONG, K_MG0_SMOOTH_Z}) prof_count(c, id, k);
     prof_count(c, faces ? K_MG_VCYCLE_V : K_MG_VCYCLE_P, vcycles);
     if (!faces) prof_count(c, K_MG_COARSE, vcycles);
 }
