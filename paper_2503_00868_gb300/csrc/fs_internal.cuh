@@ -436,6 +436,7 @@ int mg_apply_faces(fs_ctx *c, const float *r, float *z, float cc, const int *don
 void mg_free(fs_ctx *c);
 void mg_count(fs_ctx *c, long long vcycles, bool faces);  // fs_mg.cu: launch counts for fs_profile
 int mg_levels(const fs_ctx *c);
+bool mg_level0_lists(const fs_ctx *c, bool faces, const int **ql, int *n, long long *base);  // fs_mg.cu
 int pressure_pair(fs_ctx *c, float *q_hi, float *q_lo);  // fs_pcg.cu
 bool mg_rz(fs_ctx *c, bool faces, const float *r, const float *z, int first, SolveScal *s);  // fs_mg.cu
 // z = M r with r.z formed in the V-cycle's last level-0 sweep (beta = rz_new / rz,

@@ -1357,6 +1357,24 @@ bool mg_rz(fs_ctx *c, bool faces, const float *r, const float *z, int first, Sol
     return cudaPeekAtLastError() == cudaSuccess;
 }
 
+// The level-0 lists of active quads of the pressure hierarchy (one) or of the
+// three face volumes, with each volume's first element; false when a hierarchy
+// has no lists for the current mask.
+bool mg_level0_lists(const fs_ctx *c, bool faces, const int **ql, int *n, long long *base)
+{
+    const MgAll *m = static_cast<const MgAll *>(c->mg);
+    if (!m) return false;
+    const int nv = faces ? 3 : 1;
+    for (int v = 0; v < nv; v++) {
+        const MgState &h = faces ? m->face[v] : m->cell;
+        if (h.nlev < 2 || h.epoch != c->mask_epoch || !h.lev[0].ql) return false;
+        ql[v] = h.lev[0].ql;
+        n[v] = h.lev[0].nqa;
+        base[v] = faces ? (long long)c->L.face_origin(v) - c->L.PL : 0;
+    }
+    return true;
+}
+
 int mg_levels(const fs_ctx *c)
 {
     const MgAll *m = static_cast<const MgAll *>(c->mg);

@@ -41,6 +41,73 @@ __device__ __forceinline__ float inv_diag(uint8_t f, float cc)
     return d > 0.f ? __frcp_rn(d) : 0.f;
 }
 
+// The operator apply over lists of active quads (those holding an unknown; the
+// multigrid hierarchy's level-0 lists, one per volume, volume v from element
+// base[v]): per quad, p_new = z + beta p_old on the quad and its six neighbours
+// (inactive elements hold z = p_old = 0, so p_new = 0 there), q = A p_new on the
+// quad, both written whole, and p_new . q. A thread strides through the lists
+// with the next entry fetched a step ahead, so only quads with an unknown are
+// read or written, where a 128 x 8 tile carries many without.
+struct QuadLists {
+    const int *ql[3];
+    int n[3];
+    long long base[3];
+    int nv;
+};
+
+template <class Op>
+__global__ void __launch_bounds__(TH) k_spmv_list(QuadLists Ls, const float *__restrict__ src,
+                                                  const float *__restrict__ pold, float *__restrict__ pnew,
+                                                  float *__restrict__ q, const uint8_t *__restrict__ fl, int P,
+                                                  int PL, float cc, SolveScal *s, double *partials)
+{
+    if (s->done) return;
+    const float beta = (float)s->beta;
+    const float off = Op::offc(cc);
+    KSum acc;
+    const int st = gridDim.x * blockDim.x;
+    for (int v = 0; v < Ls.nv; v++) {
+        const long long base = Ls.base[v];
+        const int *ql = Ls.ql[v];
+        const int na = Ls.n[v];
+        int i = blockIdx.x * blockDim.x + threadIdx.x;
+        int qn = i < na ? __ldg(ql + i) : 0;
+        for (; i < na; i += st) {
+            const long long t = base + 4LL * qn;
+            qn = i + st < na ? __ldg(ql + i + st) : 0;
+            const uchar4 f = __ldg(reinterpret_cast<const uchar4 *>(fl + t));
+            auto pn4 = [&](long long u) {
+                const float4 a = __ldg(reinterpret_cast<const float4 *>(src + u));
+                const float4 b = __ldg(reinterpret_cast<const float4 *>(pold + u));
+                return make_float4(a.x + beta * b.x, a.y + beta * b.y, a.z + beta * b.z, a.w + beta * b.w);
+            };
+            auto pn1 = [&](long long u) { return __ldg(src + u) + beta * __ldg(pold + u); };
+            const float4 c = pn4(t), dn = pn4(t - P), up = pn4(t + P), bk = pn4(t - PL), fw = pn4(t + PL);
+            const float lf = pn1(t - 1), rt = pn1(t + 4);
+            auto one = [&](uint8_t fe, float ce, float nb) {
+                return (fe & Op::ACTIVE) ? Op::diag(fe, cc) * ce - off * nb : 0.f;
+            };
+            float4 qv;
+            qv.x = one(f.x, c.x, (lf + c.y) + (dn.x + up.x) + (bk.x + fw.x));
+            qv.y = one(f.y, c.y, (c.x + c.z) + (dn.y + up.y) + (bk.y + fw.y));
+            qv.z = one(f.z, c.z, (c.y + c.w) + (dn.z + up.z) + (bk.z + fw.z));
+            qv.w = one(f.w, c.w, (c.z + rt) + (dn.w + up.w) + (bk.w + fw.w));
+            acc.add(c.x * qv.x + c.y * qv.y + c.z * qv.z + c.w * qv.w);
+            *reinterpret_cast<float4 *>(pnew + t) = c;
+            *reinterpret_cast<float4 *>(q + t) = qv;
+        }
+    }
+    KSum vv[1] = {acc};
+    double tot[1];
+    if (grid_reduce<1>(vv, partials, &s->ticket, tot) && threadIdx.x == 0) {
+        double pq = tot[0];
+        s->pq = pq;
+        if (!isfinite(pq)) { s->done = 1; s->status = FS_ENONFINITE; }
+        else if (!(pq > 0.0)) { s->done = 1; s->status = FS_EBREAKDOWN; }
+        else s->alpha = s->rz / pq;
+    }
+}
+
 // Flat versions of the two CG kernels, for a context without tile maps.
 // p_new = z + beta p_old (z the stored preconditioned residual; for Jacobi the
 // solver keeps z = D^-1 r itself), then q = A p_new and the partial sums of
@@ -842,9 +909,15 @@ static int pcg_iterate(fs_ctx *c, SolveScal &h)
     const int b4 = grid_blocks(c, n4, TH);
     int cur = 0;
     long long launched = 0;
-    const double by_spmv = (double)L.nC + 16.0 * (double)c->n_liquid;
+    double by_spmv = (double)L.nC + 16.0 * (double)c->n_liquid;
     const double by_upd = (double)L.nC + 24.0 * (double)c->n_liquid;
     const bool tiled = c->act_cell != nullptr;
+    // with multigrid, the operator apply walks the V-cycle's lists of active quads
+    QuadLists qls{};
+    qls.nv = 1;
+    const bool listed = c->prm.precond == FS_PRECOND_MG && mg_level0_lists(c, false, qls.ql, qls.n, qls.base);
+    const long long nlisted = listed ? qls.n[0] : 0;
+    if (listed) by_spmv = 8.0 * (double)nlisted + 16.0 * (double)c->n_liquid;  // list entry and flags per quad
     const TileMap &tm = c->tm_cell;
     const dim3 tdim(TILE_X / 4, TILE_Y);
     const TmaGrids<PoisOp> tg(c, c->nitems_cell, c->nact_cell);
@@ -855,7 +928,10 @@ static int pcg_iterate(fs_ctx *c, SolveScal &h)
             const bool samp = c->prof_on && (b % c->prof_period) == 0;
             cudaEvent_t e0 = samp ? prof_mark(c) : nullptr;
             const float *zsrc = jac ? c->pr : c->pz;
-            if (tiled)
+            if (listed)
+                k_spmv_list<PoisOp><<<grid_blocks(c, nlisted, TH), TH, 0, c->stream>>>(
+                    qls, c->pz, c->pp[cur], c->pp[cur ^ 1], c->pq, c->cflag, L.P, L.PL, 0.f, s, c->partials);
+            else if (tiled)
                 k_spmv_z<PoisOp><<<tg.spmv, tdim, zmarch_smem(), c->stream>>>(
                     jac ? c->tmz_pr : c->tmz_pz, c->tmz_pp[cur], c->pp[cur ^ 1], c->pq, c->cflag, c->items_cell,
                     c->nitems_cell, tm, 0.f, s, c->partials, c->err_word);
@@ -1101,9 +1177,15 @@ int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st)
     int cur = 0;
     long long launched = 0;
     SolveScal h;
-    const double by_spmv = (double)L.nF + 16.0 * (double)c->n_fluid;
+    double by_spmv = (double)L.nF + 16.0 * (double)c->n_fluid;
     const double by_upd = (double)L.nF + 24.0 * (double)c->n_fluid;
     const bool tiled = c->act_face != nullptr;
+    // with multigrid, the operator apply walks the V-cycles' lists of active quads
+    QuadLists qls{};
+    qls.nv = 3;
+    const bool listed = mg && mg_level0_lists(c, true, qls.ql, qls.n, qls.base);
+    const long long nlisted = listed ? (long long)qls.n[0] + qls.n[1] + qls.n[2] : 0;
+    if (listed) by_spmv = 8.0 * (double)nlisted + 16.0 * (double)c->n_fluid;  // list entry and flags per quad
     const TileMap &tm = c->tm_face;
     const dim3 tdim(TILE_X / 4, TILE_Y);
     const TmaGrids<HelmOp> tg(c, c->nitems_face, c->nact_face);
@@ -1111,7 +1193,10 @@ int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st)
         for (int b = 0; b < check; b++) {
             const bool samp = c->prof_on && (b % c->prof_period) == 0;
             cudaEvent_t e0 = samp ? prof_mark(c) : nullptr;
-            if (tiled)
+            if (listed)
+                k_spmv_list<HelmOp><<<grid_blocks(c, nlisted, TH), TH, 0, c->stream>>>(
+                    qls, c->vz, c->vp[cur], c->vp[cur ^ 1], c->vq, c->fflag, L.P, L.PL, cc, s, c->partials);
+            else if (tiled)
                 k_spmv_z<HelmOp><<<tg.spmv, tdim, zmarch_smem(), c->stream>>>(
                     mg ? c->tmz_vz : c->tmz_vr, c->tmz_vp[cur], c->vp[cur ^ 1], c->vq, c->fflag, c->items_face,
                     c->nitems_face, tm, cc, s, c->partials, c->err_word);
