@@ -362,6 +362,14 @@ def precond_compare(n, seeds=(0,)):
                               "true_relres": st["true_relres_p"], "status": rc}
         g.close()
         out["rows"].append(row)
+    # the learned preconditioner in its V-cycle role against MIC(0)-PCG (the
+    # network alone is the "learned" row)
+    r0 = out["rows"][0]
+    out["learned_vs_mic0"] = {"learned_row": "learned_mg", "learned_ms": r0["learned_mg"]["ms"],
+                              "mic0_ms": r0["mic0"]["ms"],
+                              "speedup": r0["mic0"]["ms"] / max(r0["learned_mg"]["ms"], 1e-9),
+                              "learned_true_relres": r0["learned_mg"]["true_relres"],
+                              "learned_fallbacks": r0["learned_mg"]["fallbacks"]}
     return out
 
 
