@@ -407,7 +407,10 @@ int fs_set_params(fs_ctx *c, const fs_params *p)
     if (rc) return rc;
     if (p->mic_tau != c->prm.mic_tau || p->mic_sigma != c->prm.mic_sigma) c->mic_ready = 0;
     c->prm = *p;
-    c->pw_valid[0] = c->pw_valid[1] = 0;  // a new problem: no warm start from earlier solves
+    // a new problem: no warm start from earlier solves (the floor of the first
+    // CG pass stays: it depends on the mask and the scale of the pressure, and a
+    // wrong one costs one refinement step and is then measured again)
+    c->pw_valid[0] = c->pw_valid[1] = 0;
     return FS_OK;
 }
 

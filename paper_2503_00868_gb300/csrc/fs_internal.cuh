@@ -124,6 +124,11 @@ struct fs_ctx {
     // allocated on first use, invalidated by set_mask
     float *pw[2];
     int pw_valid[2];
+    // relative residual^2 (FP64-accurate) that the first CG pass of the last
+    // pressure solve of each kind left when it was above tol_p^2 (else 0): the
+    // rounding floor of the FP32 iterate, which the next solve's first pass does
+    // not try to go below
+    double p_floor2[2];
     int solve_kind;       // kind of the pressure solve being run
     // viscosity solve (face space)
     float *vx, *vr, *vp[2], *vq, *vz;  // vz: preconditioned residual of a multigrid viscosity solve

@@ -381,6 +381,7 @@ int build_mask(fs_ctx *c, const uint8_t *types_dense, const fs_mac *bc)
     c->mask_set = 1;
     c->mask_epoch += 1;
     c->pw_valid[0] = c->pw_valid[1] = 0;
+    c->p_floor2[0] = c->p_floor2[1] = 0.0;
     c->mic_ready = 0;
     c->mic_sched_ready = 0;
     return FS_OK;

@@ -1016,6 +1016,15 @@ static int solve_pressure_once(fs_ctx *c, fs_stats *st)
     long long iters = 0;
     bool checked = false;  // m holds the FP64 residual of the pass that ended the loop
     int rc = FS_OK, nref = 0;
+    const int kind = c->solve_kind & 1;
+    const double tol2 = c->prm.tol_p * c->prm.tol_p;
+    // Where the first pass of the last solve of this kind left a true residual
+    // above the tolerance, this one stops at half that residual: far above the
+    // tolerance (the rounding floor of the FP32 iterate) the refinement runs
+    // anyway and the iterations below the floor are saved; just above it (a
+    // recursive residual that drifted) the deeper first pass often makes the
+    // refinement unnecessary.
+    if (c->p_floor2[kind] > tol2) c->tol2_scale = std::min(0.25 * c->p_floor2[kind] / tol2, 1e4);
     for (int pass = 0;; pass++) {
         checked = false;
         rc = learned ? solve_pressure_fcg(c, &h, false) : pcg_iterate(c, h);
@@ -1030,8 +1039,10 @@ static int solve_pressure_once(fs_ctx *c, fs_stats *st)
         c->n_launches += 1;
         if ((rc = check_cuda(cudaGetLastError(), "k_pois_true_res")) || (rc = read_scal(c, 2, &m))) break;
         checked = true;
-        if (pass == 0) bb0 = m.aux[1];
-        const double tol2 = c->prm.tol_p * c->prm.tol_p;
+        if (pass == 0) {
+            bb0 = m.aux[1];
+            c->p_floor2[kind] = bb0 > 0.0 && m.aux[0] > tol2 * bb0 ? m.aux[0] / bb0 : 0.0;
+        }
         if (pass == kMaxRefine || !(bb0 > 0.0) || !(m.aux[0] > tol2 * bb0)) break;
         // the next correction: the terms solved so far kept in the head and the tail
         if (pass == 0) {
