@@ -348,6 +348,33 @@ __device__ __forceinline__ bool ks_block(KSum (&v)[K])
     return true;
 }
 
+// The last block's share of the merge: thread tid takes the partials of blocks
+// tid, tid + nthr, ... in that order. The loads of U of them are issued before
+// the first merge, so the thread waits for about one L2 round trip per U
+// partials instead of one per partial (U sized so that the merge needs no more
+// registers than the streaming loops of the kernels it ends).
+template <int K>
+__device__ __forceinline__ void ks_gather(KSum (&v)[K], const float2 *pp, int nblocks, int tid, int nthr)
+{
+    constexpr int U = K == 1 ? 8 : 1;
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = KSum();
+    for (int b0 = tid; b0 < nblocks; b0 += U * nthr) {
+        float2 q[U][K];
+#pragma unroll
+        for (int u = 0; u < U; u++)
+#pragma unroll
+            for (int k = 0; k < K; k++)
+                q[u][k] = b0 + u * nthr < nblocks ? __ldcg(&pp[(size_t)(b0 + u * nthr) * K + k])
+                                                  : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (b0 + u * nthr < nblocks)
+#pragma unroll
+                for (int k = 0; k < K; k++) ks_merge(v[k].s, v[k].c, q[u][k].x, q[u][k].y);
+    }
+}
+
 template <int K>
 __device__ __forceinline__ bool grid_reduce(KSum (&v)[K], double *partials, unsigned *ticket, double (&tot)[K])
 {
@@ -363,14 +390,7 @@ __device__ __forceinline__ bool grid_reduce(KSum (&v)[K], double *partials, unsi
     __syncthreads();
     if (!last) return false;
     __threadfence();
-#pragma unroll
-    for (int k = 0; k < K; k++) v[k] = KSum();
-    for (int b = tid; b < (int)gridDim.x; b += nthr)
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            const float2 q = __ldcg(&pp[(size_t)b * K + k]);
-            ks_merge(v[k].s, v[k].c, q.x, q.y);
-        }
+    ks_gather<K>(v, pp, (int)gridDim.x, tid, nthr);
     __syncthreads();  // the shared staging of ks_block is reused
     if (ks_block<K>(v) && tid == 0) {
 #pragma unroll
@@ -400,14 +420,7 @@ __device__ __forceinline__ bool multi_reduce(KSum (&v)[K], double *partials, uns
     __syncthreads();
     if (!last) return false;
     __threadfence();
-#pragma unroll
-    for (int k = 0; k < K; k++) v[k] = KSum();
-    for (int b = tid; b < nblocks; b += nthr)
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            const float2 q = __ldcg(&pp[(size_t)b * K + k]);
-            ks_merge(v[k].s, v[k].c, q.x, q.y);
-        }
+    ks_gather<K>(v, pp, nblocks, tid, nthr);
     __syncthreads();  // the shared staging of ks_block is reused
     if (ks_block<K>(v) && tid == 0) {
 #pragma unroll
