@@ -201,6 +201,32 @@ inline int grid_blocks(const fs_ctx *c, long long n, int threads, int per_thread
     return (int)(need < c->max_blocks ? need : c->max_blocks);
 }
 
+// Resident 256-thread blocks per SM of a kernel with `dyn` bytes of dynamic
+// shared memory; raises the kernel's dynamic shared memory limit to `dyn` on
+// first use.
+inline int resident_blocks(const void *fn, size_t dyn)
+{
+    if (dyn > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, dyn) != cudaSuccess || nb < 1) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    return nb;
+}
+
+// Blocks of a grid-stride launch of 256-thread blocks over n items for a kernel
+// with `resident` blocks per SM: at most one full wave. A grid of max_blocks for
+// a kernel that fits fewer blocks per SM would run its last blocks in a second,
+// mostly empty wave, each with as much work as the first wave's.
+inline int wave_blocks(const fs_ctx *c, long long n, int resident)
+{
+    long long need = (n + 255) / 256;
+    if (need < 1) need = 1;
+    const long long cap = (long long)c->num_sms * (resident > 0 ? resident : 1);
+    return (int)(need < cap ? need : cap);
+}
+
 // ---- deterministic grid reduction ------------------------------------------
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -348,6 +374,18 @@ __device__ __forceinline__ bool ks_block(KSum (&v)[K])
     return true;
 }
 
+// A block's arrival at the ticket of a grid sum, by the thread that wrote the
+// block's partials: an atomic add with release semantics (the partials are
+// visible before the count) and acquire semantics (the last block to arrive sees
+// every partial once its threads pass the barrier that follows), at device
+// scope, in place of a full fence before and after a relaxed add.
+__device__ __forceinline__ unsigned ticket_arrive(unsigned *ticket)
+{
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(ticket) : "memory");
+    return old;
+}
+
 // The last block's share of the merge: thread tid takes the partials of blocks
 // tid, tid + nthr, ... in that order. The loads of U of them are issued before
 // the first merge, so the thread waits for about one L2 round trip per U
@@ -384,12 +422,10 @@ __device__ __forceinline__ bool grid_reduce(KSum (&v)[K], double *partials, unsi
     if (ks_block<K>(v) && tid == 0) {
 #pragma unroll
         for (int k = 0; k < K; k++) pp[(size_t)blockIdx.x * K + k] = make_float2(v[k].s, v[k].c);
-        __threadfence();
-        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+        last = ticket_arrive(ticket) == gridDim.x - 1;
     }
     __syncthreads();
     if (!last) return false;
-    __threadfence();
     ks_gather<K>(v, pp, (int)gridDim.x, tid, nthr);
     __syncthreads();  // the shared staging of ks_block is reused
     if (ks_block<K>(v) && tid == 0) {
@@ -414,12 +450,10 @@ __device__ __forceinline__ bool multi_reduce(KSum (&v)[K], double *partials, uns
     if (ks_block<K>(v) && tid == 0) {
 #pragma unroll
         for (int k = 0; k < K; k++) pp[(size_t)block * K + k] = make_float2(v[k].s, v[k].c);
-        __threadfence();
-        last = atomicAdd(ticket, 1u) == (unsigned)nblocks - 1;
+        last = ticket_arrive(ticket) == (unsigned)nblocks - 1;
     }
     __syncthreads();
     if (!last) return false;
-    __threadfence();
     ks_gather<K>(v, pp, nblocks, tid, nthr);
     __syncthreads();  // the shared staging of ks_block is reused
     if (ks_block<K>(v) && tid == 0) {

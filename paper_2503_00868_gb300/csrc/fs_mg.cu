@@ -926,6 +926,25 @@ int cluster_ctas_here()
     return cached;
 }
 
+// Resident blocks per SM of the list-walking kernels, for one-wave grids.
+struct MgResidency {
+    int smooth2, residual, pre1, restrict_, prolong, smooth;
+};
+const MgResidency &mg_residency()
+{
+    static const MgResidency r{resident_blocks((const void *)k_mg0_smooth2, 0),
+                               resident_blocks((const void *)k_mg0_residual, 0),
+                               resident_blocks((const void *)k_mg0_pre1, 0),
+                               resident_blocks((const void *)k_mg0_restrict, 0),
+                               resident_blocks((const void *)k_mg0_prolong, 0),
+                               resident_blocks((const void *)k_mg0_smooth, 0)};
+    return r;
+}
+
+// blocks of the sweeps k_mg0_smooth over a level's nqa active quads (also the
+// block count of the r.z reduction the last level-0 sweep forms)
+int smooth_blocks(const fs_ctx *c, int nqa) { return wave_blocks(c, nqa, mg_residency().smooth); }
+
 int vcycle(fs_ctx *c, MgState *s, int l, bool sample, cudaStream_t st)
 {
     if (s->cl > 0 && l == s->cl) return launch_cluster(c, s, l, st);
@@ -946,33 +965,35 @@ int vcycle(fs_ctx *c, MgState *s, int l, bool sample, cudaStream_t st)
     auto end = [&](int kind, double bytes) {
         if (timed) prof_add(c, kind, e0, prof_mark(c), bytes);
     };
-    // four elements per thread: every level but the coarsest has quad-aligned rows
-    const int nb = grid_blocks(c, v.nqa, TH);  // the active quads
+    // four elements per thread: every level but the coarsest has quad-aligned rows;
+    // each kernel over the active quads in one wave of its resident blocks
+    const MgResidency &res = mg_residency();
+    const int nb = smooth_blocks(c, v.nqa);
     MgLevel &w = s->lev[l + 1];
     // one sweep each side on level 0 of a face volume (the viscosity solve), two
     // elsewhere
     const bool one = l == 0 && s->one0;
     if (one) {  // the sweep from zero and the residual it leaves, in one pass
-        k_mg0_pre1<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.b, v.c, v.scale, v.mass, done);
+        k_mg0_pre1<<<wave_blocks(c, v.nqa, res.pre1), TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.b, v.c, v.scale, v.mass, done);
         c->n_launches += 1;
     } else {
         begin();
-        k_mg0_smooth2<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.b, v.scale, v.mass, done);
+        k_mg0_smooth2<<<wave_blocks(c, v.nqa, res.smooth2), TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.b, v.scale, v.mass, done);
         end(K_MG0_SMOOTH2, s->by0[0]);
         begin();
-        k_mg0_residual<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.b, v.c, v.scale, v.mass, done);
+        k_mg0_residual<<<wave_blocks(c, v.nqa, res.residual), TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.r, v.b, v.c, v.scale, v.mass, done);
         end(K_MG0_RESIDUAL, s->by0[1]);
         c->n_launches += 2;
     }
     begin();
-    k_mg0_restrict<<<grid_blocks(c, w.npa, TH), TH, 0, st>>>(g, v.c, w.g, w.pl, w.npa, w.fl, w.r, done);
+    k_mg0_restrict<<<wave_blocks(c, w.npa, res.restrict_), TH, 0, st>>>(g, v.c, w.g, w.pl, w.npa, w.fl, w.r, done);
     end(K_MG0_RESTRICT, s->by0[2]);
     c->n_launches += 1;
     begin();
     if (int rc = vcycle(c, s, l + 1, false, st)) return rc;
     end(K_MG_COARSE, 0.0);
     begin();
-    k_mg0_prolong<<<nb, TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.b, w.g, w.a, done);
+    k_mg0_prolong<<<wave_blocks(c, v.nqa, res.prolong), TH, 0, st>>>(g, v.ql, v.nqa, v.fl, v.b, w.g, w.a, done);
     end(K_MG0_PROLONG, s->by0[3]);
     SolveScal *rzs = l == 0 ? s->rzs : nullptr;  // r.z of the solver in the last level-0 sweep
     const float *ez = v.c;                        // the input of the last sweep
@@ -1209,7 +1230,7 @@ static int apply_cell(fs_ctx *c, const float *r, float *z, const int *done, Solv
     const bool sample = c->prof_on && (m->cell.calls++ % std::max(1, c->prof_period)) == 0;
     cudaEvent_t e0 = sample ? prof_mark(c) : nullptr;
     const int rc = fuse ? apply_on(c, &m->cell, r, z, done, sample, c->stream, rzs, first, 0,
-                                   grid_blocks(c, m->cell.lev[0].nqa, TH))
+                                   smooth_blocks(c, m->cell.lev[0].nqa))
                         : apply_on(c, &m->cell, r, z, done, sample, c->stream);
     if (sample) prof_add(c, K_MG_VCYCLE_P, e0, prof_mark(c), 0.0);
     if (fused) *fused = fuse && rc == FS_OK;
@@ -1281,7 +1302,7 @@ static int apply_faces(fs_ctx *c, const float *r, float *z, float cc, const int 
     for (int k = 0; k < 3 && fuse; k++) {
         fuse = m->face[k].nlev >= 2;
         boff[k] = btot;
-        btot += grid_blocks(c, m->face[k].lev[0].nqa, TH);
+        btot += smooth_blocks(c, m->face[k].lev[0].nqa);
     }
     // volume 0 on the context's stream, 1 and 2 beside it (their sweeps share the
     // GPU, so none is timed alone: the profiled sweep is the pressure V-cycle's)

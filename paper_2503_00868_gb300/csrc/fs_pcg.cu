@@ -672,20 +672,6 @@ __global__ void __launch_bounds__(TH) k_loss_face(CF3 u, CF3 tg, const uint8_t *
 
 namespace fs {
 
-// Resident 256-thread blocks per SM of a kernel with `dyn` bytes of dynamic
-// shared memory (the persistent grids); raises the kernel's dynamic shared
-// memory limit to `dyn` on first use.
-static int resident_blocks(const void *fn, size_t dyn)
-{
-    if (dyn > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, 256, dyn) != cudaSuccess || nb < 1) {
-        cudaGetLastError();
-        nb = 1;
-    }
-    return nb;
-}
-
 // Persistent grid sizes of the two CG kernels for one operator.
 template <class Op>
 struct TmaGrids {
@@ -917,6 +903,7 @@ static int pcg_iterate(fs_ctx *c, SolveScal &h)
     qls.nv = 1;
     const bool listed = c->prm.precond == FS_PRECOND_MG && mg_level0_lists(c, false, qls.ql, qls.n, qls.base);
     const long long nlisted = listed ? qls.n[0] : 0;
+    static const int rl = resident_blocks((const void *)k_spmv_list<PoisOp>, 0);  // one wave of the list apply
     if (listed) by_spmv = 8.0 * (double)nlisted + 16.0 * (double)c->n_liquid;  // list entry and flags per quad
     const TileMap &tm = c->tm_cell;
     const dim3 tdim(TILE_X / 4, TILE_Y);
@@ -929,7 +916,7 @@ static int pcg_iterate(fs_ctx *c, SolveScal &h)
             cudaEvent_t e0 = samp ? prof_mark(c) : nullptr;
             const float *zsrc = jac ? c->pr : c->pz;
             if (listed)
-                k_spmv_list<PoisOp><<<grid_blocks(c, nlisted, TH), TH, 0, c->stream>>>(
+                k_spmv_list<PoisOp><<<wave_blocks(c, nlisted, rl), TH, 0, c->stream>>>(
                     qls, c->pz, c->pp[cur], c->pp[cur ^ 1], c->pq, c->cflag, L.P, L.PL, 0.f, s, c->partials);
             else if (tiled)
                 k_spmv_z<PoisOp><<<tg.spmv, tdim, zmarch_smem(), c->stream>>>(
@@ -1196,6 +1183,7 @@ int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st)
     qls.nv = 3;
     const bool listed = mg && mg_level0_lists(c, true, qls.ql, qls.n, qls.base);
     const long long nlisted = listed ? (long long)qls.n[0] + qls.n[1] + qls.n[2] : 0;
+    static const int rl = resident_blocks((const void *)k_spmv_list<HelmOp>, 0);  // one wave of the list apply
     if (listed) by_spmv = 8.0 * (double)nlisted + 16.0 * (double)c->n_fluid;  // list entry and flags per quad
     const TileMap &tm = c->tm_face;
     const dim3 tdim(TILE_X / 4, TILE_Y);
@@ -1205,7 +1193,7 @@ int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st)
             const bool samp = c->prof_on && (b % c->prof_period) == 0;
             cudaEvent_t e0 = samp ? prof_mark(c) : nullptr;
             if (listed)
-                k_spmv_list<HelmOp><<<grid_blocks(c, nlisted, TH), TH, 0, c->stream>>>(
+                k_spmv_list<HelmOp><<<wave_blocks(c, nlisted, rl), TH, 0, c->stream>>>(
                     qls, c->vz, c->vp[cur], c->vp[cur ^ 1], c->vq, c->fflag, L.P, L.PL, cc, s, c->partials);
             else if (tiled)
                 k_spmv_z<HelmOp><<<tg.spmv, tdim, zmarch_smem(), c->stream>>>(
