@@ -129,6 +129,10 @@ struct fs_ctx {
     // rounding floor of the FP32 iterate, which the next solve's first pass does
     // not try to go below
     double p_floor2[2];
+    // iterations of the last CG pass of each kind: pressure [kind][refining],
+    // viscosity [dirichlet]; 0 unknown. The host runs that many minus one before
+    // its first read of the convergence flag.
+    int it_last_p[2][2], it_last_v[2];
     int solve_kind;       // kind of the pressure solve being run
     // viscosity solve (face space)
     float *vx, *vr, *vp[2], *vq, *vz;  // vz: preconditioned residual of a multigrid viscosity solve

@@ -3,6 +3,7 @@
 // counts. Runs once per mask (Sec. 3.4.2: the loss is restricted by a mask
 // derived from the cell types of the grid).
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -382,6 +383,8 @@ int build_mask(fs_ctx *c, const uint8_t *types_dense, const fs_mac *bc)
     c->mask_epoch += 1;
     c->pw_valid[0] = c->pw_valid[1] = 0;
     c->p_floor2[0] = c->p_floor2[1] = 0.0;
+    std::memset(c->it_last_p, 0, sizeof(c->it_last_p));
+    std::memset(c->it_last_v, 0, sizeof(c->it_last_v));
     c->mic_ready = 0;
     c->mic_sched_ready = 0;
     return FS_OK;

@@ -686,6 +686,22 @@ struct TmaGrids {
     }
 };
 
+// Iterations launched before each read of the convergence flag. A read costs a
+// host round trip with the GPU idle, and every iteration launched after
+// convergence costs its launches (each returns at once). With the count of the
+// last pass of the same kind known, the first batch runs one fewer than it and
+// later batches two at a time; otherwise `check` at a time.
+struct CgBatches {
+    int first, later;
+    CgBatches(int last, int check, long long maxit)
+    {
+        const long long f = std::min<long long>((long long)last - 1, maxit);
+        first = last > 1 ? (int)std::max<long long>(f, 1) : check;
+        later = last > 1 ? std::min(check, 2) : check;
+    }
+    int size(long long launched) const { return launched == 0 ? first : later; }
+};
+
 int zmarch_slots(const fs_ctx *c, bool face)
 {
     const int r = face ? resident_blocks((const void *)k_spmv_z<HelmOp>, zmarch_smem())
@@ -910,9 +926,12 @@ static int pcg_iterate(fs_ctx *c, SolveScal &h)
     const TmaGrids<PoisOp> tg(c, c->nitems_cell, c->nact_cell);
     // a multigrid iteration costs several operator applies: check convergence more often
     const int check = c->prm.precond == FS_PRECOND_MG ? std::min(c->prm.check_every, 4) : c->prm.check_every;
+    int &last = c->it_last_p[c->solve_kind & 1][c->refining ? 1 : 0];
+    const CgBatches batches(last, check, c->prm.maxit_p);
     for (;;) {
-        for (int b = 0; b < check; b++) {
-            const bool samp = c->prof_on && (b % c->prof_period) == 0;
+        const int nb = batches.size(launched);
+        for (int b = 0; b < nb; b++) {
+            const bool samp = c->prof_on && ((launched + b) % c->prof_period) == 0;  // every prof_period-th
             cudaEvent_t e0 = samp ? prof_mark(c) : nullptr;
             const float *zsrc = jac ? c->pr : c->pz;
             if (listed)
@@ -949,7 +968,7 @@ static int pcg_iterate(fs_ctx *c, SolveScal &h)
                 if (int rc = precondition(0)) return rc;
             cur ^= 1;
         }
-        launched += check;
+        launched += nb;
         FS_CUDA(cudaGetLastError());
         int rc = read_scal(c, 0, &h);
         if (rc) return rc;
@@ -957,6 +976,7 @@ static int pcg_iterate(fs_ctx *c, SolveScal &h)
         if (launched > (long long)c->prm.maxit_p + c->prm.check_every)
             return set_error(FS_ECUDA, "pressure solve: iteration flag never set");
     }
+    last = h.status == FS_OK ? (int)std::min<long long>(h.iter, 1 << 20) : 0;
     prof_count(c, K_P_SPMV, h.iter);
     prof_count(c, K_P_UPDATE, h.iter);
     if (c->prm.precond == FS_PRECOND_MG) mg_count(c, h.iter, false);
@@ -1188,9 +1208,12 @@ int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st)
     const TileMap &tm = c->tm_face;
     const dim3 tdim(TILE_X / 4, TILE_Y);
     const TmaGrids<HelmOp> tg(c, c->nitems_face, c->nact_face);
+    int &last = c->it_last_v[dirichlet ? 1 : 0];
+    const CgBatches batches(last, check, c->prm.maxit_v);
     for (;;) {
-        for (int b = 0; b < check; b++) {
-            const bool samp = c->prof_on && (b % c->prof_period) == 0;
+        const int nb = batches.size(launched);
+        for (int b = 0; b < nb; b++) {
+            const bool samp = c->prof_on && ((launched + b) % c->prof_period) == 0;  // every prof_period-th
             cudaEvent_t e0 = samp ? prof_mark(c) : nullptr;
             if (listed)
                 k_spmv_list<HelmOp><<<wave_blocks(c, nlisted, rl), TH, 0, c->stream>>>(
@@ -1227,7 +1250,7 @@ int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st)
                 if (int rc = precondition(0)) return rc;
             cur ^= 1;
         }
-        launched += check;
+        launched += nb;
         FS_CUDA(cudaGetLastError());
         int rc = read_scal(c, 1, &h);
         if (rc) return rc;
@@ -1235,6 +1258,7 @@ int solve_viscosity(fs_ctx *c, bool dirichlet, fs_stats *st)
         if (launched > (long long)c->prm.maxit_v + c->prm.check_every)
             return set_error(FS_ECUDA, "viscosity solve: iteration flag never set");
     }
+    last = h.status == FS_OK ? (int)std::min<long long>(h.iter, 1 << 20) : 0;
     if (int rc = check_wait_error(c, "viscosity solve")) return rc;
     prof_count(c, K_V_SPMV, h.iter);
     prof_count(c, K_V_UPDATE, h.iter);
