@@ -65,7 +65,7 @@ NCU_TRAFFIC = {
     # the same metrics -k regex:^k_mg0_smooth$ on a 256^3 blob projection with the multigrid
     # preconditioner: the last level-0 sweep of a pressure V-cycle, which forms r.z (the mean
     # of two launches; profiles/mg0_kernels_256_ncu.md); its files include the grid sums
-    "mg0_smooth_z": {"bytes_per_launch": 83167232 + 5408384, "source": "3e5c684120e18001",
+    "mg0_smooth_z": {"bytes_per_launch": 83167232 + 5408384, "source": "5ebc55d1e28ef6ee",
                      "files": ("fs_mg.cu", "fs_internal.cuh", "fs_mask.cu")},
 }
 KERNEL_FILES = ("fs_stencil.cuh", "fs_tma.cuh", "fs_mask.cu")

@@ -372,57 +372,6 @@ __device__ __forceinline__ void pre1_q(const MgGrid &g, const uint8_t *__restric
     *reinterpret_cast<float4 *>(res + t) = v;
 }
 
-// Restriction of a column of RC coarse planes: t0 is the element of coarse cell
-// (2m, J, K0), K0 a multiple of RC. The x weights and then the y weights of each
-// fine plane 2 K0 - 1 .. 2 (K0 + RC) are formed once, and each coarse plane takes
-// the z-weighted sum of its four: a fine plane serves two coarse planes of the
-// column, where a thread per pair would read it twice.
-constexpr int RC = 4;
-template <bool CG>
-__device__ __forceinline__ void restrict_col(const MgGrid &gf, const float *res, const MgGrid &gc,
-                                             const uint8_t *__restrict__ flc, float *rc, int t0)
-{
-    const float w[4] = {0.25f, 0.75f, 0.75f, 0.25f};
-    const int rel = t0 - gc.origin;
-    const int K0 = rel / gc.sz, J = (rel - K0 * gc.sz) / gc.sy, I0 = rel - K0 * gc.sz - J * gc.sy;
-    const int m = I0 >> 1;
-    float y0[2 * RC + 2], y1[2 * RC + 2];
-#pragma unroll
-    for (int p = 0; p < 2 * RC + 2; p++) {
-        const int k = 2 * K0 - 1 + p;
-        float a0 = 0.f, a1 = 0.f;
-        if (k >= 0 && k < gf.nz) {
-#pragma unroll
-            for (int b = 0; b < 4; b++) {
-                const int j = 2 * J - 1 + b;
-                if (j < 0 || j >= gf.ny) continue;
-                const int row = gf.idx(0, j, k) + 4 * m;  // a multiple of 4
-                const float4 qd = ldv4<CG>(res, row);
-                const float lf = m > 0 ? ldv1<CG>(res, row - 1) : 0.f;
-                const float rt = 4 * m + 4 < gf.nx ? ldv1<CG>(res, row + 4) : 0.f;
-                // coarse 2m: fine 4m - 1 .. 4m + 2; coarse 2m + 1: fine 4m + 1 .. 4m + 4
-                a0 += w[b] * (0.25f * lf + 0.75f * qd.x + 0.75f * qd.y + 0.25f * qd.z);
-                a1 += w[b] * (0.25f * qd.y + 0.75f * qd.z + 0.75f * qd.w + 0.25f * rt);
-            }
-        }
-        y0[p] = a0;
-        y1[p] = a1;
-    }
-#pragma unroll
-    for (int kk = 0; kk < RC; kk++) {
-        if (K0 + kk >= gc.nz) break;
-        const int tk = t0 + kk * gc.sz;
-        float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-        for (int c = 0; c < 4; c++) {
-            a0 += w[c] * y0[2 * kk + c];
-            a1 += w[c] * y1[2 * kk + c];
-        }
-        if (liq(flc[tk])) rc[tk] = 0.125f * a0;
-        if (I0 + 1 < gc.nx && liq(flc[tk + 1])) rc[tk + 1] = 0.125f * a1;
-    }
-}
-
 // ---- one launch per step ------------------------------------------------------
 
 // One sweep over the active quads. With rzs (the last sweep of a V-cycle's level
