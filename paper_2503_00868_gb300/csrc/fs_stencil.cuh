@@ -19,7 +19,6 @@ __device__ __forceinline__ float4 fma4(float4 a, float b, float4 c)  // a + b c
     return make_float4(a.x + b * c.x, a.y + b * c.y, a.z + b * c.z, a.w + b * c.w);
 }
 
-__device__ __forceinline__ float4 zero4() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
 // Diagonal and its inverse per neighbour count, for this launch's coefficient.
 template <class Op>
