@@ -19,7 +19,6 @@ __device__ __forceinline__ float4 fma4(float4 a, float b, float4 c)  // a + b c
     return make_float4(a.x + b * c.x, a.y + b * c.y, a.z + b * c.z, a.w + b * c.w);
 }
 
-
 // Diagonal and its inverse per neighbour count, for this launch's coefficient.
 template <class Op>
 __device__ __forceinline__ void fill_diag_tables(float *dtab, float *itab, float cc)

@@ -6,7 +6,6 @@ import pytest
 import torch
 
 from paper_2503_00868_gb300 import fit as FT
-from paper_2503_00868_gb300 import fluidstep as F
 from paper_2503_00868_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu

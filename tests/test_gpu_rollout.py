@@ -1,7 +1,6 @@
 """GPU: the checkpointed rollout (torch.autograd.Function over the C ABI) against
 the oracle's forward and reverse pass over several frames, and checkpoint-length
 invariance."""
-import numpy as np
 import pytest
 import torch
 

@@ -1,7 +1,6 @@
 """Pins of the oracle's preconditioner network against torch's own conv3d,
 bf16 conversion and autograd on the CPU (library routines, float64)."""
 import numpy as np
-import pytest
 import torch
 
 from paper_2503_00868_gb300 import workloads as W

@@ -7,7 +7,6 @@ using only the free faces (a direct sparse solve)."""
 import numpy as np
 import pytest
 import scipy.sparse as sp
-import scipy.sparse.linalg as spla
 
 import oracle as O
 from paper_2503_00868_gb300 import workloads as W

@@ -6,7 +6,6 @@ shared scratch that is not cleared would show up as a mismatch.
 
 This file is named to be collected last, so a run that stops at the first
 failure has run every other test before it."""
-import numpy as np
 import pytest
 import torch
 
