@@ -123,7 +123,10 @@ typedef struct {
     int maxit_v;       /* viscosity iteration cap, >= 1 */
     double tol_p;      /* pressure relative residual target |r|/|b|, > 0 */
     double tol_v;      /* viscosity relative residual target, > 0 */
-    int check_every;   /* iterations between host convergence checks, >= 1 */
+    int check_every;   /* iterations between host convergence checks, >= 1 (at most 4 with
+                          the multigrid preconditioner). Once a pass of the same kind has
+                          run on the context, the first check comes one iteration before
+                          that pass's count and later ones every two iterations */
     int spin_limit;    /* cap on every device-side spin-wait (iterations), >= 1 */
     double mic_tau;    /* MIC(0) modification, in [0, 1] */
     double mic_sigma;  /* MIC(0) safety threshold, in [0, 1) */
@@ -161,7 +164,11 @@ typedef struct {
                               |b - A q| is above tol_p |b|, CG runs again on the correction
                               system A d = b - A q (right-hand side rounded once from FP64)
                               to tol_p |b| / 2, and the pressure is kept as the pair q + d;
-                              at most two per solve */
+                              at most two per solve. Where the first CG pass of the last
+                              solve of the same kind (forward or adjoint) left an FP64
+                              residual above tol_p |b|, the next first pass stops at half
+                              that relative residual; the context keeps it until the next
+                              fs_set_mask */
 } fs_stats;
 
 typedef struct {
