@@ -65,6 +65,10 @@ NCU_TRAFFIC = {
     # the same metrics -k regex:^k_mg0_smooth$ on a 256^3 blob projection with the multigrid
     # preconditioner: the last level-0 sweep of a pressure V-cycle, which forms r.z (the mean
     # of two launches; profiles/mg0_kernels_256_ncu.md); its files include the grid sums
+    # the same metrics -k regex:k_spmv_list on that projection: the pressure operator apply over
+    # the multigrid level-0 list of active quads (the mean of four launches; profiles/spmv_list_256_ncu.md)
+    "pressure_spmv": {"bytes_per_launch": 85581312 + 35093888, "source": "83675cdd5bd4c57e",
+                      "files": ("fs_pcg.cu", "fs_internal.cuh", "fs_mg.cu", "fs_mask.cu")},
     "mg0_smooth_z": {"bytes_per_launch": 83167232 + 5408384, "source": "5ebc55d1e28ef6ee",
                      "files": ("fs_mg.cu", "fs_internal.cuh", "fs_mask.cu")},
 }
